@@ -1,0 +1,190 @@
+/*
+ * mt.h -- C ABI of libmt, a GB300 (sm_103a) implementation of the particle
+ * mass-transfer step of Engdahl, Schmidt & Benson, "Accelerating and
+ * parallelizing Lagrangian simulations of mixing-limited reactive transport"
+ * (arXiv 1811.05474), with the random-walk move before it and the A + B -> E
+ * reaction after it.
+ *
+ * One time step (mt_step) is, in the paper's order:
+ *   1. move      Eq. 2 with alpha_L = 0: x <- x + v dt + sqrt(2 D_rw dt) xi,
+ *                xi standard normal per particle and axis; particles leaving
+ *                [0, L] are mirrored back (Sec. 3).
+ *   2. search    every pair within the cutoff s_max (Sec. 2.1), by a
+ *                uniform-grid cell list built with a counting sort over cell
+ *                keys (MT_SEARCH_CELL), or by testing all pairs
+ *                (MT_SEARCH_BRUTE), or all pairs without a cutoff, the
+ *                paper's full-matrix reference (MT_SEARCH_FULL, Sec. 1.1).
+ *   3. weights   Eq. 3: nu_ij proportional to exp(-s_ij^2 / (8 D_mt dt)),
+ *                normalised per row, P_ij = nu_ij / sum_j nu_ij (Sec. 1.1,
+ *                MT_NORM_ROW), or symmetrically (P_ij + P_ji)/2, which
+ *                conserves each species' total mass (MT_NORM_SYM, default).
+ *   4. exchange  Eq. 4 and Eq. 7: dM_i = 1/2 sum_j P_ij (M_j - M_i),
+ *                M <- M + dM for species A and B, from start-of-step masses
+ *                ("matrix explicit", Sec. 1.1).
+ *   5. react     A + B -> E, irreversible and at equilibrium, per particle
+ *                after the transfer (Sec. 3, Sec. 7): m = min(A, B);
+ *                A -= m; B -= m.
+ *
+ * Number formats.  Positions are fixed point: x = X * 2^-k with X a 64-bit
+ * integer (k = frac_bits).  Drift and random-walk displacement are rounded to
+ * that grid; the cutoff is s_max rounded down to it (Smax = floor(s_max 2^k)
+ * ticks) and the pair test is exact integer arithmetic.  MT_FP64 computes
+ * weights, normalisation, exchange and reaction in IEEE binary64.  MT_MIXED
+ * computes weights and normalised weights in binary32 and keeps the masses as
+ * unevaluated sums of two binary32 numbers (about 48 significant bits), with
+ * compensated additions for the update and the reaction.
+ *
+ * Conventions.
+ *   - Every function returns mt_status (0 = MT_OK, < 0 error) and never
+ *     aborts the process; mt_last_error() describes the last failure on the
+ *     calling thread.
+ *   - Device memory: the library allocates none.  The caller allocates one
+ *     device buffer of mt_workspace_bytes() bytes (256-byte aligned) and
+ *     passes it to mt_create; the handle owns its contents until mt_destroy.
+ *   - Work is enqueued on the stream given to mt_create (NULL: a stream the
+ *     handle creates).  mt_step / mt_run return before the GPU finishes;
+ *     mt_read_* and mt_sync wait for the stream and report device-side
+ *     errors.
+ *   - Arrays are axis-major (all x, then all y) and in the caller's particle
+ *     order; the library reorders particles internally and always reads back
+ *     in the order of mt_upload.
+ *   - A handle is used by one host thread at a time.  Several handles may
+ *     share a GPU on different streams.
+ */
+#ifndef MT_H
+#define MT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MT_OK = 0,
+  MT_ERR_INVALID = -1,    /* bad argument or parameter */
+  MT_ERR_WORKSPACE = -2,  /* workspace NULL, too small or misaligned */
+  MT_ERR_CUDA = -3,       /* a CUDA runtime call failed */
+  MT_ERR_DEVICE = -4,     /* a device-side check failed (index out of range) */
+  MT_ERR_TIMEOUT = -5,    /* a bounded device-side wait gave up */
+  MT_ERR_STATE = -6       /* call out of order (e.g. step before upload) */
+} mt_status;
+
+enum { MT_SEARCH_CELL = 0, MT_SEARCH_BRUTE = 1, MT_SEARCH_FULL = 2 };
+enum { MT_FP64 = 0, MT_MIXED = 1 };
+enum { MT_NORM_SYM = 0, MT_NORM_ROW = 1 };
+enum { MT_MEM_HOST = 0, MT_MEM_DEVICE = 1 };
+
+typedef struct mt_params {
+  int32_t dim;          /* 1 or 2 */
+  int32_t frac_bits;    /* k of x = X 2^-k; 0 = choose (largest k with
+                           s_max 2^k < 2^30 and L 2^k < 2^61) */
+  int64_t n;            /* number of particles, 0 <= n < 2^31 */
+  double L[2];          /* domain [0, L0] (x [0, L1]); L > 0 */
+  double v[2];          /* constant advection velocity (Eq. 2) */
+  double D_mt;          /* diffusion coefficient of the transfer (Eq. 3), > 0 */
+  double D_rw;          /* diffusion coefficient of the random walk, >= 0 */
+  double dt;            /* time step, > 0 */
+  double cutoff;        /* s_max; <= 0 selects 3 sqrt(4 D_mt dt) */
+  int32_t search;       /* MT_SEARCH_* */
+  int32_t precision;    /* MT_FP64 or MT_MIXED */
+  int32_t norm;         /* MT_NORM_* */
+  int32_t react;        /* 1: apply A + B -> E after the transfer */
+  uint64_t seed;        /* key of the Philox4x32-10 random-walk generator */
+  uint64_t realisation; /* counter word separating independent realisations */
+  int32_t observe_cap;  /* steps kept in the observables ring; 0 = off */
+  int32_t cell_shift;   /* log2 of the cell width in ticks; 0 = choose */
+} mt_params;
+
+typedef struct mt_handle mt_handle;
+
+/* Fill p with defaults: dim 1, n 0, L 1000, v 0, D_mt = D_rw = 0.1, dt 1,
+ * cutoff 3 sqrt(4 D_mt dt), cell search, FP64, SYM, react on, seed 0,
+ * observe_cap 0. */
+mt_status mt_params_init(mt_params* p);
+
+/* Copy p to out with every "choose" field resolved (frac_bits, cutoff,
+ * cell_shift), exactly as mt_create will use them.  Validates p. */
+mt_status mt_resolve(const mt_params* p, mt_params* out);
+
+/* Device bytes the handle needs for p (validates p). */
+mt_status mt_workspace_bytes(const mt_params* p, size_t* bytes);
+
+/* Create a handle.  workspace: device pointer to >= mt_workspace_bytes
+ * bytes, 256-byte aligned, owned by the caller and used by the handle until
+ * mt_destroy.  stream: a cudaStream_t, or NULL for a stream the handle
+ * creates and destroys.  The state is empty until mt_upload. */
+mt_status mt_create(const mt_params* p, void* workspace, size_t workspace_bytes,
+                    void* stream, mt_handle** out);
+
+/* Load the state: x (dim*n doubles, axis-major, each in [0, L_d]), A and B
+ * (n doubles each).  mem says whether the three pointers are host or device
+ * memory.  Positions are rounded to the grid (X = rint(x 2^k)).  Resets the
+ * step counter and the observables.  Asynchronous for device pointers; host
+ * arrays are copied before the call returns. */
+mt_status mt_upload(mt_handle* h, const double* x, const double* A,
+                    const double* B, int32_t mem);
+
+/* Random-walk noise for the following steps: a device pointer to dim*n
+ * floats, axis-major and indexed by the caller's particle order, read by
+ * every mt_step until it is replaced; NULL returns to the built-in
+ * Philox4x32-10 / Box-Muller generator keyed by (seed, realisation, step,
+ * particle).  The caller keeps the buffer alive and unchanged until the
+ * steps that read it have run. */
+mt_status mt_set_noise(mt_handle* h, const float* xi_device);
+
+/* Enqueue one time step (move, search, transfer, react). */
+mt_status mt_step(mt_handle* h);
+
+/* Enqueue nsteps time steps.  With the built-in generator the steps are
+ * replayed from a CUDA graph captured on the first call. */
+mt_status mt_run(mt_handle* h, int64_t nsteps);
+
+/* Wait for the handle's stream and report device-side errors. */
+mt_status mt_sync(mt_handle* h);
+
+/* Current masses (n doubles each) in the caller's particle order, into host
+ * or device memory.  Waits for the stream. */
+mt_status mt_read_masses(mt_handle* h, double* A, double* B, int32_t mem);
+
+/* Current positions as doubles (dim*n, axis-major, caller's order). */
+mt_status mt_read_positions(mt_handle* h, double* x, int32_t mem);
+
+/* Current positions as exact grid ticks X (dim*n int64). */
+mt_status mt_read_ticks(mt_handle* h, int64_t* X, int32_t mem);
+
+/* Observables of the last min(steps, cap, observe_cap) steps, oldest first,
+ * 4 doubles each: sum A, sum B, sum (A - B), mean A after the step.
+ * out: host memory for 4*cap doubles.  *count receives the rows written. */
+mt_status mt_read_observables(mt_handle* h, double* out, int64_t cap,
+                              int64_t* count);
+
+/* Pairs {i, j} (caller's particle indices, i < j) within the cutoff at the
+ * current positions, as the handle's search finds them.  pi, pj: device
+ * pointers with room for cap entries (may be NULL when cap = 0); *count
+ * receives the total number of pairs, which may exceed cap (then only cap
+ * are written).  Pair order is unspecified.  Not for MT_SEARCH_FULL. */
+mt_status mt_read_pairs(mt_handle* h, int32_t* pi, int32_t* pj, int64_t cap,
+                        int64_t* count);
+
+/* Steps taken since mt_upload. */
+mt_status mt_steps_done(const mt_handle* h, int64_t* steps);
+
+/* Test hook for the generator: out[4*i .. 4*i+3] = Philox4x32-10 of counter
+ * (c0 + i, c1, c2, c3) under key (k0, k1), for i < n; out is a device
+ * pointer.  Enqueued on the handle's stream. */
+mt_status mt_philox(mt_handle* h, uint32_t c0, uint32_t c1, uint32_t c2,
+                    uint32_t c3, uint32_t k0, uint32_t k1, int64_t n,
+                    uint32_t* out);
+
+/* Description of the last error on this thread (static storage). */
+const char* mt_last_error(void);
+
+/* Release the handle (not the workspace).  Waits for its stream. */
+void mt_destroy(mt_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,566 @@
+// mt_api.cu -- the C ABI of libmt (include/mt.h): parameter resolution and
+// validation, workspace layout, step sequencing on the handle's stream, CUDA
+// graph replay for mt_run, read-back and error reporting.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "mt_internal.cuh"
+
+using namespace mt;
+
+namespace {
+
+thread_local std::string g_err;
+
+mt_status fail(mt_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+mt_status fail(mt_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CU(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(MT_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                           \
+  } while (0)
+
+constexpr double kTwo30 = 1073741824.0;            // 2^30
+constexpr double kTwo61 = 2305843009213693952.0;   // 2^61
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+// Everything derived from mt_params that the kernels need.
+struct Derived {
+  mt_params p;  // resolved
+  long long S = 0, Lq[2] = {0, 0}, drift[2] = {0, 0};
+  float bq = 0.f;
+  int cshift = 0;
+  long long ncx = 1, ncy = 1, ncell = 0;
+  long long nbig_cap = 0, nblocks = 0, ntiles = 0;
+  // workspace offsets
+  size_t o_ctrl, o_X[2], o_id[2], o_M[2], o_src, o_rinv, o_count, o_start, o_cursor,
+      o_status, o_big, o_part, o_obs, total;
+};
+
+int default_frac_bits(const mt_params& p) {
+  double Lmax = p.L[0];
+  if (p.dim == 2 && p.L[1] > Lmax) Lmax = p.L[1];
+  int k = 62;
+  while (k > 0 && (std::ldexp(p.cutoff, k) >= kTwo30 || std::ldexp(Lmax, k) >= kTwo61)) --k;
+  return k;
+}
+
+int ceil_log2(long long v) {  // smallest c with 2^c >= v (v >= 1)
+  int c = 0;
+  while (c < 62 && (1LL << c) < v) ++c;
+  return c;
+}
+
+int floor_log2(double v) {  // v >= 1
+  int c = 0;
+  while (c < 62 && std::ldexp(1.0, c + 1) <= v) ++c;
+  return c;
+}
+
+mt_status resolve(const mt_params* in, Derived* out) {
+  if (!in) return fail(MT_ERR_INVALID, "params is NULL");
+  Derived D;
+  mt_params p = *in;
+  if (p.dim != 1 && p.dim != 2) return fail(MT_ERR_INVALID, "dim must be 1 or 2 (got %d)", p.dim);
+  if (p.n < 0 || p.n >= (1LL << 31) - 1)
+    return fail(MT_ERR_INVALID, "n must be in [0, 2^31 - 1) (got %lld)", (long long)p.n);
+  for (int a = 0; a < p.dim; ++a)
+    if (!finite_pos(p.L[a])) return fail(MT_ERR_INVALID, "L[%d] must be finite and > 0", a);
+  if (p.dim == 1) p.L[1] = 0.0, p.v[1] = 0.0;
+  if (!finite_pos(p.D_mt)) return fail(MT_ERR_INVALID, "D_mt must be finite and > 0");
+  if (!(std::isfinite(p.D_rw) && p.D_rw >= 0.0))
+    return fail(MT_ERR_INVALID, "D_rw must be finite and >= 0");
+  if (!finite_pos(p.dt)) return fail(MT_ERR_INVALID, "dt must be finite and > 0");
+  for (int a = 0; a < p.dim; ++a)
+    if (!std::isfinite(p.v[a])) return fail(MT_ERR_INVALID, "v[%d] must be finite", a);
+  if (!std::isfinite(p.cutoff)) return fail(MT_ERR_INVALID, "cutoff must be finite");
+  if (p.cutoff <= 0.0) p.cutoff = 3.0 * std::sqrt(4.0 * p.D_mt * p.dt);
+  if (p.search < MT_SEARCH_CELL || p.search > MT_SEARCH_FULL)
+    return fail(MT_ERR_INVALID, "unknown search %d", p.search);
+  if (p.precision != MT_FP64 && p.precision != MT_MIXED)
+    return fail(MT_ERR_INVALID, "unknown precision %d", p.precision);
+  if (p.norm != MT_NORM_SYM && p.norm != MT_NORM_ROW)
+    return fail(MT_ERR_INVALID, "unknown norm %d", p.norm);
+  if (p.react != 0 && p.react != 1) return fail(MT_ERR_INVALID, "react must be 0 or 1");
+  if (p.observe_cap < 0) return fail(MT_ERR_INVALID, "observe_cap must be >= 0");
+  if (p.frac_bits == 0) p.frac_bits = default_frac_bits(p);
+  const int k = p.frac_bits;
+  if (k < 1 || k > 62) return fail(MT_ERR_INVALID, "frac_bits must be in [1, 62] (got %d)", k);
+  if (std::ldexp(p.cutoff, k) >= kTwo30)
+    return fail(MT_ERR_INVALID, "cutoff * 2^frac_bits must be < 2^30");
+  for (int a = 0; a < p.dim; ++a) {
+    if (std::ldexp(p.L[a], k) >= kTwo61)
+      return fail(MT_ERR_INVALID, "L[%d] * 2^frac_bits must be < 2^61", a);
+    const double drift = std::ldexp(p.v[a] * p.dt, k);
+    if (std::fabs(drift) >= kTwo61 / 4)
+      return fail(MT_ERR_INVALID, "|v[%d] dt| 2^frac_bits must be < 2^59", a);
+    D.Lq[a] = std::llrint(std::ldexp(p.L[a], k));
+    D.drift[a] = std::llrint(drift);
+  }
+  const double b = std::ldexp(std::sqrt(2.0 * p.D_rw * p.dt), k);
+  if (b * 64.0 >= kTwo61 / 4)
+    return fail(MT_ERR_INVALID, "sqrt(2 D_rw dt) 2^frac_bits is too large for the grid");
+  D.bq = (float)b;
+  D.S = (long long)std::floor(std::ldexp(p.cutoff, k));
+  // cell grid
+  if (p.search == MT_SEARCH_CELL) {
+    const long long n1 = p.n > 0 ? p.n : 1;
+    int c = p.cell_shift;
+    if (c == 0) {
+      if (p.dim == 1) {
+        const double per = (double)D.Lq[0] / (double)n1;  // ticks per particle
+        c = per >= 2.0 ? floor_log2(per) + 1 : 1;
+      } else {
+        const int cmin = ceil_log2(D.S + 1);
+        const double side = std::sqrt((double)D.Lq[0] * (double)D.Lq[1] / (double)n1);
+        const int ct = side >= 2.0 ? floor_log2(side) : 1;
+        c = ct > cmin ? ct : cmin;
+      }
+    }
+    if (c < 1 || c > 62) return fail(MT_ERR_INVALID, "cell_shift must be in [1, 62]");
+    if (p.dim == 2 && (1LL << c) <= D.S)
+      return fail(MT_ERR_INVALID, "2-d cells must be wider than the cutoff (2^cell_shift > Smax)");
+    // keep the cell array modest
+    for (;;) {
+      D.ncx = (D.Lq[0] >> c) + 1;
+      D.ncy = p.dim == 2 ? (D.Lq[1] >> c) + 1 : 1;
+      if ((double)D.ncx * (double)D.ncy <= (double)(1LL << 28)) break;
+      ++c;
+    }
+    D.cshift = c;
+    p.cell_shift = c;
+    D.ncell = D.ncx * D.ncy;
+  } else {
+    D.ncell = 0;
+    p.cell_shift = 0;
+  }
+  D.nbig_cap = p.n / (kSmallCell + 1) + 1;
+  D.nblocks = (p.n + kThreads - 1) / kThreads;
+  if (D.nblocks < 1) D.nblocks = 1;
+  D.ntiles = (D.ncell + kScanTile - 1) / kScanTile;
+  // workspace layout
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  const size_t n = (size_t)p.n;
+  D.o_ctrl = take(sizeof(Ctrl));
+  for (int b2 = 0; b2 < 2; ++b2) D.o_X[b2] = take((size_t)p.dim * n * 8);
+  for (int b2 = 0; b2 < 2; ++b2) D.o_id[b2] = take(n * 4);
+  for (int b2 = 0; b2 < 2; ++b2) D.o_M[b2] = take(2 * n * 8);
+  D.o_src = take(n * 4);
+  D.o_rinv = take(n * 8);
+  D.o_count = take((size_t)D.ncell * 4);
+  D.o_start = take((size_t)(D.ncell + 1) * 4);
+  D.o_cursor = take((size_t)D.ncell * 4);
+  D.o_status = take((size_t)D.ntiles * 8);
+  D.o_big = take((size_t)D.nbig_cap * 4);
+  D.o_part = take((size_t)D.nblocks * 4 * 8);
+  D.o_obs = take((size_t)p.observe_cap * 4 * 8);
+  D.total = o;
+  D.p = p;
+  *out = D;
+  return MT_OK;
+}
+
+}  // namespace
+
+struct mt_handle {
+  Derived D;
+  Dev dev;
+  char* ws = nullptr;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool uploaded = false;
+  int xcur = 0, mcur = 0;  // host mirrors of the device selectors
+  long long steps = 0;     // host mirror of the step counter
+  cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+bool capturable(cudaStream_t s) {
+  return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+}
+
+mt_status check_device(mt_handle* h) {
+  CU(cudaStreamSynchronize(h->stream));
+  Ctrl c;
+  CU(cudaMemcpy(&c, h->ws + h->D.o_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+  if (c.err == kErrTimeout)
+    return fail(MT_ERR_TIMEOUT, "device wait gave up (scan tile %lld)", c.err_info);
+  if (c.err == kErrInput)
+    return fail(MT_ERR_INVALID, "uploaded position %lld outside [0, L] or NaN", c.err_info);
+  if (c.err != kErrNone)
+    return fail(MT_ERR_DEVICE, "device index check failed (code %d, at %lld)", c.err, c.err_info);
+  return MT_OK;
+}
+
+// Enqueue one step's kernels.
+mt_status enqueue_step(mt_handle* h, const Dev& d) {
+  const mt_params& p = h->D.p;
+  if (p.n == 0) return MT_OK;
+  if (p.search == MT_SEARCH_CELL) {
+    CU(launch_move(d, true, true, h->stream));
+    CU(launch_sort(d, h->stream));
+  } else {
+    CU(launch_move(d, true, false, h->stream));
+  }
+  CU(launch_transfer(d, p.search, p.precision, h->stream));
+  return MT_OK;
+}
+
+void advance_mirrors(mt_handle* h) {
+  if (h->D.p.n == 0) {
+    ++h->steps;
+    return;
+  }
+  if (h->D.p.search == MT_SEARCH_CELL)
+    h->xcur ^= 1;
+  else
+    h->mcur ^= 1;
+  ++h->steps;
+}
+
+}  // namespace
+
+extern "C" {
+
+mt_status mt_params_init(mt_params* p) {
+  if (!p) return fail(MT_ERR_INVALID, "params is NULL");
+  std::memset(p, 0, sizeof *p);
+  p->dim = 1;
+  p->L[0] = 1000.0;
+  p->L[1] = 1000.0;
+  p->D_mt = 0.1;
+  p->D_rw = 0.1;
+  p->dt = 1.0;
+  p->cutoff = 0.0;
+  p->search = MT_SEARCH_CELL;
+  p->precision = MT_FP64;
+  p->norm = MT_NORM_SYM;
+  p->react = 1;
+  return MT_OK;
+}
+
+mt_status mt_resolve(const mt_params* p, mt_params* out) {
+  Derived D;
+  const mt_status s = resolve(p, &D);
+  if (s != MT_OK) return s;
+  if (!out) return fail(MT_ERR_INVALID, "out is NULL");
+  *out = D.p;
+  return MT_OK;
+}
+
+mt_status mt_workspace_bytes(const mt_params* p, size_t* bytes) {
+  Derived D;
+  const mt_status s = resolve(p, &D);
+  if (s != MT_OK) return s;
+  if (!bytes) return fail(MT_ERR_INVALID, "bytes is NULL");
+  *bytes = D.total;
+  return MT_OK;
+}
+
+mt_status mt_create(const mt_params* p, void* workspace, size_t workspace_bytes, void* stream,
+                    mt_handle** out) {
+  if (!out) return fail(MT_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  Derived D;
+  mt_status s = resolve(p, &D);
+  if (s != MT_OK) return s;
+  if (!workspace) return fail(MT_ERR_WORKSPACE, "workspace is NULL");
+  if ((uintptr_t)workspace % kAlign != 0)
+    return fail(MT_ERR_WORKSPACE, "workspace must be %zu-byte aligned", kAlign);
+  if (workspace_bytes < D.total)
+    return fail(MT_ERR_WORKSPACE, "workspace has %zu bytes, needs %zu", workspace_bytes, D.total);
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, workspace) != cudaSuccess ||
+      attr.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return fail(MT_ERR_WORKSPACE, "workspace is not device memory");
+  }
+  mt_handle* h = new mt_handle();
+  h->D = D;
+  h->ws = static_cast<char*>(workspace);
+  if (stream) {
+    h->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return fail(MT_ERR_CUDA, "cudaStreamCreateWithFlags failed");
+    }
+    h->own_stream = true;
+  }
+  Dev& d = h->dev;
+  std::memset(&d, 0, sizeof d);
+  char* w = h->ws;
+  d.ctrl = reinterpret_cast<Ctrl*>(w + D.o_ctrl);
+  for (int b = 0; b < 2; ++b) {
+    d.X[b] = reinterpret_cast<long long*>(w + D.o_X[b]);
+    d.id[b] = reinterpret_cast<int*>(w + D.o_id[b]);
+    d.M[b] = reinterpret_cast<unsigned long long*>(w + D.o_M[b]);
+  }
+  d.src = reinterpret_cast<int*>(w + D.o_src);
+  d.rinv = w + D.o_rinv;
+  d.count = reinterpret_cast<int*>(w + D.o_count);
+  d.start = reinterpret_cast<int*>(w + D.o_start);
+  d.cursor = reinterpret_cast<int*>(w + D.o_cursor);
+  d.scan_status = reinterpret_cast<unsigned long long*>(w + D.o_status);
+  d.big = reinterpret_cast<int*>(w + D.o_big);
+  d.partials = reinterpret_cast<double*>(w + D.o_part);
+  d.obs = reinterpret_cast<double*>(w + D.o_obs);
+  d.noise = nullptr;
+  d.n = D.p.n;
+  d.dim = D.p.dim;
+  d.norm = D.p.norm;
+  d.react = D.p.react;
+  d.observe_cap = D.p.observe_cap;
+  d.cshift = D.cshift;
+  d.ncx = D.ncx;
+  d.ncy = D.ncy;
+  d.ncell = D.ncell;
+  d.S = D.S;
+  for (int a = 0; a < 2; ++a) {
+    d.Lq[a] = D.Lq[a];
+    d.drift[a] = D.drift[a];
+  }
+  d.bq = D.bq;
+  d.inv8 = 1.0 / (8.0 * D.p.D_mt * D.p.dt);
+  d.scale = std::ldexp(1.0, -D.p.frac_bits);
+  d.inv8f = (float)(d.inv8 * d.scale * d.scale);
+  d.key0 = (unsigned int)(D.p.seed & 0xffffffffu);
+  d.key1 = (unsigned int)(D.p.seed >> 32);
+  d.real = (unsigned int)D.p.realisation;
+  d.nbig_cap = (int)D.nbig_cap;
+  d.nblocks = (int)D.nblocks;
+  const cudaError_t e = cudaMemsetAsync(h->ws, 0, D.total, h->stream);
+  if (e != cudaSuccess) {
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return fail(MT_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+  }
+  *out = h;
+  return MT_OK;
+}
+
+mt_status mt_upload(mt_handle* h, const double* x, const double* A, const double* B,
+                    int32_t mem) {
+  if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
+  if (mem != MT_MEM_HOST && mem != MT_MEM_DEVICE) return fail(MT_ERR_INVALID, "bad mem kind");
+  const mt_params& p = h->D.p;
+  const size_t n = (size_t)p.n;
+  if (n > 0 && (!x || !A || !B)) return fail(MT_ERR_INVALID, "x, A and B are required");
+  CU(cudaMemsetAsync(h->ws + h->D.o_ctrl, 0, sizeof(Ctrl), h->stream));
+  // the scan epoch restarts with the control block: clear old status words
+  if (h->D.ntiles > 0) CU(cudaMemsetAsync(h->ws + h->D.o_status, 0, h->D.ntiles * 8, h->stream));
+  h->xcur = 0;
+  h->mcur = 0;
+  h->steps = 0;
+  h->uploaded = true;
+  if (n == 0) return MT_OK;
+  const Dev& d = h->dev;
+  double* xs = reinterpret_cast<double*>(d.X[1]);
+  double* ms = reinterpret_cast<double*>(d.M[1]);
+  const cudaMemcpyKind kind = mem == MT_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CU(cudaMemcpyAsync(xs, x, (size_t)p.dim * n * 8, kind, h->stream));
+  CU(cudaMemcpyAsync(ms, A, n * 8, kind, h->stream));
+  CU(cudaMemcpyAsync(ms + n, B, n * 8, kind, h->stream));
+  CU(launch_upload(d, xs, ms, ms + n, p.precision, h->stream));
+  if (p.search == MT_SEARCH_CELL) {
+    // sort once so the state is in cell order between steps
+    CU(launch_move(d, false, true, h->stream));
+    CU(launch_sort(d, h->stream));
+    CU(launch_permute(d, h->stream));
+    h->xcur = 1;
+    h->mcur = 1;
+  }
+  if (mem == MT_MEM_HOST) CU(cudaStreamSynchronize(h->stream));
+  return MT_OK;
+}
+
+mt_status mt_set_noise(mt_handle* h, const float* xi) {
+  if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
+  h->dev.noise = xi;
+  return MT_OK;
+}
+
+mt_status mt_step(mt_handle* h) {
+  if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
+  if (!h->uploaded) return fail(MT_ERR_STATE, "mt_step before mt_upload");
+  const mt_status s = enqueue_step(h, h->dev);
+  if (s != MT_OK) return s;
+  advance_mirrors(h);
+  return MT_OK;
+}
+
+mt_status mt_run(mt_handle* h, int64_t nsteps) {
+  if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
+  if (!h->uploaded) return fail(MT_ERR_STATE, "mt_run before mt_upload");
+  if (nsteps < 0) return fail(MT_ERR_INVALID, "nsteps must be >= 0");
+  if (h->dev.noise || !capturable(h->stream) || h->D.p.n == 0) {
+    for (int64_t i = 0; i < nsteps; ++i) {
+      const mt_status s = mt_step(h);
+      if (s != MT_OK) return s;
+    }
+    return MT_OK;
+  }
+  if (!h->graph) {
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    const mt_status s = enqueue_step(h, h->dev);
+    const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (s != MT_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (e != cudaSuccess) return fail(MT_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    const cudaError_t e2 = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) {
+      h->graph = nullptr;
+      return fail(MT_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e2));
+    }
+  }
+  for (int64_t i = 0; i < nsteps; ++i) {
+    CU(cudaGraphLaunch(h->graph, h->stream));
+    advance_mirrors(h);
+  }
+  return MT_OK;
+}
+
+mt_status mt_sync(mt_handle* h) {
+  if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
+  return check_device(h);
+}
+
+mt_status mt_read_masses(mt_handle* h, double* A, double* B, int32_t mem) {
+  if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
+  if (!h->uploaded) return fail(MT_ERR_STATE, "no state uploaded");
+  if (mem != MT_MEM_HOST && mem != MT_MEM_DEVICE) return fail(MT_ERR_INVALID, "bad mem kind");
+  const size_t n = (size_t)h->D.p.n;
+  if (n == 0) return check_device(h);
+  if (!A || !B) return fail(MT_ERR_INVALID, "A and B are required");
+  if (mem == MT_MEM_DEVICE) {
+    CU(launch_read_masses(h->dev, A, B, h->D.p.precision, h->stream));
+  } else {
+    double* stage = reinterpret_cast<double*>(h->dev.M[h->mcur ^ 1]);
+    CU(launch_read_masses(h->dev, stage, stage + n, h->D.p.precision, h->stream));
+    CU(cudaMemcpyAsync(A, stage, n * 8, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(B, stage + n, n * 8, cudaMemcpyDeviceToHost, h->stream));
+  }
+  return check_device(h);
+}
+
+static mt_status read_pos(mt_handle* h, double* x, long long* X, int32_t mem) {
+  if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
+  if (!h->uploaded) return fail(MT_ERR_STATE, "no state uploaded");
+  if (mem != MT_MEM_HOST && mem != MT_MEM_DEVICE) return fail(MT_ERR_INVALID, "bad mem kind");
+  const size_t n = (size_t)h->D.p.n, m = (size_t)h->D.p.dim * n;
+  if (n == 0) return check_device(h);
+  if (!x && !X) return fail(MT_ERR_INVALID, "output is NULL");
+  if (mem == MT_MEM_DEVICE) {
+    CU(launch_read_positions(h->dev, x, X, h->stream));
+  } else {
+    void* stage = h->dev.X[h->xcur ^ 1];
+    CU(launch_read_positions(h->dev, x ? static_cast<double*>(stage) : nullptr,
+                             X ? static_cast<long long*>(stage) : nullptr, h->stream));
+    CU(cudaMemcpyAsync(x ? static_cast<void*>(x) : static_cast<void*>(X), stage, m * 8,
+                       cudaMemcpyDeviceToHost, h->stream));
+  }
+  return check_device(h);
+}
+
+mt_status mt_read_positions(mt_handle* h, double* x, int32_t mem) {
+  return read_pos(h, x, nullptr, mem);
+}
+
+mt_status mt_read_ticks(mt_handle* h, int64_t* X, int32_t mem) {
+  return read_pos(h, nullptr, reinterpret_cast<long long*>(X), mem);
+}
+
+mt_status mt_read_observables(mt_handle* h, double* out, int64_t cap, int64_t* count) {
+  if (!h || !count) return fail(MT_ERR_INVALID, "handle or count is NULL");
+  const long long ocap = h->D.p.observe_cap;
+  long long have = h->steps < ocap ? h->steps : ocap;
+  if (cap < have) have = cap < 0 ? 0 : cap;
+  *count = 0;
+  const mt_status s = check_device(h);
+  if (s != MT_OK) return s;
+  if (have == 0) return MT_OK;
+  if (!out) return fail(MT_ERR_INVALID, "out is NULL");
+  double* ring = new double[(size_t)ocap * 4];
+  const cudaError_t e = cudaMemcpy(ring, h->dev.obs, (size_t)ocap * 32, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    delete[] ring;
+    return fail(MT_ERR_CUDA, "reading observables: %s", cudaGetErrorString(e));
+  }
+  const long long first = h->steps - have;  // step index of the oldest row returned
+  for (long long i = 0; i < have; ++i) {
+    const long long row = (first + i) % ocap;
+    std::memcpy(out + 4 * i, ring + 4 * row, 32);
+  }
+  delete[] ring;
+  *count = have;
+  return MT_OK;
+}
+
+mt_status mt_read_pairs(mt_handle* h, int32_t* pi, int32_t* pj, int64_t cap, int64_t* count) {
+  if (!h || !count) return fail(MT_ERR_INVALID, "handle or count is NULL");
+  if (!h->uploaded) return fail(MT_ERR_STATE, "no state uploaded");
+  if (h->D.p.search == MT_SEARCH_FULL)
+    return fail(MT_ERR_INVALID, "no cutoff pair set for MT_SEARCH_FULL");
+  if (cap < 0 || (cap > 0 && (!pi || !pj))) return fail(MT_ERR_INVALID, "bad pair buffers");
+  CU(launch_pairs(h->dev, h->D.p.search, pi, pj, cap, h->stream));
+  const mt_status s = check_device(h);
+  if (s != MT_OK) return s;
+  unsigned long long np = 0;
+  CU(cudaMemcpy(&np, &h->dev.ctrl->npairs, 8, cudaMemcpyDeviceToHost));
+  *count = (int64_t)np;
+  return MT_OK;
+}
+
+mt_status mt_steps_done(const mt_handle* h, int64_t* steps) {
+  if (!h || !steps) return fail(MT_ERR_INVALID, "handle or steps is NULL");
+  *steps = h->steps;
+  return MT_OK;
+}
+
+mt_status mt_philox(mt_handle* h, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                    uint32_t k1, int64_t n, uint32_t* out) {
+  if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
+  if (n < 0 || (n > 0 && !out)) return fail(MT_ERR_INVALID, "bad output");
+  CU(launch_philox(make_uint4(c0, c1, c2, c3), k0, k1, n, out, h->stream));
+  return MT_OK;
+}
+
+const char* mt_last_error(void) { return g_err.c_str(); }
+
+void mt_destroy(mt_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+}  // extern "C"

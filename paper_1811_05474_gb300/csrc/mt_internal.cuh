@@ -1,0 +1,204 @@
+// mt_internal.cuh -- device-side state, shared device helpers and kernel
+// launchers of libmt.  See include/mt.h for the public contract.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mt.h"
+
+namespace mt {
+
+constexpr int kThreads = 256;          // threads per CTA for per-particle kernels
+constexpr int kScanItems = 16;         // cell counts per thread in the scan
+constexpr int kScanTile = kThreads * kScanItems;
+constexpr int kSmallCell = 32;         // cells up to this size sort in one thread
+constexpr int kBigSortCap = 2048;      // cells up to this size sort in shared memory
+constexpr int kBruteTile = 256;        // j-particles staged per tile, brute force
+constexpr long long kSpinLimit = 1LL << 22;  // bounded waits (scan look-back)
+
+// Device error codes (Ctrl::err); the first one raised is kept.
+enum : int { kErrNone = 0, kErrIndex = 1, kErrTimeout = 2, kErrInput = 3 };
+
+// Per-handle control block in device memory.  Kernels read the ping-pong
+// selectors and the step counter from here, so a captured graph replays
+// correctly step after step.
+struct Ctrl {
+  unsigned long long step;      // completed steps since upload
+  unsigned long long epoch;     // scan epoch (tags look-back status words)
+  unsigned long long npairs;    // pair export counter
+  int xcur;                     // which X / id buffer holds the current state
+  int mcur;                     // which mass buffer holds the current masses
+  int err;                      // first device error code
+  int nbig;                     // cells too large for the per-thread sort
+  unsigned int done;            // CTAs finished (last-CTA reductions)
+  unsigned int tile_ctr;        // scan tile ticket
+  long long err_info;           // detail for err (an index)
+  unsigned long long pad[8];
+};
+
+// Everything a kernel needs, passed by value.
+struct Dev {
+  Ctrl* ctrl;
+  long long* X[2];          // [dim][n] grid ticks, ping-pong
+  int* id[2];               // caller's index of each slot, ping-pong
+  unsigned long long* M[2]; // [2][n] 8-byte mass words (A then B), ping-pong
+  int* src;                 // slot -> slot before the sort
+  void* rinv;               // 1 / r_i (double in FP64, float in MIXED)
+  int* count;               // [ncell] particles per cell
+  int* start;               // [ncell + 1] first slot of each cell
+  int* cursor;              // [ncell] scatter cursor
+  unsigned long long* scan_status;  // [ntiles] look-back words
+  int* big;                 // [nbig_cap] cells for the large-cell sort
+  double* partials;         // [nblocks][4] per-CTA observables
+  double* obs;              // [observe_cap][4] observables ring
+  const float* noise;       // injected normals [dim][n] by caller index, or null
+  long long n;
+  int dim;
+  int norm;                 // MT_NORM_*
+  int react;
+  int observe_cap;
+  int cshift;               // cell width 2^cshift ticks
+  long long ncx, ncy, ncell;
+  long long S;              // cutoff in ticks
+  long long Lq[2];          // domain length in ticks
+  long long drift[2];       // v dt in ticks
+  float bq;                 // sqrt(2 D_rw dt) 2^k as float
+  float inv8f;              // 1 / (8 D_mt dt) 2^-2k, float
+  double inv8;              // 1 / (8 D_mt dt), double
+  double scale;             // 2^-k
+  unsigned int key0, key1;  // Philox key (seed)
+  unsigned int real;        // realisation counter word
+  int nbig_cap;
+  int nblocks;              // CTAs of the per-particle kernels
+};
+
+// ---------------------------------------------------------------- helpers --
+
+__device__ __forceinline__ void raise_error(Ctrl* c, int code, long long info) {
+  if (atomicCAS(&c->err, 0, code) == 0) c->err_info = info;
+}
+
+// Mirror y back into [0, Lq] (Sec. 3 reflecting walls), at most 64 times.
+__device__ __forceinline__ long long reflect(long long y, long long Lq) {
+#pragma unroll 1
+  for (int it = 0; it < 64; ++it) {
+    if (y < 0)
+      y = -y;
+    else if (y > Lq)
+      y = 2 * Lq - y;
+    else
+      return y;
+  }
+  return y < 0 ? 0 : (y > Lq ? Lq : y);
+}
+
+__device__ __forceinline__ long long cell_of(const Dev& d, long long x, long long y) {
+  long long kx = x >> d.cshift;
+  kx = kx < 0 ? 0 : (kx >= d.ncx ? d.ncx - 1 : kx);
+  if (d.dim == 1) return kx;
+  long long ky = y >> d.cshift;
+  ky = ky < 0 ? 0 : (ky >= d.ncy ? d.ncy - 1 : ky);
+  return ky * d.ncx + kx;
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): 10 rounds of the
+// 2x(32x32->64) multiply / xor network with Weyl key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned int k0, unsigned int k1) {
+  const unsigned int M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const unsigned int W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned int lo0 = M0 * c.x, hi0 = __umulhi(M0, c.x);
+    const unsigned int lo1 = M1 * c.z, hi1 = __umulhi(M1, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += W0;
+    k1 += W1;
+  }
+  return c;
+}
+
+// Two standard normals from two 32-bit words (Box-Muller, binary32):
+// u1 in (0, 1], u2 in [0, 1).
+__device__ __forceinline__ float2 box_muller(unsigned int a, unsigned int b) {
+  const float u1 = ((a >> 8) + 1u) * (1.0f / 16777216.0f);
+  const float u2 = (b >> 8) * (1.0f / 16777216.0f);
+  const float rad = sqrtf(-2.0f * logf(u1));
+  float s, c;
+  sincospif(2.0f * u2, &s, &c);
+  return make_float2(rad * c, rad * s);
+}
+
+// ------------------------------------------ double-binary32 mass arithmetic --
+// A mass in MIXED precision is hi + lo with |lo| <= ulp(hi)/2.  The additions
+// are error-free transformations (Knuth two-sum, Dekker fast-two-sum).
+
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df df_add_f(df a, float b) {
+  const df s = two_sum(a.hi, b);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+  const df s = two_sum(a.hi, b.hi);
+  const df t = two_sum(a.lo, b.lo);
+  df u = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return fast_two_sum(u.hi, __fadd_rn(u.lo, t.lo));
+}
+
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, {-b.hi, -b.lo}); }
+
+__device__ __forceinline__ bool df_le(df a, df b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo);
+}
+
+__device__ __forceinline__ df df_load(const unsigned long long* M, long long i) {
+  const float2 v = reinterpret_cast<const float2*>(M)[i];
+  return {v.x, v.y};
+}
+
+__device__ __forceinline__ void df_store(unsigned long long* M, long long i, df v) {
+  reinterpret_cast<float2*>(M)[i] = make_float2(v.hi, v.lo);
+}
+
+__device__ __forceinline__ double f64_load(const unsigned long long* M, long long i) {
+  return __longlong_as_double((long long)M[i]);
+}
+
+__device__ __forceinline__ void f64_store(unsigned long long* M, long long i, double v) {
+  M[i] = (unsigned long long)__double_as_longlong(v);
+}
+
+// ---------------------------------------------------------------- launchers --
+// Each returns the cudaError_t of its launch.  grid sizes are computed from d.
+
+cudaError_t launch_move(const Dev& d, bool move, bool hist, cudaStream_t s);
+cudaError_t launch_sort(const Dev& d, cudaStream_t s);  // scan, scatter, cell sort
+cudaError_t launch_permute(const Dev& d, cudaStream_t s);  // gather id/masses after sort, flip
+cudaError_t launch_transfer(const Dev& d, int search, int precision, cudaStream_t s);
+cudaError_t launch_upload(const Dev& d, const double* x, const double* A,
+                          const double* B, int precision, cudaStream_t s);
+cudaError_t launch_read_masses(const Dev& d, double* A, double* B, int precision,
+                               cudaStream_t s);
+cudaError_t launch_read_positions(const Dev& d, double* x, long long* X, cudaStream_t s);
+cudaError_t launch_pairs(const Dev& d, int search, int* pi, int* pj, long long cap,
+                         cudaStream_t s);
+cudaError_t launch_philox(uint4 c, unsigned int k0, unsigned int k1, long long n,
+                          unsigned int* out, cudaStream_t s);
+
+}  // namespace mt

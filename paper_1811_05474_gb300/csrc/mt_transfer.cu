@@ -1,0 +1,553 @@
+// mt_transfer.cu -- weights (Eq. 3), normalisation (Sec. 1.1), exchange
+// (Eq. 4, Eq. 7) and the A + B -> E reaction (Sec. 3, Sec. 7), in two
+// passes: pass 1 forms the row sums r_i = sum_j nu_ij (self included) and
+// stores 1 / r_i; pass 2 forms dM_i = 1/2 sum_j P_ij (M_j - M_i) for A and B,
+// updates, reacts and reduces the per-step observables.
+//
+// Neighbour search variants:
+//   walk  (1-d cell list) particles are sorted by position, so the pairs of
+//         particle p are the contiguous slots around p whose tick distance is
+//         <= Smax; each thread walks left and right until it leaves range.
+//   cell2 (2-d cell list) candidates are the 3 x 3 block of cells around the
+//         particle's cell (cell width > Smax), contiguous per row.
+//   brute all n particles in shared-memory tiles, with (BRUTE) or without
+//         (FULL, the paper's full-matrix reference) the cutoff test.
+// Precision: MIX = false is IEEE binary64 throughout; MIX = true forms
+// weights and normalised weights in binary32 and updates the double-binary32
+// masses with compensated additions.
+#include "mt_internal.cuh"
+
+namespace mt {
+
+// ---------------------------------------------------------- pair weights --
+
+__device__ __forceinline__ bool in_range2(long long dx, long long dy, long long S) {
+  const unsigned long long ax = (unsigned long long)(dx < 0 ? -dx : dx);
+  const unsigned long long ay = (unsigned long long)(dy < 0 ? -dy : dy);
+  if (ax > (unsigned long long)S || ay > (unsigned long long)S) return false;
+  return ax * ax + ay * ay <= (unsigned long long)S * (unsigned long long)S;
+}
+
+// nu_ij without its prefactor (it cancels in the normalisation):
+// exp(-s^2 / (8 D_mt dt)) with s = |dX| 2^-k (Eq. 3).
+template <bool MIX, int DIM>
+struct Weight;
+
+template <int DIM>
+struct Weight<false, DIM> {
+  using T = double;
+  static __device__ __forceinline__ double eval(const Dev& d, long long dx, long long dy) {
+    const double sx = __dmul_rn((double)dx, d.scale);
+    double s2 = __dmul_rn(sx, sx);
+    if (DIM == 2) {
+      const double sy = __dmul_rn((double)dy, d.scale);
+      s2 = __dadd_rn(s2, __dmul_rn(sy, sy));
+    }
+    return exp(-__dmul_rn(s2, d.inv8));
+  }
+};
+
+template <int DIM>
+struct Weight<true, DIM> {
+  using T = float;
+  static __device__ __forceinline__ float eval(const Dev& d, long long dx, long long dy) {
+    const float fx = __ll2float_rn(dx);
+    float s2 = __fmul_rn(fx, fx);
+    if (DIM == 2) {
+      const float fy = __ll2float_rn(dy);
+      s2 = __fadd_rn(s2, __fmul_rn(fy, fy));
+    }
+    return __expf(-__fmul_rn(s2, d.inv8f));
+  }
+};
+
+// ------------------------------------------------------------ mass access --
+
+template <bool MIX>
+struct Mass;
+
+// Per-particle accumulation of sum_j P_ij (M_j - M_i): binary64 in FP64;
+// in MIXED each binary32 term is added into a double-binary32 sum (two-sum),
+// so the flux P_ij (M_j - M_i), bitwise antisymmetric between i and j, is
+// accumulated to about 48 bits and the transfer conserves mass to that
+// precision.
+template <>
+struct Mass<false> {
+  using V = double;
+  using Acc = double;
+  static __device__ __forceinline__ void acc(double& a, double P, double d) { a += P * d; }
+  static __device__ __forceinline__ double load(const unsigned long long* M, long long i) {
+    return f64_load(M, i);
+  }
+  static __device__ __forceinline__ void store(unsigned long long* M, long long i, double v) {
+    f64_store(M, i, v);
+  }
+  static __device__ __forceinline__ double diff(double a, double b) { return a - b; }
+  // M + dM/2 (Eq. 7 with the 1/2 of Eq. 4), then the reaction.
+  static __device__ __forceinline__ void update(double& A, double& B, double dA, double dB,
+                                                int react) {
+    A = A + 0.5 * dA;
+    B = B + 0.5 * dB;
+    if (react) {
+      const double m = A < B ? A : B;
+      A = A - m;
+      B = B - m;
+    }
+  }
+  static __device__ __forceinline__ double to_double(double v) { return v; }
+};
+
+template <>
+struct Mass<true> {
+  using V = df;
+  using Acc = df;
+  static __device__ __forceinline__ void acc(df& a, float P, float d) {
+    a = df_add_f(a, __fmul_rn(P, d));
+  }
+  static __device__ __forceinline__ df load(const unsigned long long* M, long long i) {
+    return df_load(M, i);
+  }
+  static __device__ __forceinline__ void store(unsigned long long* M, long long i, df v) {
+    df_store(M, i, v);
+  }
+  static __device__ __forceinline__ float diff(df a, df b) {
+    return __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo));
+  }
+  static __device__ __forceinline__ void update(df& A, df& B, df dA, df dB, int react) {
+    A = df_add(A, {0.5f * dA.hi, 0.5f * dA.lo});
+    B = df_add(B, {0.5f * dB.hi, 0.5f * dB.lo});
+    if (react) {
+      if (df_le(A, B)) {
+        B = df_sub(B, A);
+        A = {0.0f, 0.0f};
+      } else {
+        A = df_sub(A, B);
+        B = {0.0f, 0.0f};
+      }
+    }
+  }
+  static __device__ __forceinline__ double to_double(df v) { return (double)v.hi + (double)v.lo; }
+};
+
+template <bool MIX>
+__device__ __forceinline__ void store_rinv(const Dev& d, long long p, typename Weight<MIX, 1>::T r) {
+  if (MIX)
+    static_cast<float*>(d.rinv)[p] = __frcp_rn((float)r);
+  else
+    static_cast<double*>(d.rinv)[p] = 1.0 / (double)r;
+}
+
+template <bool MIX>
+__device__ __forceinline__ typename Weight<MIX, 1>::T load_rinv(const Dev& d, long long p) {
+  if (MIX)
+    return static_cast<const float*>(d.rinv)[p];
+  else
+    return static_cast<const double*>(d.rinv)[p];
+}
+
+// Normalised weight of the ordered pair (p, q) (Sec. 1.1): ROW w / r_p, or
+// SYM (w / r_p + w / r_q) / 2.
+template <typename T>
+__device__ __forceinline__ T normalised(int norm, T w, T ip, T iq) {
+  return norm == MT_NORM_ROW ? w * ip : T(0.5) * w * (ip + iq);
+}
+
+// ------------------------------------------- step epilogue (last CTA) --
+// Per-CTA partial observables -> the last CTA to finish reduces them in a
+// fixed order, appends a row to the ring, advances the step counter and
+// flips the buffer selectors.  Deterministic: no floating-point atomics.
+// Per-particle sums stay in the precision's own arithmetic (binary64, or
+// double-binary32 in MIXED); only per-CTA totals are converted to binary64.
+
+__device__ __forceinline__ double obs_add(double a, double b) { return a + b; }
+__device__ __forceinline__ df obs_add(df a, df b) { return df_add(a, b); }
+__device__ __forceinline__ double obs_shfl(double v, int o) {
+  return __shfl_down_sync(0xffffffffu, v, o);
+}
+__device__ __forceinline__ df obs_shfl(df v, int o) {
+  return {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ double obs_double(double v) { return v; }
+__device__ __forceinline__ double obs_double(df v) { return (double)v.hi + (double)v.lo; }
+__device__ __forceinline__ double obs_diff(double a, double b) { return a - b; }
+__device__ __forceinline__ df obs_diff(df a, df b) { return df_sub(a, b); }
+
+template <bool MIX>
+__device__ void finish_step(const Dev& d, typename Mass<MIX>::V a, typename Mass<MIX>::V b,
+                            bool valid, int flip_x, int flip_m) {
+  using MV = typename Mass<MIX>::V;
+  __shared__ MV s_part[kThreads / 32][3];
+  __shared__ double s_tot[kThreads / 32][3];
+  __shared__ bool s_last;
+  Ctrl* c = d.ctrl;
+  const bool observe = d.observe_cap > 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (observe) {
+    MV sa{}, sb{}, sd{};
+    if (valid) {
+      sa = a;
+      sb = b;
+      sd = obs_diff(a, b);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sa = obs_add(sa, obs_shfl(sa, o));
+      sb = obs_add(sb, obs_shfl(sb, o));
+      sd = obs_add(sd, obs_shfl(sd, o));
+    }
+    if (lane == 0) {
+      s_part[warp][0] = sa;
+      s_part[warp][1] = sb;
+      s_part[warp][2] = sd;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      MV ta = s_part[0][0], tb = s_part[0][1], td = s_part[0][2];
+      for (int w = 1; w < kThreads / 32; ++w) {
+        ta = obs_add(ta, s_part[w][0]);
+        tb = obs_add(tb, s_part[w][1]);
+        td = obs_add(td, s_part[w][2]);
+      }
+      d.partials[4 * blockIdx.x + 0] = obs_double(ta);
+      d.partials[4 * blockIdx.x + 1] = obs_double(tb);
+      d.partials[4 * blockIdx.x + 2] = obs_double(td);
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&c->done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (observe) {
+    double ta = 0, tb = 0, td = 0;
+    for (unsigned int blk = threadIdx.x; blk < gridDim.x; blk += blockDim.x) {
+      ta += __ldcg(&d.partials[4 * blk + 0]);
+      tb += __ldcg(&d.partials[4 * blk + 1]);
+      td += __ldcg(&d.partials[4 * blk + 2]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ta += __shfl_down_sync(0xffffffffu, ta, o);
+      tb += __shfl_down_sync(0xffffffffu, tb, o);
+      td += __shfl_down_sync(0xffffffffu, td, o);
+    }
+    if (lane == 0) {
+      s_tot[warp][0] = ta;
+      s_tot[warp][1] = tb;
+      s_tot[warp][2] = td;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      ta = tb = td = 0;
+      for (int w = 0; w < kThreads / 32; ++w) {
+        ta += s_tot[w][0];
+        tb += s_tot[w][1];
+        td += s_tot[w][2];
+      }
+      const long long row = (long long)(c->step % (unsigned long long)d.observe_cap);
+      d.obs[4 * row + 0] = ta;
+      d.obs[4 * row + 1] = tb;
+      d.obs[4 * row + 2] = td;
+      d.obs[4 * row + 3] = d.n > 0 ? ta / (double)d.n : 0.0;
+    }
+  }
+  if (threadIdx.x == 0) {
+    c->step += 1;
+    c->xcur ^= flip_x;
+    c->mcur ^= flip_m;
+    c->done = 0;
+  }
+}
+
+// ================================================================ 1-d walk ==
+
+template <bool MIX>
+__global__ void __launch_bounds__(kThreads) k_rowsum_walk(Dev d) {
+  using W = Weight<MIX, 1>;
+  using T = typename W::T;
+  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (p >= d.n) return;
+  const int xc = d.ctrl->xcur, mc = d.ctrl->mcur;
+  const long long* Xs = d.X[xc ^ 1];
+  const long long x = Xs[p];
+  T r = T(1);  // self: nu_pp = 1
+  for (long long q = p - 1; q >= 0; --q) {
+    const long long D = x - Xs[q];
+    if (D > d.S) break;
+    r += W::eval(d, D, 0);
+  }
+  for (long long q = p + 1; q < d.n; ++q) {
+    const long long D = Xs[q] - x;
+    if (D > d.S) break;
+    r += W::eval(d, D, 0);
+  }
+  store_rinv<MIX>(d, p, r);
+  // gather id and masses into the sorted slots (stage buffer)
+  const int s = d.src[p];
+  d.id[xc ^ 1][p] = d.id[xc][s];
+  d.M[mc ^ 1][p] = d.M[mc][s];
+  d.M[mc ^ 1][d.n + p] = d.M[mc][d.n + s];
+}
+
+template <bool MIX>
+__global__ void __launch_bounds__(kThreads) k_exchange_walk(Dev d) {
+  using W = Weight<MIX, 1>;
+  using T = typename W::T;
+  using MS = Mass<MIX>;
+  using MV = typename MS::V;
+  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const bool valid = p < d.n;
+  const int xc = d.ctrl->xcur, mc = d.ctrl->mcur;
+  MV A{}, B{};
+  if (valid) {
+    const long long* Xs = d.X[xc ^ 1];
+    const unsigned long long* Min = d.M[mc ^ 1];
+    const long long x = Xs[p];
+    const T ip = load_rinv<MIX>(d, p);
+    A = MS::load(Min, p);
+    B = MS::load(Min, d.n + p);
+    typename MS::Acc dA{}, dB{};
+    for (long long q = p - 1; q >= 0; --q) {
+      const long long D = x - Xs[q];
+      if (D > d.S) break;
+      const T P = normalised<T>(d.norm, W::eval(d, D, 0), ip, load_rinv<MIX>(d, q));
+      MS::acc(dA, P, MS::diff(MS::load(Min, q), A));
+      MS::acc(dB, P, MS::diff(MS::load(Min, d.n + q), B));
+    }
+    for (long long q = p + 1; q < d.n; ++q) {
+      const long long D = Xs[q] - x;
+      if (D > d.S) break;
+      const T P = normalised<T>(d.norm, W::eval(d, D, 0), ip, load_rinv<MIX>(d, q));
+      MS::acc(dA, P, MS::diff(MS::load(Min, q), A));
+      MS::acc(dB, P, MS::diff(MS::load(Min, d.n + q), B));
+    }
+    MS::update(A, B, dA, dB, d.react);
+    MS::store(d.M[mc], p, A);
+    MS::store(d.M[mc], d.n + p, B);
+  }
+  finish_step<MIX>(d, A, B, valid, 1, 0);
+}
+
+// =============================================================== 2-d cells ==
+
+template <bool MIX, bool EXCHANGE>
+__device__ __forceinline__ void cell2_loop(const Dev& d, const long long* Xs, long long p,
+                                           long long x, long long y,
+                                           typename Weight<MIX, 2>::T& r,
+                                           const unsigned long long* Min,
+                                           typename Weight<MIX, 2>::T ip,
+                                           typename Mass<MIX>::V A, typename Mass<MIX>::V B,
+                                           typename Mass<MIX>::Acc& dA,
+                                           typename Mass<MIX>::Acc& dB) {
+  using W = Weight<MIX, 2>;
+  using T = typename W::T;
+  using MS = Mass<MIX>;
+  long long kx = x >> d.cshift, ky = y >> d.cshift;
+  kx = kx >= d.ncx ? d.ncx - 1 : kx;
+  ky = ky >= d.ncy ? d.ncy - 1 : ky;
+  const long long kx0 = kx > 0 ? kx - 1 : 0;
+  const long long kx1 = kx + 1 < d.ncx ? kx + 1 : d.ncx - 1;
+  for (long long row = ky - 1; row <= ky + 1; ++row) {
+    if (row < 0 || row >= d.ncy) continue;
+    const int q0 = d.start[row * d.ncx + kx0];
+    const int q1 = d.start[row * d.ncx + kx1 + 1];
+    for (int q = q0; q < q1; ++q) {
+      const long long dx = Xs[q] - x, dy = Xs[d.n + q] - y;
+      if (!in_range2(dx, dy, d.S)) continue;
+      const T w = W::eval(d, dx, dy);
+      if (!EXCHANGE) {
+        r += w;
+      } else if (q != p) {
+        const T P = normalised<T>(d.norm, w, ip, load_rinv<MIX>(d, q));
+        MS::acc(dA, P, MS::diff(MS::load(Min, q), A));
+        MS::acc(dB, P, MS::diff(MS::load(Min, d.n + q), B));
+      }
+    }
+  }
+}
+
+template <bool MIX>
+__global__ void __launch_bounds__(kThreads) k_rowsum_cell2(Dev d) {
+  using T = typename Weight<MIX, 2>::T;
+  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (p >= d.n) return;
+  const int xc = d.ctrl->xcur, mc = d.ctrl->mcur;
+  const long long* Xs = d.X[xc ^ 1];
+  T r = T(0);
+  typename Mass<MIX>::Acc dummy{};
+  typename Mass<MIX>::V z{};
+  cell2_loop<MIX, false>(d, Xs, p, Xs[p], Xs[d.n + p], r, nullptr, T(0), z, z, dummy, dummy);
+  store_rinv<MIX>(d, p, r);
+  const int s = d.src[p];
+  d.id[xc ^ 1][p] = d.id[xc][s];
+  d.M[mc ^ 1][p] = d.M[mc][s];
+  d.M[mc ^ 1][d.n + p] = d.M[mc][d.n + s];
+}
+
+template <bool MIX>
+__global__ void __launch_bounds__(kThreads) k_exchange_cell2(Dev d) {
+  using T = typename Weight<MIX, 2>::T;
+  using MS = Mass<MIX>;
+  using MV = typename MS::V;
+  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const bool valid = p < d.n;
+  const int xc = d.ctrl->xcur, mc = d.ctrl->mcur;
+  MV A{}, B{};
+  if (valid) {
+    const long long* Xs = d.X[xc ^ 1];
+    const unsigned long long* Min = d.M[mc ^ 1];
+    A = MS::load(Min, p);
+    B = MS::load(Min, d.n + p);
+    T r = T(0);
+    typename MS::Acc dA{}, dB{};
+    cell2_loop<MIX, true>(d, Xs, p, Xs[p], Xs[d.n + p], r, Min, load_rinv<MIX>(d, p), A, B,
+                          dA, dB);
+    MS::update(A, B, dA, dB, d.react);
+    MS::store(d.M[mc], p, A);
+    MS::store(d.M[mc], d.n + p, B);
+  }
+  finish_step<MIX>(d, A, B, valid, 1, 0);
+}
+
+// ============================================================ brute force ==
+// All pairs, j-particles staged through shared memory in tiles.  Particles
+// keep their caller order (no sort); masses ping-pong between buffers.
+
+template <bool MIX, bool CUT, int DIM>
+__global__ void __launch_bounds__(kThreads) k_rowsum_brute(Dev d) {
+  using W = Weight<MIX, DIM>;
+  using T = typename W::T;
+  __shared__ long long s_x[kBruteTile];
+  __shared__ long long s_y[DIM == 2 ? kBruteTile : 1];
+  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const bool valid = p < d.n;
+  const long long* X = d.X[d.ctrl->xcur];
+  const long long x = valid ? X[p] : 0;
+  const long long y = (valid && DIM == 2) ? X[d.n + p] : 0;
+  T r = T(0);
+  for (long long j0 = 0; j0 < d.n; j0 += kBruteTile) {
+    const long long j = j0 + threadIdx.x;
+    if (j < d.n) {
+      s_x[threadIdx.x] = X[j];
+      if (DIM == 2) s_y[threadIdx.x] = X[d.n + j];
+    }
+    __syncthreads();
+    const int jn = (int)min((long long)kBruteTile, d.n - j0);
+    if (valid) {
+      for (int jj = 0; jj < jn; ++jj) {
+        const long long dx = s_x[jj] - x;
+        const long long dy = DIM == 2 ? s_y[jj] - y : 0;
+        if (CUT) {
+          if (DIM == 1 ? (dx > d.S || -dx > d.S) : !in_range2(dx, dy, d.S)) continue;
+        }
+        r += W::eval(d, dx, dy);
+      }
+    }
+    __syncthreads();
+  }
+  if (valid) store_rinv<MIX>(d, p, r);
+}
+
+template <bool MIX, bool CUT, int DIM>
+__global__ void __launch_bounds__(kThreads) k_exchange_brute(Dev d) {
+  using W = Weight<MIX, DIM>;
+  using T = typename W::T;
+  using MS = Mass<MIX>;
+  using MV = typename MS::V;
+  __shared__ long long s_x[kBruteTile];
+  __shared__ long long s_y[DIM == 2 ? kBruteTile : 1];
+  __shared__ T s_ri[kBruteTile];
+  __shared__ MV s_a[kBruteTile];
+  __shared__ MV s_b[kBruteTile];
+  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const bool valid = p < d.n;
+  const int mc = d.ctrl->mcur;
+  const long long* X = d.X[d.ctrl->xcur];
+  const unsigned long long* Min = d.M[mc];
+  const long long x = valid ? X[p] : 0;
+  const long long y = (valid && DIM == 2) ? X[d.n + p] : 0;
+  MV A{}, B{};
+  T ip = T(0);
+  if (valid) {
+    A = MS::load(Min, p);
+    B = MS::load(Min, d.n + p);
+    ip = load_rinv<MIX>(d, p);
+  }
+  typename MS::Acc dA{}, dB{};
+  for (long long j0 = 0; j0 < d.n; j0 += kBruteTile) {
+    const long long j = j0 + threadIdx.x;
+    if (j < d.n) {
+      s_x[threadIdx.x] = X[j];
+      if (DIM == 2) s_y[threadIdx.x] = X[d.n + j];
+      s_ri[threadIdx.x] = load_rinv<MIX>(d, j);
+      s_a[threadIdx.x] = MS::load(Min, j);
+      s_b[threadIdx.x] = MS::load(Min, d.n + j);
+    }
+    __syncthreads();
+    const int jn = (int)min((long long)kBruteTile, d.n - j0);
+    if (valid) {
+      for (int jj = 0; jj < jn; ++jj) {
+        if (j0 + jj == p) continue;
+        const long long dx = s_x[jj] - x;
+        const long long dy = DIM == 2 ? s_y[jj] - y : 0;
+        if (CUT) {
+          if (DIM == 1 ? (dx > d.S || -dx > d.S) : !in_range2(dx, dy, d.S)) continue;
+        }
+        const T P = normalised<T>(d.norm, W::eval(d, dx, dy), ip, s_ri[jj]);
+        MS::acc(dA, P, MS::diff(s_a[jj], A));
+        MS::acc(dB, P, MS::diff(s_b[jj], B));
+      }
+    }
+    __syncthreads();
+  }
+  if (valid) {
+    MS::update(A, B, dA, dB, d.react);
+    MS::store(d.M[mc ^ 1], p, A);
+    MS::store(d.M[mc ^ 1], d.n + p, B);
+  }
+  finish_step<MIX>(d, A, B, valid, 0, 1);
+}
+
+// --------------------------------------------------------------- launch --
+
+template <bool MIX>
+static void transfer_t(const Dev& d, int search, cudaStream_t s) {
+  const unsigned int g = (unsigned int)((d.n + kThreads - 1) / kThreads);
+  if (search == MT_SEARCH_CELL) {
+    if (d.dim == 1) {
+      k_rowsum_walk<MIX><<<g, kThreads, 0, s>>>(d);
+      k_exchange_walk<MIX><<<g, kThreads, 0, s>>>(d);
+    } else {
+      k_rowsum_cell2<MIX><<<g, kThreads, 0, s>>>(d);
+      k_exchange_cell2<MIX><<<g, kThreads, 0, s>>>(d);
+    }
+  } else if (search == MT_SEARCH_BRUTE) {
+    if (d.dim == 1) {
+      k_rowsum_brute<MIX, true, 1><<<g, kThreads, 0, s>>>(d);
+      k_exchange_brute<MIX, true, 1><<<g, kThreads, 0, s>>>(d);
+    } else {
+      k_rowsum_brute<MIX, true, 2><<<g, kThreads, 0, s>>>(d);
+      k_exchange_brute<MIX, true, 2><<<g, kThreads, 0, s>>>(d);
+    }
+  } else {
+    if (d.dim == 1) {
+      k_rowsum_brute<MIX, false, 1><<<g, kThreads, 0, s>>>(d);
+      k_exchange_brute<MIX, false, 1><<<g, kThreads, 0, s>>>(d);
+    } else {
+      k_rowsum_brute<MIX, false, 2><<<g, kThreads, 0, s>>>(d);
+      k_exchange_brute<MIX, false, 2><<<g, kThreads, 0, s>>>(d);
+    }
+  }
+}
+
+cudaError_t launch_transfer(const Dev& d, int search, int precision, cudaStream_t s) {
+  if (precision == MT_MIXED)
+    transfer_t<true>(d, search, s);
+  else
+    transfer_t<false>(d, search, s);
+  return cudaGetLastError();
+}
+
+}  // namespace mt

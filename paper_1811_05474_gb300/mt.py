@@ -1,0 +1,316 @@
+"""ctypes binding of libmt (include/mt.h).
+
+Functions keep the C names and only marshal arguments; every step of the
+computation runs in the library's CUDA kernels.  ``Simulation`` bundles a
+handle with a PyTorch-allocated device workspace and stream.  Loading fails
+loudly (``RuntimeError``) when the compiled library is missing: there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+from .build import LIB
+
+MT_OK = 0
+MT_ERR_INVALID = -1
+MT_ERR_WORKSPACE = -2
+MT_ERR_CUDA = -3
+MT_ERR_DEVICE = -4
+MT_ERR_TIMEOUT = -5
+MT_ERR_STATE = -6
+
+MT_SEARCH_CELL, MT_SEARCH_BRUTE, MT_SEARCH_FULL = 0, 1, 2
+MT_FP64, MT_MIXED = 0, 1
+MT_NORM_SYM, MT_NORM_ROW = 0, 1
+MT_MEM_HOST, MT_MEM_DEVICE = 0, 1
+
+
+class mt_params(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int32),
+        ("frac_bits", ctypes.c_int32),
+        ("n", ctypes.c_int64),
+        ("L", ctypes.c_double * 2),
+        ("v", ctypes.c_double * 2),
+        ("D_mt", ctypes.c_double),
+        ("D_rw", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("cutoff", ctypes.c_double),
+        ("search", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("norm", ctypes.c_int32),
+        ("react", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("realisation", ctypes.c_uint64),
+        ("observe_cap", ctypes.c_int32),
+        ("cell_shift", ctypes.c_int32),
+    ]
+
+
+class MtError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libmt status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def lib(path: Path | None = None):
+    """Load libmt (once).  Raises RuntimeError if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = Path(path) if path else LIB
+    if not p.exists():
+        raise RuntimeError(f"libmt is not built ({p} missing); run __graft_entry__.build()")
+    L = ctypes.CDLL(str(p))
+    P = ctypes.POINTER(mt_params)
+    H = ctypes.c_void_p
+    i32, i64, u32, u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
+    sig = {
+        "mt_params_init": [P],
+        "mt_resolve": [P, P],
+        "mt_workspace_bytes": [P, ctypes.POINTER(ctypes.c_size_t)],
+        "mt_create": [P, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(H)],
+        "mt_upload": [H, _vp, _vp, _vp, i32],
+        "mt_set_noise": [H, _vp],
+        "mt_step": [H],
+        "mt_run": [H, i64],
+        "mt_sync": [H],
+        "mt_read_masses": [H, _vp, _vp, i32],
+        "mt_read_positions": [H, _vp, i32],
+        "mt_read_ticks": [H, _vp, i32],
+        "mt_read_observables": [H, _vp, i64, ctypes.POINTER(i64)],
+        "mt_read_pairs": [H, _vp, _vp, i64, ctypes.POINTER(i64)],
+        "mt_steps_done": [H, ctypes.POINTER(i64)],
+        "mt_philox": [H, u32, u32, u32, u32, u32, u32, i64, _vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.mt_last_error.argtypes = []
+    L.mt_last_error.restype = ctypes.c_char_p
+    L.mt_destroy.argtypes = [H]
+    L.mt_destroy.restype = None
+    _lib = L
+    return L
+
+
+def mt_last_error() -> str:
+    return lib().mt_last_error().decode(errors="replace")
+
+
+def check(status: int) -> None:
+    if status != MT_OK:
+        raise MtError(status, mt_last_error())
+
+
+# ------------------------------------------------------------ thin wrappers --
+
+def mt_params_init(**kw) -> mt_params:
+    p = mt_params()
+    check(lib().mt_params_init(ctypes.byref(p)))
+    for k, v in kw.items():
+        if k in ("L", "v"):
+            vals = list(v) + [0.0] * (2 - len(v))
+            setattr(p, k, (ctypes.c_double * 2)(*vals))
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def mt_resolve(p: mt_params) -> mt_params:
+    out = mt_params()
+    check(lib().mt_resolve(ctypes.byref(p), ctypes.byref(out)))
+    return out
+
+
+def mt_workspace_bytes(p: mt_params) -> int:
+    b = ctypes.c_size_t(0)
+    check(lib().mt_workspace_bytes(ctypes.byref(p), ctypes.byref(b)))
+    return int(b.value)
+
+
+def mt_create(p: mt_params, workspace_ptr: int, workspace_bytes: int, stream_ptr: int | None):
+    h = ctypes.c_void_p(0)
+    check(lib().mt_create(ctypes.byref(p), workspace_ptr, workspace_bytes, stream_ptr or None,
+                          ctypes.byref(h)))
+    return h
+
+
+def mt_upload(h, x_ptr, A_ptr, B_ptr, mem: int) -> None:
+    check(lib().mt_upload(h, x_ptr, A_ptr, B_ptr, mem))
+
+
+def mt_set_noise(h, xi_ptr) -> None:
+    check(lib().mt_set_noise(h, xi_ptr))
+
+
+def mt_step(h) -> None:
+    check(lib().mt_step(h))
+
+
+def mt_run(h, nsteps: int) -> None:
+    check(lib().mt_run(h, nsteps))
+
+
+def mt_sync(h) -> None:
+    check(lib().mt_sync(h))
+
+
+def mt_read_masses(h, A_ptr, B_ptr, mem: int) -> None:
+    check(lib().mt_read_masses(h, A_ptr, B_ptr, mem))
+
+
+def mt_read_positions(h, x_ptr, mem: int) -> None:
+    check(lib().mt_read_positions(h, x_ptr, mem))
+
+
+def mt_read_ticks(h, X_ptr, mem: int) -> None:
+    check(lib().mt_read_ticks(h, X_ptr, mem))
+
+
+def mt_read_observables(h, out_ptr, cap: int) -> int:
+    cnt = ctypes.c_int64(0)
+    check(lib().mt_read_observables(h, out_ptr, cap, ctypes.byref(cnt)))
+    return int(cnt.value)
+
+
+def mt_read_pairs(h, pi_ptr, pj_ptr, cap: int) -> int:
+    cnt = ctypes.c_int64(0)
+    check(lib().mt_read_pairs(h, pi_ptr, pj_ptr, cap, ctypes.byref(cnt)))
+    return int(cnt.value)
+
+
+def mt_steps_done(h) -> int:
+    s = ctypes.c_int64(0)
+    check(lib().mt_steps_done(h, ctypes.byref(s)))
+    return int(s.value)
+
+
+def mt_philox(h, ctr, key, n: int, out_ptr) -> None:
+    check(lib().mt_philox(h, *[int(c) & 0xFFFFFFFF for c in ctr],
+                          *[int(k) & 0xFFFFFFFF for k in key], n, out_ptr))
+
+
+def mt_destroy(h) -> None:
+    lib().mt_destroy(h)
+
+
+# -------------------------------------------------------------- Simulation --
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Simulation:
+    """A handle plus its device workspace (a torch uint8 tensor) and stream.
+
+    Host-array helpers copy through the C ABI with MT_MEM_HOST; the ``*_dev``
+    variants take torch CUDA tensors.
+    """
+
+    def __init__(self, params: mt_params, device="cuda", stream=None):
+        import torch
+
+        self.torch = torch
+        self.params = mt_resolve(params)
+        self.device = torch.device(device)
+        self.nbytes = mt_workspace_bytes(self.params)
+        self.workspace = torch.empty(max(self.nbytes, 256), dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        self.h = mt_create(self.params, self.workspace.data_ptr(), self.workspace.numel(),
+                           self.stream.cuda_stream)
+        self._noise = None
+
+    @property
+    def n(self) -> int:
+        return int(self.params.n)
+
+    @property
+    def dim(self) -> int:
+        return int(self.params.dim)
+
+    def close(self):
+        if getattr(self, "h", None):
+            mt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # state in / out (host numpy)
+    def upload(self, x: np.ndarray, A: np.ndarray, B: np.ndarray) -> None:
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(self.dim, self.n)
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        assert A.shape == (self.n,) and B.shape == (self.n,)
+        mt_upload(self.h, _ptr(x), _ptr(A), _ptr(B), MT_MEM_HOST)
+
+    def masses(self):
+        A = np.empty(self.n, dtype=np.float64)
+        B = np.empty(self.n, dtype=np.float64)
+        mt_read_masses(self.h, _ptr(A), _ptr(B), MT_MEM_HOST)
+        return A, B
+
+    def positions(self) -> np.ndarray:
+        x = np.empty((self.dim, self.n), dtype=np.float64)
+        mt_read_positions(self.h, _ptr(x), MT_MEM_HOST)
+        return x
+
+    def ticks(self) -> np.ndarray:
+        X = np.empty((self.dim, self.n), dtype=np.int64)
+        mt_read_ticks(self.h, _ptr(X), MT_MEM_HOST)
+        return X
+
+    def observables(self) -> np.ndarray:
+        cap = int(self.params.observe_cap)
+        out = np.zeros((max(cap, 1), 4), dtype=np.float64)
+        cnt = mt_read_observables(self.h, _ptr(out), cap)
+        return out[:cnt]
+
+    def set_noise(self, xi: np.ndarray | None) -> None:
+        """Inject standard normals (dim, n) for the following steps; None
+        returns to the built-in generator."""
+        if xi is None:
+            self._noise = None
+            mt_set_noise(self.h, None)
+            return
+        t = self.torch.as_tensor(np.ascontiguousarray(xi, dtype=np.float32).reshape(-1))
+        dev = t.to(self.device)
+        self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+        dev.record_stream(self.stream)  # the handle's stream reads it
+        self._noise = dev
+        mt_set_noise(self.h, dev.data_ptr())
+
+    def step(self, n: int = 1) -> None:
+        for _ in range(n):
+            mt_step(self.h)
+
+    def run(self, n: int) -> None:
+        mt_run(self.h, n)
+
+    def sync(self) -> None:
+        mt_sync(self.h)
+
+    def pairs(self):
+        cnt = mt_read_pairs(self.h, None, None, 0)
+        torch = self.torch
+        pi = torch.empty(max(cnt, 1), dtype=torch.int32, device=self.device)
+        pj = torch.empty(max(cnt, 1), dtype=torch.int32, device=self.device)
+        cnt2 = mt_read_pairs(self.h, pi.data_ptr(), pj.data_ptr(), cnt)
+        assert cnt2 == cnt
+        return pi[:cnt].cpu().numpy(), pj[:cnt].cpu().numpy()
+
+    def steps_done(self) -> int:
+        return mt_steps_done(self.h)
