@@ -1,0 +1,472 @@
+#!/usr/bin/env python
+"""Benchmark of the mass-transfer particle-tracking hot path on GB300.
+
+One step = one time step of the whole path (random-walk move, cell-list
+search, weight normalisation, mass exchange, A + B -> E reaction, per-step
+observables) for every particle of the workload.  Workload: 1-d, N = 1e6
+particles uniform on [0, 1e6], A and B masses uniform on [0, 1), D = 0.1,
+dt = 1, advection v = 0.5, cutoff 3 sigma of the co-location kernel,
+synthetic and seeded.  The headline runs the MIXED precision path (binary32
+weights, double-binary32 mass accumulation); the FP64 path is reported in
+the "fp64" object.
+
+Timing: W warm-up steps, then K steps each replayed from a CUDA graph and
+bracketed by CUDA events on the simulation's stream, with a 512 MiB write
+(then read, so no dirty line is left) between steps to flush L2 (129 MB);
+value = particles * K / sum of step
+times, max over ranks.  Per-kernel durations come from a second pass of
+the same steps with events recorded between the step's kernels inside the
+graph.
+
+``--impl reference`` times the CPU oracle (single thread) on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N = 10 ** 6
+L = 1e6
+V = 0.5
+D = 0.1
+DT = 1.0
+WORKLOAD = "1d_uniform_n1e6_L1e6_v0.5_D0.1_dt1_cutoff3sigma"
+
+# Algorithmic bytes per particle for each kernel (what the kernel's job must
+# read and write at minimum; sort scaffolding, ids and 1/r are overhead).
+ALGO_BYTES = {
+    "move": 16,            # x in, x out
+    "scan": 0,
+    "scatter": 16,         # x in, x out (sorted)
+    "cellsort": 0,
+    "bigsort": 0,
+    "rowsum_walk": 8,      # x in
+    "exchange_walk": 40,   # x, A, B in; A, B out
+    "step": 48,            # whole step: x, A, B in and out
+}
+
+CSRC = os.path.join(ROOT, "paper_1811_05474_gb300", "csrc")
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(CSRC)):
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison line")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--ncu", action="store_true",
+                    help="profiling mode: upload, W graph steps, then K direct steps, nothing else")
+    ap.add_argument("--n", type=int, default=N, help="particles (profiling mode only)")
+    return ap.parse_args()
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi samples (every 20 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu=timestamp,{self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "20"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.proc:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r.split(", ") for r in self.tmp.read().splitlines() if r.strip()]
+        os.unlink(self.tmp.name)
+        mine = [r for r in rows if len(r) >= 11 and (self.uuid is None or r[2].strip() == self.uuid)]
+        if not mine and rows:
+            idx0 = rows[0][1]
+            mine = [r for r in rows if len(r) >= 11 and r[1] == idx0]
+        if self.t0 is not None and self.t1 is not None:
+            from datetime import datetime
+
+            def ts(r):
+                try:
+                    return datetime.strptime(r[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    return None
+
+            inside = [r for r in mine if (ts(r) or 0) >= self.t0 - 0.05 and (ts(r) or 0) <= self.t1 + 0.05]
+            if inside:
+                mine = inside
+        sm = [float(r[3]) for r in mine if r[3].replace(".", "").isdigit()]
+        mx = [float(r[4]) for r in mine if r[4].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in mine for i in range(4) if r[7 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle --
+
+def cpu_oracle_rate(n: int, steps: int, seed: int = 0):
+    """Time the oracle (single thread) for `steps` steps of an n-particle,
+    density-1 sample of the workload; returns particle-steps/s."""
+    import oracle as O
+    from paper_1811_05474_gb300 import synth
+
+    Ln = float(n) * (L / N)
+    p = O.params(L=(Ln,), v=(V,), D_mt=D, D_rw=D, dt=DT, frac_bits=29)
+    X = O.quantize(synth.uniform_positions(n, Ln, seed=seed), 29)
+    A, B = synth.uniform_masses(n, seed=seed)
+    xi = synth.normals(steps, 1, n, seed=seed + 1)
+    t0 = time.perf_counter()
+    for s in range(steps):
+        X, A, B = O.step(p, X, xi[s], A, B)
+    dt = time.perf_counter() - t0
+    return n * steps / dt, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist()
+    if rank != 0:
+        return 0
+    # size the per-step sample so that warm-up + timed steps take ~2 minutes
+    per_particle = 0.7e-6
+    budget = 120.0
+    n = int(min(N, max(10 ** 4, budget / max(args.steps + args.warmup, 1) / per_particle)))
+    cpu_oracle_rate(n, max(args.warmup, 0))
+    rate, secs = cpu_oracle_rate(n, args.steps, seed=1)
+    line = {
+        "impl": "reference", "metric": "particle-steps/s", "value": rate,
+        "unit": "particle-steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / max(args.steps, 1) * (N / n), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_particles": n, "search": "sorted window (1-d)"},
+        "cpu_baseline": {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} steps of a {n}-particle density-1 sample"},
+        "e2e": {"value": rate, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU --
+
+def gpu_run(args, precision: str, steps: int, warmup: int, local: int, realisation: int,
+            sampler: ClockSampler | None):
+    import torch
+
+    from paper_1811_05474_gb300 import mt, synth
+
+    dev = torch.device("cuda", local)
+    prec = mt.MT_MIXED if precision == "mixed" else mt.MT_FP64
+    p = mt.mt_params_init(n=N, L=(L,), v=(V, 0.0), D_mt=D, D_rw=D, dt=DT,
+                          search=mt.MT_SEARCH_CELL, precision=prec, norm=mt.MT_NORM_SYM,
+                          react=1, seed=2024, realisation=realisation,
+                          observe_cap=steps + warmup)
+    sim = mt.Simulation(p, device=dev)
+    x = synth.uniform_positions(N, L, seed=realisation)
+    A, B = synth.uniform_masses(N, seed=realisation)
+    sim.upload(x, A, B)
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    flush_sum = torch.empty((), dtype=torch.int64, device=dev)
+    s = sim.stream
+
+    def flush_l2():
+        # write 512 MiB (evicts the state), then read it back so the lines
+        # left in L2 are clean and no write-back lands in the timed step
+        with torch.cuda.stream(s):
+            flush.zero_()
+            torch.sum(flush.view(torch.int64), dim=0, out=flush_sum)
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for _ in range(warmup):
+        flush_l2()
+        sim.run(1)
+    sim.sync()
+    # timed region: steps enqueued back to back (no host sync inside), each
+    # bracketed by events after its L2 flush
+    if sampler:
+        sampler.mark("t0")
+    for i in range(steps):
+        flush_l2()
+        e0[i].record(s)
+        sim.run(1)
+        e1[i].record(s)
+    torch.cuda.synchronize(dev)
+    if sampler:
+        sampler.mark("t1")
+    # kernel breakdown: a second timed pass with events between the step's
+    # kernels inside the graph (read after each step)
+    mt.mt_set_profiling(sim.h, True)
+    kernel_ms = {}
+    order = []
+    for i in range(min(steps, 200)):
+        flush_l2()
+        sim.run(1)
+        for name, ms in mt.mt_read_profile(sim.h):
+            if name not in kernel_ms:
+                kernel_ms[name] = []
+                order.append(name)
+            kernel_ms[name].append(ms)
+    mt.mt_set_profiling(sim.h, False)
+    step_ms = [e0[i].elapsed_time(e1[i]) for i in range(steps)]
+    sim.sync()
+    npairs = mt.mt_read_pairs(sim.h, None, None, 0)
+    kernels = [{"name": k, "ms": sum(kernel_ms[k]) / len(kernel_ms[k])} for k in order]
+    launches_per_step = len(order)
+    obs = sim.observables()
+    sim.close()
+    del flush
+    return {"total_ms": sum(step_ms), "step_ms": step_ms, "kernels": kernels,
+            "launches_per_step": launches_per_step, "npairs": npairs,
+            "mean_A_last": float(obs[-1, 3]) if len(obs) else None}
+
+
+def e2e_run(steps: int, local: int, realisation: int):
+    """Through the public API with host buffers: upload from pinned host
+    memory, then every step run it and read its observables row back, then
+    read the final masses.  Wall-clock, synchronous."""
+    import numpy as np
+    import torch
+
+    from paper_1811_05474_gb300 import mt, synth
+
+    dev = torch.device("cuda", local)
+    p = mt.mt_params_init(n=N, L=(L,), v=(V, 0.0), D_mt=D, D_rw=D, dt=DT,
+                          precision=mt.MT_MIXED, seed=7, realisation=realisation,
+                          observe_cap=1)
+    sim = mt.Simulation(p, device=dev)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    x = pin(synth.uniform_positions(N, L, seed=realisation))
+    A, B = (pin(v) for v in synth.uniform_masses(N, seed=realisation))
+    oa, ob = pin(np.empty(N)), pin(np.empty(N))
+    row = np.empty((1, 4))
+    ptr = mt._ptr
+    sim.upload(x, A, B)  # warm the graph and the pages
+    sim.run(2)
+    sim.masses()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    mt.mt_upload(sim.h, ptr(x), ptr(A), ptr(B), mt.MT_MEM_HOST)
+    for _ in range(steps):
+        mt.mt_run(sim.h, 1)
+        mt.mt_read_observables(sim.h, ptr(row), 1)
+    mt.mt_read_masses(sim.h, ptr(oa), ptr(ob), mt.MT_MEM_HOST)
+    secs = time.perf_counter() - t0
+    sim.close()
+    return {"value": N * steps / secs, "unit": "particle-steps/s",
+            "h2d_bytes_per_step": (24 * N) / steps, "d2h_bytes_per_step": 32 + (16 * N) / steps}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def load_traffic(kernel: str):
+    """dram bytes per launch from a committed ncu summary, if it was taken on
+    the current sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if t.get("source_hash") != source_hash():
+        return None
+    v = t.get("kernels", {}).get(kernel)
+    return float(v) if v is not None else None
+
+
+def run_ncu(args):
+    """Minimal run for ncu: the workload's state, W steps replayed from the
+    CUDA graph, then K directly launched steps."""
+    import torch
+
+    from paper_1811_05474_gb300 import mt, synth
+
+    n = args.n
+    Ln = float(n) * (L / N)
+    prec = mt.MT_MIXED if args.precision == "mixed" else mt.MT_FP64
+    p = mt.mt_params_init(n=n, L=(Ln,), v=(V, 0.0), D_mt=D, D_rw=D, dt=DT, precision=prec,
+                          seed=2024, observe_cap=args.steps + args.warmup)
+    sim = mt.Simulation(p)
+    sim.upload(synth.uniform_positions(n, Ln, seed=0), *synth.uniform_masses(n, seed=0))
+    sim.run(args.warmup)
+    sim.step(args.steps)
+    sim.sync()
+    torch.cuda.synchronize()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.ncu:
+        return run_ncu(args)
+    import torch
+
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as tdist
+
+        tdist.init_process_group("nccl")
+    from paper_1811_05474_gb300 import build as _b
+
+    if rank == 0:
+        _b.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    main_run = gpu_run(args, args.precision, args.steps, max(args.warmup, 3), local, rank, sampler)
+    total_ms = main_run["total_ms"]
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    fp64 = None
+    if not args.no_fp64 and args.precision == "mixed":
+        k64 = max(10, min(args.steps, 200))
+        r64 = gpu_run(args, "fp64", k64, 3, local, rank, None)
+        dom = max(r64["kernels"], key=lambda k: k["ms"])
+        fp64 = {"value": N * k64 / (r64["total_ms"] * 1e-3), "unit": "particle-steps/s",
+                "ms_per_step": r64["total_ms"] / k64, "steps": k64,
+                "dominant_kernel": dom["name"], "dominant_ms": dom["ms"],
+                "bound": "alu (binary64 pipe)"}
+    e2e = e2e_run(args.steps, local, rank)
+    if ws > 1:
+        t = torch.tensor([e2e["value"]], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MIN)
+        e2e["value"] = float(t.item()) * ws
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return 0
+
+    K = args.steps
+    value = ws * N * K / (total_ms * 1e-3)
+    ms_step = total_ms / K
+    kernels = main_run["kernels"]
+    ksum = sum(k["ms"] for k in kernels)
+    for k in kernels:
+        k["share"] = k["ms"] / ksum if ksum else None
+    dom = max(kernels, key=lambda k: k["ms"])
+    peak, peak_kind = load_peaks()
+    dom_bytes = ALGO_BYTES.get(dom["name"], 0) * N
+    achieved = dom_bytes / (dom["ms"] * 1e-3) / 1e9 if dom["ms"] > 0 else 0.0
+    step_bytes = ALGO_BYTES["step"] * N
+    path_achieved = step_bytes / (ms_step * 1e-3) / 1e9
+    cpu = None
+    if ws == 1 and not args.no_cpu:
+        n_cpu, steps_cpu = N, 20
+        rate, secs = cpu_oracle_rate(n_cpu, steps_cpu, seed=0)
+        cpu = {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"{steps_cpu} steps of the full {n_cpu}-particle workload "
+                         f"({secs:.1f} s, single thread, sorted-window search)"}
+    line = {
+        "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
+        "n_gpus": ws, "steps": K, "warmup": max(args.warmup, 3), "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": ("mixed: f32 weights, f32x2 mass accumulation, i64 positions"
+                  if args.precision == "mixed" else "f64 weights and masses, i64 positions"),
+        "data": "synthetic: seeded uniform positions and U[0,1) masses",
+        "config": {"workload": WORKLOAD, "n_particles": N, "L": L, "v": V, "D_mt": D, "D_rw": D,
+                   "dt": DT, "cutoff": "3*sqrt(4*D_mt*dt)", "search": "cell list (walk)",
+                   "precision": args.precision, "normalisation": "symmetric",
+                   "l2": "flushed between timed steps (512 MiB write, then read)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "pair_interactions_per_s": ws * main_run["npairs"] * K / (total_ms * 1e-3),
+        "pairs_per_step": main_run["npairs"],
+        "roofline": {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                     "algo_bytes_per_launch": dom_bytes,
+                     "traffic": load_traffic(dom["name"])},
+        "path_roofline": {"bound": "hbm", "achieved": path_achieved, "peak": peak, "unit": "GB/s",
+                          "frac": path_achieved / peak, "algo_bytes_per_step": step_bytes},
+        "kernels": kernels,
+        "gpu_launches": K * main_run["launches_per_step"],
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "fp64": fp64,
+        "mean_A_last_step": main_run["mean_A_last"],
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -178,6 +178,20 @@ mt_status mt_philox(mt_handle* h, uint32_t c0, uint32_t c1, uint32_t c2,
                     uint32_t c3, uint32_t k0, uint32_t k1, int64_t n,
                     uint32_t* out);
 
+/* Per-kernel timing: with on = 1 every following step records a CUDA event
+ * on the handle's stream before each of its kernels and one after the last
+ * (graph replays included; turning it on or off drops a captured graph).
+ * Not part of the paper; instrumentation for roofline measurements. */
+mt_status mt_set_profiling(mt_handle* h, int32_t on);
+
+/* Durations in milliseconds of the kernels of the last profiled step, in
+ * launch order (waits for that step).  ms: host array of cap floats;
+ * *count receives the number of kernels in a step (may exceed cap). */
+mt_status mt_read_profile(mt_handle* h, float* ms, int32_t cap, int32_t* count);
+
+/* Name of kernel idx of the last profiled step ("" if out of range). */
+const char* mt_profile_name(const mt_handle* h, int32_t idx);
+
 /* Description of the last error on this thread (static storage). */
 const char* mt_last_error(void);
 

@@ -195,6 +195,10 @@ struct mt_handle {
   int xcur = 0, mcur = 0;  // host mirrors of the device selectors
   long long steps = 0;     // host mirror of the step counter
   cudaGraphExec_t graph = nullptr;
+  bool profile = false;
+  cudaEvent_t ev[kMaxMarks + 1] = {};
+  const char* ev_names[kMaxMarks] = {};
+  int ev_count = 0;  // kernels marked in the last profiled step
 };
 
 namespace {
@@ -216,17 +220,28 @@ mt_status check_device(mt_handle* h) {
   return MT_OK;
 }
 
-// Enqueue one step's kernels.
+// Enqueue one step's kernels (with an event before each kernel and one
+// after the last when profiling is on).
 mt_status enqueue_step(mt_handle* h, const Dev& d) {
   const mt_params& p = h->D.p;
   if (p.n == 0) return MT_OK;
+  Marker mk;
+  if (h->profile) {
+    mk.ev = h->ev;
+    mk.names = h->ev_names;
+  }
+  mk("move", h->stream);
   if (p.search == MT_SEARCH_CELL) {
     CU(launch_move(d, true, true, h->stream));
-    CU(launch_sort(d, h->stream));
+    CU(launch_sort(d, h->stream, mk));
   } else {
     CU(launch_move(d, true, false, h->stream));
   }
-  CU(launch_transfer(d, p.search, p.precision, h->stream));
+  CU(launch_transfer(d, p.search, p.precision, h->stream, mk));
+  if (h->profile) {
+    CU(Marker::record(h->ev[mk.count], h->stream));
+    h->ev_count = mk.count;
+  }
   return MT_OK;
 }
 
@@ -388,8 +403,9 @@ mt_status mt_upload(mt_handle* h, const double* x, const double* A, const double
   CU(launch_upload(d, xs, ms, ms + n, p.precision, h->stream));
   if (p.search == MT_SEARCH_CELL) {
     // sort once so the state is in cell order between steps
+    Marker none;
     CU(launch_move(d, false, true, h->stream));
-    CU(launch_sort(d, h->stream));
+    CU(launch_sort(d, h->stream, none));
     CU(launch_permute(d, h->stream));
     h->xcur = 1;
     h->mcur = 1;
@@ -553,12 +569,50 @@ mt_status mt_philox(mt_handle* h, uint32_t c0, uint32_t c1, uint32_t c2, uint32_
   return MT_OK;
 }
 
+mt_status mt_set_profiling(mt_handle* h, int32_t on) {
+  if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
+  const bool want = on != 0;
+  if (want == h->profile) return MT_OK;
+  if (want && !h->ev[0]) {
+    for (int i = 0; i <= kMaxMarks; ++i) CU(cudaEventCreate(&h->ev[i]));
+  }
+  h->profile = want;
+  h->ev_count = 0;
+  if (h->graph) {  // the captured graph must (not) contain the event records
+    CU(cudaStreamSynchronize(h->stream));
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return MT_OK;
+}
+
+mt_status mt_read_profile(mt_handle* h, float* ms, int32_t cap, int32_t* count) {
+  if (!h || !count) return fail(MT_ERR_INVALID, "handle or count is NULL");
+  *count = 0;
+  if (!h->profile || h->ev_count == 0) return MT_OK;
+  CU(cudaEventSynchronize(h->ev[h->ev_count]));
+  const int m = h->ev_count < cap ? h->ev_count : cap;
+  for (int i = 0; i < m; ++i) {
+    if (!ms) return fail(MT_ERR_INVALID, "ms is NULL");
+    CU(cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]));
+  }
+  *count = h->ev_count;
+  return MT_OK;
+}
+
+const char* mt_profile_name(const mt_handle* h, int32_t idx) {
+  if (!h || idx < 0 || idx >= h->ev_count) return "";
+  return h->ev_names[idx];
+}
+
 const char* mt_last_error(void) { return g_err.c_str(); }
 
 void mt_destroy(mt_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (int i = 0; i <= kMaxMarks; ++i)
+    if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
 }

@@ -118,6 +118,29 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned int k0, unsigne
   return c;
 }
 
+// 64-bit integer <-> binary32 conversions through 32-bit instructions
+// (conversions with a 64-bit integer operand run on the binary64 pipe, which
+// is narrow on this GPU).  Both round to nearest even, like the 64-bit forms.
+__device__ __forceinline__ float ll_to_float(long long v) {
+  if (v >= -2147483647LL && v <= 2147483647LL) return __int2float_rn((int)v);
+  // |v| >= 2^31: the high word carries every bit binary32 can keep except
+  // a possible sticky tail, which the low word's contribution rounds in.
+  const float hi = __int2float_rn((int)(v >> 32)) * 4294967296.0f;
+  const float lo = __uint2float_rn((unsigned int)(v & 0xffffffffLL));
+  return __fadd_rn(hi, lo);
+}
+
+__device__ __forceinline__ long long float_to_ll_rn(float f) {
+  if (fabsf(f) < 2147483520.0f) return (long long)__float2int_rn(f);
+  // |f| >= 2^31 - 128: f is an integer (at most 24 significant bits), so
+  // shift its significand into place exactly.
+  const unsigned int b = __float_as_uint(f);
+  const int e = (int)((b >> 23) & 0xff) - 127;  // >= 30
+  const long long m = (long long)((b & 0x7fffff) | 0x800000);
+  const long long mag = e >= 23 ? (e - 23 < 40 ? (m << (e - 23)) : 0x7fffffffffffffffLL) : m;
+  return (b >> 31) ? -mag : mag;
+}
+
 // Two standard normals from two 32-bit words (Box-Muller, binary32):
 // u1 in (0, 1], u2 in [0, 1).
 __device__ __forceinline__ float2 box_muller(unsigned int a, unsigned int b) {
@@ -186,11 +209,36 @@ __device__ __forceinline__ void f64_store(unsigned long long* M, long long i, do
 
 // ---------------------------------------------------------------- launchers --
 // Each returns the cudaError_t of its launch.  grid sizes are computed from d.
+// A Marker, when enabled, records a CUDA event on the stream before each
+// kernel so that a step's kernels can be timed one by one.
+
+constexpr int kMaxMarks = 16;
+
+struct Marker {
+  cudaEvent_t* ev = nullptr;  // null: disabled
+  const char** names = nullptr;
+  int count = 0;
+  void operator()(const char* name, cudaStream_t s) {
+    if (!ev || count >= kMaxMarks) return;
+    names[count] = name;
+    record(ev[count], s);
+    ++count;
+  }
+  // Inside stream capture the record must become an external event node
+  // so that every graph replay records it.
+  static cudaError_t record(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &st);
+    return st == cudaStreamCaptureStatusActive
+               ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+               : cudaEventRecord(e, s);
+  }
+};
 
 cudaError_t launch_move(const Dev& d, bool move, bool hist, cudaStream_t s);
-cudaError_t launch_sort(const Dev& d, cudaStream_t s);  // scan, scatter, cell sort
+cudaError_t launch_sort(const Dev& d, cudaStream_t s, Marker& mk);  // scan, scatter, cell sort
 cudaError_t launch_permute(const Dev& d, cudaStream_t s);  // gather id/masses after sort, flip
-cudaError_t launch_transfer(const Dev& d, int search, int precision, cudaStream_t s);
+cudaError_t launch_transfer(const Dev& d, int search, int precision, cudaStream_t s, Marker& mk);
 cudaError_t launch_upload(const Dev& d, const double* x, const double* A,
                           const double* B, int precision, cudaStream_t s);
 cudaError_t launch_read_masses(const Dev& d, double* A, double* B, int precision,

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kThreads) k_move(Dev d) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       // Eq. 2 on the grid: drift + rint(b * xi), then the wall mirror.
-      const long long step = __float2ll_rn(__fmul_rn(d.bq, z[a]));
+      const long long step = float_to_ll_rn(__fmul_rn(d.bq, z[a]));
       pos[a] = reflect(pos[a] + d.drift[a] + step, d.Lq[a]);
       X[(long long)a * d.n + p] = pos[a];
     }
@@ -339,19 +339,26 @@ cudaError_t launch_move(const Dev& d, bool move, bool hist, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_sort(const Dev& d, cudaStream_t s) {
+cudaError_t launch_sort(const Dev& d, cudaStream_t s, Marker& mk) {
   const unsigned int gs = blocks_for(d.ncell, kScanTile);
+  mk("scan", s);
   k_scan<<<gs, kThreads, 0, s>>>(d);
   const unsigned int gp = blocks_for(d.n, kThreads);
   const unsigned int gc = blocks_for(d.ncell, kThreads);
   const unsigned int gb = (unsigned int)(d.nbig_cap < 304 ? d.nbig_cap : 304);
   if (d.dim == 1) {
+    mk("scatter", s);
     k_scatter<1><<<gp, kThreads, 0, s>>>(d);
+    mk("cellsort", s);
     k_cellsort<1><<<gc, kThreads, 0, s>>>(d);
+    mk("bigsort", s);
     k_bigsort<1><<<gb, 1024, 0, s>>>(d);
   } else {
+    mk("scatter", s);
     k_scatter<2><<<gp, kThreads, 0, s>>>(d);
+    mk("cellsort", s);
     k_cellsort<2><<<gc, kThreads, 0, s>>>(d);
+    mk("bigsort", s);
     k_bigsort<2><<<gb, 1024, 0, s>>>(d);
   }
   return cudaGetLastError();

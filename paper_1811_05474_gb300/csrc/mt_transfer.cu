@@ -51,10 +51,10 @@ template <int DIM>
 struct Weight<true, DIM> {
   using T = float;
   static __device__ __forceinline__ float eval(const Dev& d, long long dx, long long dy) {
-    const float fx = __ll2float_rn(dx);
+    const float fx = ll_to_float(dx);
     float s2 = __fmul_rn(fx, fx);
     if (DIM == 2) {
-      const float fy = __ll2float_rn(dy);
+      const float fy = ll_to_float(dy);
       s2 = __fadd_rn(s2, __fmul_rn(fy, fy));
     }
     return __expf(-__fmul_rn(s2, d.inv8f));
@@ -513,40 +513,51 @@ __global__ void __launch_bounds__(kThreads) k_exchange_brute(Dev d) {
 // --------------------------------------------------------------- launch --
 
 template <bool MIX>
-static void transfer_t(const Dev& d, int search, cudaStream_t s) {
+static void transfer_t(const Dev& d, int search, cudaStream_t s, Marker& mk) {
   const unsigned int g = (unsigned int)((d.n + kThreads - 1) / kThreads);
   if (search == MT_SEARCH_CELL) {
     if (d.dim == 1) {
+      mk("rowsum_walk", s);
       k_rowsum_walk<MIX><<<g, kThreads, 0, s>>>(d);
+      mk("exchange_walk", s);
       k_exchange_walk<MIX><<<g, kThreads, 0, s>>>(d);
     } else {
+      mk("rowsum_cell2", s);
       k_rowsum_cell2<MIX><<<g, kThreads, 0, s>>>(d);
+      mk("exchange_cell2", s);
       k_exchange_cell2<MIX><<<g, kThreads, 0, s>>>(d);
     }
   } else if (search == MT_SEARCH_BRUTE) {
-    if (d.dim == 1) {
+    mk("rowsum_brute", s);
+    if (d.dim == 1)
       k_rowsum_brute<MIX, true, 1><<<g, kThreads, 0, s>>>(d);
-      k_exchange_brute<MIX, true, 1><<<g, kThreads, 0, s>>>(d);
-    } else {
+    else
       k_rowsum_brute<MIX, true, 2><<<g, kThreads, 0, s>>>(d);
+    mk("exchange_brute", s);
+    if (d.dim == 1)
+      k_exchange_brute<MIX, true, 1><<<g, kThreads, 0, s>>>(d);
+    else
       k_exchange_brute<MIX, true, 2><<<g, kThreads, 0, s>>>(d);
-    }
   } else {
-    if (d.dim == 1) {
+    mk("rowsum_full", s);
+    if (d.dim == 1)
       k_rowsum_brute<MIX, false, 1><<<g, kThreads, 0, s>>>(d);
-      k_exchange_brute<MIX, false, 1><<<g, kThreads, 0, s>>>(d);
-    } else {
+    else
       k_rowsum_brute<MIX, false, 2><<<g, kThreads, 0, s>>>(d);
+    mk("exchange_full", s);
+    if (d.dim == 1)
+      k_exchange_brute<MIX, false, 1><<<g, kThreads, 0, s>>>(d);
+    else
       k_exchange_brute<MIX, false, 2><<<g, kThreads, 0, s>>>(d);
-    }
   }
 }
 
-cudaError_t launch_transfer(const Dev& d, int search, int precision, cudaStream_t s) {
+cudaError_t launch_transfer(const Dev& d, int search, int precision, cudaStream_t s,
+                            Marker& mk) {
   if (precision == MT_MIXED)
-    transfer_t<true>(d, search, s);
+    transfer_t<true>(d, search, s, mk);
   else
-    transfer_t<false>(d, search, s);
+    transfer_t<false>(d, search, s, mk);
   return cudaGetLastError();
 }
 

@@ -90,11 +90,15 @@ def lib(path: Path | None = None):
         "mt_read_pairs": [H, _vp, _vp, i64, ctypes.POINTER(i64)],
         "mt_steps_done": [H, ctypes.POINTER(i64)],
         "mt_philox": [H, u32, u32, u32, u32, u32, u32, i64, _vp],
+        "mt_set_profiling": [H, i32],
+        "mt_read_profile": [H, _vp, i32, ctypes.POINTER(i32)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
         f.argtypes = args
         f.restype = ctypes.c_int
+    L.mt_profile_name.argtypes = [H, i32]
+    L.mt_profile_name.restype = ctypes.c_char_p
     L.mt_last_error.argtypes = []
     L.mt_last_error.restype = ctypes.c_char_p
     L.mt_destroy.argtypes = [H]
@@ -198,6 +202,23 @@ def mt_steps_done(h) -> int:
 def mt_philox(h, ctr, key, n: int, out_ptr) -> None:
     check(lib().mt_philox(h, *[int(c) & 0xFFFFFFFF for c in ctr],
                           *[int(k) & 0xFFFFFFFF for k in key], n, out_ptr))
+
+
+def mt_set_profiling(h, on: bool) -> None:
+    check(lib().mt_set_profiling(h, 1 if on else 0))
+
+
+def mt_read_profile(h):
+    """[(kernel name, ms), ...] for the last profiled step."""
+    ms = (ctypes.c_float * 16)()
+    cnt = ctypes.c_int32(0)
+    check(lib().mt_read_profile(h, ms, 16, ctypes.byref(cnt)))
+    n = min(int(cnt.value), 16)
+    return [(mt_profile_name(h, i), float(ms[i])) for i in range(n)]
+
+
+def mt_profile_name(h, idx: int) -> str:
+    return lib().mt_profile_name(h, idx).decode()
 
 
 def mt_destroy(h) -> None:

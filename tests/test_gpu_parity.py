@@ -345,3 +345,21 @@ def test_step_before_upload_and_bad_positions():
         sim.upload(x, np.ones(10), np.ones(10))
         sim.sync()
     assert e.value.status == mt.MT_ERR_INVALID
+
+
+def test_profiling_events_in_graph_and_direct_steps():
+    n, L = 100000, 100000.0
+    x = synth.uniform_positions(n, L, seed=41)
+    A, B = synth.uniform_masses(n, seed=41)
+    sim = make(n, L, precision=mt.MT_MIXED)
+    sim.upload(x, A, B)
+    mt.mt_set_profiling(sim.h, True)
+    for runner in (lambda: sim.run(3), lambda: sim.step(1)):
+        runner()
+        prof = mt.mt_read_profile(sim.h)
+        names = [k for k, _ in prof]
+        assert names[0] == "move" and names[-1] == "exchange_walk"
+        assert all(ms > 0 for _, ms in prof)
+    mt.mt_set_profiling(sim.h, False)
+    sim.run(2)
+    sim.sync()
