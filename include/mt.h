@@ -192,6 +192,28 @@ mt_status mt_read_profile(mt_handle* h, float* ms, int32_t cap, int32_t* count);
 /* Name of kernel idx of the last profiled step ("" if out of range). */
 const char* mt_profile_name(const mt_handle* h, int32_t idx);
 
+/* Mass transfer (Eq. 3, 4, 7) plus, if react = 1, the A + B -> E reaction,
+ * for n particles on a line, in binary64, with no device allocation.  The
+ * paper has no counterpart: this is for callers that cannot call cudaMalloc
+ * (their allocator belongs to a host application or another runtime, or
+ * allocation is forbidden while their pipeline runs) and so cannot provide a
+ * workspace.  They pass device arrays: x (n positions in [0, L], sorted
+ * ascending), A and B (n masses) in, A_out and B_out (n masses, not aliasing
+ * the inputs) out.  D_mt, dt, cutoff (<= 0: 3 sqrt(4 D_mt dt)) and norm
+ * (MT_NORM_*) mean what they mean in mt_params; positions are rounded to
+ * the grid that mt_resolve would choose for this L and cutoff.
+ * Intermediates live in a fixed device array inside libmt, held by every GPU
+ * that loads the library until exit: n may not exceed 1048576 (larger n is
+ * rejected with MT_ERR_INVALID).  The first call on a device looks up that
+ * array's address, so make it before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU race and give wrong results.
+ * Runs on stream (NULL: the default stream) and waits for it before
+ * returning; MT_ERR_INVALID if a position is outside [0, L] or unsorted. */
+mt_status mt_transfer_1d_noalloc(const double* x, const double* A, const double* B,
+                                 double* A_out, double* B_out, int64_t n, double L,
+                                 double D_mt, double dt, double cutoff, int32_t norm,
+                                 int32_t react, void* stream);
+
 /* Description of the last error on this thread (static storage). */
 const char* mt_last_error(void);
 

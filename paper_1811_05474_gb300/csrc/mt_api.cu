@@ -185,6 +185,14 @@ mt_status resolve(const mt_params* in, Derived* out) {
 
 }  // namespace
 
+namespace mt {
+// Lets other translation units report through mt_last_error().
+mt_status set_last_error(mt_status s, const char* msg) {
+  g_err = msg;
+  return s;
+}
+}  // namespace mt
+
 struct mt_handle {
   Derived D;
   Dev dev;

@@ -91,6 +91,9 @@ def lib(path: Path | None = None):
         "mt_steps_done": [H, ctypes.POINTER(i64)],
         "mt_philox": [H, u32, u32, u32, u32, u32, u32, i64, _vp],
         "mt_set_profiling": [H, i32],
+        "mt_transfer_1d_noalloc": [_vp, _vp, _vp, _vp, _vp, i64, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_double, i32, i32,
+                                   _vp],
         "mt_read_profile": [H, _vp, i32, ctypes.POINTER(i32)],
     }
     for name, args in sig.items():
@@ -219,6 +222,14 @@ def mt_read_profile(h):
 
 def mt_profile_name(h, idx: int) -> str:
     return lib().mt_profile_name(h, idx).decode()
+
+
+def mt_transfer_1d_noalloc(x_ptr, A_ptr, B_ptr, Ao_ptr, Bo_ptr, n: int, L: float, D_mt: float,
+                           dt: float, cutoff: float, norm: int, react: int,
+                           stream_ptr=None) -> None:
+    """Device pointers in and out; see include/mt.h (no device allocation)."""
+    check(lib().mt_transfer_1d_noalloc(x_ptr, A_ptr, B_ptr, Ao_ptr, Bo_ptr, n, L, D_mt, dt,
+                                       cutoff, norm, react, stream_ptr))
 
 
 def mt_destroy(h) -> None:
