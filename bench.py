@@ -54,6 +54,7 @@ ALGO_BYTES = {
     "bigsort": 0,
     "rowsum_walk": 8,      # x in
     "exchange_walk": 40,   # x, A, B in; A, B out
+    "fused_step": 48,      # the whole step in one kernel: x, A, B in and out
     "step": 48,            # whole step: x, A, B in and out
 }
 
@@ -335,7 +336,7 @@ def load_traffic(kernel: str):
 
 def run_ncu(args):
     """Minimal run for ncu: the workload's state, W steps replayed from the
-    CUDA graph, then K directly launched steps."""
+    CUDA graph, then K directly launched steps (profiling mode)."""
     import torch
 
     from paper_1811_05474_gb300 import mt, synth
@@ -348,7 +349,10 @@ def run_ncu(args):
     sim = mt.Simulation(p)
     sim.upload(synth.uniform_positions(n, Ln, seed=0), *synth.uniform_masses(n, seed=0))
     sim.run(args.warmup)
-    sim.step(args.steps)
+    # direct launches (ncu does not profile kernels inside graphs that
+    # contain conditional nodes)
+    mt.mt_set_profiling(sim.h, True)
+    sim.run(args.steps)
     sim.sync()
     torch.cuda.synchronize()
     return 0
@@ -441,7 +445,7 @@ def main():
                   if args.precision == "mixed" else "f64 weights and masses, i64 positions"),
         "data": "synthetic: seeded uniform positions and U[0,1) masses",
         "config": {"workload": WORKLOAD, "n_particles": N, "L": L, "v": V, "D_mt": D, "D_rw": D,
-                   "dt": DT, "cutoff": "3*sqrt(4*D_mt*dt)", "search": "cell list (walk)",
+                   "dt": DT, "cutoff": "3*sqrt(4*D_mt*dt)", "search": "cell list (fused 1-d step)",
                    "precision": args.precision, "normalisation": "symmetric",
                    "l2": "flushed between timed steps (512 MiB write, then read)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},

@@ -50,9 +50,12 @@ struct Derived {
   int cshift = 0;
   long long ncx = 1, ncy = 1, ncell = 0;
   long long nbig_cap = 0, nblocks = 0, ntiles = 0;
+  // fused 1-d step (one kernel per step) and its tiling
+  bool fused = false;
+  long long seg_target = 0, nseg = 0, hc = 0;
   // workspace offsets
   size_t o_ctrl, o_X[2], o_id[2], o_M[2], o_src, o_rinv, o_count, o_start, o_cursor,
-      o_status, o_big, o_part, o_obs, total;
+      o_status, o_big, o_part, o_obs, o_fstart[2], o_cb[2], o_ovlist, total;
 };
 
 int default_frac_bits(const mt_params& p) {
@@ -155,6 +158,26 @@ mt_status resolve(const mt_params* in, Derived* out) {
   D.nbig_cap = p.n / (kSmallCell + 1) + 1;
   D.nblocks = (p.n + kThreads - 1) / kThreads;
   if (D.nblocks < 1) D.nblocks = 1;
+  // Fused 1-d step: segments of seg_target particles staged with a halo of
+  // hc cells (2 Smax) and the displacement bound; pick the largest target
+  // (<= 1024) whose expected staging, with 50% headroom, fits kFusedCap.
+  if (p.search == MT_SEARCH_CELL && p.dim == 1 && p.n > 0) {
+    const long long w = 1LL << D.cshift;
+    D.hc = (2 * D.S + w - 1) / w + 1;
+    double dr = std::fabs((double)D.drift[0]);
+    const long long dc = (long long)((dr + std::ceil((double)D.bq * 5.78) + 2.0) / (double)w) + 2;
+    const double per_cell = (double)p.n / (double)D.ncell;
+    long long T = 1024;
+    while (T >= 64 && (double)T + 2.0 * (double)(D.hc + dc + 1) * per_cell * 1.5 + 64.0 >
+                          (double)kFusedCap)
+      T /= 2;
+    if (T >= 64) {
+      D.fused = true;
+      D.seg_target = T;
+      D.nseg = (p.n + T - 1) / T;
+      D.nblocks = D.nblocks > D.nseg ? D.nblocks : D.nseg;
+    }
+  }
   D.ntiles = (D.ncell + kScanTile - 1) / kScanTile;
   // workspace layout
   size_t o = 0;
@@ -177,6 +200,9 @@ mt_status resolve(const mt_params* in, Derived* out) {
   D.o_big = take((size_t)D.nbig_cap * 4);
   D.o_part = take((size_t)D.nblocks * 4 * 8);
   D.o_obs = take((size_t)p.observe_cap * 4 * 8);
+  for (int b2 = 0; b2 < 2; ++b2) D.o_fstart[b2] = take(D.fused ? (size_t)(D.ncell + 1) * 4 : 0);
+  for (int b2 = 0; b2 < 2; ++b2) D.o_cb[b2] = take(D.fused ? (size_t)(D.nseg + 1) * 4 : 0);
+  D.o_ovlist = take(D.fused ? (size_t)D.nseg * 4 : 0);
   D.total = o;
   D.p = p;
   *out = D;
@@ -200,8 +226,8 @@ struct mt_handle {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   bool uploaded = false;
-  int xcur = 0, mcur = 0;  // host mirrors of the device selectors
   long long steps = 0;     // host mirror of the step counter
+  const float* noise = nullptr;
   cudaGraphExec_t graph = nullptr;
   bool profile = false;
   cudaEvent_t ev[kMaxMarks + 1] = {};
@@ -215,10 +241,16 @@ bool capturable(cudaStream_t s) {
   return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
 }
 
-mt_status check_device(mt_handle* h) {
+mt_status read_ctrl(mt_handle* h, Ctrl* c) {
   CU(cudaStreamSynchronize(h->stream));
+  CU(cudaMemcpy(c, h->ws + h->D.o_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+  return MT_OK;
+}
+
+mt_status check_device(mt_handle* h) {
   Ctrl c;
-  CU(cudaMemcpy(&c, h->ws + h->D.o_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+  const mt_status s = read_ctrl(h, &c);
+  if (s != MT_OK) return s;
   if (c.err == kErrTimeout)
     return fail(MT_ERR_TIMEOUT, "device wait gave up (scan tile %lld)", c.err_info);
   if (c.err == kErrInput)
@@ -228,16 +260,11 @@ mt_status check_device(mt_handle* h) {
   return MT_OK;
 }
 
-// Enqueue one step's kernels (with an event before each kernel and one
-// after the last when profiling is on).
-mt_status enqueue_step(mt_handle* h, const Dev& d) {
+// The general pipeline: move + histogram, scan, scatter, cell sort, two
+// transfer passes; on the 1-d cell path it also refreshes the fused path's
+// cell starts and segment boundaries.
+mt_status enqueue_general(mt_handle* h, const Dev& d, Marker& mk) {
   const mt_params& p = h->D.p;
-  if (p.n == 0) return MT_OK;
-  Marker mk;
-  if (h->profile) {
-    mk.ev = h->ev;
-    mk.names = h->ev_names;
-  }
   mk("move", h->stream);
   if (p.search == MT_SEARCH_CELL) {
     CU(launch_move(d, true, true, h->stream));
@@ -246,6 +273,45 @@ mt_status enqueue_step(mt_handle* h, const Dev& d) {
     CU(launch_move(d, true, false, h->stream));
   }
   CU(launch_transfer(d, p.search, p.precision, h->stream, mk));
+  if (h->D.fused) {
+    mk("fused_prep", h->stream);
+    CU(launch_fused_prep(d, 1, h->stream));
+  }
+  return MT_OK;
+}
+
+// Enqueue one step's kernels directly (no graph), with an event before each
+// kernel and one after the last when profiling is on.  On the fused path the
+// host reads whether a segment overflowed and, if so, runs the general
+// pipeline for the step.
+mt_status enqueue_step(mt_handle* h, const Dev& d) {
+  const mt_params& p = h->D.p;
+  if (p.n == 0) return MT_OK;
+  Marker mk;
+  if (h->profile) {
+    mk.ev = h->ev;
+    mk.names = h->ev_names;
+  }
+  if (h->D.fused) {
+    mk("fused_step", h->stream);
+    CU(launch_fused_step(d, p.precision, 0, 0, h->stream));
+    Ctrl c;
+    mt_status s = read_ctrl(h, &c);
+    if (s != MT_OK) return s;
+    if (c.nov > 0) {
+      mk("fused_big", h->stream);
+      CU(launch_fused_big(d, p.precision, 0, 0, h->stream));
+      s = read_ctrl(h, &c);
+      if (s != MT_OK) return s;
+      if (c.fallback) {
+        const mt_status s2 = enqueue_general(h, d, mk);
+        if (s2 != MT_OK) return s2;
+      }
+    }
+  } else {
+    const mt_status s = enqueue_general(h, d, mk);
+    if (s != MT_OK) return s;
+  }
   if (h->profile) {
     CU(Marker::record(h->ev[mk.count], h->stream));
     h->ev_count = mk.count;
@@ -253,16 +319,83 @@ mt_status enqueue_step(mt_handle* h, const Dev& d) {
   return MT_OK;
 }
 
-void advance_mirrors(mt_handle* h) {
-  if (h->D.p.n == 0) {
-    ++h->steps;
-    return;
+// Capture one step into an executable graph.  On the fused path the graph
+// is [fused step] -> IF(overflow) {general pipeline}.
+mt_status build_graph(mt_handle* h) {
+  const Dev& d = h->dev;
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  cudaGraph_t g = nullptr;
+  CU(cudaGraphCreate(&g, 0));
+  mt_status s = MT_OK;
+  Marker none;
+  if (h->D.fused) {
+    // g: [fast tier] -> IF(queued) { [second tier] -> IF(overflow) { general } }
+    cudaGraphConditionalHandle cond1, cond2;
+    CU(cudaGraphConditionalHandleCreate(&cond1, g, 0, 0));
+    CU(cudaStreamBeginCaptureToGraph(h->stream, g, nullptr, nullptr, 0, mode));
+    cudaError_t e1 = launch_fused_step(d, h->D.p.precision, cond1, 1, h->stream);
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return fail(MT_ERR_CUDA, "graph capture of the fused step failed");
+    }
+    cudaGraph_t body1 = nullptr;
+    {
+      cudaGraphNode_t knode = nullptr;
+      size_t nn = 1;
+      CU(cudaGraphGetNodes(g, &knode, &nn));
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = cond1;
+      cp.conditional.type = cudaGraphCondTypeIf;
+      cp.conditional.size = 1;
+      cudaGraphNode_t cnode = nullptr;
+      CU(cudaGraphAddNode(&cnode, g, &knode, nullptr, 1, &cp));
+      body1 = cp.conditional.phGraph_out[0];
+    }
+    CU(cudaGraphConditionalHandleCreate(&cond2, body1, 0, 0));
+    CU(cudaStreamBeginCaptureToGraph(h->stream, body1, nullptr, nullptr, 0, mode));
+    e1 = launch_fused_big(d, h->D.p.precision, cond2, 1, h->stream);
+    e2 = cudaStreamEndCapture(h->stream, &body1);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return fail(MT_ERR_CUDA, "graph capture of the second fused tier failed");
+    }
+    cudaGraph_t body2 = nullptr;
+    {
+      cudaGraphNode_t bnode = nullptr;
+      size_t nn = 1;
+      CU(cudaGraphGetNodes(body1, &bnode, &nn));
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = cond2;
+      cp.conditional.type = cudaGraphCondTypeIf;
+      cp.conditional.size = 1;
+      cudaGraphNode_t cnode = nullptr;
+      CU(cudaGraphAddNode(&cnode, body1, &bnode, nullptr, 1, &cp));
+      body2 = cp.conditional.phGraph_out[0];
+    }
+    CU(cudaStreamBeginCaptureToGraph(h->stream, body2, nullptr, nullptr, 0, mode));
+    s = enqueue_general(h, d, none);
+    const cudaError_t e3 = cudaStreamEndCapture(h->stream, &body2);
+    if (s == MT_OK && e3 != cudaSuccess) s = fail(MT_ERR_CUDA, "graph capture of the fallback failed");
+  } else {
+    CU(cudaStreamBeginCaptureToGraph(h->stream, g, nullptr, nullptr, 0, mode));
+    s = enqueue_general(h, d, none);
+    const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (s == MT_OK && e != cudaSuccess) s = fail(MT_ERR_CUDA, "graph capture failed");
   }
-  if (h->D.p.search == MT_SEARCH_CELL)
-    h->xcur ^= 1;
-  else
-    h->mcur ^= 1;
-  ++h->steps;
+  if (s != MT_OK) {
+    cudaGraphDestroy(g);
+    return s;
+  }
+  const cudaError_t e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->graph = nullptr;
+    return fail(MT_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  return MT_OK;
 }
 
 }  // namespace
@@ -352,7 +485,14 @@ mt_status mt_create(const mt_params* p, void* workspace, size_t workspace_bytes,
   d.big = reinterpret_cast<int*>(w + D.o_big);
   d.partials = reinterpret_cast<double*>(w + D.o_part);
   d.obs = reinterpret_cast<double*>(w + D.o_obs);
-  d.noise = nullptr;
+  for (int b = 0; b < 2; ++b) {
+    d.fstart[b] = reinterpret_cast<int*>(w + D.o_fstart[b]);
+    d.cb[b] = reinterpret_cast<int*>(w + D.o_cb[b]);
+  }
+  d.ovlist = reinterpret_cast<int*>(w + D.o_ovlist);
+  d.nseg = (int)D.nseg;
+  d.seg_target = (int)D.seg_target;
+  d.hc = D.hc;
   d.n = D.p.n;
   d.dim = D.p.dim;
   d.norm = D.p.norm;
@@ -376,7 +516,8 @@ mt_status mt_create(const mt_params* p, void* workspace, size_t workspace_bytes,
   d.real = (unsigned int)D.p.realisation;
   d.nbig_cap = (int)D.nbig_cap;
   d.nblocks = (int)D.nblocks;
-  const cudaError_t e = cudaMemsetAsync(h->ws, 0, D.total, h->stream);
+  cudaError_t e = D.fused ? fused_configure() : cudaSuccess;
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->ws, 0, D.total, h->stream);
   if (e != cudaSuccess) {
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -396,12 +537,14 @@ mt_status mt_upload(mt_handle* h, const double* x, const double* A, const double
   CU(cudaMemsetAsync(h->ws + h->D.o_ctrl, 0, sizeof(Ctrl), h->stream));
   // the scan epoch restarts with the control block: clear old status words
   if (h->D.ntiles > 0) CU(cudaMemsetAsync(h->ws + h->D.o_status, 0, h->D.ntiles * 8, h->stream));
-  h->xcur = 0;
-  h->mcur = 0;
   h->steps = 0;
   h->uploaded = true;
   if (n == 0) return MT_OK;
   const Dev& d = h->dev;
+  // the control block was cleared: restore the noise source and its bound
+  CU(cudaMemcpyAsync(&d.ctrl->noise, &h->noise, sizeof(h->noise), cudaMemcpyHostToDevice,
+                     h->stream));
+  CU(launch_noise_bound(d, h->noise, h->stream));
   double* xs = reinterpret_cast<double*>(d.X[1]);
   double* ms = reinterpret_cast<double*>(d.M[1]);
   const cudaMemcpyKind kind = mem == MT_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -415,8 +558,7 @@ mt_status mt_upload(mt_handle* h, const double* x, const double* A, const double
     CU(launch_move(d, false, true, h->stream));
     CU(launch_sort(d, h->stream, none));
     CU(launch_permute(d, h->stream));
-    h->xcur = 1;
-    h->mcur = 1;
+    if (h->D.fused) CU(launch_fused_prep(d, 0, h->stream));
   }
   if (mem == MT_MEM_HOST) CU(cudaStreamSynchronize(h->stream));
   return MT_OK;
@@ -424,16 +566,11 @@ mt_status mt_upload(mt_handle* h, const double* x, const double* A, const double
 
 mt_status mt_set_noise(mt_handle* h, const float* xi) {
   if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
-  h->dev.noise = xi;
-  return MT_OK;
-}
-
-mt_status mt_step(mt_handle* h) {
-  if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
-  if (!h->uploaded) return fail(MT_ERR_STATE, "mt_step before mt_upload");
-  const mt_status s = enqueue_step(h, h->dev);
-  if (s != MT_OK) return s;
-  advance_mirrors(h);
+  h->noise = xi;
+  if (!h->uploaded) return MT_OK;  // mt_upload installs it
+  CU(cudaMemcpyAsync(&h->dev.ctrl->noise, &h->noise, sizeof(h->noise), cudaMemcpyHostToDevice,
+                     h->stream));
+  CU(launch_noise_bound(h->dev, xi, h->stream));
   return MT_OK;
 }
 
@@ -441,35 +578,29 @@ mt_status mt_run(mt_handle* h, int64_t nsteps) {
   if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
   if (!h->uploaded) return fail(MT_ERR_STATE, "mt_run before mt_upload");
   if (nsteps < 0) return fail(MT_ERR_INVALID, "nsteps must be >= 0");
-  if (h->dev.noise || !capturable(h->stream) || h->D.p.n == 0) {
+  if (h->profile || !capturable(h->stream) || h->D.p.n == 0) {
     for (int64_t i = 0; i < nsteps; ++i) {
-      const mt_status s = mt_step(h);
+      const mt_status s = enqueue_step(h, h->dev);
       if (s != MT_OK) return s;
+      ++h->steps;
     }
     return MT_OK;
   }
   if (!h->graph) {
-    cudaGraph_t g = nullptr;
-    CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    const mt_status s = enqueue_step(h, h->dev);
-    const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
-    if (s != MT_OK) {
-      if (g) cudaGraphDestroy(g);
-      return s;
-    }
-    if (e != cudaSuccess) return fail(MT_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
-    const cudaError_t e2 = cudaGraphInstantiate(&h->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e2 != cudaSuccess) {
-      h->graph = nullptr;
-      return fail(MT_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e2));
-    }
+    const mt_status s = build_graph(h);
+    if (s != MT_OK) return s;
   }
   for (int64_t i = 0; i < nsteps; ++i) {
     CU(cudaGraphLaunch(h->graph, h->stream));
-    advance_mirrors(h);
+    ++h->steps;
   }
   return MT_OK;
+}
+
+mt_status mt_step(mt_handle* h) {
+  if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
+  if (!h->uploaded) return fail(MT_ERR_STATE, "mt_step before mt_upload");
+  return mt_run(h, 1);
 }
 
 mt_status mt_sync(mt_handle* h) {
@@ -487,7 +618,10 @@ mt_status mt_read_masses(mt_handle* h, double* A, double* B, int32_t mem) {
   if (mem == MT_MEM_DEVICE) {
     CU(launch_read_masses(h->dev, A, B, h->D.p.precision, h->stream));
   } else {
-    double* stage = reinterpret_cast<double*>(h->dev.M[h->mcur ^ 1]);
+    Ctrl c;
+    const mt_status s = read_ctrl(h, &c);
+    if (s != MT_OK) return s;
+    double* stage = reinterpret_cast<double*>(h->dev.M[c.mcur ^ 1]);
     CU(launch_read_masses(h->dev, stage, stage + n, h->D.p.precision, h->stream));
     CU(cudaMemcpyAsync(A, stage, n * 8, cudaMemcpyDeviceToHost, h->stream));
     CU(cudaMemcpyAsync(B, stage + n, n * 8, cudaMemcpyDeviceToHost, h->stream));
@@ -505,7 +639,10 @@ static mt_status read_pos(mt_handle* h, double* x, long long* X, int32_t mem) {
   if (mem == MT_MEM_DEVICE) {
     CU(launch_read_positions(h->dev, x, X, h->stream));
   } else {
-    void* stage = h->dev.X[h->xcur ^ 1];
+    Ctrl c;
+    const mt_status s = read_ctrl(h, &c);
+    if (s != MT_OK) return s;
+    void* stage = h->dev.X[c.xcur ^ 1];
     CU(launch_read_positions(h->dev, x ? static_cast<double*>(stage) : nullptr,
                              X ? static_cast<long long*>(stage) : nullptr, h->stream));
     CU(cudaMemcpyAsync(x ? static_cast<void*>(x) : static_cast<void*>(X), stage, m * 8,

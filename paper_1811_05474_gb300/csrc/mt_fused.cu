@@ -1,0 +1,636 @@
+// mt_fused.cu -- the whole 1-d time step (move, cell-list sort, weights,
+// normalisation, exchange, reaction, observables) in one kernel launch.
+//
+// The particles are kept sorted by (x, id).  fstart[c] is the first sorted
+// slot of cell c (cells 2^cshift ticks wide) and cb[s] the first cell of
+// segment s; segments hold about seg_target particles each.  A CTA that
+// processes segment s = [c0, c1):
+//   1. loads the old slots of its cells widened by a halo (hc cells, which
+//      covers 2 Smax) and by the displacement bound (Dc cells), coalesced,
+//      into registers;
+//   2. moves them (Eq. 2 on the grid, Sec. 3 walls) -- a particle near a
+//      segment edge is moved by more than one CTA, with the same result;
+//   3. keeps those whose new cell lies in [c0 - hc, c1 + hc), counting-sorts
+//      them into shared-memory bins and sorts each bin by (x, id) (bins of
+//      more than kBinMax particles, e.g. particles piled against a wall, are
+//      sorted by the whole CTA);
+//   4. finds its output offset without a global scan: every particle whose
+//      old cell is below c0 - Dc ends below c0, every particle whose old cell
+//      is at or above c0 + Dc ends at or above c0, so the offset is fstart
+//      [c0 - Dc] plus the particles of the old cells in between that moved
+//      below c0;
+//   5. forms r_i = sum_j nu_ij for every staged particle within Smax of its
+//      cells and dM_i = 1/2 sum_j P_ij (M_j - M_i) for its own particles
+//      (Eq. 3, 4, 7), walking the sorted shared-memory array, then reacts;
+//   6. writes its own particles, the next step's fstart for its cells and
+//      the next step's segment boundaries that fall in its output range.
+//
+// Two tiers.  k_step1d stages up to 1024 particles per CTA (256 threads, 3
+// CTAs per SM).  A segment that does not fit is queued; a CUDA-graph
+// conditional node then runs k_step1d_big over the queue, staging up to 4096
+// particles per CTA (512 threads).  Only if a segment does not fit there
+// either does a second conditional node redo the step with the general
+// pipeline (scan, scatter, cell sort, two transfer passes).  Whichever tier
+// completes the step reduces the observables and advances the step.
+#include "mt_pair.cuh"
+
+namespace mt {
+
+constexpr int kBinMax = 32;  // bins up to this size sort in one thread
+constexpr int kBigMax = 64;  // larger bins a CTA sorts cooperatively
+
+template <int NT, int PER>
+struct Tier {
+  static constexpr int kT = NT;
+  static constexpr int kPer = PER;
+  static constexpr int kCap = NT * PER;
+  static constexpr int kBins = NT * 4;
+  static constexpr int kBinsPerThread = 4;
+};
+using Fast = Tier<256, 4>;
+using Big = Tier<512, 8>;
+static_assert(Fast::kCap == kFusedCap, "staging capacity");
+
+template <typename TR>
+size_t tier_smem(int precision) {
+  const size_t r = precision == MT_MIXED ? 4 : 8;
+  return (size_t)TR::kCap * (8 + 8 + 8 + 4 + r) + (size_t)(2 * TR::kBins + 1) * 4;
+}
+
+size_t fused_smem_bytes(int precision) { return tier_smem<Fast>(precision); }
+
+__device__ __forceinline__ long long lmin(long long a, long long b) { return a < b ? a : b; }
+__device__ __forceinline__ long long lmax(long long a, long long b) { return a > b ? a : b; }
+
+enum : int { kSegOk = 0, kSegCapacity = 1, kSegDense = 2 };
+
+// Process one segment with the CTA (all NT threads call it).  Returns
+// kSegOk, or why the segment does not fit this tier (then nothing of it has
+// been written except a zero observables partial).
+template <bool MIX, typename TR>
+__device__ int fused_segment(const Dev& d, int seg, unsigned char* smem) {
+  using W = Weight<MIX, 1>;
+  using T = typename W::T;
+  using MS = Mass<MIX>;
+  using MV = typename MS::V;
+  constexpr int NT = TR::kT, PER = TR::kPer, CAP = TR::kCap, NB = TR::kBins;
+  long long* sx = reinterpret_cast<long long*>(smem);
+  unsigned long long* sA = reinterpret_cast<unsigned long long*>(sx + CAP);
+  unsigned long long* sB = sA + CAP;
+  int* sid = reinterpret_cast<int*>(sB + CAP);
+  T* sr = reinterpret_cast<T*>(sid + CAP);
+  int* bstart = reinterpret_cast<int*>(sr + CAP);  // [NB + 1]
+  int* bcur = bstart + NB + 1;                     // [NB]
+  __shared__ int s_lt, s_w0, s_w1, s_bad, s_nbig;
+  __shared__ int s_big[kBigMax];
+  __shared__ int s_scan[NT / 32];
+  __shared__ MV s_red[3][NT];
+
+  Ctrl* c = d.ctrl;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int xc = c->xcur, mc = c->mcur, sc = c->scur;
+  const long long* Xo = d.X[xc];
+  const int* Io = d.id[xc];
+  const unsigned long long* Mo = d.M[mc];
+  const int* So = d.fstart[sc];
+  const long long c0 = d.cb[sc][seg], c1 = d.cb[sc][seg + 1];
+  const int wsh = d.cshift;
+  const long long ncell = d.ncell;
+  const long long Dc = (c->dmax >> wsh) + 2;
+  const long long Hc = d.hc;
+  const long long a0 = So[lmax(c0 - Hc - Dc, 0)];
+  const long long L = So[lmin(c1 + Hc + Dc, ncell)] - a0;
+  const long long o0 = So[lmax(c0 - Dc, 0)], o1 = So[lmin(c0 + Dc, ncell)];
+  const long long wlo = lmax(c0 - Hc, 0) << wsh;
+  const long long whi = lmin(c1 + Hc, ncell) << wsh;
+  const long long xlo = c0 << wsh, xhi = c1 << wsh;  // own cells in ticks
+  int sh2 = wsh;
+  while (sh2 < 62 && ((whi - wlo) >> sh2) >= NB) ++sh2;
+  int status = kSegOk;
+  bool active = c0 < c1;
+  if (active && L > CAP) {
+    status = kSegCapacity;
+    active = false;
+  }
+  if (tid == 0) {
+    s_lt = 0;
+    s_w0 = 0;
+    s_w1 = 0;
+    s_bad = 0;
+    s_nbig = 0;
+  }
+  for (int b = tid; b <= NB; b += NT) bstart[b] = 0;
+  __syncthreads();
+
+  // ---- 1-2: stage and move ------------------------------------------------
+  long long rx[PER];
+  int rid[PER], rbin[PER];
+  unsigned long long ra[PER], rb[PER];
+  if (active) {
+    const unsigned long long step = c->step;
+    const float* noise = c->noise;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const long long e = tid + (long long)k * NT;
+      rbin[k] = -1;
+      if (e < L) {
+        const long long slot = a0 + e;
+        const int id = Io[slot];
+        float z;
+        if (noise) {
+          z = noise[id];
+        } else {
+          const uint4 u = philox4x32_10(
+              make_uint4((unsigned int)id, (unsigned int)step, (unsigned int)(step >> 32), d.real),
+              d.key0, d.key1);
+          z = box_muller(u.x, u.y).x;
+        }
+        const long long x = reflect(Xo[slot] + d.drift[0] + float_to_ll_rn(__fmul_rn(d.bq, z)),
+                                    d.Lq[0]);
+        rx[k] = x;
+        rid[k] = id;
+        ra[k] = Mo[slot];
+        rb[k] = Mo[d.n + slot];
+        if (slot >= o0 && slot < o1 && x < xlo) atomicAdd(&s_lt, 1);
+        if (x >= wlo && x < whi) {
+          const int b = (int)((x - wlo) >> sh2);
+          rbin[k] = b;
+          atomicAdd(&bstart[b + 1], 1);
+          if (x < xlo) atomicAdd(&s_w0, 1);
+          if (x < xhi) atomicAdd(&s_w1, 1);
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- 3: counting sort into bins, then (x, id) order inside each bin -----
+  if (active) {
+    constexpr int BPT = TR::kBinsPerThread;
+    int v[BPT];
+    int sum = 0;
+#pragma unroll
+    for (int j = 0; j < BPT; ++j) {
+      v[j] = bstart[1 + tid * BPT + j];
+      sum += v[j];
+      if (v[j] > kBinMax) {
+        const int at = atomicAdd(&s_nbig, 1);
+        if (at < kBigMax)
+          s_big[at] = tid * BPT + j;
+        else
+          s_bad = 1;
+      }
+    }
+    int inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) s_scan[warp] = inc;
+    __syncthreads();
+    int run = inc - sum;
+    for (int w = 0; w < warp; ++w) run += s_scan[w];
+#pragma unroll
+    for (int j = 0; j < BPT; ++j) {
+      run += v[j];
+      bstart[1 + tid * BPT + j] = run;
+    }
+  } else {
+    __syncthreads();
+  }
+  __syncthreads();
+  if (active && s_bad) {
+    status = kSegDense;
+    active = false;
+  }
+  for (int b = tid; b < NB; b += NT) bcur[b] = bstart[b];
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      if (rbin[k] >= 0) {
+        const int slot = atomicAdd(&bcur[rbin[k]], 1);
+        sx[slot] = rx[k];
+        sid[slot] = rid[k];
+        sA[slot] = ra[k];
+        sB[slot] = rb[k];
+      }
+    }
+  }
+  __syncthreads();
+  if (active) {
+    for (int b = tid; b < NB; b += NT) {
+      const int lo = bstart[b], hi = bstart[b + 1];
+      if (hi - lo > kBinMax) continue;  // dense bin: sorted below by the whole CTA
+      for (int i = lo + 1; i < hi; ++i) {
+        const long long xi = sx[i];
+        const int ii = sid[i];
+        const unsigned long long ai = sA[i], bi = sB[i];
+        int j = i - 1;
+        while (j >= lo && (sx[j] > xi || (sx[j] == xi && sid[j] > ii))) {
+          sx[j + 1] = sx[j];
+          sid[j + 1] = sid[j];
+          sA[j + 1] = sA[j];
+          sB[j + 1] = sB[j];
+          --j;
+        }
+        sx[j + 1] = xi;
+        sid[j + 1] = ii;
+        sA[j + 1] = ai;
+        sB[j + 1] = bi;
+      }
+    }
+  }
+  __syncthreads();
+  // Dense bins: in-place bitonic sort of the bin's records by the whole CTA,
+  // every comparator ascending (partner i ^ (2j - 1) first in each merge) so
+  // any length sorts.
+  if (active) {
+    const int nbig = s_nbig < kBigMax ? s_nbig : kBigMax;
+    for (int t = 0; t < nbig; ++t) {
+      const int lo = bstart[s_big[t]], len = bstart[s_big[t] + 1] - lo;
+      int np2 = 1;
+      while (np2 < len) np2 <<= 1;
+      for (int mm = 2; mm <= np2; mm <<= 1) {
+        for (int jj = mm >> 1; jj > 0; jj >>= 1) {
+          for (int i = tid; i < np2; i += NT) {
+            const int l = (jj == (mm >> 1)) ? (i ^ (mm - 1)) : (i ^ jj);
+            if (l > i && l < len) {
+              const int a = lo + i, b = lo + l;
+              if (sx[b] < sx[a] || (sx[b] == sx[a] && sid[b] < sid[a])) {
+                const long long tx = sx[a];
+                sx[a] = sx[b];
+                sx[b] = tx;
+                const int ti = sid[a];
+                sid[a] = sid[b];
+                sid[b] = ti;
+                const unsigned long long ta = sA[a];
+                sA[a] = sA[b];
+                sA[b] = ta;
+                const unsigned long long tb = sB[a];
+                sB[a] = sB[b];
+                sB[b] = tb;
+              }
+            }
+          }
+          __syncthreads();
+        }
+      }
+    }
+  }
+
+  // ---- 5: row sums, then exchange and reaction for own particles ----------
+  const int m = bstart[NB];
+  const int w0 = s_w0, w1 = s_w1;
+  const long long out0 = o0 + s_lt;
+  const long long S = d.S;
+  if (active) {
+    for (int j = tid; j < m; j += NT) {
+      const long long x = sx[j];
+      if (x < xlo - S || x >= xhi + S) continue;  // not a neighbour of an own particle
+      T r = T(1);
+      for (int q = j - 1; q >= 0 && x - sx[q] <= S; --q) r += W::near(d, x - sx[q]);
+      for (int q = j + 1; q < m && sx[q] - x <= S; ++q) r += W::near(d, sx[q] - x);
+      sr[j] = MIX ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
+    }
+  }
+  __syncthreads();
+  MV oa{}, ob{}, od{};
+  if (active) {
+    long long* Xn = d.X[xc ^ 1];
+    int* In = d.id[xc ^ 1];
+    unsigned long long* Mn = d.M[mc ^ 1];
+    if (out0 + (w1 - w0) > d.n) raise_error(c, kErrIndex, out0);
+    for (int j = w0 + tid; j < w1; j += NT) {
+      const long long x = sx[j];
+      const T ip = sr[j];
+      MV A = MS::load(sA, j), B = MS::load(sB, j);
+      typename MS::Acc dA{}, dB{};
+      for (int q = j - 1; q >= 0; --q) {
+        const long long D = x - sx[q];
+        if (D > S) break;
+        const T P = normalised<T>(d.norm, W::near(d, D), ip, sr[q]);
+        MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
+        MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
+      }
+      for (int q = j + 1; q < m; ++q) {
+        const long long D = sx[q] - x;
+        if (D > S) break;
+        const T P = normalised<T>(d.norm, W::near(d, D), ip, sr[q]);
+        MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
+        MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
+      }
+      MS::update(A, B, dA, dB, d.react);
+      const long long o = out0 + (j - w0);
+      if (o < d.n) {
+        Xn[o] = x;
+        In[o] = sid[j];
+        MS::store(Mn, o, A);
+        MS::store(Mn, d.n + o, B);
+      }
+      if (d.observe_cap > 0) {
+        oa = obs_add(oa, A);
+        ob = obs_add(ob, B);
+        od = obs_add(od, obs_diff(A, B));
+      }
+    }
+    // ---- 6: next step's cell starts and segment boundaries ----------------
+    int* Sn = d.fstart[sc ^ 1];
+    for (long long cc = c0 + tid; cc < c1; cc += NT) {
+      const long long key = cc << wsh;
+      int lo;
+      if (sh2 == wsh) {
+        lo = bstart[(key - wlo) >> sh2];  // bins are the cells
+      } else {
+        lo = w0;  // first own slot with x >= key
+        int hi = w1;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (sx[mid] < key)
+            lo = mid + 1;
+          else
+            hi = mid;
+        }
+      }
+      Sn[cc] = (int)(out0 + (lo - w0));
+    }
+    int* CBn = d.cb[sc ^ 1];
+    const long long own = w1 - w0;
+    const long long T0 = d.seg_target;
+    for (long long s2 = (out0 + T0) / T0 + tid; s2 < d.nseg; s2 += NT) {
+      const long long q = s2 * T0 - 1;  // last slot before segment s2's first
+      if (q >= out0 + own) break;
+      if (q >= out0) CBn[s2] = (int)((sx[w0 + (q - out0)] >> wsh) + 1);
+    }
+  }
+  // per-segment observables by a shared-memory tree in the precision's own
+  // arithmetic (zero for a segment this tier could not take)
+  if (d.observe_cap > 0) {
+    s_red[0][tid] = oa;
+    s_red[1][tid] = ob;
+    s_red[2][tid] = od;
+    __syncthreads();
+    for (int st = NT / 2; st > 0; st >>= 1) {
+      if (tid < st) {
+        s_red[0][tid] = obs_add(s_red[0][tid], s_red[0][tid + st]);
+        s_red[1][tid] = obs_add(s_red[1][tid], s_red[1][tid + st]);
+        s_red[2][tid] = obs_add(s_red[2][tid], s_red[2][tid + st]);
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      d.partials[4 * seg + 0] = obs_double(s_red[0][0]);
+      d.partials[4 * seg + 1] = obs_double(s_red[1][0]);
+      d.partials[4 * seg + 2] = obs_double(s_red[2][0]);
+    }
+  }
+  __syncthreads();
+  return status;
+}
+
+// End of a fused step, run by one CTA after every segment is done: reduce
+// the per-segment observables in a fixed order and advance the state.
+template <int NT>
+__device__ void fused_finish(const Dev& d) {
+  __shared__ double s_tot[NT / 32][3];
+  Ctrl* c = d.ctrl;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (d.observe_cap > 0) {
+    double ta = 0, tb = 0, td = 0;
+    for (int blk = tid; blk < d.nseg; blk += NT) {
+      ta += __ldcg(&d.partials[4 * blk + 0]);
+      tb += __ldcg(&d.partials[4 * blk + 1]);
+      td += __ldcg(&d.partials[4 * blk + 2]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ta += __shfl_down_sync(0xffffffffu, ta, o);
+      tb += __shfl_down_sync(0xffffffffu, tb, o);
+      td += __shfl_down_sync(0xffffffffu, td, o);
+    }
+    if (lane == 0) {
+      s_tot[warp][0] = ta;
+      s_tot[warp][1] = tb;
+      s_tot[warp][2] = td;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      ta = tb = td = 0;
+      for (int w = 0; w < NT / 32; ++w) {
+        ta += s_tot[w][0];
+        tb += s_tot[w][1];
+        td += s_tot[w][2];
+      }
+      const long long row = (long long)(c->step % (unsigned long long)d.observe_cap);
+      d.obs[4 * row + 0] = ta;
+      d.obs[4 * row + 1] = tb;
+      d.obs[4 * row + 2] = td;
+      d.obs[4 * row + 3] = d.n > 0 ? ta / (double)d.n : 0.0;
+    }
+  }
+  if (tid == 0) {
+    c->step += 1;
+    c->xcur ^= 1;
+    c->mcur ^= 1;
+    c->scur ^= 1;
+    c->fallback = 0;
+  }
+}
+
+// First tier: one CTA per segment.
+template <bool MIX>
+__global__ void __launch_bounds__(Fast::kT, 3) k_step1d(Dev d, cudaGraphConditionalHandle cond,
+                                                         int use_cond) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ bool s_last;
+  Ctrl* c = d.ctrl;
+  const int seg = blockIdx.x;
+  const int st = fused_segment<MIX, Fast>(d, seg, smem);
+  if (threadIdx.x == 0) {
+    if (st != kSegOk) d.ovlist[atomicAdd(&c->nov, 1)] = seg;
+    __threadfence();
+    s_last = atomicAdd(&c->done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int nov = atomicAdd(&c->nov, 0);
+  if (nov == 0) fused_finish<Fast::kT>(d);
+  if (threadIdx.x == 0) {
+    if (nov > 0) c->big_steps += 1;
+    if (use_cond) cudaGraphSetConditional(cond, nov > 0 ? 1u : 0u);
+    c->done = 0;
+  }
+}
+
+// Second tier: the queued segments, larger staging, CTAs loop over the queue.
+template <bool MIX>
+__global__ void __launch_bounds__(Big::kT, 1) k_step1d_big(Dev d, cudaGraphConditionalHandle cond,
+                                                           int use_cond) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ bool s_last;
+  Ctrl* c = d.ctrl;
+  const int nov = c->nov;
+  for (int b = blockIdx.x; b < nov; b += gridDim.x) {
+    const int seg = d.ovlist[b];
+    const int st = fused_segment<MIX, Big>(d, seg, smem);
+    if (st != kSegOk && threadIdx.x == 0 && atomicExch(&c->overflow, 1) == 0) {
+      c->ov_reason = st;
+      c->ov_seg = seg;
+      c->ov_value = 0;
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&c->done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int ov = atomicAdd(&c->overflow, 0);
+  if (!ov) fused_finish<Big::kT>(d);
+  if (threadIdx.x == 0) {
+    if (ov) {
+      c->fallback = 1;
+      c->fallbacks += 1;
+      c->overflow = 0;
+    }
+    c->nov = 0;
+    if (use_cond) cudaGraphSetConditional(cond, ov ? 1u : 0u);
+    c->done = 0;
+  }
+}
+
+// fstart[target] := start (the general pipeline's cell starts), and the
+// segment boundaries cb[target][s] = first cell c with start[c] >= s T.
+__global__ void k_fused_prep(Dev d, int flip) {
+  const int target = d.ctrl->scur ^ flip;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= d.ncell) {
+    d.fstart[target][i] = d.start[i];
+    if (i == d.ncell) {
+      d.fstart[0][i] = (int)d.n;
+      d.fstart[1][i] = (int)d.n;
+    }
+  }
+  if (i <= d.nseg) {
+    int* cb = d.cb[target];
+    if (i == 0) {
+      cb[0] = 0;
+    } else if (i == d.nseg) {
+      cb[i] = (int)d.ncell;
+      d.cb[target ^ 1][i] = (int)d.ncell;
+      d.cb[target ^ 1][0] = 0;
+    } else {
+      const long long want = i * (long long)d.seg_target;
+      long long lo = 0, hi = d.ncell;
+      while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (d.start[mid] < want)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      cb[i] = (int)lo;
+    }
+  }
+}
+
+__global__ void k_fused_flip(Dev d, int flip) {
+  if (flip) d.ctrl->scur ^= 1;
+  d.ctrl->fallback = 0;
+  d.ctrl->nov = 0;
+}
+
+// Largest |rint(b xi)| over an injected noise buffer -> Ctrl::dmax.
+__global__ void k_noise_bound(Dev d, const float* xi, long long count) {
+  __shared__ unsigned long long s_max;
+  if (threadIdx.x == 0) s_max = 0;
+  __syncthreads();
+  unsigned long long mine = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long v = float_to_ll_rn(__fmul_rn(d.bq, xi[i]));
+    const unsigned long long a = (unsigned long long)(v < 0 ? -v : v);
+    mine = a > mine ? a : mine;
+  }
+  atomicMax(&s_max, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long dr = d.drift[0] < 0 ? -d.drift[0] : d.drift[0];
+    if (d.dim == 2) {
+      const long long d2 = d.drift[1] < 0 ? -d.drift[1] : d.drift[1];
+      dr = d2 > dr ? d2 : dr;
+    }
+    atomicMax(reinterpret_cast<unsigned long long*>(&d.ctrl->dmax),
+              s_max + (unsigned long long)dr + 2ULL);
+  }
+}
+
+__global__ void k_set_dmax(Dev d, long long v) { d.ctrl->dmax = v; }
+
+cudaError_t fused_configure() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_step1d<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tier_smem<Fast>(MT_MIXED))) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_step1d<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tier_smem<Fast>(MT_FP64))) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_step1d_big<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tier_smem<Big>(MT_MIXED))) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(k_step1d_big<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tier_smem<Big>(MT_FP64));
+}
+
+cudaError_t launch_fused_step(const Dev& d, int precision, cudaGraphConditionalHandle cond,
+                              int use_cond, cudaStream_t s) {
+  const size_t sm = tier_smem<Fast>(precision);
+  if (precision == MT_MIXED)
+    k_step1d<true><<<d.nseg, Fast::kT, sm, s>>>(d, cond, use_cond);
+  else
+    k_step1d<false><<<d.nseg, Fast::kT, sm, s>>>(d, cond, use_cond);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused_big(const Dev& d, int precision, cudaGraphConditionalHandle cond,
+                             int use_cond, cudaStream_t s) {
+  const size_t sm = tier_smem<Big>(precision);
+  const unsigned int g = (unsigned int)(d.nseg < 148 ? d.nseg : 148);
+  if (precision == MT_MIXED)
+    k_step1d_big<true><<<g, Big::kT, sm, s>>>(d, cond, use_cond);
+  else
+    k_step1d_big<false><<<g, Big::kT, sm, s>>>(d, cond, use_cond);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused_prep(const Dev& d, int flip, cudaStream_t s) {
+  const long long cnt = (d.ncell > d.nseg ? d.ncell : d.nseg) + 1;
+  k_fused_prep<<<(unsigned int)((cnt + 255) / 256), 256, 0, s>>>(d, flip);
+  k_fused_flip<<<1, 1, 0, s>>>(d, flip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_noise_bound(const Dev& d, const float* xi, cudaStream_t s) {
+  if (!xi) {
+    // built-in generator: |z| <= sqrt(-2 ln 2^-24) < 5.78
+    long long dr = d.drift[0] < 0 ? -d.drift[0] : d.drift[0];
+    if (d.dim == 2) {
+      const long long d2 = d.drift[1] < 0 ? -d.drift[1] : d.drift[1];
+      dr = d2 > dr ? d2 : dr;
+    }
+    k_set_dmax<<<1, 1, 0, s>>>(d, dr + (long long)ceil((double)d.bq * 5.78) + 2);
+    return cudaGetLastError();
+  }
+  k_set_dmax<<<1, 1, 0, s>>>(d, 0);
+  const long long cnt = (long long)d.dim * d.n;
+  if (cnt > 0) {
+    const unsigned int g = (unsigned int)((cnt + 255) / 256 < 1024 ? (cnt + 255) / 256 : 1024);
+    k_noise_bound<<<g, 256, 0, s>>>(d, xi, cnt);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mt

@@ -16,6 +16,7 @@ constexpr int kSmallCell = 32;         // cells up to this size sort in one thre
 constexpr int kBigSortCap = 2048;      // cells up to this size sort in shared memory
 constexpr int kBruteTile = 256;        // j-particles staged per tile, brute force
 constexpr long long kSpinLimit = 1LL << 22;  // bounded waits (scan look-back)
+constexpr int kFusedCap = 1024;        // particles one fused-step CTA stages
 
 // Device error codes (Ctrl::err); the first one raised is kept.
 enum : int { kErrNone = 0, kErrIndex = 1, kErrTimeout = 2, kErrInput = 3 };
@@ -34,7 +35,18 @@ struct Ctrl {
   unsigned int done;            // CTAs finished (last-CTA reductions)
   unsigned int tile_ctr;        // scan tile ticket
   long long err_info;           // detail for err (an index)
-  unsigned long long pad[8];
+  const float* noise;           // injected normals [dim][n] by caller index, or null
+  long long dmax;               // bound on one step's displacement, in ticks
+  int scur;                     // which fused start / segment array is current
+  int overflow;                 // a fused-step segment did not fit (this step)
+  int fallback;                 // the general pipeline must redo this step
+  int ov_reason;                // first second-tier overflow: 1 capacity, 2 dense bins
+  long long ov_seg;             // ... its segment
+  long long ov_value;           // ... (reserved)
+  unsigned long long fallbacks; // steps the general pipeline redid since upload
+  unsigned long long big_steps; // steps that needed the second fused tier
+  int nov;                      // segments queued for the second tier this step
+  int pad1;
 };
 
 // Everything a kernel needs, passed by value.
@@ -52,7 +64,9 @@ struct Dev {
   int* big;                 // [nbig_cap] cells for the large-cell sort
   double* partials;         // [nblocks][4] per-CTA observables
   double* obs;              // [observe_cap][4] observables ring
-  const float* noise;       // injected normals [dim][n] by caller index, or null
+  int* fstart[2];           // [ncell + 1] cell starts of the sorted state (fused path)
+  int* cb[2];               // [nseg + 1] first cell of each fused segment
+  int* ovlist;              // [nseg] segments queued for the second fused tier
   long long n;
   int dim;
   int norm;                 // MT_NORM_*
@@ -71,6 +85,9 @@ struct Dev {
   unsigned int real;        // realisation counter word
   int nbig_cap;
   int nblocks;              // CTAs of the per-particle kernels
+  int nseg;                 // fused segments (CTAs of the fused step)
+  int seg_target;           // particles a fused segment aims for
+  long long hc;             // fused halo in cells (covers 2 Smax)
 };
 
 // ---------------------------------------------------------------- helpers --
@@ -141,14 +158,15 @@ __device__ __forceinline__ long long float_to_ll_rn(float f) {
   return (b >> 31) ? -mag : mag;
 }
 
-// Two standard normals from two 32-bit words (Box-Muller, binary32):
-// u1 in (0, 1], u2 in [0, 1).
+// Two standard normals from two 32-bit words (Box-Muller, binary32, with
+// the hardware logarithm and sine/cosine): u1 in (0, 1], angle uniform on
+// [-pi, pi).  |z| <= sqrt(-2 ln 2^-24) < 5.78.
 __device__ __forceinline__ float2 box_muller(unsigned int a, unsigned int b) {
   const float u1 = ((a >> 8) + 1u) * (1.0f / 16777216.0f);
   const float u2 = (b >> 8) * (1.0f / 16777216.0f);
-  const float rad = sqrtf(-2.0f * logf(u1));
+  const float rad = sqrtf(-2.0f * __logf(u1));
   float s, c;
-  sincospif(2.0f * u2, &s, &c);
+  __sincosf(__fmaf_rn(6.28318530717958648f, u2, -3.14159265358979324f), &s, &c);
   return make_float2(rad * c, rad * s);
 }
 
@@ -246,6 +264,16 @@ cudaError_t launch_read_masses(const Dev& d, double* A, double* B, int precision
 cudaError_t launch_read_positions(const Dev& d, double* x, long long* X, cudaStream_t s);
 cudaError_t launch_pairs(const Dev& d, int search, int* pi, int* pj, long long cap,
                          cudaStream_t s);
+// Fused 1-d step (mt_fused.cu).
+size_t fused_smem_bytes(int precision);
+cudaError_t fused_configure();  // opt in to the large dynamic shared memory
+cudaError_t launch_fused_step(const Dev& d, int precision, cudaGraphConditionalHandle cond,
+                              int use_cond, cudaStream_t s);
+cudaError_t launch_fused_big(const Dev& d, int precision, cudaGraphConditionalHandle cond,
+                             int use_cond, cudaStream_t s);
+cudaError_t launch_fused_prep(const Dev& d, int flip, cudaStream_t s);  // start/cb from d.start
+cudaError_t launch_noise_bound(const Dev& d, const float* xi, cudaStream_t s);
+
 cudaError_t launch_philox(uint4 c, unsigned int k0, unsigned int k1, long long n,
                           unsigned int* out, cudaStream_t s);
 

@@ -26,9 +26,10 @@ __global__ void __launch_bounds__(kThreads) k_move(Dev d) {
   if (MOVE) {
     const int id = d.id[xc][p];
     float z[2];
-    if (d.noise) {
-      z[0] = d.noise[id];
-      if (DIM == 2) z[1] = d.noise[d.n + id];
+    const float* noise = c->noise;
+    if (noise) {
+      z[0] = noise[id];
+      if (DIM == 2) z[1] = noise[d.n + id];
     } else {
       const unsigned long long st = c->step;
       const uint4 u = philox4x32_10(

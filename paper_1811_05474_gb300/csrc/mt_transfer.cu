@@ -15,142 +15,9 @@
 // Precision: MIX = false is IEEE binary64 throughout; MIX = true forms
 // weights and normalised weights in binary32 and updates the double-binary32
 // masses with compensated additions.
-#include "mt_internal.cuh"
+#include "mt_pair.cuh"
 
 namespace mt {
-
-// ---------------------------------------------------------- pair weights --
-
-__device__ __forceinline__ bool in_range2(long long dx, long long dy, long long S) {
-  const unsigned long long ax = (unsigned long long)(dx < 0 ? -dx : dx);
-  const unsigned long long ay = (unsigned long long)(dy < 0 ? -dy : dy);
-  if (ax > (unsigned long long)S || ay > (unsigned long long)S) return false;
-  return ax * ax + ay * ay <= (unsigned long long)S * (unsigned long long)S;
-}
-
-// nu_ij without its prefactor (it cancels in the normalisation):
-// exp(-s^2 / (8 D_mt dt)) with s = |dX| 2^-k (Eq. 3).
-template <bool MIX, int DIM>
-struct Weight;
-
-template <int DIM>
-struct Weight<false, DIM> {
-  using T = double;
-  static __device__ __forceinline__ double eval(const Dev& d, long long dx, long long dy) {
-    const double sx = __dmul_rn((double)dx, d.scale);
-    double s2 = __dmul_rn(sx, sx);
-    if (DIM == 2) {
-      const double sy = __dmul_rn((double)dy, d.scale);
-      s2 = __dadd_rn(s2, __dmul_rn(sy, sy));
-    }
-    return exp(-__dmul_rn(s2, d.inv8));
-  }
-};
-
-template <int DIM>
-struct Weight<true, DIM> {
-  using T = float;
-  static __device__ __forceinline__ float eval(const Dev& d, long long dx, long long dy) {
-    const float fx = ll_to_float(dx);
-    float s2 = __fmul_rn(fx, fx);
-    if (DIM == 2) {
-      const float fy = ll_to_float(dy);
-      s2 = __fadd_rn(s2, __fmul_rn(fy, fy));
-    }
-    return __expf(-__fmul_rn(s2, d.inv8f));
-  }
-};
-
-// ------------------------------------------------------------ mass access --
-
-template <bool MIX>
-struct Mass;
-
-// Per-particle accumulation of sum_j P_ij (M_j - M_i): binary64 in FP64;
-// in MIXED each binary32 term is added into a double-binary32 sum (two-sum),
-// so the flux P_ij (M_j - M_i), bitwise antisymmetric between i and j, is
-// accumulated to about 48 bits and the transfer conserves mass to that
-// precision.
-template <>
-struct Mass<false> {
-  using V = double;
-  using Acc = double;
-  static __device__ __forceinline__ void acc(double& a, double P, double d) { a += P * d; }
-  static __device__ __forceinline__ double load(const unsigned long long* M, long long i) {
-    return f64_load(M, i);
-  }
-  static __device__ __forceinline__ void store(unsigned long long* M, long long i, double v) {
-    f64_store(M, i, v);
-  }
-  static __device__ __forceinline__ double diff(double a, double b) { return a - b; }
-  // M + dM/2 (Eq. 7 with the 1/2 of Eq. 4), then the reaction.
-  static __device__ __forceinline__ void update(double& A, double& B, double dA, double dB,
-                                                int react) {
-    A = A + 0.5 * dA;
-    B = B + 0.5 * dB;
-    if (react) {
-      const double m = A < B ? A : B;
-      A = A - m;
-      B = B - m;
-    }
-  }
-  static __device__ __forceinline__ double to_double(double v) { return v; }
-};
-
-template <>
-struct Mass<true> {
-  using V = df;
-  using Acc = df;
-  static __device__ __forceinline__ void acc(df& a, float P, float d) {
-    a = df_add_f(a, __fmul_rn(P, d));
-  }
-  static __device__ __forceinline__ df load(const unsigned long long* M, long long i) {
-    return df_load(M, i);
-  }
-  static __device__ __forceinline__ void store(unsigned long long* M, long long i, df v) {
-    df_store(M, i, v);
-  }
-  static __device__ __forceinline__ float diff(df a, df b) {
-    return __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo));
-  }
-  static __device__ __forceinline__ void update(df& A, df& B, df dA, df dB, int react) {
-    A = df_add(A, {0.5f * dA.hi, 0.5f * dA.lo});
-    B = df_add(B, {0.5f * dB.hi, 0.5f * dB.lo});
-    if (react) {
-      if (df_le(A, B)) {
-        B = df_sub(B, A);
-        A = {0.0f, 0.0f};
-      } else {
-        A = df_sub(A, B);
-        B = {0.0f, 0.0f};
-      }
-    }
-  }
-  static __device__ __forceinline__ double to_double(df v) { return (double)v.hi + (double)v.lo; }
-};
-
-template <bool MIX>
-__device__ __forceinline__ void store_rinv(const Dev& d, long long p, typename Weight<MIX, 1>::T r) {
-  if (MIX)
-    static_cast<float*>(d.rinv)[p] = __frcp_rn((float)r);
-  else
-    static_cast<double*>(d.rinv)[p] = 1.0 / (double)r;
-}
-
-template <bool MIX>
-__device__ __forceinline__ typename Weight<MIX, 1>::T load_rinv(const Dev& d, long long p) {
-  if (MIX)
-    return static_cast<const float*>(d.rinv)[p];
-  else
-    return static_cast<const double*>(d.rinv)[p];
-}
-
-// Normalised weight of the ordered pair (p, q) (Sec. 1.1): ROW w / r_p, or
-// SYM (w / r_p + w / r_q) / 2.
-template <typename T>
-__device__ __forceinline__ T normalised(int norm, T w, T ip, T iq) {
-  return norm == MT_NORM_ROW ? w * ip : T(0.5) * w * (ip + iq);
-}
 
 // ------------------------------------------- step epilogue (last CTA) --
 // Per-CTA partial observables -> the last CTA to finish reduces them in a
@@ -158,19 +25,6 @@ __device__ __forceinline__ T normalised(int norm, T w, T ip, T iq) {
 // flips the buffer selectors.  Deterministic: no floating-point atomics.
 // Per-particle sums stay in the precision's own arithmetic (binary64, or
 // double-binary32 in MIXED); only per-CTA totals are converted to binary64.
-
-__device__ __forceinline__ double obs_add(double a, double b) { return a + b; }
-__device__ __forceinline__ df obs_add(df a, df b) { return df_add(a, b); }
-__device__ __forceinline__ double obs_shfl(double v, int o) {
-  return __shfl_down_sync(0xffffffffu, v, o);
-}
-__device__ __forceinline__ df obs_shfl(df v, int o) {
-  return {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
-}
-__device__ __forceinline__ double obs_double(double v) { return v; }
-__device__ __forceinline__ double obs_double(df v) { return (double)v.hi + (double)v.lo; }
-__device__ __forceinline__ double obs_diff(double a, double b) { return a - b; }
-__device__ __forceinline__ df obs_diff(df a, df b) { return df_sub(a, b); }
 
 template <bool MIX>
 __device__ void finish_step(const Dev& d, typename Mass<MIX>::V a, typename Mass<MIX>::V b,
