@@ -175,7 +175,9 @@ mt_status resolve(const mt_params* in, Derived* out) {
       D.fused = true;
       D.seg_target = T;
       D.nseg = (p.n + T - 1) / T;
-      D.nblocks = D.nblocks > D.nseg ? D.nblocks : D.nseg;
+      // partial slots: one per segment, plus kFusedSlices per queued segment
+      const long long slots = D.nseg * (1 + kFusedSlices);
+      D.nblocks = D.nblocks > slots ? D.nblocks : slots;
     }
   }
   D.ntiles = (D.ncell + kScanTile - 1) / kScanTile;
@@ -493,6 +495,13 @@ mt_status mt_create(const mt_params* p, void* workspace, size_t workspace_bytes,
   d.nseg = (int)D.nseg;
   d.seg_target = (int)D.seg_target;
   d.hc = D.hc;
+  {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+      nsm = 1;
+    d.nsm = nsm;
+  }
   d.n = D.p.n;
   d.dim = D.p.dim;
   d.norm = D.p.norm;

@@ -25,14 +25,20 @@
 //   6. writes its own particles, the next step's fstart for its cells and
 //      the next step's segment boundaries that fall in its output range.
 //
-// Two tiers.  k_step1d stages up to 1024 particles per CTA (256 threads, 3
-// CTAs per SM).  A segment that does not fit is queued; a CUDA-graph
-// conditional node then runs k_step1d_big over the queue, staging up to 4096
-// particles per CTA (512 threads).  Only if a segment does not fit there
+// Two tiers.  k_step1d stages up to 1024 particles per CTA (256 threads, a
+// persistent grid of 3 CTAs per SM).  A segment that does not fit, or whose
+// pair work is heavy (a dense cluster), is queued; a CUDA-graph conditional
+// node then runs k_step1d_big over the queue: a cluster of 8 CTAs (512
+// threads, up to 4096 staged particles each) per segment, splitting its row
+// sums and exchange across 8 SMs.  Only if a segment does not fit there
 // either does a second conditional node redo the step with the general
 // pipeline (scan, scatter, cell sort, two transfer passes).  Whichever tier
 // completes the step reduces the observables and advances the step.
+#include <cooperative_groups.h>
+
 #include "mt_pair.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace mt {
 
@@ -62,13 +68,57 @@ size_t fused_smem_bytes(int precision) { return tier_smem<Fast>(precision); }
 __device__ __forceinline__ long long lmin(long long a, long long b) { return a < b ? a : b; }
 __device__ __forceinline__ long long lmax(long long a, long long b) { return a > b ? a : b; }
 
-enum : int { kSegOk = 0, kSegCapacity = 1, kSegDense = 2 };
+enum : int { kSegOk = 0, kSegCapacity = 1, kSegDense = 2, kSegHeavy = 3 };
 
-// Process one segment with the CTA (all NT threads call it).  Returns
-// kSegOk, or why the segment does not fit this tier (then nothing of it has
-// been written except a zero observables partial).
-template <bool MIX, typename TR>
-__device__ int fused_segment(const Dev& d, int seg, unsigned char* smem) {
+// A segment whose sum over bins of (particles per bin)^2 exceeds this is
+// pair-heavy (a dense cluster, e.g. particles piled against a wall): the
+// first tier hands it to the second, which splits its exchange across
+// kSlices CTAs so that its O(n^2) work does not sit on one SM.
+constexpr int kHeavyWork = 16384;
+constexpr int kSlices = kFusedSlices;
+constexpr int kWalk = 32;  // neighbours per side a thread walks before a warp takes over
+
+// First index q in [0, m) with a[q] >= key (a sorted ascending).
+__device__ __forceinline__ int lower_at_least(const long long* a, int m, long long key) {
+  int lo = 0, hi = m;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] < key)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// The per-segment scalars read from the previous step's boundaries and cell
+// starts (loaded one segment ahead by the persistent loop).
+struct SegScalars {
+  long long c0, c1, a0, L, o0, o1;
+};
+
+__device__ __forceinline__ SegScalars load_seg(const Dev& d, int sc, long long Dc, int seg) {
+  const int* So = d.fstart[sc];
+  SegScalars s;
+  s.c0 = d.cb[sc][seg];
+  s.c1 = d.cb[sc][seg + 1];
+  const long long Hc = d.hc, ncell = d.ncell;
+  s.a0 = So[lmax(s.c0 - Hc - Dc, 0)];
+  s.L = So[lmin(s.c1 + Hc + Dc, ncell)] - s.a0;
+  s.o0 = So[lmax(s.c0 - Dc, 0)];
+  s.o1 = So[lmin(s.c0 + Dc, ncell)];
+  return s;
+}
+
+// Process one segment with the CTA (all NT threads call it).  The CTA
+// computes the exchange for the own particles j with (j - first own) %
+// nslice == slice, and the cell starts / segment boundaries only for slice
+// 0; its observables go to partial slot part_slot.  Returns kSegOk, or why
+// the segment does not fit this tier (then nothing of it has been written
+// except a zero observables partial).
+template <bool MIX, typename TR, int CL>
+__device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const SegScalars& g,
+                             int slice, int nslice, int part_slot, bool route_heavy) {
   using W = Weight<MIX, 1>;
   using T = typename W::T;
   using MS = Mass<MIX>;
@@ -81,10 +131,10 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem) {
   T* sr = reinterpret_cast<T*>(sid + CAP);
   int* bstart = reinterpret_cast<int*>(sr + CAP);  // [NB + 1]
   int* bcur = bstart + NB + 1;                     // [NB]
-  __shared__ int s_lt, s_w0, s_w1, s_bad, s_nbig;
+  __shared__ int s_lt, s_w0, s_w1, s_bad, s_nbig, s_work, s_nd, s_nd2;
   __shared__ int s_big[kBigMax];
   __shared__ int s_scan[NT / 32];
-  __shared__ MV s_red[3][NT];
+  __shared__ MV s_red[3][NT / 32];
 
   Ctrl* c = d.ctrl;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -92,15 +142,10 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem) {
   const long long* Xo = d.X[xc];
   const int* Io = d.id[xc];
   const unsigned long long* Mo = d.M[mc];
-  const int* So = d.fstart[sc];
-  const long long c0 = d.cb[sc][seg], c1 = d.cb[sc][seg + 1];
+  const long long c0 = g.c0, c1 = g.c1, a0 = g.a0, L = g.L, o0 = g.o0, o1 = g.o1;
   const int wsh = d.cshift;
   const long long ncell = d.ncell;
-  const long long Dc = (c->dmax >> wsh) + 2;
   const long long Hc = d.hc;
-  const long long a0 = So[lmax(c0 - Hc - Dc, 0)];
-  const long long L = So[lmin(c1 + Hc + Dc, ncell)] - a0;
-  const long long o0 = So[lmax(c0 - Dc, 0)], o1 = So[lmin(c0 + Dc, ncell)];
   const long long wlo = lmax(c0 - Hc, 0) << wsh;
   const long long whi = lmin(c1 + Hc, ncell) << wsh;
   const long long xlo = c0 << wsh, xhi = c1 << wsh;  // own cells in ticks
@@ -118,6 +163,9 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem) {
     s_w1 = 0;
     s_bad = 0;
     s_nbig = 0;
+    s_work = 0;
+    s_nd = 0;
+    s_nd2 = 0;
   }
   for (int b = tid; b <= NB; b += NT) bstart[b] = 0;
   __syncthreads();
@@ -133,6 +181,7 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem) {
     for (int k = 0; k < PER; ++k) {
       const long long e = tid + (long long)k * NT;
       rbin[k] = -1;
+      bool lt = false, in0 = false, in1 = false;
       if (e < L) {
         const long long slot = a0 + e;
         const int id = Io[slot];
@@ -151,14 +200,23 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem) {
         rid[k] = id;
         ra[k] = Mo[slot];
         rb[k] = Mo[d.n + slot];
-        if (slot >= o0 && slot < o1 && x < xlo) atomicAdd(&s_lt, 1);
+        lt = slot >= o0 && slot < o1 && x < xlo;
         if (x >= wlo && x < whi) {
           const int b = (int)((x - wlo) >> sh2);
           rbin[k] = b;
           atomicAdd(&bstart[b + 1], 1);
-          if (x < xlo) atomicAdd(&s_w0, 1);
-          if (x < xhi) atomicAdd(&s_w1, 1);
+          in0 = x < xlo;
+          in1 = x < xhi;
         }
+      }
+      // warp-aggregated counts (one shared atomic per warp, not per particle)
+      const int n_lt = __popc(__ballot_sync(0xffffffffu, lt));
+      const int n_0 = __popc(__ballot_sync(0xffffffffu, in0));
+      const int n_1 = __popc(__ballot_sync(0xffffffffu, in1));
+      if (lane == 0) {
+        if (n_lt) atomicAdd(&s_lt, n_lt);
+        if (n_0) atomicAdd(&s_w0, n_0);
+        if (n_1) atomicAdd(&s_w1, n_1);
       }
     }
   }
@@ -168,11 +226,12 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem) {
   if (active) {
     constexpr int BPT = TR::kBinsPerThread;
     int v[BPT];
-    int sum = 0;
+    int sum = 0, work = 0;
 #pragma unroll
     for (int j = 0; j < BPT; ++j) {
       v[j] = bstart[1 + tid * BPT + j];
       sum += v[j];
+      work += v[j] * v[j];
       if (v[j] > kBinMax) {
         const int at = atomicAdd(&s_nbig, 1);
         if (at < kBigMax)
@@ -188,6 +247,7 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem) {
       if (lane >= o) inc += t;
     }
     if (lane == 31) s_scan[warp] = inc;
+    if (work > 0) atomicAdd(&s_work, work < kHeavyWork ? work : kHeavyWork);
     __syncthreads();
     int run = inc - sum;
     for (int w = 0; w < warp; ++w) run += s_scan[w];
@@ -202,6 +262,10 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem) {
   __syncthreads();
   if (active && s_bad) {
     status = kSegDense;
+    active = false;
+  }
+  if (active && route_heavy && s_work >= kHeavyWork) {
+    status = kSegHeavy;
     active = false;
   }
   for (int b = tid; b < NB; b += NT) bcur[b] = bstart[b];
@@ -285,41 +349,123 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem) {
   const int w0 = s_w0, w1 = s_w1;
   const long long out0 = o0 + s_lt;
   const long long S = d.S;
+  // Row sums.  A particle with more than kWalk neighbours on a side is
+  // dense: it is queued (in bcur, free by now) and summed by a whole warp,
+  // lanes striding over its neighbour range, combined in a fixed tree.  The
+  // choice and the order depend only on the neighbourhood, so every CTA that
+  // forms r_j forms the same value.
+  int* dlist = bcur;
   if (active) {
-    for (int j = tid; j < m; j += NT) {
+    for (int t = tid;; t += NT) {
+      const int j = CL > 1 ? t * CL + slice : t;  // with a cluster: every CL-th
+      if (j >= m) break;
       const long long x = sx[j];
       if (x < xlo - S || x >= xhi + S) continue;  // not a neighbour of an own particle
       T r = T(1);
-      for (int q = j - 1; q >= 0 && x - sx[q] <= S; --q) r += W::near(d, x - sx[q]);
-      for (int q = j + 1; q < m && sx[q] - x <= S; ++q) r += W::near(d, sx[q] - x);
+      int q = j - 1, k = 0;
+      for (; q >= 0 && k < kWalk && x - sx[q] <= S; --q, ++k) r += W::near(d, x - sx[q]);
+      bool dense = k == kWalk && q >= 0 && x - sx[q] <= S;
+      if (!dense) {
+        q = j + 1;
+        k = 0;
+        for (; q < m && k < kWalk && sx[q] - x <= S; ++q, ++k) r += W::near(d, sx[q] - x);
+        dense = k == kWalk && q < m && sx[q] - x <= S;
+      }
+      if (dense) {
+        const int at = atomicAdd(&s_nd, 1);
+        if (at < NB) {
+          dlist[at] = j;
+          continue;
+        }
+        // list full: finish on this thread
+        r = T(1);
+        for (q = j - 1; q >= 0 && x - sx[q] <= S; --q) r += W::near(d, x - sx[q]);
+        for (q = j + 1; q < m && sx[q] - x <= S; ++q) r += W::near(d, sx[q] - x);
+      }
       sr[j] = MIX ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
     }
   }
   __syncthreads();
+  if (active) {
+    const int nd = s_nd < NB ? s_nd : NB;
+    for (int k = warp; k < nd; k += NT / 32) {
+      const int j = dlist[k];
+      const long long x = sx[j];
+      const int lo = lower_at_least(sx, m, x - S), hi = lower_at_least(sx, m, x + S + 1);
+      T r = T(0);
+      for (int q = lo + lane; q < hi; q += 32) r += W::near(d, x > sx[q] ? x - sx[q] : sx[q] - x);
+      r = warp_sum(r);
+      if (lane == 0) sr[j] = MIX ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
+    }
+  }
+  if constexpr (CL > 1) {
+    // Every CTA of the cluster staged and sorted the same particles; each
+    // formed the row sums of every CL-th one.  Gather the rest from the
+    // peers' shared memory (distributed shared memory), between two cluster
+    // barriers so no CTA reads a peer that has moved on.
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    if (active) {
+      for (int j = tid; j < m; j += NT) {
+        const int owner = j % CL;
+        if (owner == slice) continue;
+        const long long x = sx[j];
+        if (x < xlo - S || x >= xhi + S) continue;
+        sr[j] = *cl.map_shared_rank(&sr[j], owner);
+      }
+    }
+    cl.sync();
+  } else {
+    __syncthreads();
+  }
   MV oa{}, ob{}, od{};
   if (active) {
     long long* Xn = d.X[xc ^ 1];
     int* In = d.id[xc ^ 1];
     unsigned long long* Mn = d.M[mc ^ 1];
     if (out0 + (w1 - w0) > d.n) raise_error(c, kErrIndex, out0);
-    for (int j = w0 + tid; j < w1; j += NT) {
+    for (int j = w0 + slice + tid * nslice; j < w1; j += NT * nslice) {
       const long long x = sx[j];
       const T ip = sr[j];
       MV A = MS::load(sA, j), B = MS::load(sB, j);
       typename MS::Acc dA{}, dB{};
-      for (int q = j - 1; q >= 0; --q) {
+      int q = j - 1, k = 0;
+      for (; q >= 0 && k < kWalk; --q, ++k) {
         const long long D = x - sx[q];
         if (D > S) break;
         const T P = normalised<T>(d.norm, W::near(d, D), ip, sr[q]);
         MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
         MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
       }
-      for (int q = j + 1; q < m; ++q) {
-        const long long D = sx[q] - x;
-        if (D > S) break;
-        const T P = normalised<T>(d.norm, W::near(d, D), ip, sr[q]);
-        MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
-        MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
+      bool dense = k == kWalk && q >= 0 && x - sx[q] <= S;
+      if (!dense) {
+        for (q = j + 1, k = 0; q < m && k < kWalk; ++q, ++k) {
+          const long long D = sx[q] - x;
+          if (D > S) break;
+          const T P = normalised<T>(d.norm, W::near(d, D), ip, sr[q]);
+          MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
+          MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
+        }
+        dense = k == kWalk && q < m && sx[q] - x <= S;
+      }
+      if (dense) {
+        const int at = atomicAdd(&s_nd2, 1);
+        if (at < NB) {
+          dlist[at] = j;  // a warp does it below
+          continue;
+        }
+        dA = typename MS::Acc{};
+        dB = typename MS::Acc{};
+        for (q = j - 1; q >= 0 && x - sx[q] <= S; --q) {
+          const T P = normalised<T>(d.norm, W::near(d, x - sx[q]), ip, sr[q]);
+          MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
+          MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
+        }
+        for (q = j + 1; q < m && sx[q] - x <= S; ++q) {
+          const T P = normalised<T>(d.norm, W::near(d, sx[q] - x), ip, sr[q]);
+          MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
+          MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
+        }
       }
       MS::update(A, B, dA, dB, d.react);
       const long long o = out0 + (j - w0);
@@ -335,6 +481,47 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem) {
         od = obs_add(od, obs_diff(A, B));
       }
     }
+  }
+  __syncthreads();
+  if (active) {
+    // dense own particles: one warp each, lanes striding the neighbourhood
+    long long* Xn = d.X[xc ^ 1];
+    int* In = d.id[xc ^ 1];
+    unsigned long long* Mn = d.M[mc ^ 1];
+    const int nd = s_nd2 < NB ? s_nd2 : NB;
+    for (int k = warp; k < nd; k += NT / 32) {
+      const int j = dlist[k];
+      const long long x = sx[j];
+      const T ip = sr[j];
+      MV A = MS::load(sA, j), B = MS::load(sB, j);
+      typename MS::Acc dA{}, dB{};
+      const int lo = lower_at_least(sx, m, x - S), hi = lower_at_least(sx, m, x + S + 1);
+      for (int q = lo + lane; q < hi; q += 32) {
+        if (q == j) continue;
+        const T P = normalised<T>(d.norm, W::near(d, x > sx[q] ? x - sx[q] : sx[q] - x), ip, sr[q]);
+        MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
+        MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
+      }
+      dA = acc_warp_sum(dA);
+      dB = acc_warp_sum(dB);
+      if (lane == 0) {
+        MS::update(A, B, dA, dB, d.react);
+        const long long o = out0 + (j - w0);
+        if (o < d.n) {
+          Xn[o] = x;
+          In[o] = sid[j];
+          MS::store(Mn, o, A);
+          MS::store(Mn, d.n + o, B);
+        }
+        if (d.observe_cap > 0) {
+          oa = obs_add(oa, A);
+          ob = obs_add(ob, B);
+          od = obs_add(od, obs_diff(A, B));
+        }
+      }
+    }
+  }
+  if (active && slice == 0) {
     // ---- 6: next step's cell starts and segment boundaries ----------------
     int* Sn = d.fstart[sc ^ 1];
     for (long long cc = c0 + tid; cc < c1; cc += NT) {
@@ -364,25 +551,33 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem) {
       if (q >= out0) CBn[s2] = (int)((sx[w0 + (q - out0)] >> wsh) + 1);
     }
   }
-  // per-segment observables by a shared-memory tree in the precision's own
-  // arithmetic (zero for a segment this tier could not take)
+  // per-segment observables in the precision's own arithmetic: warp shuffles,
+  // then the warp totals in a fixed order (zero for a segment this tier could
+  // not take)
   if (d.observe_cap > 0) {
-    s_red[0][tid] = oa;
-    s_red[1][tid] = ob;
-    s_red[2][tid] = od;
-    __syncthreads();
-    for (int st = NT / 2; st > 0; st >>= 1) {
-      if (tid < st) {
-        s_red[0][tid] = obs_add(s_red[0][tid], s_red[0][tid + st]);
-        s_red[1][tid] = obs_add(s_red[1][tid], s_red[1][tid + st]);
-        s_red[2][tid] = obs_add(s_red[2][tid], s_red[2][tid + st]);
-      }
-      __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      oa = obs_add(oa, obs_shfl(oa, o));
+      ob = obs_add(ob, obs_shfl(ob, o));
+      od = obs_add(od, obs_shfl(od, o));
     }
+    if (lane == 0) {
+      s_red[0][warp] = oa;
+      s_red[1][warp] = ob;
+      s_red[2][warp] = od;
+    }
+    __syncthreads();
     if (tid == 0) {
-      d.partials[4 * seg + 0] = obs_double(s_red[0][0]);
-      d.partials[4 * seg + 1] = obs_double(s_red[1][0]);
-      d.partials[4 * seg + 2] = obs_double(s_red[2][0]);
+      MV ta = s_red[0][0], tb = s_red[1][0], td = s_red[2][0];
+      for (int w = 1; w < NT / 32; ++w) {
+        ta = obs_add(ta, s_red[0][w]);
+        tb = obs_add(tb, s_red[1][w]);
+        td = obs_add(td, s_red[2][w]);
+      }
+      MV* part = reinterpret_cast<MV*>(d.partials);  // one 8-byte slot each
+      part[4 * part_slot + 0] = ta;
+      part[4 * part_slot + 1] = tb;
+      part[4 * part_slot + 2] = td;
     }
   }
   __syncthreads();
@@ -390,24 +585,33 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem) {
 }
 
 // End of a fused step, run by one CTA after every segment is done: reduce
-// the per-segment observables in a fixed order and advance the state.
-template <int NT>
-__device__ void fused_finish(const Dev& d) {
-  __shared__ double s_tot[NT / 32][3];
+// the per-segment observables (binary64, or double-binary32 in MIXED) in a
+// fixed order and advance the state.
+__device__ __forceinline__ double ldcg_obs(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ df ldcg_obs(const df* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return {v.x, v.y};
+}
+
+template <bool MIX, int NT>
+__device__ void fused_finish(const Dev& d, int nslots) {
+  using MV = typename Mass<MIX>::V;
+  __shared__ MV s_tot[NT / 32][3];
   Ctrl* c = d.ctrl;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (d.observe_cap > 0) {
-    double ta = 0, tb = 0, td = 0;
-    for (int blk = tid; blk < d.nseg; blk += NT) {
-      ta += __ldcg(&d.partials[4 * blk + 0]);
-      tb += __ldcg(&d.partials[4 * blk + 1]);
-      td += __ldcg(&d.partials[4 * blk + 2]);
+    const MV* part = reinterpret_cast<const MV*>(d.partials);
+    MV ta{}, tb{}, td{};
+    for (int blk = tid; blk < nslots; blk += NT) {
+      ta = obs_add(ta, ldcg_obs(&part[4 * blk + 0]));
+      tb = obs_add(tb, ldcg_obs(&part[4 * blk + 1]));
+      td = obs_add(td, ldcg_obs(&part[4 * blk + 2]));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      ta += __shfl_down_sync(0xffffffffu, ta, o);
-      tb += __shfl_down_sync(0xffffffffu, tb, o);
-      td += __shfl_down_sync(0xffffffffu, td, o);
+      ta = obs_add(ta, obs_shfl(ta, o));
+      tb = obs_add(tb, obs_shfl(tb, o));
+      td = obs_add(td, obs_shfl(td, o));
     }
     if (lane == 0) {
       s_tot[warp][0] = ta;
@@ -416,17 +620,20 @@ __device__ void fused_finish(const Dev& d) {
     }
     __syncthreads();
     if (tid == 0) {
-      ta = tb = td = 0;
-      for (int w = 0; w < NT / 32; ++w) {
-        ta += s_tot[w][0];
-        tb += s_tot[w][1];
-        td += s_tot[w][2];
+      ta = s_tot[0][0];
+      tb = s_tot[0][1];
+      td = s_tot[0][2];
+      for (int w = 1; w < NT / 32; ++w) {
+        ta = obs_add(ta, s_tot[w][0]);
+        tb = obs_add(tb, s_tot[w][1]);
+        td = obs_add(td, s_tot[w][2]);
       }
       const long long row = (long long)(c->step % (unsigned long long)d.observe_cap);
-      d.obs[4 * row + 0] = ta;
-      d.obs[4 * row + 1] = tb;
-      d.obs[4 * row + 2] = td;
-      d.obs[4 * row + 3] = d.n > 0 ? ta / (double)d.n : 0.0;
+      const double sa = obs_double(ta);
+      d.obs[4 * row + 0] = sa;
+      d.obs[4 * row + 1] = obs_double(tb);
+      d.obs[4 * row + 2] = obs_double(td);
+      d.obs[4 * row + 3] = d.n > 0 ? sa / (double)d.n : 0.0;
     }
   }
   if (tid == 0) {
@@ -438,17 +645,28 @@ __device__ void fused_finish(const Dev& d) {
   }
 }
 
-// First tier: one CTA per segment.
+// First tier: a persistent grid (a few CTAs per SM) looping over the
+// segments; each segment's boundary scalars are loaded while the previous
+// segment is processed.
 template <bool MIX>
 __global__ void __launch_bounds__(Fast::kT, 3) k_step1d(Dev d, cudaGraphConditionalHandle cond,
                                                          int use_cond) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ bool s_last;
   Ctrl* c = d.ctrl;
-  const int seg = blockIdx.x;
-  const int st = fused_segment<MIX, Fast>(d, seg, smem);
+  const int sc = c->scur;
+  const long long Dc = (c->dmax >> d.cshift) + 2;
+  int seg = blockIdx.x;
+  SegScalars cur = {};
+  if (seg < d.nseg) cur = load_seg(d, sc, Dc, seg);
+  for (; seg < d.nseg; seg += gridDim.x) {
+    SegScalars nxt = {};
+    if (seg + (int)gridDim.x < d.nseg) nxt = load_seg(d, sc, Dc, seg + gridDim.x);
+    const int st = fused_segment<MIX, Fast, 1>(d, seg, smem, cur, 0, 1, seg, true);
+    if (st != kSegOk && threadIdx.x == 0) d.ovlist[atomicAdd(&c->nov, 1)] = seg;
+    cur = nxt;
+  }
   if (threadIdx.x == 0) {
-    if (st != kSegOk) d.ovlist[atomicAdd(&c->nov, 1)] = seg;
     __threadfence();
     s_last = atomicAdd(&c->done, 1u) == gridDim.x - 1;
   }
@@ -456,29 +674,38 @@ __global__ void __launch_bounds__(Fast::kT, 3) k_step1d(Dev d, cudaGraphConditio
   if (!s_last) return;
   __threadfence();
   const int nov = atomicAdd(&c->nov, 0);
-  if (nov == 0) fused_finish<Fast::kT>(d);
+  if (nov == 0) fused_finish<MIX, Fast::kT>(d, d.nseg);
   if (threadIdx.x == 0) {
     if (nov > 0) c->big_steps += 1;
+    if (nov > c->ov_value) c->ov_value = nov;  // largest queue seen (diagnostic)
     if (use_cond) cudaGraphSetConditional(cond, nov > 0 ? 1u : 0u);
     c->done = 0;
   }
 }
 
-// Second tier: the queued segments, larger staging, CTAs loop over the queue.
+// Second tier: the queued segments with larger staging.  Each segment is
+// taken by one thread-block cluster of kSlices CTAs (on kSlices SMs): all
+// stage and sort it, each forms the row sums of every kSlices-th particle
+// (shared through distributed shared memory) and the exchange of every
+// kSlices-th own particle.  Clusters loop over the queue.
 template <bool MIX>
-__global__ void __launch_bounds__(Big::kT, 1) k_step1d_big(Dev d, cudaGraphConditionalHandle cond,
-                                                           int use_cond) {
+__global__ void __cluster_dims__(kSlices, 1, 1) __launch_bounds__(Big::kT, 1)
+    k_step1d_big(Dev d, cudaGraphConditionalHandle cond, int use_cond) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ bool s_last;
   Ctrl* c = d.ctrl;
   const int nov = c->nov;
-  for (int b = blockIdx.x; b < nov; b += gridDim.x) {
-    const int seg = d.ovlist[b];
-    const int st = fused_segment<MIX, Big>(d, seg, smem);
+  const int sc = c->scur;
+  const long long Dc = (c->dmax >> d.cshift) + 2;
+  const int rank = blockIdx.x % kSlices, cid = blockIdx.x / kSlices;
+  const int ncl = gridDim.x / kSlices;
+  for (int q = cid; q < nov; q += ncl) {
+    const int seg = d.ovlist[q];
+    const int st = fused_segment<MIX, Big, kSlices>(d, seg, smem, load_seg(d, sc, Dc, seg), rank,
+                                                    kSlices, d.nseg + q * kSlices + rank, false);
     if (st != kSegOk && threadIdx.x == 0 && atomicExch(&c->overflow, 1) == 0) {
       c->ov_reason = st;
       c->ov_seg = seg;
-      c->ov_value = 0;
     }
   }
   if (threadIdx.x == 0) {
@@ -489,7 +716,7 @@ __global__ void __launch_bounds__(Big::kT, 1) k_step1d_big(Dev d, cudaGraphCondi
   if (!s_last) return;
   __threadfence();
   const int ov = atomicAdd(&c->overflow, 0);
-  if (!ov) fused_finish<Big::kT>(d);
+  if (!ov) fused_finish<MIX, Big::kT>(d, d.nseg + nov * kSlices);
   if (threadIdx.x == 0) {
     if (ov) {
       c->fallback = 1;
@@ -588,17 +815,21 @@ cudaError_t fused_configure() {
 cudaError_t launch_fused_step(const Dev& d, int precision, cudaGraphConditionalHandle cond,
                               int use_cond, cudaStream_t s) {
   const size_t sm = tier_smem<Fast>(precision);
+  const int g = d.nseg < 3 * d.nsm ? d.nseg : 3 * d.nsm;
   if (precision == MT_MIXED)
-    k_step1d<true><<<d.nseg, Fast::kT, sm, s>>>(d, cond, use_cond);
+    k_step1d<true><<<g, Fast::kT, sm, s>>>(d, cond, use_cond);
   else
-    k_step1d<false><<<d.nseg, Fast::kT, sm, s>>>(d, cond, use_cond);
+    k_step1d<false><<<g, Fast::kT, sm, s>>>(d, cond, use_cond);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fused_big(const Dev& d, int precision, cudaGraphConditionalHandle cond,
                              int use_cond, cudaStream_t s) {
   const size_t sm = tier_smem<Big>(precision);
-  const unsigned int g = (unsigned int)(d.nseg < 148 ? d.nseg : 148);
+  // up to 16 clusters (two per GPC fit at one CTA per SM), fewer if there
+  // are fewer segments
+  const int clusters = d.nseg < 16 ? d.nseg : 16;
+  const unsigned int g = (unsigned int)(clusters * kSlices);
   if (precision == MT_MIXED)
     k_step1d_big<true><<<g, Big::kT, sm, s>>>(d, cond, use_cond);
   else

@@ -157,6 +157,31 @@ __device__ __forceinline__ T normalised(int norm, T w, T ip, T iq) {
   return norm == MT_NORM_ROW ? w * ip : T(0.5) * w * (ip + iq);
 }
 
+// Combining per-lane partial sums in a fixed shuffle tree (warp-cooperative
+// sums over a dense neighbourhood): row sums in T, flux accumulators in Acc.
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double acc_warp_sum(double v) { return warp_sum(v); }
+__device__ __forceinline__ kahan acc_warp_sum(kahan v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_down_sync(0xffffffffu, v.s, o);
+    const float c2 = __shfl_down_sync(0xffffffffu, v.c, o);
+    const df e = two_sum(v.s, s2);
+    v.s = e.hi;
+    v.c = __fadd_rn(__fadd_rn(v.c, c2), e.lo);
+  }
+  return v;
+}
+
 // Observables arithmetic: sums in the precision's own format (binary64 or
 // double-binary32), converted to binary64 per CTA.
 __device__ __forceinline__ double obs_add(double a, double b) { return a + b; }

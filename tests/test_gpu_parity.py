@@ -426,16 +426,18 @@ def test_fused_segments_many_steps_with_drift_and_walls():
             assert_masses(gb, b, TOL[mt.MT_MIXED], f"B step {s}")
 
 
-def test_fused_dense_bins_sorted_in_place():
-    """A cluster far denser than a cell (a few hundred particles within one
-    unit, like particles piled against a wall) stays on the fused path: its
-    bins are sorted by the whole CTA.  Results match the oracle."""
+@pytest.mark.parametrize("cluster,tiers", [(60, ["fused_step"]), (300, ["fused_step", "fused_big"])])
+def test_fused_dense_bins_sorted_in_place(cluster, tiers):
+    """A cluster denser than a cell (particles piled up like at a wall) is
+    sorted in place by the whole CTA; a small one stays in the first tier, a
+    pair-heavy one (O(n^2) work) goes to the second tier, whose exchange is
+    split across several CTAs.  Results match the oracle."""
     n = 5000
     x = synth.uniform_positions(n, 5000.0, seed=23)
-    x[0, :300] = 2500.0 + synth.uniform_positions(300, 1.0, seed=24)[0]
+    x[0, :cluster] = 2500.0 + synth.uniform_positions(cluster, 1.0, seed=24)[0]
     A, B = synth.uniform_masses(n, seed=23)
     sim = make(n, 5000.0, D_rw=0.01)
     run_both(sim, x, A, B, 3, pairs=True)
     mt.mt_set_profiling(sim.h, True)
     sim.step()
-    assert [k for k, _ in mt.mt_read_profile(sim.h)] == ["fused_step"]
+    assert [k for k, _ in mt.mt_read_profile(sim.h)] == tiers
