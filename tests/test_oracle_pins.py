@@ -422,3 +422,12 @@ def test_sorted_window_edges_at_exactly_smax():
     A, B = synth.uniform_masses(len(base), seed=61)
     for u, v in zip(O.mass_transfer(p, X, [A, B]), O.mass_transfer_sorted_1d(p, X, [A, B])):
         np.testing.assert_allclose(u, v, rtol=0, atol=1e-16)
+
+
+def test_observables_closed_form():
+    """sum A, sum B, sum (A - B) and mean A of A = 1..n, B = n..1."""
+    n = 1000
+    A = np.arange(1, n + 1, dtype=np.float64)
+    B = A[::-1].copy()
+    o = O.observables(A, B)
+    assert o.tolist() == [n * (n + 1) / 2, n * (n + 1) / 2, 0.0, (n + 1) / 2]
