@@ -95,7 +95,27 @@ typedef struct mt_params {
   uint64_t realisation; /* counter word separating independent realisations */
   int32_t observe_cap;  /* steps kept in the observables ring; 0 = off */
   int32_t cell_shift;   /* log2 of the cell width in ticks; 0 = choose */
+  int32_t seg_target;   /* 1-d cell search: particles per segment of the
+                           one-kernel step, in [16, 1024]; 0 = choose */
+  int32_t reserved;     /* 0 */
 } mt_params;
+
+/* A batch: count independent 1-d realisations (the ensembles of repeated
+ * simulations behind the paper's averaged results, Sec. 3 and Sec. 6.1)
+ * advanced together, each step in one pass over all of them.  Realisation r
+ * has n[r] >= 1 particles on its own domain [0, L[r]] with its own walls,
+ * and its random walk uses the counter word realisation[r] (NULL:
+ * p->realisation + r); everything else is shared.  Each realisation's result
+ * is the one a single handle with the same parameters, n = n[r], L = L[r]
+ * and realisation = realisation[r] would compute (up to the summation order
+ * of ties and of a step the general pipeline redoes). */
+typedef struct mt_batch {
+  int32_t count;                /* realisations, >= 1 */
+  int32_t reserved;             /* 0 */
+  const int64_t* n;             /* host array [count] */
+  const double* L;              /* host array [count] */
+  const uint64_t* realisation;  /* host array [count] or NULL */
+} mt_batch;
 
 typedef struct mt_handle mt_handle;
 
@@ -117,6 +137,20 @@ mt_status mt_workspace_bytes(const mt_params* p, size_t* bytes);
  * creates and destroys.  The state is empty until mt_upload. */
 mt_status mt_create(const mt_params* p, void* workspace, size_t workspace_bytes,
                     void* stream, mt_handle** out);
+
+/* Batch versions of mt_resolve, mt_workspace_bytes and mt_create.  p gives
+ * the shared parameters: dim must be 1 and search MT_SEARCH_CELL; p->n and
+ * p->L[0] are ignored (the resolved p has n = sum of n[r] and L[0] = the
+ * length of the axis the realisations share, side by side).  The default
+ * frac_bits follows the largest L[r].  The handle then works like any
+ * other, with the realisations' arrays concatenated in order (realisation 0's
+ * particles first, each in its own coordinates [0, L[r]]); observables rows
+ * hold 4 doubles per realisation and pairs never join two realisations.
+ * The batch arrays are read during the call only. */
+mt_status mt_batch_resolve(const mt_params* p, const mt_batch* b, mt_params* out);
+mt_status mt_batch_workspace_bytes(const mt_params* p, const mt_batch* b, size_t* bytes);
+mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace,
+                          size_t workspace_bytes, void* stream, mt_handle** out);
 
 /* Load the state: x (dim*n doubles, axis-major, each in [0, L_d]), A and B
  * (n doubles each).  mem says whether the three pointers are host or device
@@ -155,8 +189,10 @@ mt_status mt_read_positions(mt_handle* h, double* x, int32_t mem);
 mt_status mt_read_ticks(mt_handle* h, int64_t* X, int32_t mem);
 
 /* Observables of the last min(steps, cap, observe_cap) steps, oldest first,
- * 4 doubles each: sum A, sum B, sum (A - B), mean A after the step.
- * out: host memory for 4*cap doubles.  *count receives the rows written. */
+ * 4 doubles each: sum A, sum B, sum (A - B), mean A after the step (a batch
+ * handle: 4 per realisation, realisation 0 first).  out: host memory for
+ * 4*cap doubles (4*count*cap for a batch).  *count receives the rows
+ * written. */
 mt_status mt_read_observables(mt_handle* h, double* out, int64_t cap,
                               int64_t* count);
 
@@ -185,8 +221,10 @@ mt_status mt_philox(mt_handle* h, uint32_t c0, uint32_t c1, uint32_t c2,
 mt_status mt_set_profiling(mt_handle* h, int32_t on);
 
 /* Durations in milliseconds of the kernels of the last profiled step, in
- * launch order (waits for that step).  ms: host array of cap floats;
- * *count receives the number of kernels in a step (may exceed cap). */
+ * launch order (waits for that step).  Where a step without a graph waits
+ * for the host to read device state between two kernels, that idle time is
+ * counted in neither.  ms: host array of cap floats; *count receives the
+ * number of kernels in a step (may exceed cap). */
 mt_status mt_read_profile(mt_handle* h, float* ms, int32_t cap, int32_t* count);
 
 /* Name of kernel idx of the last profiled step ("" if out of range). */

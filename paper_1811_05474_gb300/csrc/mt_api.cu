@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "mt_internal.cuh"
 
@@ -53,9 +54,14 @@ struct Derived {
   // fused 1-d step (one kernel per step) and its tiling
   bool fused = false;
   long long seg_target = 0, nseg = 0, hc = 0;
+  // realisations (one for a single system) and the fused segments' targets
+  int nreal = 1, lbits = 31;
+  std::vector<Real> rt;
+  std::vector<int> sslot, sreal;
   // workspace offsets
   size_t o_ctrl, o_X[2], o_id[2], o_M[2], o_src, o_rinv, o_count, o_start, o_cursor,
-      o_status, o_big, o_part, o_obs, o_fstart[2], o_cb[2], o_ovlist, total;
+      o_status, o_big, o_part, o_obs, o_fstart[2], o_cb[2], o_ovlist, o_rt, o_sslot, o_sreal,
+      o_rdone, total;
 };
 
 int default_frac_bits(const mt_params& p) {
@@ -78,11 +84,38 @@ int floor_log2(double v) {  // v >= 1
   return c;
 }
 
-mt_status resolve(const mt_params* in, Derived* out) {
+// b: a batch of independent 1-d realisations, or NULL for one system.
+mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
   if (!in) return fail(MT_ERR_INVALID, "params is NULL");
   Derived D;
   mt_params p = *in;
   if (p.dim != 1 && p.dim != 2) return fail(MT_ERR_INVALID, "dim must be 1 or 2 (got %d)", p.dim);
+  long long nmax = 0;
+  if (b) {
+    if (b->count < 1) return fail(MT_ERR_INVALID, "a batch needs >= 1 realisation");
+    if (!b->n || !b->L) return fail(MT_ERR_INVALID, "batch n and L arrays are required");
+    if (p.dim != 1) return fail(MT_ERR_INVALID, "batches are 1-d");
+    if (p.search != MT_SEARCH_CELL) return fail(MT_ERR_INVALID, "batches use MT_SEARCH_CELL");
+    long long tot = 0;
+    double Lmax = 0.0;
+    for (int r = 0; r < b->count; ++r) {
+      if (b->n[r] < 1 || b->n[r] >= (1LL << 31))
+        return fail(MT_ERR_INVALID, "realisation %d: n must be in [1, 2^31)", r);
+      if (!finite_pos(b->L[r]))
+        return fail(MT_ERR_INVALID, "realisation %d: L must be finite and > 0", r);
+      tot += b->n[r];
+      if (tot >= (1LL << 31) - 1) return fail(MT_ERR_INVALID, "batch has >= 2^31 - 1 particles");
+      nmax = b->n[r] > nmax ? b->n[r] : nmax;
+      Lmax = b->L[r] > Lmax ? b->L[r] : Lmax;
+    }
+    const int lb = ceil_log2(nmax);
+    if (lb > 30 || ((long long)b->count << lb) > (1LL << 31))
+      return fail(MT_ERR_INVALID, "batch: count * 2^ceil(log2(max n)) must be <= 2^31");
+    D.nreal = b->count;
+    D.lbits = lb;
+    p.n = tot;
+    p.L[0] = Lmax;  // for the grid rule; replaced by the shared axis below
+  }
   if (p.n < 0 || p.n >= (1LL << 31) - 1)
     return fail(MT_ERR_INVALID, "n must be in [0, 2^31 - 1) (got %lld)", (long long)p.n);
   for (int a = 0; a < p.dim; ++a)
@@ -118,18 +151,27 @@ mt_status resolve(const mt_params* in, Derived* out) {
     D.Lq[a] = std::llrint(std::ldexp(p.L[a], k));
     D.drift[a] = std::llrint(drift);
   }
-  const double b = std::ldexp(std::sqrt(2.0 * p.D_rw * p.dt), k);
-  if (b * 64.0 >= kTwo61 / 4)
+  const double bw = std::ldexp(std::sqrt(2.0 * p.D_rw * p.dt), k);
+  if (bw * 64.0 >= kTwo61 / 4)
     return fail(MT_ERR_INVALID, "sqrt(2 D_rw dt) 2^frac_bits is too large for the grid");
-  D.bq = (float)b;
+  D.bq = (float)bw;
   D.S = (long long)std::floor(std::ldexp(p.cutoff, k));
   // cell grid
+  std::vector<long long> lq;  // batch: each realisation's length in ticks
+  double lq_sum = (double)D.Lq[0];
+  if (b) {
+    lq_sum = 0.0;
+    for (int r = 0; r < b->count; ++r) {
+      lq.push_back(std::llrint(std::ldexp(b->L[r], k)));
+      lq_sum += (double)lq.back();
+    }
+  }
   if (p.search == MT_SEARCH_CELL) {
     const long long n1 = p.n > 0 ? p.n : 1;
     int c = p.cell_shift;
     if (c == 0) {
       if (p.dim == 1) {
-        const double per = (double)D.Lq[0] / (double)n1;  // ticks per particle
+        const double per = lq_sum / (double)n1;  // ticks per particle
         c = per >= 2.0 ? floor_log2(per) + 1 : 1;
       } else {
         const int cmin = ceil_log2(D.S + 1);
@@ -143,7 +185,19 @@ mt_status resolve(const mt_params* in, Derived* out) {
       return fail(MT_ERR_INVALID, "2-d cells must be wider than the cutoff (2^cell_shift > Smax)");
     // keep the cell array modest
     for (;;) {
-      D.ncx = (D.Lq[0] >> c) + 1;
+      if (b) {
+        // realisations side by side, gaps of more than Smax between them
+        const long long w = 1LL << c, gapc = (D.S + w - 1) / w + 1;
+        double cells = 0.0;
+        for (int r = 0; r < b->count; ++r) cells += (double)((lq[r] >> c) + 1 + gapc);
+        cells -= (double)gapc;
+        if (std::ldexp(cells, c) >= kTwo61)
+          return fail(MT_ERR_INVALID, "batch too long for the grid: lower frac_bits");
+        D.ncx = (long long)cells;
+        D.Lq[0] = (D.ncx << c) - 1;  // the shared axis
+      } else {
+        D.ncx = (D.Lq[0] >> c) + 1;
+      }
       D.ncy = p.dim == 2 ? (D.Lq[1] >> c) + 1 : 1;
       if ((double)D.ncx * (double)D.ncy <= (double)(1LL << 28)) break;
       ++c;
@@ -171,15 +225,48 @@ mt_status resolve(const mt_params* in, Derived* out) {
     while (T >= 64 && (double)T + 2.0 * (double)(D.hc + dc + 1) * per_cell * 1.5 + 64.0 >
                           (double)kFusedCap)
       T /= 2;
-    if (T >= 64) {
+    if (p.seg_target != 0) {
+      if (p.seg_target < 16 || p.seg_target > kFusedCap)
+        return fail(MT_ERR_INVALID, "seg_target must be 0 or in [16, %d]", kFusedCap);
+      T = p.seg_target;
+    }
+    if (T >= 16 && (T >= 64 || p.seg_target != 0)) {
       D.fused = true;
       D.seg_target = T;
-      D.nseg = (p.n + T - 1) / T;
-      // partial slots: one per segment, plus kFusedSlices per queued segment
-      const long long slots = D.nseg * (1 + kFusedSlices);
-      D.nblocks = D.nblocks > slots ? D.nblocks : slots;
+      p.seg_target = (int32_t)T;
     }
   }
+  if (!D.fused) p.seg_target = 0;
+  // realisation table and fused segments (each realisation's own, so its
+  // particles' slot range [off, off + n) is split at off + j T)
+  {
+    const long long T = D.fused ? D.seg_target : 0;
+    long long off = 0, cb = 0;
+    const long long w = p.search == MT_SEARCH_CELL ? (1LL << D.cshift) : 1;
+    const long long gapc = (D.S + w - 1) / w + 1;
+    for (int r = 0; r < D.nreal; ++r) {
+      Real R = {};
+      R.n = b ? b->n[r] : p.n;
+      R.Lq = b ? lq[r] : D.Lq[0];
+      R.base = b ? (cb << D.cshift) : 0;
+      R.off = off;
+      R.real = (unsigned int)(b && b->realisation ? b->realisation[r] : p.realisation + r);
+      R.seg0 = (int)D.sslot.size();
+      R.nseg = T > 0 ? (int)((R.n + T - 1) / T) : 0;
+      for (int j = 0; j < R.nseg; ++j) {
+        D.sslot.push_back((int)(off + j * T));
+        D.sreal.push_back(r);
+      }
+      if (b) cb += (lq[r] >> D.cshift) + 1 + gapc;
+      off += R.n;
+      D.rt.push_back(R);
+    }
+    D.nseg = (long long)D.sslot.size();
+    D.sslot.push_back((int)p.n);
+    if (D.sreal.empty()) D.sreal.push_back(0);
+    if (D.fused) D.nblocks = D.nblocks > D.nseg ? D.nblocks : D.nseg;  // partial slots
+  }
+  if (b) p.L[0] = std::ldexp((double)D.Lq[0], -k);
   D.ntiles = (D.ncell + kScanTile - 1) / kScanTile;
   // workspace layout
   size_t o = 0;
@@ -201,10 +288,14 @@ mt_status resolve(const mt_params* in, Derived* out) {
   D.o_status = take((size_t)D.ntiles * 8);
   D.o_big = take((size_t)D.nbig_cap * 4);
   D.o_part = take((size_t)D.nblocks * 4 * 8);
-  D.o_obs = take((size_t)p.observe_cap * 4 * 8);
+  D.o_obs = take((size_t)p.observe_cap * D.nreal * 4 * 8);
   for (int b2 = 0; b2 < 2; ++b2) D.o_fstart[b2] = take(D.fused ? (size_t)(D.ncell + 1) * 4 : 0);
   for (int b2 = 0; b2 < 2; ++b2) D.o_cb[b2] = take(D.fused ? (size_t)(D.nseg + 1) * 4 : 0);
   D.o_ovlist = take(D.fused ? (size_t)D.nseg * 4 : 0);
+  D.o_rt = take(D.rt.size() * sizeof(Real));
+  D.o_sslot = take(D.sslot.size() * 4);
+  D.o_sreal = take(D.sreal.size() * 4);
+  D.o_rdone = take((size_t)D.nreal * 4);
   D.total = o;
   D.p = p;
   *out = D;
@@ -275,6 +366,10 @@ mt_status enqueue_general(mt_handle* h, const Dev& d, Marker& mk) {
     CU(launch_move(d, true, false, h->stream));
   }
   CU(launch_transfer(d, p.search, p.precision, h->stream, mk));
+  if (h->D.nreal > 1 && p.observe_cap > 0) {
+    mk("observables", h->stream);
+    CU(launch_real_obs(d, p.precision, h->stream));
+  }
   if (h->D.fused) {
     mk("fused_prep", h->stream);
     CU(launch_fused_prep(d, 1, h->stream));
@@ -297,12 +392,16 @@ mt_status enqueue_step(mt_handle* h, const Dev& d) {
   if (h->D.fused) {
     mk("fused_step", h->stream);
     CU(launch_fused_step(d, p.precision, 0, 0, h->stream));
+    // a gap mark: the idle time while the host reads the control block is
+    // not counted in the kernel before it
+    mk(nullptr, h->stream);
     Ctrl c;
     mt_status s = read_ctrl(h, &c);
     if (s != MT_OK) return s;
     if (c.nov > 0) {
       mk("fused_big", h->stream);
       CU(launch_fused_big(d, p.precision, 0, 0, h->stream));
+      mk(nullptr, h->stream);
       s = read_ctrl(h, &c);
       if (s != MT_OK) return s;
       if (c.fallback) {
@@ -421,9 +520,11 @@ mt_status mt_params_init(mt_params* p) {
   return MT_OK;
 }
 
-mt_status mt_resolve(const mt_params* p, mt_params* out) {
+mt_status mt_resolve(const mt_params* p, mt_params* out) { return mt_batch_resolve(p, nullptr, out); }
+
+mt_status mt_batch_resolve(const mt_params* p, const mt_batch* b, mt_params* out) {
   Derived D;
-  const mt_status s = resolve(p, &D);
+  const mt_status s = resolve(p, b, &D);
   if (s != MT_OK) return s;
   if (!out) return fail(MT_ERR_INVALID, "out is NULL");
   *out = D.p;
@@ -431,8 +532,12 @@ mt_status mt_resolve(const mt_params* p, mt_params* out) {
 }
 
 mt_status mt_workspace_bytes(const mt_params* p, size_t* bytes) {
+  return mt_batch_workspace_bytes(p, nullptr, bytes);
+}
+
+mt_status mt_batch_workspace_bytes(const mt_params* p, const mt_batch* b, size_t* bytes) {
   Derived D;
-  const mt_status s = resolve(p, &D);
+  const mt_status s = resolve(p, b, &D);
   if (s != MT_OK) return s;
   if (!bytes) return fail(MT_ERR_INVALID, "bytes is NULL");
   *bytes = D.total;
@@ -441,10 +546,15 @@ mt_status mt_workspace_bytes(const mt_params* p, size_t* bytes) {
 
 mt_status mt_create(const mt_params* p, void* workspace, size_t workspace_bytes, void* stream,
                     mt_handle** out) {
+  return mt_batch_create(p, nullptr, workspace, workspace_bytes, stream, out);
+}
+
+mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace,
+                          size_t workspace_bytes, void* stream, mt_handle** out) {
   if (!out) return fail(MT_ERR_INVALID, "out is NULL");
   *out = nullptr;
   Derived D;
-  mt_status s = resolve(p, &D);
+  mt_status s = resolve(p, b, &D);
   if (s != MT_OK) return s;
   if (!workspace) return fail(MT_ERR_WORKSPACE, "workspace is NULL");
   if ((uintptr_t)workspace % kAlign != 0)
@@ -525,8 +635,26 @@ mt_status mt_create(const mt_params* p, void* workspace, size_t workspace_bytes,
   d.real = (unsigned int)D.p.realisation;
   d.nbig_cap = (int)D.nbig_cap;
   d.nblocks = (int)D.nblocks;
+  d.rt = reinterpret_cast<const Real*>(w + D.o_rt);
+  d.nreal = D.nreal;
+  d.lbits = D.lbits;
+  d.lmask = (int)((1LL << D.lbits) - 1);
+  d.sslot = reinterpret_cast<const int*>(w + D.o_sslot);
+  d.sreal = reinterpret_cast<const int*>(w + D.o_sreal);
+  d.rdone = reinterpret_cast<int*>(w + D.o_rdone);
+  const Derived& hd = h->D;  // the tables live as long as the handle
   cudaError_t e = D.fused ? fused_configure() : cudaSuccess;
   if (e == cudaSuccess) e = cudaMemsetAsync(h->ws, 0, D.total, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(w + D.o_rt, hd.rt.data(), hd.rt.size() * sizeof(Real),
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(w + D.o_sslot, hd.sslot.data(), hd.sslot.size() * 4,
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(w + D.o_sreal, hd.sreal.data(), hd.sreal.size() * 4,
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -678,18 +806,16 @@ mt_status mt_read_observables(mt_handle* h, double* out, int64_t cap, int64_t* c
   if (s != MT_OK) return s;
   if (have == 0) return MT_OK;
   if (!out) return fail(MT_ERR_INVALID, "out is NULL");
-  double* ring = new double[(size_t)ocap * 4];
-  const cudaError_t e = cudaMemcpy(ring, h->dev.obs, (size_t)ocap * 32, cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) {
-    delete[] ring;
-    return fail(MT_ERR_CUDA, "reading observables: %s", cudaGetErrorString(e));
-  }
+  const size_t width = (size_t)h->D.nreal * 4;  // doubles per row
+  std::vector<double> ring((size_t)ocap * width);
+  const cudaError_t e =
+      cudaMemcpy(ring.data(), h->dev.obs, ring.size() * 8, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(MT_ERR_CUDA, "reading observables: %s", cudaGetErrorString(e));
   const long long first = h->steps - have;  // step index of the oldest row returned
   for (long long i = 0; i < have; ++i) {
     const long long row = (first + i) % ocap;
-    std::memcpy(out + 4 * i, ring + 4 * row, 32);
+    std::memcpy(out + width * i, ring.data() + width * row, width * 8);
   }
-  delete[] ring;
   *count = have;
   return MT_OK;
 }
@@ -745,18 +871,27 @@ mt_status mt_read_profile(mt_handle* h, float* ms, int32_t cap, int32_t* count) 
   *count = 0;
   if (!h->profile || h->ev_count == 0) return MT_OK;
   CU(cudaEventSynchronize(h->ev[h->ev_count]));
-  const int m = h->ev_count < cap ? h->ev_count : cap;
-  for (int i = 0; i < m; ++i) {
-    if (!ms) return fail(MT_ERR_INVALID, "ms is NULL");
-    CU(cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]));
+  int k = 0;  // marks with a null name are gaps, not kernels
+  for (int i = 0; i < h->ev_count; ++i) {
+    if (!h->ev_names[i]) continue;
+    if (k < cap) {
+      if (!ms) return fail(MT_ERR_INVALID, "ms is NULL");
+      CU(cudaEventElapsedTime(&ms[k], h->ev[i], h->ev[i + 1]));
+    }
+    ++k;
   }
-  *count = h->ev_count;
+  *count = k;
   return MT_OK;
 }
 
 const char* mt_profile_name(const mt_handle* h, int32_t idx) {
-  if (!h || idx < 0 || idx >= h->ev_count) return "";
-  return h->ev_names[idx];
+  if (!h || idx < 0) return "";
+  int k = 0;
+  for (int i = 0; i < h->ev_count; ++i) {
+    if (!h->ev_names[i]) continue;
+    if (k++ == idx) return h->ev_names[i];
+  }
+  return "";
 }
 
 const char* mt_last_error(void) { return g_err.c_str(); }

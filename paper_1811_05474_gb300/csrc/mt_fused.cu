@@ -33,7 +33,14 @@
 // sums and exchange across 8 SMs.  Only if a segment does not fit there
 // either does a second conditional node redo the step with the general
 // pipeline (scan, scatter, cell sort, two transfer passes).  Whichever tier
-// completes the step reduces the observables and advances the step.
+// completes the step advances it.
+//
+// Batches.  Independent realisations share the kernel: each has its own
+// stretch of the tick axis and its own segments (segment starts sslot[] are
+// fixed slots, since a realisation's particles stay in its slot range, and a
+// realisation's first segment starts at its first cell, which no other
+// realisation's particle can reach).  The CTA that finishes the last segment
+// of a realisation reduces that realisation's observables.
 #include <cooperative_groups.h>
 
 #include "mt_pair.cuh"
@@ -95,6 +102,7 @@ __device__ __forceinline__ int lower_at_least(const long long* a, int m, long lo
 // starts (loaded one segment ahead by the persistent loop).
 struct SegScalars {
   long long c0, c1, a0, L, o0, o1;
+  int t0, t1;  // first target slots of this segment and the next
 };
 
 __device__ __forceinline__ SegScalars load_seg(const Dev& d, int sc, long long Dc, int seg) {
@@ -107,18 +115,20 @@ __device__ __forceinline__ SegScalars load_seg(const Dev& d, int sc, long long D
   s.L = So[lmin(s.c1 + Hc + Dc, ncell)] - s.a0;
   s.o0 = So[lmax(s.c0 - Dc, 0)];
   s.o1 = So[lmin(s.c0 + Dc, ncell)];
+  s.t0 = d.sslot[seg];
+  s.t1 = d.sslot[seg + 1];
   return s;
 }
 
 // Process one segment with the CTA (all NT threads call it).  The CTA
 // computes the exchange for the own particles j with (j - first own) %
 // nslice == slice, and the cell starts / segment boundaries only for slice
-// 0; its observables go to partial slot part_slot.  Returns kSegOk, or why
-// the segment does not fit this tier (then nothing of it has been written
-// except a zero observables partial).
+// 0; the segment's observables go to partial slot seg.  Returns kSegOk, or
+// why the segment does not fit this tier (then nothing of it has been
+// written except a zero observables partial).
 template <bool MIX, typename TR, int CL>
 __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const SegScalars& g,
-                             int slice, int nslice, int part_slot, bool route_heavy) {
+                             int slice, int nslice, bool route_heavy) {
   using W = Weight<MIX, 1>;
   using T = typename W::T;
   using MS = Mass<MIX>;
@@ -185,17 +195,20 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
       if (e < L) {
         const long long slot = a0 + e;
         const int id = Io[slot];
+        const Real* R = d.rt + (id >> d.lbits);
+        const int loc = id & d.lmask;
+        const long long base = R->base;
         float z;
         if (noise) {
-          z = noise[id];
+          z = noise[R->off + loc];
         } else {
           const uint4 u = philox4x32_10(
-              make_uint4((unsigned int)id, (unsigned int)step, (unsigned int)(step >> 32), d.real),
+              make_uint4((unsigned int)loc, (unsigned int)step, (unsigned int)(step >> 32), R->real),
               d.key0, d.key1);
           z = box_muller(u.x, u.y).x;
         }
-        const long long x = reflect(Xo[slot] + d.drift[0] + float_to_ll_rn(__fmul_rn(d.bq, z)),
-                                    d.Lq[0]);
+        const long long x =
+            base + reflect(Xo[slot] - base + d.drift[0] + float_to_ll_rn(__fmul_rn(d.bq, z)), R->Lq);
         rx[k] = x;
         rid[k] = id;
         ra[k] = Mo[slot];
@@ -542,13 +555,23 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
       }
       Sn[cc] = (int)(out0 + (lo - w0));
     }
+    // Segment s2 >= 1 starts after the cell that holds slot sslot[s2] - 1;
+    // this CTA sets the boundaries whose slot it wrote.  The first such s2
+    // is found by a short walk from seg + 1 (out0 is near sslot[seg]).
     int* CBn = d.cb[sc ^ 1];
     const long long own = w1 - w0;
-    const long long T0 = d.seg_target;
-    for (long long s2 = (out0 + T0) / T0 + tid; s2 < d.nseg; s2 += NT) {
-      const long long q = s2 * T0 - 1;  // last slot before segment s2's first
+    int s2 = seg + 1;
+    if (g.t0 > out0) {
+      while (s2 > 1 && d.sslot[s2 - 1] > out0) --s2;
+    } else if (g.t1 <= out0) {
+      while (s2 < d.nseg && d.sslot[s2] <= out0) ++s2;
+    }
+    for (s2 += tid; s2 < d.nseg; s2 += NT) {
+      const long long q = d.sslot[s2] - 1;  // last slot before segment s2's first
       if (q >= out0 + own) break;
-      if (q >= out0) CBn[s2] = (int)((sx[w0 + (q - out0)] >> wsh) + 1);
+      // a realisation's first segment starts at its first cell, fixed
+      if (q >= out0 && d.sreal[s2] == d.sreal[s2 - 1])
+        CBn[s2] = (int)((sx[w0 + (q - out0)] >> wsh) + 1);
     }
   }
   // per-segment observables in the precision's own arithmetic: warp shuffles,
@@ -567,6 +590,7 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
       s_red[2][warp] = od;
     }
     __syncthreads();
+    __shared__ MV s_seg[3];
     if (tid == 0) {
       MV ta = s_red[0][0], tb = s_red[1][0], td = s_red[2][0];
       for (int w = 1; w < NT / 32; ++w) {
@@ -574,19 +598,38 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
         tb = obs_add(tb, s_red[1][w]);
         td = obs_add(td, s_red[2][w]);
       }
+      s_seg[0] = ta;
+      s_seg[1] = tb;
+      s_seg[2] = td;
+    }
+    if constexpr (CL > 1) {
+      // the cluster's CTAs hold the sums of their own slices: the first one
+      // adds them in rank order (distributed shared memory)
+      cg::cluster_group cl = cg::this_cluster();
+      cl.sync();
+      if (slice == 0 && tid == 0) {
+        for (int k = 0; k < 3; ++k) {
+          MV t = s_seg[k];
+          for (int rk = 1; rk < CL; ++rk) t = obs_add(t, *cl.map_shared_rank(&s_seg[k], rk));
+          s_seg[k] = t;
+        }
+      }
+      cl.sync();
+    }
+    if (tid == 0 && slice == 0) {
       MV* part = reinterpret_cast<MV*>(d.partials);  // one 8-byte slot each
-      part[4 * part_slot + 0] = ta;
-      part[4 * part_slot + 1] = tb;
-      part[4 * part_slot + 2] = td;
+      part[4 * seg + 0] = s_seg[0];
+      part[4 * seg + 1] = s_seg[1];
+      part[4 * seg + 2] = s_seg[2];
     }
   }
   __syncthreads();
   return status;
 }
 
-// End of a fused step, run by one CTA after every segment is done: reduce
-// the per-segment observables (binary64, or double-binary32 in MIXED) in a
-// fixed order and advance the state.
+// Observables of realisation r, by the CTA that completed its last segment
+// this step: its segments' partials (binary64, or double-binary32 in MIXED)
+// reduced in a fixed order, one row of the ring.
 __device__ __forceinline__ double ldcg_obs(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ df ldcg_obs(const df* p) {
   const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
@@ -594,55 +637,80 @@ __device__ __forceinline__ df ldcg_obs(const df* p) {
 }
 
 template <bool MIX, int NT>
-__device__ void fused_finish(const Dev& d, int nslots) {
+__device__ void reduce_realisation(const Dev& d, int r) {
   using MV = typename Mass<MIX>::V;
   __shared__ MV s_tot[NT / 32][3];
   Ctrl* c = d.ctrl;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (d.observe_cap > 0) {
-    const MV* part = reinterpret_cast<const MV*>(d.partials);
-    MV ta{}, tb{}, td{};
-    for (int blk = tid; blk < nslots; blk += NT) {
-      ta = obs_add(ta, ldcg_obs(&part[4 * blk + 0]));
-      tb = obs_add(tb, ldcg_obs(&part[4 * blk + 1]));
-      td = obs_add(td, ldcg_obs(&part[4 * blk + 2]));
-    }
+  const Real R = d.rt[r];
+  const MV* part = reinterpret_cast<const MV*>(d.partials);
+  MV ta{}, tb{}, td{};
+  for (int blk = R.seg0 + tid; blk < R.seg0 + R.nseg; blk += NT) {
+    ta = obs_add(ta, ldcg_obs(&part[4 * blk + 0]));
+    tb = obs_add(tb, ldcg_obs(&part[4 * blk + 1]));
+    td = obs_add(td, ldcg_obs(&part[4 * blk + 2]));
+  }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      ta = obs_add(ta, obs_shfl(ta, o));
-      tb = obs_add(tb, obs_shfl(tb, o));
-      td = obs_add(td, obs_shfl(td, o));
-    }
-    if (lane == 0) {
-      s_tot[warp][0] = ta;
-      s_tot[warp][1] = tb;
-      s_tot[warp][2] = td;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      ta = s_tot[0][0];
-      tb = s_tot[0][1];
-      td = s_tot[0][2];
-      for (int w = 1; w < NT / 32; ++w) {
-        ta = obs_add(ta, s_tot[w][0]);
-        tb = obs_add(tb, s_tot[w][1]);
-        td = obs_add(td, s_tot[w][2]);
-      }
-      const long long row = (long long)(c->step % (unsigned long long)d.observe_cap);
-      const double sa = obs_double(ta);
-      d.obs[4 * row + 0] = sa;
-      d.obs[4 * row + 1] = obs_double(tb);
-      d.obs[4 * row + 2] = obs_double(td);
-      d.obs[4 * row + 3] = d.n > 0 ? sa / (double)d.n : 0.0;
-    }
+  for (int o = 16; o > 0; o >>= 1) {
+    ta = obs_add(ta, obs_shfl(ta, o));
+    tb = obs_add(tb, obs_shfl(tb, o));
+    td = obs_add(td, obs_shfl(td, o));
   }
+  if (lane == 0) {
+    s_tot[warp][0] = ta;
+    s_tot[warp][1] = tb;
+    s_tot[warp][2] = td;
+  }
+  __syncthreads();
   if (tid == 0) {
-    c->step += 1;
-    c->xcur ^= 1;
-    c->mcur ^= 1;
-    c->scur ^= 1;
-    c->fallback = 0;
+    ta = s_tot[0][0];
+    tb = s_tot[0][1];
+    td = s_tot[0][2];
+    for (int w = 1; w < NT / 32; ++w) {
+      ta = obs_add(ta, s_tot[w][0]);
+      tb = obs_add(tb, s_tot[w][1]);
+      td = obs_add(td, s_tot[w][2]);
+    }
+    const long long row = (long long)(c->step % (unsigned long long)d.observe_cap);
+    double* o = d.obs + 4 * (row * d.nreal + r);
+    const double sa = obs_double(ta);
+    o[0] = sa;
+    o[1] = obs_double(tb);
+    o[2] = obs_double(td);
+    o[3] = sa / (double)R.n;
+    d.rdone[r] = 0;
   }
+  __syncthreads();
+}
+
+// Count segment seg as done; the CTA that completes its realisation's last
+// segment reduces that realisation's observables.  Called by every thread of
+// the CTA after the segment's partial is written.
+template <bool MIX, int NT>
+__device__ void complete_segment(const Dev& d, int seg) {
+  __shared__ int s_r;
+  if (d.observe_cap <= 0) return;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const int r = d.sreal[seg];
+    s_r = atomicAdd(&d.rdone[r], 1) == d.rt[r].nseg - 1 ? r : -1;
+  }
+  __syncthreads();
+  const int r = s_r;
+  __syncthreads();
+  if (r < 0) return;
+  __threadfence();
+  reduce_realisation<MIX, NT>(d, r);
+}
+
+// End of a fused step (one thread, after every segment is done).
+__device__ __forceinline__ void fused_advance(const Dev& d) {
+  Ctrl* c = d.ctrl;
+  c->step += 1;
+  c->xcur ^= 1;
+  c->mcur ^= 1;
+  c->scur ^= 1;
+  c->fallback = 0;
 }
 
 // First tier: a persistent grid (a few CTAs per SM) looping over the
@@ -662,8 +730,11 @@ __global__ void __launch_bounds__(Fast::kT, 3) k_step1d(Dev d, cudaGraphConditio
   for (; seg < d.nseg; seg += gridDim.x) {
     SegScalars nxt = {};
     if (seg + (int)gridDim.x < d.nseg) nxt = load_seg(d, sc, Dc, seg + gridDim.x);
-    const int st = fused_segment<MIX, Fast, 1>(d, seg, smem, cur, 0, 1, seg, true);
-    if (st != kSegOk && threadIdx.x == 0) d.ovlist[atomicAdd(&c->nov, 1)] = seg;
+    const int st = fused_segment<MIX, Fast, 1>(d, seg, smem, cur, 0, 1, true);
+    if (st == kSegOk)
+      complete_segment<MIX, Fast::kT>(d, seg);
+    else if (threadIdx.x == 0)
+      d.ovlist[atomicAdd(&c->nov, 1)] = seg;
     cur = nxt;
   }
   if (threadIdx.x == 0) {
@@ -674,8 +745,8 @@ __global__ void __launch_bounds__(Fast::kT, 3) k_step1d(Dev d, cudaGraphConditio
   if (!s_last) return;
   __threadfence();
   const int nov = atomicAdd(&c->nov, 0);
-  if (nov == 0) fused_finish<MIX, Fast::kT>(d, d.nseg);
   if (threadIdx.x == 0) {
+    if (nov == 0) fused_advance(d);
     if (nov > 0) c->big_steps += 1;
     if (nov > c->ov_value) c->ov_value = nov;  // largest queue seen (diagnostic)
     if (use_cond) cudaGraphSetConditional(cond, nov > 0 ? 1u : 0u);
@@ -702,8 +773,10 @@ __global__ void __cluster_dims__(kSlices, 1, 1) __launch_bounds__(Big::kT, 1)
   for (int q = cid; q < nov; q += ncl) {
     const int seg = d.ovlist[q];
     const int st = fused_segment<MIX, Big, kSlices>(d, seg, smem, load_seg(d, sc, Dc, seg), rank,
-                                                    kSlices, d.nseg + q * kSlices + rank, false);
-    if (st != kSegOk && threadIdx.x == 0 && atomicExch(&c->overflow, 1) == 0) {
+                                                    kSlices, false);
+    if (st == kSegOk) {
+      if (rank == 0) complete_segment<MIX, Big::kT>(d, seg);
+    } else if (threadIdx.x == 0 && atomicExch(&c->overflow, 1) == 0) {
       c->ov_reason = st;
       c->ov_seg = seg;
     }
@@ -716,8 +789,8 @@ __global__ void __cluster_dims__(kSlices, 1, 1) __launch_bounds__(Big::kT, 1)
   if (!s_last) return;
   __threadfence();
   const int ov = atomicAdd(&c->overflow, 0);
-  if (!ov) fused_finish<MIX, Big::kT>(d, d.nseg + nov * kSlices);
   if (threadIdx.x == 0) {
+    if (!ov) fused_advance(d);
     if (ov) {
       c->fallback = 1;
       c->fallbacks += 1;
@@ -730,10 +803,12 @@ __global__ void __cluster_dims__(kSlices, 1, 1) __launch_bounds__(Big::kT, 1)
 }
 
 // fstart[target] := start (the general pipeline's cell starts), and the
-// segment boundaries cb[target][s] = first cell c with start[c] >= s T.
+// segment boundaries cb[target][s] = first cell c with start[c] >= sslot[s]
+// (a realisation's first segment: the realisation's first cell).
 __global__ void k_fused_prep(Dev d, int flip) {
   const int target = d.ctrl->scur ^ flip;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < d.nreal) d.rdone[i] = 0;  // a step the general pipeline redid
   if (i <= d.ncell) {
     d.fstart[target][i] = d.start[i];
     if (i == d.ncell) {
@@ -749,8 +824,15 @@ __global__ void k_fused_prep(Dev d, int flip) {
       cb[i] = (int)d.ncell;
       d.cb[target ^ 1][i] = (int)d.ncell;
       d.cb[target ^ 1][0] = 0;
+    } else if (d.sreal[i] != d.sreal[i - 1]) {
+      // the first segment of a realisation starts at its first cell in both
+      // buffers: no particle of another realisation ever enters it, so every
+      // segment's own particles belong to one realisation
+      const int first = (int)(d.rt[d.sreal[i]].base >> d.cshift);
+      cb[i] = first;
+      d.cb[target ^ 1][i] = first;
     } else {
-      const long long want = i * (long long)d.seg_target;
+      const long long want = d.sslot[i];
       long long lo = 0, hi = d.ncell;
       while (lo < hi) {
         const long long mid = (lo + hi) >> 1;
@@ -838,7 +920,8 @@ cudaError_t launch_fused_big(const Dev& d, int precision, cudaGraphConditionalHa
 }
 
 cudaError_t launch_fused_prep(const Dev& d, int flip, cudaStream_t s) {
-  const long long cnt = (d.ncell > d.nseg ? d.ncell : d.nseg) + 1;
+  long long cnt = (d.ncell > d.nseg ? d.ncell : d.nseg) + 1;
+  cnt = cnt > d.nreal ? cnt : d.nreal;
   k_fused_prep<<<(unsigned int)((cnt + 255) / 256), 256, 0, s>>>(d, flip);
   k_fused_flip<<<1, 1, 0, s>>>(d, flip);
   return cudaGetLastError();

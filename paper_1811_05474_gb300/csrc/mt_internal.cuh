@@ -50,6 +50,22 @@ struct Ctrl {
   int pad1;
 };
 
+// One realisation of a batch (a single system is a batch of one).  Batched
+// realisations are 1-d and sit side by side on one tick axis: realisation r
+// owns [base, base + Lq], and consecutive domains are more than Smax apart,
+// so no pair crosses two realisations.  A particle's id is (r << lbits) |
+// its index within r, and its caller index is off + that index.
+struct Real {
+  long long base;      // first tick of its domain on the shared axis
+  long long Lq;        // its domain length in ticks
+  long long off;       // its first particle in the caller's order
+  long long n;         // its particles
+  unsigned int real;   // Philox counter word of its random walk
+  int seg0;            // its first fused segment
+  int nseg;            // its fused segments
+  int pad;
+};
+
 // Everything a kernel needs, passed by value.
 struct Dev {
   Ctrl* ctrl;
@@ -90,7 +106,19 @@ struct Dev {
   int seg_target;           // particles a fused segment aims for
   int nsm;                  // multiprocessors of the device
   long long hc;             // fused halo in cells (covers 2 Smax)
+  const Real* rt;           // [nreal] realisations
+  int nreal;
+  int lbits;                // id = (realisation << lbits) | index within it
+  int lmask;                // (1 << lbits) - 1
+  const int* sslot;         // [nseg + 1] first slot each fused segment aims for
+  const int* sreal;         // [nseg] realisation of each fused segment
+  int* rdone;               // [nreal] segments of the step done (observables)
 };
+
+// Caller index of a particle id.
+__device__ __forceinline__ long long caller_index(const Dev& d, int id) {
+  return d.rt[id >> d.lbits].off + (id & d.lmask);
+}
 
 // ---------------------------------------------------------------- helpers --
 
@@ -238,6 +266,8 @@ struct Marker {
   cudaEvent_t* ev = nullptr;  // null: disabled
   const char** names = nullptr;
   int count = 0;
+  // Mark the start of kernel `name`; a null name marks the start of a gap
+  // (the stream idles while the host reads device state), not a kernel.
   void operator()(const char* name, cudaStream_t s) {
     if (!ev || count >= kMaxMarks) return;
     names[count] = name;
@@ -259,6 +289,7 @@ cudaError_t launch_move(const Dev& d, bool move, bool hist, cudaStream_t s);
 cudaError_t launch_sort(const Dev& d, cudaStream_t s, Marker& mk);  // scan, scatter, cell sort
 cudaError_t launch_permute(const Dev& d, cudaStream_t s);  // gather id/masses after sort, flip
 cudaError_t launch_transfer(const Dev& d, int search, int precision, cudaStream_t s, Marker& mk);
+cudaError_t launch_real_obs(const Dev& d, int precision, cudaStream_t s);  // batches
 cudaError_t launch_upload(const Dev& d, const double* x, const double* A,
                           const double* B, int precision, cudaStream_t s);
 cudaError_t launch_read_masses(const Dev& d, double* A, double* B, int precision,

@@ -7,7 +7,8 @@ namespace mt {
 static unsigned int blocks_for(long long n, int t) { return (unsigned int)((n + t - 1) / t); }
 
 // x (dim*n doubles), A, B (n doubles), all device memory in the caller's
-// order -> grid ticks X = rint(x 2^k), id = identity, masses in the
+// order -> grid ticks X = rint(x 2^k) (plus the realisation's base on the
+// shared axis), id = (realisation << lbits) | index within it, masses in the
 // precision's format.  Positions outside [0, L] or NaN raise kErrInput.
 __global__ void k_upload(Dev d, const double* x, const double* A, const double* B, double pow2k,
                          int mixed) {
@@ -15,21 +16,32 @@ __global__ void k_upload(Dev d, const double* x, const double* A, const double* 
   if (i >= d.n) return;
   Ctrl* c = d.ctrl;
   const int xc = c->xcur, mc = c->mcur;
+  int lo = 0, hi = d.nreal - 1;  // last realisation with off <= i
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (d.rt[mid].off <= i)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const int r = lo;
+  const Real R = d.rt[r];
   for (int a = 0; a < d.dim; ++a) {
+    const long long Lq = a == 0 ? R.Lq : d.Lq[a];
     const double v = x[(long long)a * d.n + i];
     long long X = 0;
     if (!(v >= 0.0)) {
       raise_error(c, kErrInput, i);
     } else {
       X = __double2ll_rn(v * pow2k);
-      if (X > d.Lq[a]) {
+      if (X > Lq) {
         raise_error(c, kErrInput, i);
-        X = d.Lq[a];
+        X = Lq;
       }
     }
-    d.X[xc][(long long)a * d.n + i] = X;
+    d.X[xc][(long long)a * d.n + i] = a == 0 ? R.base + X : X;
   }
-  d.id[xc][i] = (int)i;
+  d.id[xc][i] = (r << d.lbits) | (int)(i - R.off);
   if (mixed) {
     const double a = A[i], b = B[i];
     const float ah = __double2float_rn(a), bh = __double2float_rn(b);
@@ -53,7 +65,8 @@ __global__ void k_read_masses(Dev d, double* A, double* B, int mixed) {
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (p >= d.n) return;
   const int xc = d.ctrl->xcur, mc = d.ctrl->mcur;
-  const int id = d.id[xc][p];
+  const int idp = d.id[xc][p];
+  const long long id = idp < 0 || (idp >> d.lbits) >= d.nreal ? -1 : caller_index(d, idp);
   if (id < 0 || id >= d.n) {
     raise_error(d.ctrl, kErrIndex, p);
     return;
@@ -80,13 +93,15 @@ __global__ void k_read_positions(Dev d, double* x, long long* X) {
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (p >= d.n) return;
   const int xc = d.ctrl->xcur;
-  const int id = d.id[xc][p];
+  const int idp = d.id[xc][p];
+  const long long id = idp < 0 || (idp >> d.lbits) >= d.nreal ? -1 : caller_index(d, idp);
   if (id < 0 || id >= d.n) {
     raise_error(d.ctrl, kErrIndex, p);
     return;
   }
+  const long long base = d.rt[idp >> d.lbits].base;
   for (int a = 0; a < d.dim; ++a) {
-    const long long v = d.X[xc][(long long)a * d.n + p];
+    const long long v = d.X[xc][(long long)a * d.n + p] - (a == 0 ? base : 0);
     if (x) x[(long long)a * d.n + id] = (double)v * d.scale;
     if (X) X[(long long)a * d.n + id] = v;
   }
@@ -102,6 +117,8 @@ cudaError_t launch_read_positions(const Dev& d, double* x, long long* X, cudaStr
 __device__ __forceinline__ void emit(const Dev& d, int a, int b, int* pi, int* pj,
                                      long long cap) {
   const unsigned long long slot = atomicAdd(&d.ctrl->npairs, 1ULL);
+  a = (int)caller_index(d, a);
+  b = (int)caller_index(d, b);
   if ((long long)slot < cap) {
     pi[slot] = a < b ? a : b;
     pj[slot] = a < b ? b : a;

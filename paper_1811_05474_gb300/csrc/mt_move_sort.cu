@@ -25,15 +25,19 @@ __global__ void __launch_bounds__(kThreads) k_move(Dev d) {
   long long pos[2] = {X[p], DIM == 2 ? X[d.n + p] : 0};
   if (MOVE) {
     const int id = d.id[xc][p];
+    // realisation of the particle (always 0 in 2-d, where base = 0)
+    const Real* R = d.rt + (id >> d.lbits);
+    const int loc = id & d.lmask;
+    const long long base = R->base;
     float z[2];
     const float* noise = c->noise;
     if (noise) {
-      z[0] = noise[id];
-      if (DIM == 2) z[1] = noise[d.n + id];
+      z[0] = noise[R->off + loc];
+      if (DIM == 2) z[1] = noise[d.n + loc];
     } else {
       const unsigned long long st = c->step;
       const uint4 u = philox4x32_10(
-          make_uint4((unsigned int)id, (unsigned int)st, (unsigned int)(st >> 32), d.real),
+          make_uint4((unsigned int)loc, (unsigned int)st, (unsigned int)(st >> 32), R->real),
           d.key0, d.key1);
       const float2 g = box_muller(u.x, u.y);
       z[0] = g.x;
@@ -43,7 +47,10 @@ __global__ void __launch_bounds__(kThreads) k_move(Dev d) {
     for (int a = 0; a < DIM; ++a) {
       // Eq. 2 on the grid: drift + rint(b * xi), then the wall mirror.
       const long long step = float_to_ll_rn(__fmul_rn(d.bq, z[a]));
-      pos[a] = reflect(pos[a] + d.drift[a] + step, d.Lq[a]);
+      if (a == 0)
+        pos[0] = base + reflect(pos[0] - base + d.drift[0] + step, R->Lq);
+      else
+        pos[a] = reflect(pos[a] + d.drift[a] + step, d.Lq[a]);
       X[(long long)a * d.n + p] = pos[a];
     }
   }

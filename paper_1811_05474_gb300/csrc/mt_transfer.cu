@@ -74,7 +74,7 @@ __device__ void finish_step(const Dev& d, typename Mass<MIX>::V a, typename Mass
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  if (observe) {
+  if (observe && d.nreal == 1) {  // batches: k_real_obs after the step
     double ta = 0, tb = 0, td = 0;
     for (unsigned int blk = threadIdx.x; blk < gridDim.x; blk += blockDim.x) {
       ta += __ldcg(&d.partials[4 * blk + 0]);
@@ -113,6 +113,65 @@ __device__ void finish_step(const Dev& d, typename Mass<MIX>::V a, typename Mass
     c->mcur ^= flip_m;
     c->done = 0;
   }
+}
+
+// Observables of each realisation of a batch after a step of the general
+// pipeline: one CTA per realisation sums the masses of its slot range (the
+// state is sorted, so realisation r holds slots [off, off + n)) in the
+// precision's arithmetic, in a fixed order.
+template <bool MIX>
+__global__ void __launch_bounds__(kThreads) k_real_obs(Dev d) {
+  using MS = Mass<MIX>;
+  using MV = typename MS::V;
+  __shared__ MV s_part[kThreads / 32][3];
+  const int r = blockIdx.x;
+  const Real R = d.rt[r];
+  const Ctrl* c = d.ctrl;
+  const unsigned long long* M = d.M[c->mcur];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  MV sa{}, sb{}, sd{};
+  for (long long p = R.off + threadIdx.x; p < R.off + R.n; p += kThreads) {
+    const MV a = MS::load(M, p), b = MS::load(M, d.n + p);
+    sa = obs_add(sa, a);
+    sb = obs_add(sb, b);
+    sd = obs_add(sd, obs_diff(a, b));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sa = obs_add(sa, obs_shfl(sa, o));
+    sb = obs_add(sb, obs_shfl(sb, o));
+    sd = obs_add(sd, obs_shfl(sd, o));
+  }
+  if (lane == 0) {
+    s_part[warp][0] = sa;
+    s_part[warp][1] = sb;
+    s_part[warp][2] = sd;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    MV ta = s_part[0][0], tb = s_part[0][1], td = s_part[0][2];
+    for (int w = 1; w < kThreads / 32; ++w) {
+      ta = obs_add(ta, s_part[w][0]);
+      tb = obs_add(tb, s_part[w][1]);
+      td = obs_add(td, s_part[w][2]);
+    }
+    const long long row = (long long)((c->step - 1) % (unsigned long long)d.observe_cap);
+    double* o = d.obs + 4 * (row * d.nreal + r);
+    const double a = obs_double(ta);
+    o[0] = a;
+    o[1] = obs_double(tb);
+    o[2] = obs_double(td);
+    o[3] = a / (double)R.n;
+  }
+}
+
+cudaError_t launch_real_obs(const Dev& d, int precision, cudaStream_t s) {
+  if (d.observe_cap <= 0 || d.nreal <= 1) return cudaSuccess;
+  if (precision == MT_MIXED)
+    k_real_obs<true><<<d.nreal, kThreads, 0, s>>>(d);
+  else
+    k_real_obs<false><<<d.nreal, kThreads, 0, s>>>(d);
+  return cudaGetLastError();
 }
 
 // ================================================================ 1-d walk ==

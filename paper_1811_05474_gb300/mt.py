@@ -48,7 +48,35 @@ class mt_params(ctypes.Structure):
         ("realisation", ctypes.c_uint64),
         ("observe_cap", ctypes.c_int32),
         ("cell_shift", ctypes.c_int32),
+        ("seg_target", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
+
+
+class mt_batch(ctypes.Structure):
+    _fields_ = [
+        ("count", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("n", ctypes.POINTER(ctypes.c_int64)),
+        ("L", ctypes.POINTER(ctypes.c_double)),
+        ("realisation", ctypes.POINTER(ctypes.c_uint64)),
+    ]
+
+
+def make_batch(n, L, realisation=None) -> mt_batch:
+    """An mt_batch over Python sequences; the arrays are kept alive on the
+    returned object."""
+    R = len(n)
+    b = mt_batch()
+    b._n = (ctypes.c_int64 * R)(*[int(v) for v in n])
+    b._L = (ctypes.c_double * R)(*[float(v) for v in L])
+    b.count = R
+    b.n = ctypes.cast(b._n, ctypes.POINTER(ctypes.c_int64))
+    b.L = ctypes.cast(b._L, ctypes.POINTER(ctypes.c_double))
+    if realisation is not None:
+        b._r = (ctypes.c_uint64 * R)(*[int(v) for v in realisation])
+        b.realisation = ctypes.cast(b._r, ctypes.POINTER(ctypes.c_uint64))
+    return b
 
 
 class MtError(RuntimeError):
@@ -71,6 +99,7 @@ def lib(path: Path | None = None):
         raise RuntimeError(f"libmt is not built ({p} missing); run __graft_entry__.build()")
     L = ctypes.CDLL(str(p))
     P = ctypes.POINTER(mt_params)
+    BP = ctypes.POINTER(mt_batch)
     H = ctypes.c_void_p
     i32, i64, u32, u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
     sig = {
@@ -78,6 +107,9 @@ def lib(path: Path | None = None):
         "mt_resolve": [P, P],
         "mt_workspace_bytes": [P, ctypes.POINTER(ctypes.c_size_t)],
         "mt_create": [P, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(H)],
+        "mt_batch_resolve": [P, BP, P],
+        "mt_batch_workspace_bytes": [P, BP, ctypes.POINTER(ctypes.c_size_t)],
+        "mt_batch_create": [P, BP, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(H)],
         "mt_upload": [H, _vp, _vp, _vp, i32],
         "mt_set_noise": [H, _vp],
         "mt_step": [H],
@@ -149,6 +181,30 @@ def mt_create(p: mt_params, workspace_ptr: int, workspace_bytes: int, stream_ptr
     h = ctypes.c_void_p(0)
     check(lib().mt_create(ctypes.byref(p), workspace_ptr, workspace_bytes, stream_ptr or None,
                           ctypes.byref(h)))
+    return h
+
+
+def _bref(b):
+    return ctypes.byref(b) if b is not None else None
+
+
+def mt_batch_resolve(p: mt_params, b: mt_batch | None) -> mt_params:
+    out = mt_params()
+    check(lib().mt_batch_resolve(ctypes.byref(p), _bref(b), ctypes.byref(out)))
+    return out
+
+
+def mt_batch_workspace_bytes(p: mt_params, b: mt_batch | None) -> int:
+    n = ctypes.c_size_t(0)
+    check(lib().mt_batch_workspace_bytes(ctypes.byref(p), _bref(b), ctypes.byref(n)))
+    return int(n.value)
+
+
+def mt_batch_create(p: mt_params, b: mt_batch | None, workspace_ptr: int, workspace_bytes: int,
+                    stream_ptr: int | None):
+    h = ctypes.c_void_p(0)
+    check(lib().mt_batch_create(ctypes.byref(p), _bref(b), workspace_ptr, workspace_bytes,
+                                stream_ptr or None, ctypes.byref(h)))
     return h
 
 
@@ -249,17 +305,19 @@ class Simulation:
     variants take torch CUDA tensors.
     """
 
-    def __init__(self, params: mt_params, device="cuda", stream=None):
+    def __init__(self, params: mt_params, device="cuda", stream=None, batch: mt_batch | None = None):
         import torch
 
         self.torch = torch
-        self.params = mt_resolve(params)
+        self.batch = batch
+        self.nreal = int(batch.count) if batch is not None else 1
+        self.params = mt_batch_resolve(params, batch)
         self.device = torch.device(device)
-        self.nbytes = mt_workspace_bytes(self.params)
+        self.nbytes = mt_batch_workspace_bytes(params, batch)
         self.workspace = torch.empty(max(self.nbytes, 256), dtype=torch.uint8, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
-        self.h = mt_create(self.params, self.workspace.data_ptr(), self.workspace.numel(),
-                           self.stream.cuda_stream)
+        self.h = mt_batch_create(params, batch, self.workspace.data_ptr(), self.workspace.numel(),
+                                 self.stream.cuda_stream)
         self._noise = None
 
     @property
@@ -306,10 +364,11 @@ class Simulation:
         return X
 
     def observables(self) -> np.ndarray:
+        """(steps, 4) rows; (steps, realisations, 4) for a batch."""
         cap = int(self.params.observe_cap)
-        out = np.zeros((max(cap, 1), 4), dtype=np.float64)
+        out = np.zeros((max(cap, 1), self.nreal, 4), dtype=np.float64)
         cnt = mt_read_observables(self.h, _ptr(out), cap)
-        return out[:cnt]
+        return out[:cnt] if self.batch is not None else out[:cnt, 0]
 
     def set_noise(self, xi: np.ndarray | None) -> None:
         """Inject standard normals (dim, n) for the following steps; None

@@ -103,3 +103,52 @@ def test_philox_reference_matches_published_kat():
 
     for ctr, key, out in load_kat():
         assert philox4x32_10(ctr, key) == out
+
+
+def _batch_params(**kw):
+    return mt.mt_params_init(dim=1, L=(1.0,), **kw)
+
+
+def test_batch_resolve_lays_realisations_side_by_side():
+    ns, Ls = [1000, 10, 250000], [1000.0, 3.5, 2.5e5]
+    b = mt.make_batch(ns, Ls)
+    r = mt.mt_batch_resolve(_batch_params(), b)
+    assert r.n == sum(ns)
+    assert r.frac_bits == mt.mt_resolve(mt.mt_params_init(n=ns[2], L=(Ls[2],))).frac_bits
+    # the shared axis holds every domain plus gaps wider than the cutoff
+    w = 2.0 ** (r.cell_shift - r.frac_bits)
+    assert r.L[0] >= sum(Ls) + 2 * r.cutoff
+    assert r.L[0] <= sum(Ls) + len(ns) * (2 * r.cutoff + 3 * w)
+    assert 16 <= r.seg_target <= 1024
+    single = mt.mt_workspace_bytes(mt.mt_params_init(n=sum(ns), L=(r.L[0],)))
+    assert mt.mt_batch_workspace_bytes(_batch_params(), b) >= single // 2
+    # a batch of one is a single system
+    one = mt.mt_batch_resolve(_batch_params(), mt.make_batch([5000], [5000.0]))
+    ref = mt.mt_resolve(mt.mt_params_init(n=5000, L=(5000.0,)))
+    assert (one.n, one.frac_bits, one.cell_shift, one.seg_target) == \
+        (ref.n, ref.frac_bits, ref.cell_shift, ref.seg_target)
+    assert one.L[0] >= 5000.0
+
+
+def test_batch_rejects_bad_descriptions():
+    p = _batch_params()
+    for ns, Ls in (([10, 0], [10.0, 10.0]), ([10], [-1.0]), ([], []), ([10], [float("nan")])):
+        with pytest.raises(mt.MtError) as e:
+            mt.mt_batch_resolve(p, mt.make_batch(ns, Ls))
+        assert e.value.status == mt.MT_ERR_INVALID
+    with pytest.raises(mt.MtError):
+        mt.mt_batch_resolve(mt.mt_params_init(dim=2, L=(10.0, 10.0)), mt.make_batch([10], [10.0]))
+    with pytest.raises(mt.MtError):
+        mt.mt_batch_resolve(_batch_params(search=mt.MT_SEARCH_BRUTE), mt.make_batch([10], [10.0]))
+    # realisation index bits: 2^20 particles leave room for 2^11 realisations
+    with pytest.raises(mt.MtError):
+        mt.mt_batch_resolve(p, mt.make_batch([2 ** 20] + [1] * 2048, [1e6] + [1.0] * 2048))
+
+
+def test_seg_target_is_validated_and_kept():
+    r = mt.mt_resolve(mt.mt_params_init(n=100000, L=(1e5,), seg_target=256))
+    assert r.seg_target == 256
+    with pytest.raises(mt.MtError):
+        mt.mt_resolve(mt.mt_params_init(n=100000, L=(1e5,), seg_target=8))
+    # no one-kernel step for 2-d or brute force
+    assert mt.mt_resolve(mt.mt_params_init(dim=2, n=100, L=(10.0, 10.0))).seg_target == 0
