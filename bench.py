@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--ncu", action="store_true",
                     help="profiling mode: upload, W graph steps, then K direct steps, nothing else")
     ap.add_argument("--n", type=int, default=N, help="particles (profiling mode only)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble object")
+    ap.add_argument("--no-precision", action="store_true", help="skip the precision report")
     return ap.parse_args()
 
 
@@ -263,8 +265,11 @@ def gpu_run(args, precision: str, steps: int, warmup: int, local: int, realisati
     step_ms = [e0[i].elapsed_time(e1[i]) for i in range(steps)]
     sim.sync()
     npairs = mt.mt_read_pairs(sim.h, None, None, 0)
-    kernels = [{"name": k, "ms": sum(kernel_ms[k]) / len(kernel_ms[k])} for k in order]
-    launches_per_step = len(order)
+    nprof = min(steps, 200)
+    kernels = [{"name": k, "ms": sum(kernel_ms[k]) / len(kernel_ms[k]),
+                "launches_per_step": len(kernel_ms[k]) / nprof,
+                "ms_per_step": sum(kernel_ms[k]) / nprof} for k in order]
+    launches_per_step = sum(len(v) for v in kernel_ms.values()) / nprof
     obs = sim.observables()
     sim.close()
     del flush
@@ -307,6 +312,164 @@ def e2e_run(steps: int, local: int, realisation: int):
     sim.close()
     return {"value": N * steps / secs, "unit": "particle-steps/s",
             "h2d_bytes_per_step": (24 * N) / steps, "d2h_bytes_per_step": 32 + (16 * N) / steps}
+
+
+BATCH_R = 256
+BATCH_WORKLOAD = "batch_256x1d_N_loguniform_1e3_1e5_L_eq_N_D0.1_dt1_cutoff3sigma"
+
+
+def batch_inputs():
+    """256 realisations, N_r = floor(10^U(3, 5)) from seed r, uniform on
+    [0, N_r] (density 1), masses U[0, 1) from seed r."""
+    import numpy as np
+
+    from paper_1811_05474_gb300 import synth
+
+    ns = synth.ensemble_sizes(BATCH_R, 1e3, 1e5)
+    Ls = [float(n) for n in ns]
+    xs, As, Bs = [], [], []
+    for r, n in enumerate(ns):
+        xs.append(synth.uniform_positions(int(n), Ls[r], seed=r)[0])
+        a, b = synth.uniform_masses(int(n), seed=r)
+        As.append(a)
+        Bs.append(b)
+    return ns, Ls, xs, As, Bs, (np.concatenate(xs)[None, :], np.concatenate(As),
+                                np.concatenate(Bs))
+
+
+def timed_steps(sim, steps: int, warmup: int, flush_l2=None):
+    """Sum of per-step CUDA-event times over `steps` graph steps (after
+    `warmup` untimed ones), each step bracketed on the simulation's stream."""
+    import torch
+
+    s = sim.stream
+    for _ in range(warmup):
+        if flush_l2:
+            flush_l2(s)
+        sim.run(1)
+    sim.sync()
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        if flush_l2:
+            flush_l2(s)
+        e0[i].record(s)
+        sim.run(1)
+        e1[i].record(s)
+    sim.sync()
+    return sum(e0[i].elapsed_time(e1[i]) for i in range(steps))
+
+
+def batch_run(local: int, steps: int, peak: float):
+    """The batched form: 256 uneven realisations in one handle, one fused
+    kernel per step replayed from a CUDA graph, cell width and segment size
+    picked by mt_autotune; MIXED, then FP64, then the same realisations as
+    separate single handles run one after another (FP64 and MIXED)."""
+    import numpy as np
+    import torch
+
+    from paper_1811_05474_gb300 import mt
+
+    dev = torch.device("cuda", local)
+    ns, Ls, xs, As, Bs, (x, A, B) = batch_inputs()
+    ntot = int(sum(ns))
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    fsum = torch.empty((), dtype=torch.int64, device=dev)
+
+    def flush_l2(s):
+        with torch.cuda.stream(s):
+            flush.zero_()
+            torch.sum(flush.view(torch.int64), dim=0, out=fsum)
+
+    b = mt.make_batch(ns, Ls)
+    out = {"workload": BATCH_WORKLOAD, "realisations": BATCH_R, "particles": ntot,
+           "n_min": int(min(ns)), "n_max": int(max(ns)), "unit": "particle-steps/s"}
+    res = {}
+    for prec, name in ((mt.MT_MIXED, "mixed"), (mt.MT_FP64, "fp64")):
+        p = mt.mt_params_init(dim=1, L=(1.0,), D_mt=D, D_rw=D, dt=DT, precision=prec, seed=2024,
+                              observe_cap=16)
+        t0 = time.perf_counter()
+        best, tune_ms = mt.autotune(p, x, A, B, batch=b, warmup=2, steps=5, device=dev)
+        tune_s = time.perf_counter() - t0
+        auto = mt.mt_batch_resolve(p, b)
+        sim = mt.Simulation(best, device=dev, batch=b)
+        sim.upload(x, A, B)
+        k = steps if prec == mt.MT_MIXED else max(10, steps // 5)
+        ms = timed_steps(sim, k, 3, flush_l2)
+        mt.mt_set_profiling(sim.h, True)
+        prof = {}
+        for _ in range(20):
+            sim.run(1)
+            for kn, kms in mt.mt_read_profile(sim.h):
+                prof[kn] = prof.get(kn, 0.0) + kms / 20
+        mt.mt_set_profiling(sim.h, False)
+        sim.close()
+        fused_ms = prof.get("fused_step", 0.0)
+        achieved = 48.0 * ntot / (fused_ms * 1e-3) / 1e9 if fused_ms > 0 else 0.0
+        res[name] = {"value": ntot * k / (ms * 1e-3), "ms_per_step": ms / k, "steps": k,
+                     "kernels_ms_per_step": prof,
+                     "tuned": {"cell_shift": int(best.cell_shift), "seg_target": int(best.seg_target),
+                               "resolver_cell_shift": int(auto.cell_shift),
+                               "resolver_seg_target": int(auto.seg_target),
+                               "tuned_ms_per_step": tune_ms, "tuner_seconds": tune_s},
+                     "roofline": {"bound": "hbm", "kernel": "fused_step", "achieved": achieved,
+                                  "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                                  "algo_bytes_per_launch": 48 * ntot}}
+    out.update(res["mixed"])
+    out["fp64"] = res["fp64"]
+    # the same realisations one handle at a time (each its own graph)
+    for prec, name in ((mt.MT_FP64, "sequential_fp64"), (mt.MT_MIXED, "sequential_mixed")):
+        k = 10
+        tot_ms = 0.0
+        for r in range(BATCH_R):
+            q = mt.mt_params_init(dim=1, n=int(ns[r]), L=(Ls[r],), D_mt=D, D_rw=D, dt=DT,
+                                  precision=prec, seed=2024, realisation=r, observe_cap=16)
+            sim = mt.Simulation(q, device=dev)
+            sim.upload(xs[r][None, :], As[r], Bs[r])
+            tot_ms += timed_steps(sim, k, 2)
+            sim.close()
+        out[name] = {"value": ntot * k / (tot_ms * 1e-3), "ms_per_step": tot_ms / k, "steps": k,
+                     "note": "256 single handles, one after another, 10 graph steps each"}
+    del flush
+    return out
+
+
+def precision_report(local: int, steps: int):
+    """MIXED against the FP64 GPU path on the headline workload: both run
+    `steps` steps from the same state with the same random walk (positions
+    are identical integers), then masses and the mean-A series are compared.
+    (Each path's error against the CPU oracle is asserted by the parity
+    tests: 1e-12 FP64, 1e-6 MIXED.)"""
+    import numpy as np
+    import torch
+
+    from paper_1811_05474_gb300 import mt, synth
+
+    dev = torch.device("cuda", local)
+    x = synth.uniform_positions(N, L, seed=5)
+    A0, B0 = synth.uniform_masses(N, seed=5)
+    rel = lambda g, o: float(np.max(np.abs(g - o) / np.maximum(np.abs(o), 0.5)))
+    res = {}
+    for prec, name in ((mt.MT_FP64, "fp64"), (mt.MT_MIXED, "mixed")):
+        p = mt.mt_params_init(n=N, L=(L,), v=(V, 0.0), D_mt=D, D_rw=D, dt=DT, precision=prec,
+                              seed=99, observe_cap=steps)
+        sim = mt.Simulation(p, device=dev)
+        sim.upload(x, A0, B0)
+        sim.run(steps)
+        res[name] = (sim.ticks(), *sim.masses(), sim.observables())
+        sim.close()
+    (X64, a64, b64, o64), (X32, a32, b32, o32) = res["fp64"], res["mixed"]
+    d0 = float(np.sum(A0 - B0))
+    return {"workload": WORKLOAD, "steps": steps,
+            "relative_to": "max(|m_fp64|, 0.5) per particle (0.5 = mean initial mass)",
+            "positions_identical": bool(np.array_equal(X64, X32)),
+            "mixed_vs_fp64_max_rel_err_A": rel(a32, a64),
+            "mixed_vs_fp64_max_rel_err_B": rel(b32, b64),
+            "mean_A_series_max_abs_diff": float(np.max(np.abs(o32[:, 3] - o64[:, 3]))),
+            "mean_A_last": {"mixed": float(o32[-1, 3]), "fp64": float(o64[-1, 3])},
+            "sum_A_minus_B_drift": {"mixed": float(abs(o32[-1, 2] - d0)),
+                                    "fp64": float(abs(o64[-1, 2] - d0)),
+                                    "sum_A_plus_B_initial": float(np.sum(A0 + B0))}}
 
 
 def load_peaks():
@@ -401,12 +564,19 @@ def main():
     if not args.no_fp64 and args.precision == "mixed":
         k64 = max(10, min(args.steps, 200))
         r64 = gpu_run(args, "fp64", k64, 3, local, rank, None)
-        dom = max(r64["kernels"], key=lambda k: k["ms"])
+        dom = max(r64["kernels"], key=lambda k: k["ms_per_step"])
         fp64 = {"value": N * k64 / (r64["total_ms"] * 1e-3), "unit": "particle-steps/s",
                 "ms_per_step": r64["total_ms"] / k64, "steps": k64,
                 "dominant_kernel": dom["name"], "dominant_ms": dom["ms"],
                 "bound": "alu (binary64 pipe)"}
     e2e = e2e_run(args.steps, local, rank)
+    peak, peak_kind = load_peaks()
+    batched = None
+    if not args.no_batch and rank == 0:
+        batched = batch_run(local, args.steps, peak)
+    precision = None
+    if not args.no_precision and rank == 0:
+        precision = precision_report(local, args.steps)
     if ws > 1:
         t = torch.tensor([e2e["value"]], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MIN)
@@ -421,11 +591,10 @@ def main():
     value = ws * N * K / (total_ms * 1e-3)
     ms_step = total_ms / K
     kernels = main_run["kernels"]
-    ksum = sum(k["ms"] for k in kernels)
+    ksum = sum(k["ms_per_step"] for k in kernels)
     for k in kernels:
-        k["share"] = k["ms"] / ksum if ksum else None
-    dom = max(kernels, key=lambda k: k["ms"])
-    peak, peak_kind = load_peaks()
+        k["share"] = k["ms_per_step"] / ksum if ksum else None
+    dom = max(kernels, key=lambda k: k["ms_per_step"])
     dom_bytes = ALGO_BYTES.get(dom["name"], 0) * N
     achieved = dom_bytes / (dom["ms"] * 1e-3) / 1e9 if dom["ms"] > 0 else 0.0
     step_bytes = ALGO_BYTES["step"] * N
@@ -458,11 +627,13 @@ def main():
         "path_roofline": {"bound": "hbm", "achieved": path_achieved, "peak": peak, "unit": "GB/s",
                           "frac": path_achieved / peak, "algo_bytes_per_step": step_bytes},
         "kernels": kernels,
-        "gpu_launches": K * main_run["launches_per_step"],
+        "gpu_launches": int(round(K * main_run["launches_per_step"])),
         "clocks": clocks,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "fp64": fp64,
+        "batched": batched,
+        "precision": precision,
         "mean_A_last_step": main_run["mean_A_last"],
     }
     print(json.dumps(line), flush=True)

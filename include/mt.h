@@ -152,6 +152,25 @@ mt_status mt_batch_workspace_bytes(const mt_params* p, const mt_batch* b, size_t
 mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace,
                           size_t workspace_bytes, void* stream, mt_handle** out);
 
+/* Autotuner for the 1-d cell path: times `steps` steps (after `warmup`
+ * steps, the first of which captures the CUDA graph) of each candidate cell
+ * width (cell_shift c - 1 .. c + 2 around the resolver's choice c) and
+ * segment size (seg_target: the resolver's choice, 256, 512, 1024) on the
+ * inputs x, A, B (as mt_upload takes them) and returns in *best the resolved
+ * parameters of the fastest, and its time per step in *best_ms (may be
+ * NULL).  b may be NULL (one system).  The candidates run one after another
+ * on workspace (device, >= mt_autotune_workspace_bytes to try them all;
+ * candidates that do not fit are skipped) and stream; the caller's arrays
+ * are only read, and the workspace holds no usable state afterwards.  Other
+ * parameter sets (2-d, brute force) have a single candidate.  Not part of
+ * the paper: the cell list replaces its KD-tree, and this picks the list's
+ * cell width and the kernel's tiling. */
+mt_status mt_autotune_workspace_bytes(const mt_params* p, const mt_batch* b, size_t* bytes);
+mt_status mt_autotune(const mt_params* p, const mt_batch* b, const double* x, const double* A,
+                      const double* B, int32_t mem, void* workspace, size_t workspace_bytes,
+                      void* stream, int32_t warmup, int32_t steps, mt_params* best,
+                      float* best_ms);
+
 /* Load the state: x (dim*n doubles, axis-major, each in [0, L_d]), A and B
  * (n doubles each).  mem says whether the three pointers are host or device
  * memory.  Positions are rounded to the grid (X = rint(x 2^k)).  Resets the

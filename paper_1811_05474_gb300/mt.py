@@ -110,6 +110,9 @@ def lib(path: Path | None = None):
         "mt_batch_resolve": [P, BP, P],
         "mt_batch_workspace_bytes": [P, BP, ctypes.POINTER(ctypes.c_size_t)],
         "mt_batch_create": [P, BP, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(H)],
+        "mt_autotune_workspace_bytes": [P, BP, ctypes.POINTER(ctypes.c_size_t)],
+        "mt_autotune": [P, BP, _vp, _vp, _vp, i32, _vp, ctypes.c_size_t, _vp, i32, i32, P,
+                        ctypes.POINTER(ctypes.c_float)],
         "mt_upload": [H, _vp, _vp, _vp, i32],
         "mt_set_noise": [H, _vp],
         "mt_step": [H],
@@ -206,6 +209,43 @@ def mt_batch_create(p: mt_params, b: mt_batch | None, workspace_ptr: int, worksp
     check(lib().mt_batch_create(ctypes.byref(p), _bref(b), workspace_ptr, workspace_bytes,
                                 stream_ptr or None, ctypes.byref(h)))
     return h
+
+
+def mt_autotune_workspace_bytes(p: mt_params, b: mt_batch | None) -> int:
+    n = ctypes.c_size_t(0)
+    check(lib().mt_autotune_workspace_bytes(ctypes.byref(p), _bref(b), ctypes.byref(n)))
+    return int(n.value)
+
+
+def mt_autotune(p: mt_params, b: mt_batch | None, x_ptr, A_ptr, B_ptr, mem: int,
+                workspace_ptr: int, workspace_bytes: int, stream_ptr, warmup: int, steps: int):
+    """Returns (best resolved mt_params, ms per step)."""
+    best = mt_params()
+    ms = ctypes.c_float(0.0)
+    check(lib().mt_autotune(ctypes.byref(p), _bref(b), x_ptr, A_ptr, B_ptr, mem, workspace_ptr,
+                            workspace_bytes, stream_ptr or None, warmup, steps, ctypes.byref(best),
+                            ctypes.byref(ms)))
+    return best, float(ms.value)
+
+
+def autotune(params: mt_params, x, A, B, batch: mt_batch | None = None, warmup: int = 3,
+             steps: int = 10, device="cuda"):
+    """mt_autotune on host arrays with a torch-allocated workspace and
+    stream; returns (best params, ms per step)."""
+    import torch
+
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    nbytes = mt_autotune_workspace_bytes(params, batch)
+    ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+    stream = torch.cuda.Stream(device=device)
+    try:
+        return mt_autotune(params, batch, _ptr(x), _ptr(A), _ptr(B), MT_MEM_HOST, ws.data_ptr(),
+                           ws.numel(), stream.cuda_stream, warmup, steps)
+    finally:
+        stream.synchronize()
+        del ws
 
 
 def mt_upload(h, x_ptr, A_ptr, B_ptr, mem: int) -> None:

@@ -204,3 +204,37 @@ def test_batch_of_256_log_uniform_realisations_invariants():
     for r in range(256):
         np.testing.assert_allclose(obs[-1, r, 0], ga[r].sum(), rtol=1e-9)
         np.testing.assert_allclose(obs[-1, r, 3], ga[r].mean(), rtol=1e-9)
+
+
+def test_autotune_picks_a_candidate_and_results_do_not_depend_on_it():
+    """The tuner returns a resolved parameter set from its candidate list;
+    the cell width and segment size change the schedule, not the results
+    (positions bit for bit, masses to the tolerance)."""
+    ns = synth.ensemble_sizes(16, 1e3, 2e4, seed0=40)
+    Ls = [float(n) for n in ns]
+    xs, As, Bs = batch_inputs(ns, Ls, seed=41)
+    b = mt.make_batch(ns, Ls)
+    p = batch_params(mt.MT_MIXED, observe_cap=4)
+    x, A, B = np.concatenate(xs)[None, :], np.concatenate(As), np.concatenate(Bs)
+    best, ms = mt.autotune(p, x, A, B, batch=b, warmup=2, steps=4)
+    assert ms > 0.0
+    auto = mt.mt_batch_resolve(p, b)
+    assert abs(best.cell_shift - auto.cell_shift) <= 2 and 16 <= best.seg_target <= 1024
+    out = []
+    for q in (auto, best):
+        sim = mt.Simulation(q, batch=b)
+        sim.upload(x, A, B)
+        sim.run(6)
+        out.append((sim.ticks(), *sim.masses()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert_masses(out[1][1], out[0][1], 1e-6)
+    assert_masses(out[1][2], out[0][2], 1e-6)
+
+
+def test_autotune_single_system():
+    n = 50000
+    x = synth.uniform_positions(n, float(n), seed=50)
+    A, B = synth.uniform_masses(n, seed=50)
+    p = mt.mt_params_init(n=n, L=(float(n),), precision=mt.MT_MIXED)
+    best, ms = mt.autotune(p, x, A, B, warmup=2, steps=3)
+    assert ms > 0.0 and best.n == n and best.seg_target > 0

@@ -441,3 +441,35 @@ def test_fused_dense_bins_sorted_in_place(cluster, tiers):
     mt.mt_set_profiling(sim.h, True)
     sim.step()
     assert [k for k, _ in mt.mt_read_profile(sim.h)] == tiers
+
+
+@pytest.mark.parametrize("precision", [mt.MT_FP64, mt.MT_MIXED])
+def test_workload2_n1e5_1000_steps_oracle_on_strided_steps(precision):
+    """N = 1e5 uniform on [0, 1e5], no advection, 1000 steps on the built-in
+    generator; every 100th step is taken from the GPU's own state with
+    injected noise on both sides and checked against one oracle step from
+    that identical state (positions bit for bit, masses to the tolerance)."""
+    n, L = 100000, 1e5
+    x = synth.uniform_positions(n, L, seed=0)
+    A, B = synth.uniform_masses(n, seed=0)
+    sim = make(n, L, precision=precision, observe_cap=1000)
+    po = oracle_params(sim)
+    sim.upload(x, A, B)
+    tol = TOL[precision]
+    for block in range(10):
+        sim.run(99)
+        X = sim.ticks()
+        a, b = sim.masses()
+        xi = synth.normals(1, 1, n, seed=700 + block)[0]
+        sim.set_noise(xi)
+        sim.step()
+        sim.set_noise(None)
+        Xo, ao, bo = O.step(po, X, xi, a, b)
+        assert np.array_equal(sim.ticks(), Xo), f"positions at step {100 * block + 99}"
+        ga, gb = sim.masses()
+        assert_masses(ga, ao, tol, f"A at step {100 * block + 99}")
+        assert_masses(gb, bo, tol, f"B at step {100 * block + 99}")
+    assert sim.steps_done() == 1000
+    obs = sim.observables()
+    assert obs.shape == (1000, 4)
+    np.testing.assert_allclose(obs[-1, 2], np.sum(A - B), rtol=0, atol=1e-10 * np.sum(A + B))
