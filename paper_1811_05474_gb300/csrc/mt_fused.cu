@@ -80,9 +80,9 @@ enum : int { kSegOk = 0, kSegCapacity = 1, kSegDense = 2, kSegHeavy = 3 };
 // A segment whose sum over bins of (particles per bin)^2 exceeds this is
 // pair-heavy (a dense cluster, e.g. particles piled against a wall): the
 // first tier hands it to the second, which splits its exchange across
-// kSlices CTAs so that its O(n^2) work does not sit on one SM.
+// the CTAs of a thread-block cluster so that its O(n^2) work does not sit
+// on one SM.
 constexpr int kHeavyWork = 16384;
-constexpr int kSlices = kFusedSlices;
 constexpr int kWalk = 32;  // neighbours per side a thread walks before a warp takes over
 
 // First index q in [0, m) with a[q] >= key (a sorted ascending).
@@ -96,6 +96,13 @@ __device__ __forceinline__ int lower_at_least(const long long* a, int m, long lo
       hi = mid;
   }
   return lo;
+}
+
+// More than kWalk neighbours on a side of sorted slot j: the (kWalk + 1)-th
+// slot to the left or right is within S.
+__device__ __forceinline__ bool dense_at(const long long* sx, int m, int j, long long x,
+                                         long long S) {
+  return (j > kWalk && x - sx[j - kWalk - 1] <= S) || (j + kWalk + 1 < m && sx[j + kWalk + 1] - x <= S);
 }
 
 // The per-segment scalars read from the previous step's boundaries and cell
@@ -320,13 +327,67 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
     }
   }
   __syncthreads();
-  // Dense bins: in-place bitonic sort of the bin's records by the whole CTA,
-  // every comparator ascending (partner i ^ (2j - 1) first in each merge) so
-  // any length sorts.
+  // Dense bins, sorted by the whole CTA.  Up to kRankMax records: each
+  // record's rank is the number of smaller (x, id) keys in the bin, packed
+  // into 64 bits as (x - bin start) << 31 | id (bins are at most 2^32 ticks
+  // wide here), then every record moves to its rank.  Larger bins: in-place
+  // bitonic sort, every comparator ascending (partner i ^ (2j - 1) first in
+  // each merge) so any length sorts.
   if (active) {
     const int nbig = s_nbig < kBigMax ? s_nbig : kBigMax;
+    // the scatter cursors are free now: they hold the packed keys
+    unsigned long long* key = reinterpret_cast<unsigned long long*>(
+        (reinterpret_cast<uintptr_t>(bcur) + 7) & ~static_cast<uintptr_t>(7));
+    constexpr int kRankMax = NB / 2 - 1;
+    constexpr int E = (kRankMax + NT - 1) / NT;  // records per thread
     for (int t = 0; t < nbig; ++t) {
       const int lo = bstart[s_big[t]], len = bstart[s_big[t] + 1] - lo;
+      if (len <= kRankMax && sh2 <= 32) {
+        const long long blo = wlo + ((long long)s_big[t] << sh2);
+        for (int i = tid; i < len; i += NT)
+          key[i] = ((unsigned long long)(sx[lo + i] - blo) << 31) | (unsigned int)sid[lo + i];
+        __syncthreads();
+        unsigned long long mk[E];
+        int rk[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = tid + e * NT;
+          mk[e] = i < len ? key[i] : ~0ULL;
+          rk[e] = 0;
+        }
+#pragma unroll 4
+        for (int q = 0; q < len; ++q) {
+          const unsigned long long kq = key[q];
+#pragma unroll
+          for (int e = 0; e < E; ++e) rk[e] += kq < mk[e] ? 1 : 0;
+        }
+        long long vx[E];
+        int vid[E];
+        unsigned long long va[E], vb[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = lo + tid + e * NT;
+          if (tid + e * NT < len) {
+            vx[e] = sx[i];
+            vid[e] = sid[i];
+            va[e] = sA[i];
+            vb[e] = sB[i];
+          }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          if (tid + e * NT < len) {
+            const int to = lo + rk[e];
+            sx[to] = vx[e];
+            sid[to] = vid[e];
+            sA[to] = va[e];
+            sB[to] = vb[e];
+          }
+        }
+        __syncthreads();
+        continue;
+      }
       int np2 = 1;
       while (np2 < len) np2 <<= 1;
       for (int mm = 2; mm <= np2; mm <<= 1) {
@@ -374,27 +435,17 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
       if (j >= m) break;
       const long long x = sx[j];
       if (x < xlo - S || x >= xhi + S) continue;  // not a neighbour of an own particle
-      T r = T(1);
-      int q = j - 1, k = 0;
-      for (; q >= 0 && k < kWalk && x - sx[q] <= S; --q, ++k) r += W::near(d, x - sx[q]);
-      bool dense = k == kWalk && q >= 0 && x - sx[q] <= S;
-      if (!dense) {
-        q = j + 1;
-        k = 0;
-        for (; q < m && k < kWalk && sx[q] - x <= S; ++q, ++k) r += W::near(d, sx[q] - x);
-        dense = k == kWalk && q < m && sx[q] - x <= S;
-      }
-      if (dense) {
+      if (dense_at(sx, m, j, x, S)) {
         const int at = atomicAdd(&s_nd, 1);
         if (at < NB) {
           dlist[at] = j;
           continue;
         }
-        // list full: finish on this thread
-        r = T(1);
-        for (q = j - 1; q >= 0 && x - sx[q] <= S; --q) r += W::near(d, x - sx[q]);
-        for (q = j + 1; q < m && sx[q] - x <= S; ++q) r += W::near(d, sx[q] - x);
       }
+      // at most kWalk neighbours a side (or the dense list is full)
+      T r = T(1);
+      for (int q = j - 1; q >= 0 && x - sx[q] <= S; --q) r += W::near(d, x - sx[q]);
+      for (int q = j + 1; q < m && sx[q] - x <= S; ++q) r += W::near(d, sx[q] - x);
       sr[j] = MIX ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
     }
   }
@@ -440,45 +491,24 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
     for (int j = w0 + slice + tid * nslice; j < w1; j += NT * nslice) {
       const long long x = sx[j];
       const T ip = sr[j];
-      MV A = MS::load(sA, j), B = MS::load(sB, j);
-      typename MS::Acc dA{}, dB{};
-      int q = j - 1, k = 0;
-      for (; q >= 0 && k < kWalk; --q, ++k) {
-        const long long D = x - sx[q];
-        if (D > S) break;
-        const T P = normalised<T>(d.norm, W::near(d, D), ip, sr[q]);
-        MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
-        MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
-      }
-      bool dense = k == kWalk && q >= 0 && x - sx[q] <= S;
-      if (!dense) {
-        for (q = j + 1, k = 0; q < m && k < kWalk; ++q, ++k) {
-          const long long D = sx[q] - x;
-          if (D > S) break;
-          const T P = normalised<T>(d.norm, W::near(d, D), ip, sr[q]);
-          MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
-          MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
-        }
-        dense = k == kWalk && q < m && sx[q] - x <= S;
-      }
-      if (dense) {
+      if (dense_at(sx, m, j, x, S)) {
         const int at = atomicAdd(&s_nd2, 1);
         if (at < NB) {
           dlist[at] = j;  // a warp does it below
           continue;
         }
-        dA = typename MS::Acc{};
-        dB = typename MS::Acc{};
-        for (q = j - 1; q >= 0 && x - sx[q] <= S; --q) {
-          const T P = normalised<T>(d.norm, W::near(d, x - sx[q]), ip, sr[q]);
-          MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
-          MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
-        }
-        for (q = j + 1; q < m && sx[q] - x <= S; ++q) {
-          const T P = normalised<T>(d.norm, W::near(d, sx[q] - x), ip, sr[q]);
-          MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
-          MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
-        }
+      }
+      MV A = MS::load(sA, j), B = MS::load(sB, j);
+      typename MS::Acc dA{}, dB{};
+      for (int q = j - 1; q >= 0 && x - sx[q] <= S; --q) {
+        const T P = normalised<T>(d.norm, W::near(d, x - sx[q]), ip, sr[q]);
+        MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
+        MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
+      }
+      for (int q = j + 1; q < m && sx[q] - x <= S; ++q) {
+        const T P = normalised<T>(d.norm, W::near(d, sx[q] - x), ip, sr[q]);
+        MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
+        MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
       }
       MS::update(A, B, dA, dB, d.react);
       const long long o = out0 + (j - w0);
@@ -574,9 +604,10 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
         CBn[s2] = (int)((sx[w0 + (q - out0)] >> wsh) + 1);
     }
   }
-  // per-segment observables in the precision's own arithmetic: warp shuffles,
-  // then the warp totals in a fixed order (zero for a segment this tier could
-  // not take)
+  // per-segment observables in the precision's own arithmetic: warp
+  // shuffles, then the warp totals and (second tier) the cluster's CTA
+  // totals in fixed shuffle trees (zero for a segment this tier could not
+  // take)
   if (d.observe_cap > 0) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -591,30 +622,56 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
     }
     __syncthreads();
     __shared__ MV s_seg[3];
-    if (tid == 0) {
-      MV ta = s_red[0][0], tb = s_red[1][0], td = s_red[2][0];
-      for (int w = 1; w < NT / 32; ++w) {
-        ta = obs_add(ta, s_red[0][w]);
-        tb = obs_add(tb, s_red[1][w]);
-        td = obs_add(td, s_red[2][w]);
+    if (warp == 0) {
+      static_assert(NT / 32 <= 32, "one warp reduces the warp totals");
+      MV ta{}, tb{}, td{};
+      if (lane < NT / 32) {
+        ta = s_red[0][lane];
+        tb = s_red[1][lane];
+        td = s_red[2][lane];
       }
-      s_seg[0] = ta;
-      s_seg[1] = tb;
-      s_seg[2] = td;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ta = obs_add(ta, obs_shfl(ta, o));
+        tb = obs_add(tb, obs_shfl(tb, o));
+        td = obs_add(td, obs_shfl(td, o));
+      }
+      if (lane == 0) {
+        s_seg[0] = ta;
+        s_seg[1] = tb;
+        s_seg[2] = td;
+      }
     }
     if constexpr (CL > 1) {
       // the cluster's CTAs hold the sums of their own slices: the first one
-      // adds them in rank order (distributed shared memory)
+      // gathers them (distributed shared memory, one lane per CTA)
+      static_assert(CL <= 32, "one warp gathers the cluster");
       cg::cluster_group cl = cg::this_cluster();
       cl.sync();
-      if (slice == 0 && tid == 0) {
-        for (int k = 0; k < 3; ++k) {
-          MV t = s_seg[k];
-          for (int rk = 1; rk < CL; ++rk) t = obs_add(t, *cl.map_shared_rank(&s_seg[k], rk));
-          s_seg[k] = t;
+      if (slice == 0 && warp == 0) {
+        MV ta{}, tb{}, td{};
+        if (lane < CL) {
+          const MV* peer = cl.map_shared_rank(&s_seg[0], lane);
+          ta = peer[0];
+          tb = peer[1];
+          td = peer[2];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          ta = obs_add(ta, obs_shfl(ta, o));
+          tb = obs_add(tb, obs_shfl(tb, o));
+          td = obs_add(td, obs_shfl(td, o));
+        }
+        __syncwarp();
+        if (lane == 0) {
+          s_seg[0] = ta;
+          s_seg[1] = tb;
+          s_seg[2] = td;
         }
       }
       cl.sync();
+    } else {
+      __syncthreads();
     }
     if (tid == 0 && slice == 0) {
       MV* part = reinterpret_cast<MV*>(d.partials);  // one 8-byte slot each
@@ -662,15 +719,21 @@ __device__ void reduce_realisation(const Dev& d, int r) {
     s_tot[warp][2] = td;
   }
   __syncthreads();
-  if (tid == 0) {
-    ta = s_tot[0][0];
-    tb = s_tot[0][1];
-    td = s_tot[0][2];
-    for (int w = 1; w < NT / 32; ++w) {
-      ta = obs_add(ta, s_tot[w][0]);
-      tb = obs_add(tb, s_tot[w][1]);
-      td = obs_add(td, s_tot[w][2]);
+  if (warp == 0) {
+    ta = tb = td = MV{};
+    if (lane < NT / 32) {
+      ta = s_tot[lane][0];
+      tb = s_tot[lane][1];
+      td = s_tot[lane][2];
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ta = obs_add(ta, obs_shfl(ta, o));
+      tb = obs_add(tb, obs_shfl(tb, o));
+      td = obs_add(td, obs_shfl(td, o));
+    }
+  }
+  if (tid == 0) {
     const long long row = (long long)(c->step % (unsigned long long)d.observe_cap);
     double* o = d.obs + 4 * (row * d.nreal + r);
     const double sa = obs_double(ta);
@@ -755,12 +818,13 @@ __global__ void __launch_bounds__(Fast::kT, 3) k_step1d(Dev d, cudaGraphConditio
 }
 
 // Second tier: the queued segments with larger staging.  Each segment is
-// taken by one thread-block cluster of kSlices CTAs (on kSlices SMs): all
-// stage and sort it, each forms the row sums of every kSlices-th particle
-// (shared through distributed shared memory) and the exchange of every
-// kSlices-th own particle.  Clusters loop over the queue.
-template <bool MIX>
-__global__ void __cluster_dims__(kSlices, 1, 1) __launch_bounds__(Big::kT, 1)
+// taken by one thread-block cluster of CL CTAs (on CL SMs; 16 where the
+// device can co-schedule a cluster that large, else 8): all stage and sort
+// it, each forms the row sums of every CL-th particle (shared through
+// distributed shared memory) and the exchange of every CL-th own particle.
+// Clusters loop over the queue.
+template <bool MIX, int CL>
+__global__ void __launch_bounds__(Big::kT, 1)
     k_step1d_big(Dev d, cudaGraphConditionalHandle cond, int use_cond) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ bool s_last;
@@ -768,12 +832,12 @@ __global__ void __cluster_dims__(kSlices, 1, 1) __launch_bounds__(Big::kT, 1)
   const int nov = c->nov;
   const int sc = c->scur;
   const long long Dc = (c->dmax >> d.cshift) + 2;
-  const int rank = blockIdx.x % kSlices, cid = blockIdx.x / kSlices;
-  const int ncl = gridDim.x / kSlices;
+  const int rank = blockIdx.x % CL, cid = blockIdx.x / CL;
+  const int ncl = gridDim.x / CL;
   for (int q = cid; q < nov; q += ncl) {
     const int seg = d.ovlist[q];
-    const int st = fused_segment<MIX, Big, kSlices>(d, seg, smem, load_seg(d, sc, Dc, seg), rank,
-                                                    kSlices, false);
+    const int st =
+        fused_segment<MIX, Big, CL>(d, seg, smem, load_seg(d, sc, Dc, seg), rank, CL, false);
     if (st == kSegOk) {
       if (rank == 0) complete_segment<MIX, Big::kT>(d, seg);
     } else if (threadIdx.x == 0 && atomicExch(&c->overflow, 1) == 0) {
@@ -879,6 +943,41 @@ __global__ void k_noise_bound(Dev d, const float* xi, long long count) {
 
 __global__ void k_set_dmax(Dev d, long long v) { d.ctrl->dmax = v; }
 
+// Cluster size of the second tier: 16 if a 16-CTA cluster of it can be
+// resident (non-portable size), else 8.
+static int g_big_cluster = 8;
+
+template <bool MIX, int CL>
+static cudaError_t configure_big(int precision) {
+  auto k = k_step1d_big<MIX, CL>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tier_smem<Big>(precision));
+  if (e == cudaSuccess && CL > 8)
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+template <bool MIX, int CL>
+static int max_active_clusters(int precision) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(CL * 8);
+  cfg.blockDim = dim3(Big::kT);
+  cfg.dynamicSmemBytes = tier_smem<Big>(precision);
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_step1d_big<MIX, CL>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
 cudaError_t fused_configure() {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_step1d<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -887,11 +986,15 @@ cudaError_t fused_configure() {
   if ((e = cudaFuncSetAttribute(k_step1d<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)tier_smem<Fast>(MT_FP64))) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(k_step1d_big<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)tier_smem<Big>(MT_MIXED))) != cudaSuccess)
-    return e;
-  return cudaFuncSetAttribute(k_step1d_big<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tier_smem<Big>(MT_FP64));
+  if ((e = configure_big<true, 8>(MT_MIXED)) != cudaSuccess) return e;
+  if ((e = configure_big<false, 8>(MT_FP64)) != cudaSuccess) return e;
+  g_big_cluster = 8;
+  if (configure_big<true, 16>(MT_MIXED) == cudaSuccess &&
+      configure_big<false, 16>(MT_FP64) == cudaSuccess &&
+      max_active_clusters<true, 16>(MT_MIXED) >= 1 && max_active_clusters<false, 16>(MT_FP64) >= 1)
+    g_big_cluster = 16;
+  cudaGetLastError();  // a refused non-portable size leaves the 8-CTA choice
+  return cudaSuccess;
 }
 
 cudaError_t launch_fused_step(const Dev& d, int precision, cudaGraphConditionalHandle cond,
@@ -905,18 +1008,33 @@ cudaError_t launch_fused_step(const Dev& d, int precision, cudaGraphConditionalH
   return cudaGetLastError();
 }
 
+template <bool MIX, int CL>
+static cudaError_t launch_big(const Dev& d, int precision, cudaGraphConditionalHandle cond,
+                              int use_cond, cudaStream_t s) {
+  // up to 8 clusters, fewer if there are fewer segments
+  const int clusters = d.nseg < 8 ? d.nseg : 8;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned int)(clusters * CL));
+  cfg.blockDim = dim3(Big::kT);
+  cfg.dynamicSmemBytes = tier_smem<Big>(precision);
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_step1d_big<MIX, CL>, d, cond, use_cond);
+}
+
 cudaError_t launch_fused_big(const Dev& d, int precision, cudaGraphConditionalHandle cond,
                              int use_cond, cudaStream_t s) {
-  const size_t sm = tier_smem<Big>(precision);
-  // up to 16 clusters (two per GPC fit at one CTA per SM), fewer if there
-  // are fewer segments
-  const int clusters = d.nseg < 16 ? d.nseg : 16;
-  const unsigned int g = (unsigned int)(clusters * kSlices);
-  if (precision == MT_MIXED)
-    k_step1d_big<true><<<g, Big::kT, sm, s>>>(d, cond, use_cond);
-  else
-    k_step1d_big<false><<<g, Big::kT, sm, s>>>(d, cond, use_cond);
-  return cudaGetLastError();
+  if (g_big_cluster == 16)
+    return precision == MT_MIXED ? launch_big<true, 16>(d, precision, cond, use_cond, s)
+                                 : launch_big<false, 16>(d, precision, cond, use_cond, s);
+  return precision == MT_MIXED ? launch_big<true, 8>(d, precision, cond, use_cond, s)
+                               : launch_big<false, 8>(d, precision, cond, use_cond, s);
 }
 
 cudaError_t launch_fused_prep(const Dev& d, int flip, cudaStream_t s) {
