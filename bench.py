@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--n", type=int, default=N, help="particles (profiling mode only)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble object")
     ap.add_argument("--no-precision", action="store_true", help="skip the precision report")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving object")
+    ap.add_argument("--serve-requests", type=int, default=64, help="requests in the serving run")
     return ap.parse_args()
 
 
@@ -434,6 +436,64 @@ def batch_run(local: int, steps: int, peak: float):
     return out
 
 
+SERVE_WORKLOAD = "poisson_200_per_s_N_loguniform_1e3_1e6_d1_or_2_steps_100_1000_mixed"
+
+
+def serve_run(local: int, count: int, pool_gb: float = 8.0, max_active: int = 16,
+              chunk_steps: int = 25):
+    """The serving form: `count` requests with Poisson arrivals (200/s),
+    N log-uniform in [1e3, 1e6], d in {1, 2} (2-d on [0, sqrt(N) 10]^2),
+    100 to 1000 steps, MIXED, submitted at their arrival times to an
+    mt_server with a `pool_gb` device pool; host arrays in, host results out.
+    Step latency: per resident chunk, its CUDA-event time / its steps."""
+    import numpy as np
+    import torch
+
+    from paper_1811_05474_gb300 import mt, synth
+
+    torch.cuda.set_device(local)
+    reqs = synth.poisson_requests(count, rate=200.0, seed=0)
+    inputs = []
+    for r in reqs:
+        L = (float(np.sqrt(r["n"]) * 10.0),) * 2 if r["dim"] == 2 else (float(r["n"]),)
+        p = mt.mt_params_init(dim=r["dim"], n=r["n"], L=L, D_mt=D, D_rw=D, dt=DT,
+                              precision=mt.MT_MIXED, seed=r["seed"], observe_cap=1)
+        x = synth.uniform_positions(r["n"], L if r["dim"] == 2 else L[0], dim=r["dim"],
+                                    seed=r["seed"])
+        A, B = synth.uniform_masses(r["n"], seed=r["seed"])
+        inputs.append((p, x, A, B, r["steps"]))
+    srv = mt.Server(pool_bytes=int(pool_gb * 2 ** 30), max_active=max_active,
+                    chunk_steps=chunk_steps, device=torch.device("cuda", local))
+    ids = []
+    t0 = time.perf_counter()
+    for r, (p, x, A, B, steps) in zip(reqs, inputs):
+        while time.perf_counter() - t0 < r["t"]:
+            srv.poll()
+        ids.append(srv.submit(p, x, A, B, steps))
+        srv.poll()
+    srv.drain()
+    wall = time.perf_counter() - t0
+    st, step_ms = srv.stats()
+    infos = [srv.info(i) for i in ids]
+    lat = np.array([i.t_done - i.t_submit for i in infos])
+    wait = np.array([i.t_admit - i.t_submit for i in infos])
+    work = sum(r["n"] * r["steps"] for r in reqs)
+    span = max(i.t_done for i in infos) - min(i.t_submit for i in infos)
+    srv.close()
+    pct = lambda a, q: float(np.percentile(a, q))
+    return {"workload": SERVE_WORKLOAD, "requests": count,
+            "requests_1d": sum(1 for r in reqs if r["dim"] == 1),
+            "requests_2d": sum(1 for r in reqs if r["dim"] == 2),
+            "arrival_span_s": reqs[-1]["t"], "pool_bytes": int(pool_gb * 2 ** 30),
+            "max_active": max_active, "chunk_steps": chunk_steps, "admission": "first fit, backfill",
+            "done": int(st.done), "failed": int(st.failed),
+            "p50_step_ms": pct(step_ms, 50), "p99_step_ms": pct(step_ms, 99),
+            "p50_request_s": pct(lat, 50), "p99_request_s": pct(lat, 99),
+            "p50_queue_s": pct(wait, 50), "p99_queue_s": pct(wait, 99),
+            "particle_steps_per_s": work / span, "requests_per_s": count / span,
+            "makespan_s": span, "wall_s": wall, "pool_peak_bytes": int(st.pool_peak)}
+
+
 def precision_report(local: int, steps: int):
     """MIXED against the FP64 GPU path on the headline workload: both run
     `steps` steps from the same state with the same random walk (positions
@@ -577,6 +637,9 @@ def main():
     precision = None
     if not args.no_precision and rank == 0:
         precision = precision_report(local, args.steps)
+    serving = None
+    if not args.no_serve and rank == 0:
+        serving = serve_run(local, args.serve_requests)
     if ws > 1:
         t = torch.tensor([e2e["value"]], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MIN)
@@ -633,6 +696,7 @@ def main():
         "cpu_baseline": cpu,
         "fp64": fp64,
         "batched": batched,
+        "serving": serving,
         "precision": precision,
         "mean_A_last_step": main_run["mean_A_last"],
     }

@@ -171,6 +171,83 @@ mt_status mt_autotune(const mt_params* p, const mt_batch* b, const double* x, co
                       void* stream, int32_t warmup, int32_t steps, mt_params* best,
                       float* best_ms);
 
+/* ---- Serving ----------------------------------------------------------
+ * A request server: simulations of different sizes and dimensions are
+ * submitted over time (host arrays, copied at submission) and each is
+ * admitted when a slot and room in the device pool are free (its footprint
+ * is its workspace size).  Resident requests keep their state on the device
+ * and are advanced in chunks of graph-replayed steps, each on its own
+ * stream, so their work overlaps on the device; finished requests free
+ * their slot and memory for the next.  Each request computes exactly what
+ * a single handle with its parameters computes.  Not part of the paper. */
+typedef struct mt_server mt_server;
+
+enum { MT_REQ_QUEUED = 0, MT_REQ_RUNNING = 1, MT_REQ_DONE = 2, MT_REQ_FAILED = 3 };
+
+typedef struct mt_server_config {
+  int32_t max_active;   /* requests resident at once (streams), 1 .. 1024 */
+  int32_t chunk_steps;  /* steps a resident request runs per round, >= 1 */
+  int32_t backfill;     /* 1: admit a later request while the oldest waits
+                           for memory; 0: strict arrival order */
+  int32_t reserved;     /* 0 */
+} mt_server_config;
+
+typedef struct mt_request_info {
+  int32_t state;        /* MT_REQ_* */
+  int32_t status;       /* mt_status of a failed request */
+  int64_t steps_done;
+  double t_submit;      /* seconds since mt_server_create */
+  double t_admit;
+  double t_done;
+  double gpu_ms;        /* sum of its chunks' times (CUDA events) */
+  size_t footprint;     /* device bytes it holds while resident */
+} mt_request_info;
+
+typedef struct mt_server_summary {
+  int64_t queued, running, done, failed;
+  size_t pool_used;     /* device bytes held now */
+  size_t pool_peak;     /* most device bytes held at once */
+  int64_t step_samples; /* finished chunks (one step-latency sample each) */
+} mt_server_summary;
+
+/* Device bytes a request with params p holds while resident. */
+mt_status mt_server_footprint(const mt_params* p, size_t* bytes);
+
+/* pool: device memory (256-byte aligned) of pool_bytes, the HBM budget for
+ * resident requests; owned by the caller, used until mt_server_destroy. */
+mt_status mt_server_create(const mt_server_config* cfg, void* pool, size_t pool_bytes,
+                           mt_server** out);
+
+/* Queue a request: params p, host arrays x (dim*n), A, B (n), steps to run.
+ * *id receives its identifier.  A request whose footprint exceeds the whole
+ * pool is refused (MT_ERR_WORKSPACE). */
+mt_status mt_server_submit(mt_server* s, const mt_params* p, const double* x, const double* A,
+                           const double* B, int64_t steps, int64_t* id);
+
+/* One scheduling round (retire finished chunks, enqueue next chunks, admit
+ * queued requests); does not wait for running work.  *queued and *running
+ * (may be NULL) receive the counts after the round. */
+mt_status mt_server_poll(mt_server* s, int32_t* queued, int32_t* running);
+
+mt_status mt_server_info(const mt_server* s, int64_t id, mt_request_info* info);
+
+/* Results of a finished request: masses (n each, the caller's order, host)
+ * and up to cap observables rows (4 doubles each, the last ones; may be NULL
+ * when cap = 0); *rows (may be NULL) receives the rows written. */
+mt_status mt_server_result(const mt_server* s, int64_t id, double* A, double* B,
+                           double* observables, int64_t cap, int64_t* rows);
+
+/* Forget a finished or failed request (frees its host copy). */
+mt_status mt_server_release(mt_server* s, int64_t id);
+
+/* Counters, and the first cap per-step latencies (ms; one per finished
+ * chunk: its event time divided by its steps) into step_ms (host). */
+mt_status mt_server_stats(const mt_server* s, mt_server_summary* out, float* step_ms,
+                          int64_t cap);
+
+/* Waits for the slots' streams, destroys resident handles and the server. */
+void mt_server_destroy(mt_server* s);
+
 /* Load the state: x (dim*n doubles, axis-major, each in [0, L_d]), A and B
  * (n doubles each).  mem says whether the three pointers are host or device
  * memory.  Positions are rounded to the grid (X = rint(x 2^k)).  Resets the

@@ -79,6 +79,28 @@ def make_batch(n, L, realisation=None) -> mt_batch:
     return b
 
 
+MT_REQ_QUEUED, MT_REQ_RUNNING, MT_REQ_DONE, MT_REQ_FAILED = 0, 1, 2, 3
+
+
+class mt_server_config(ctypes.Structure):
+    _fields_ = [("max_active", ctypes.c_int32), ("chunk_steps", ctypes.c_int32),
+                ("backfill", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class mt_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("steps_done", ctypes.c_int64), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("gpu_ms", ctypes.c_double), ("footprint", ctypes.c_size_t)]
+
+
+class mt_server_summary(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int64), ("running", ctypes.c_int64),
+                ("done", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("pool_used", ctypes.c_size_t), ("pool_peak", ctypes.c_size_t),
+                ("step_samples", ctypes.c_int64)]
+
+
 class MtError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"libmt status {status}: {msg}")
@@ -130,6 +152,15 @@ def lib(path: Path | None = None):
                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, i32, i32,
                                    _vp],
         "mt_read_profile": [H, _vp, i32, ctypes.POINTER(i32)],
+        "mt_server_footprint": [P, ctypes.POINTER(ctypes.c_size_t)],
+        "mt_server_create": [ctypes.POINTER(mt_server_config), _vp, ctypes.c_size_t,
+                             ctypes.POINTER(H)],
+        "mt_server_submit": [H, P, _vp, _vp, _vp, i64, ctypes.POINTER(i64)],
+        "mt_server_poll": [H, ctypes.POINTER(i32), ctypes.POINTER(i32)],
+        "mt_server_info": [H, i64, ctypes.POINTER(mt_request_info)],
+        "mt_server_result": [H, i64, _vp, _vp, _vp, i64, ctypes.POINTER(i64)],
+        "mt_server_release": [H, i64],
+        "mt_server_stats": [H, ctypes.POINTER(mt_server_summary), _vp, i64],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -141,6 +172,8 @@ def lib(path: Path | None = None):
     L.mt_last_error.restype = ctypes.c_char_p
     L.mt_destroy.argtypes = [H]
     L.mt_destroy.restype = None
+    L.mt_server_destroy.argtypes = [H]
+    L.mt_server_destroy.restype = None
     _lib = L
     return L
 
@@ -332,6 +365,57 @@ def mt_destroy(h) -> None:
     lib().mt_destroy(h)
 
 
+def mt_server_footprint(p: mt_params) -> int:
+    b = ctypes.c_size_t(0)
+    check(lib().mt_server_footprint(ctypes.byref(p), ctypes.byref(b)))
+    return int(b.value)
+
+
+def mt_server_create(cfg: mt_server_config, pool_ptr: int, pool_bytes: int):
+    s = ctypes.c_void_p(0)
+    check(lib().mt_server_create(ctypes.byref(cfg), pool_ptr, pool_bytes, ctypes.byref(s)))
+    return s
+
+
+def mt_server_submit(s, p: mt_params, x_ptr, A_ptr, B_ptr, steps: int) -> int:
+    rid = ctypes.c_int64(0)
+    check(lib().mt_server_submit(s, ctypes.byref(p), x_ptr, A_ptr, B_ptr, steps,
+                                 ctypes.byref(rid)))
+    return int(rid.value)
+
+
+def mt_server_poll(s):
+    q, r = ctypes.c_int32(0), ctypes.c_int32(0)
+    check(lib().mt_server_poll(s, ctypes.byref(q), ctypes.byref(r)))
+    return int(q.value), int(r.value)
+
+
+def mt_server_info(s, rid: int) -> mt_request_info:
+    info = mt_request_info()
+    check(lib().mt_server_info(s, rid, ctypes.byref(info)))
+    return info
+
+
+def mt_server_result(s, rid: int, A_ptr, B_ptr, obs_ptr, cap: int) -> int:
+    rows = ctypes.c_int64(0)
+    check(lib().mt_server_result(s, rid, A_ptr, B_ptr, obs_ptr, cap, ctypes.byref(rows)))
+    return int(rows.value)
+
+
+def mt_server_release(s, rid: int) -> None:
+    check(lib().mt_server_release(s, rid))
+
+
+def mt_server_stats(s, step_ms_ptr=None, cap: int = 0) -> mt_server_summary:
+    out = mt_server_summary()
+    check(lib().mt_server_stats(s, ctypes.byref(out), step_ms_ptr, cap))
+    return out
+
+
+def mt_server_destroy(s) -> None:
+    lib().mt_server_destroy(s)
+
+
 # -------------------------------------------------------------- Simulation --
 
 def _ptr(a: np.ndarray):
@@ -445,3 +529,75 @@ class Simulation:
 
     def steps_done(self) -> int:
         return mt_steps_done(self.h)
+
+
+# ------------------------------------------------------------------ Server --
+
+class Server:
+    """An mt_server over a torch-allocated device pool of pool_bytes."""
+
+    def __init__(self, pool_bytes: int, max_active: int = 16, chunk_steps: int = 25,
+                 backfill: bool = True, device="cuda"):
+        import torch
+
+        self.pool = torch.empty(int(pool_bytes), dtype=torch.uint8, device=device)
+        cfg = mt_server_config(max_active=max_active, chunk_steps=chunk_steps,
+                               backfill=1 if backfill else 0)
+        self.s = mt_server_create(cfg, self.pool.data_ptr(), self.pool.numel())
+        self.params = {}
+
+    def submit(self, p: mt_params, x, A, B, steps: int) -> int:
+        r = mt_resolve(p)
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        assert x.size == r.dim * r.n and A.size == r.n and B.size == r.n
+        rid = mt_server_submit(self.s, p, _ptr(x), _ptr(A), _ptr(B), steps)
+        self.params[rid] = r
+        return rid
+
+    def poll(self):
+        return mt_server_poll(self.s)
+
+    def drain(self, sleep: float = 0.0):
+        import time
+
+        while True:
+            q, r = self.poll()
+            if q == 0 and r == 0:
+                return
+            if sleep:
+                time.sleep(sleep)
+
+    def info(self, rid: int) -> mt_request_info:
+        return mt_server_info(self.s, rid)
+
+    def result(self, rid: int):
+        r = self.params[rid]
+        A = np.empty(int(r.n))
+        B = np.empty(int(r.n))
+        cap = int(r.observe_cap)
+        obs = np.zeros((max(cap, 1), 4))
+        rows = mt_server_result(self.s, rid, _ptr(A), _ptr(B), _ptr(obs), cap)
+        return A, B, obs[:rows]
+
+    def release(self, rid: int):
+        mt_server_release(self.s, rid)
+        self.params.pop(rid, None)
+
+    def stats(self):
+        st = mt_server_stats(self.s)
+        ms = np.zeros(max(int(st.step_samples), 1), dtype=np.float32)
+        st = mt_server_stats(self.s, _ptr(ms), int(st.step_samples))
+        return st, ms[:int(st.step_samples)]
+
+    def close(self):
+        if getattr(self, "s", None):
+            mt_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
