@@ -672,6 +672,8 @@ mt_status mt_upload(mt_handle* h, const double* x, const double* A, const double
   const size_t n = (size_t)p.n;
   if (n > 0 && (!x || !A || !B)) return fail(MT_ERR_INVALID, "x, A and B are required");
   CU(cudaMemsetAsync(h->ws + h->D.o_ctrl, 0, sizeof(Ctrl), h->stream));
+  // partial slots carry the step they were written in: clear old ones
+  CU(cudaMemsetAsync(h->ws + h->D.o_part, 0, (size_t)h->D.nblocks * 32, h->stream));
   // the scan epoch restarts with the control block: clear old status words
   if (h->D.ntiles > 0) CU(cudaMemsetAsync(h->ws + h->D.o_status, 0, h->D.ntiles * 8, h->stream));
   h->steps = 0;

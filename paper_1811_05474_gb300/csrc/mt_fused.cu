@@ -108,8 +108,8 @@ __device__ __forceinline__ bool dense_at(const long long* sx, int m, int j, long
 // The per-segment scalars read from the previous step's boundaries and cell
 // starts (loaded one segment ahead by the persistent loop).
 struct SegScalars {
-  long long c0, c1, a0, L, o0, o1;
-  int t0, t1;  // first target slots of this segment and the next
+  int c0, c1;          // own cells [c0, c1)
+  int a0, L, o0, o1;   // staged old slots [a0, a0 + L); old slots of cells c0 -+ Dc
 };
 
 __device__ __forceinline__ SegScalars load_seg(const Dev& d, int sc, long long Dc, int seg) {
@@ -122,20 +122,18 @@ __device__ __forceinline__ SegScalars load_seg(const Dev& d, int sc, long long D
   s.L = So[lmin(s.c1 + Hc + Dc, ncell)] - s.a0;
   s.o0 = So[lmax(s.c0 - Dc, 0)];
   s.o1 = So[lmin(s.c0 + Dc, ncell)];
-  s.t0 = d.sslot[seg];
-  s.t1 = d.sslot[seg + 1];
   return s;
 }
 
 // Process one segment with the CTA (all NT threads call it).  The CTA
 // computes the exchange for the own particles j with (j - first own) %
 // nslice == slice, and the cell starts / segment boundaries only for slice
-// 0; the segment's observables go to partial slot seg.  Returns kSegOk, or
-// why the segment does not fit this tier (then nothing of it has been
-// written except a zero observables partial).
+// 0; each thread adds the particles it updates to its observables
+// accumulators (obs_sum, in shared memory).  Returns kSegOk, or why the
+// segment does not fit this tier (then nothing of it has been written).
 template <bool MIX, typename TR, int CL>
 __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const SegScalars& g,
-                             int slice, int nslice, bool route_heavy) {
+                             int slice, int nslice, bool route_heavy, ObsAcc<MIX>& obs_sum) {
   using W = Weight<MIX, 1>;
   using T = typename W::T;
   using MS = Mass<MIX>;
@@ -151,7 +149,6 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
   __shared__ int s_lt, s_w0, s_w1, s_bad, s_nbig, s_work, s_nd, s_nd2;
   __shared__ int s_big[kBigMax];
   __shared__ int s_scan[NT / 32];
-  __shared__ MV s_red[3][NT / 32];
 
   Ctrl* c = d.ctrl;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -327,10 +324,11 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
     }
   }
   __syncthreads();
-  // Dense bins, sorted by the whole CTA.  Up to kRankMax records: each
-  // record's rank is the number of smaller (x, id) keys in the bin, packed
-  // into 64 bits as (x - bin start) << 31 | id (bins are at most 2^32 ticks
-  // wide here), then every record moves to its rank.  Larger bins: in-place
+  // Dense bins, sorted by the whole CTA.  Up to kRankMax records (256 in
+  // the first tier, 1023 in the second): each record's rank is the number of
+  // smaller (x, id) keys in the bin, packed into 64 bits as (x - bin start)
+  // << 31 | id (bins are at most 2^32 ticks wide here), then every record
+  // moves to its rank.  Larger bins: in-place
   // bitonic sort, every comparator ascending (partner i ^ (2j - 1) first in
   // each merge) so any length sorts.
   if (active) {
@@ -338,7 +336,9 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
     // the scatter cursors are free now: they hold the packed keys
     unsigned long long* key = reinterpret_cast<unsigned long long*>(
         (reinterpret_cast<uintptr_t>(bcur) + 7) & ~static_cast<uintptr_t>(7));
-    constexpr int kRankMax = NB / 2 - 1;
+    // first tier: one record per thread (registers); second tier: up to 2
+    constexpr int kRankMax = (NB / 2 - 1) < (NT > 256 ? 2 * NT : NT) ? (NB / 2 - 1)
+                                                                      : (NT > 256 ? 2 * NT : NT);
     constexpr int E = (kRankMax + NT - 1) / NT;  // records per thread
     for (int t = 0; t < nbig; ++t) {
       const int lo = bstart[s_big[t]], len = bstart[s_big[t] + 1] - lo;
@@ -482,7 +482,7 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
   } else {
     __syncthreads();
   }
-  MV oa{}, ob{}, od{};
+  ObsAcc<MIX> obs{};
   if (active) {
     long long* Xn = d.X[xc ^ 1];
     int* In = d.id[xc ^ 1];
@@ -518,11 +518,7 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
         MS::store(Mn, o, A);
         MS::store(Mn, d.n + o, B);
       }
-      if (d.observe_cap > 0) {
-        oa = obs_add(oa, A);
-        ob = obs_add(ob, B);
-        od = obs_add(od, obs_diff(A, B));
-      }
+      if (d.observe_cap > 0) obs.add(A, B);
     }
   }
   __syncthreads();
@@ -556,14 +552,11 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
           MS::store(Mn, o, A);
           MS::store(Mn, d.n + o, B);
         }
-        if (d.observe_cap > 0) {
-          oa = obs_add(oa, A);
-          ob = obs_add(ob, B);
-          od = obs_add(od, obs_diff(A, B));
-        }
+        if (d.observe_cap > 0) obs.add(A, B);
       }
     }
   }
+  if (active && d.observe_cap > 0) obs_sum.merge(obs);
   if (active && slice == 0) {
     // ---- 6: next step's cell starts and segment boundaries ----------------
     int* Sn = d.fstart[sc ^ 1];
@@ -591,9 +584,9 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
     int* CBn = d.cb[sc ^ 1];
     const long long own = w1 - w0;
     int s2 = seg + 1;
-    if (g.t0 > out0) {
+    if (d.sslot[seg] > out0) {
       while (s2 > 1 && d.sslot[s2 - 1] > out0) --s2;
-    } else if (g.t1 <= out0) {
+    } else if (d.sslot[seg + 1] <= out0) {
       while (s2 < d.nseg && d.sslot[s2] <= out0) ++s2;
     }
     for (s2 += tid; s2 < d.nseg; s2 += NT) {
@@ -604,31 +597,68 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
         CBn[s2] = (int)((sx[w0 + (q - out0)] >> wsh) + 1);
     }
   }
-  // per-segment observables in the precision's own arithmetic: warp
-  // shuffles, then the warp totals and (second tier) the cluster's CTA
-  // totals in fixed shuffle trees (zero for a segment this tier could not
-  // take)
-  if (d.observe_cap > 0) {
+  __syncthreads();
+  return status;
+}
+
+// Reduce the CTA's (second tier: the cluster's) observables accumulators in
+// fixed shuffle trees -- warps, then warp totals, then the cluster's CTA
+// totals -- into partial slot `slot` (3 words in the precision's own
+// arithmetic, then the step number), and clear them.  Called by every
+// thread (of every CTA of the cluster).
+template <bool MIX, int NT, int CL>
+__device__ void flush_obs(const Dev& d, int slot, int slice, ObsAcc<MIX>& obs) {
+  using MV = typename Mass<MIX>::V;
+  __shared__ MV s_red[3][NT / 32];
+  __shared__ MV s_seg[3];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  MV oa = obs.va(), ob = obs.vb(), od = obs.vd();
+  obs = ObsAcc<MIX>{};
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    oa = obs_add(oa, obs_shfl(oa, o));
+    ob = obs_add(ob, obs_shfl(ob, o));
+    od = obs_add(od, obs_shfl(od, o));
+  }
+  if (lane == 0) {
+    s_red[0][warp] = oa;
+    s_red[1][warp] = ob;
+    s_red[2][warp] = od;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    static_assert(NT / 32 <= 32, "one warp reduces the warp totals");
+    MV ta{}, tb{}, td{};
+    if (lane < NT / 32) {
+      ta = s_red[0][lane];
+      tb = s_red[1][lane];
+      td = s_red[2][lane];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      oa = obs_add(oa, obs_shfl(oa, o));
-      ob = obs_add(ob, obs_shfl(ob, o));
-      od = obs_add(od, obs_shfl(od, o));
+      ta = obs_add(ta, obs_shfl(ta, o));
+      tb = obs_add(tb, obs_shfl(tb, o));
+      td = obs_add(td, obs_shfl(td, o));
     }
     if (lane == 0) {
-      s_red[0][warp] = oa;
-      s_red[1][warp] = ob;
-      s_red[2][warp] = od;
+      s_seg[0] = ta;
+      s_seg[1] = tb;
+      s_seg[2] = td;
     }
-    __syncthreads();
-    __shared__ MV s_seg[3];
-    if (warp == 0) {
-      static_assert(NT / 32 <= 32, "one warp reduces the warp totals");
+  }
+  if constexpr (CL > 1) {
+    // the cluster's CTAs hold the sums of their own slices: the first one
+    // gathers them (distributed shared memory, one lane per CTA)
+    static_assert(CL <= 32, "one warp gathers the cluster");
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    if (slice == 0 && warp == 0) {
       MV ta{}, tb{}, td{};
-      if (lane < NT / 32) {
-        ta = s_red[0][lane];
-        tb = s_red[1][lane];
-        td = s_red[2][lane];
+      if (lane < CL) {
+        const MV* peer = cl.map_shared_rank(&s_seg[0], lane);
+        ta = peer[0];
+        tb = peer[1];
+        td = peer[2];
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -636,57 +666,32 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
         tb = obs_add(tb, obs_shfl(tb, o));
         td = obs_add(td, obs_shfl(td, o));
       }
+      __syncwarp();
       if (lane == 0) {
         s_seg[0] = ta;
         s_seg[1] = tb;
         s_seg[2] = td;
       }
     }
-    if constexpr (CL > 1) {
-      // the cluster's CTAs hold the sums of their own slices: the first one
-      // gathers them (distributed shared memory, one lane per CTA)
-      static_assert(CL <= 32, "one warp gathers the cluster");
-      cg::cluster_group cl = cg::this_cluster();
-      cl.sync();
-      if (slice == 0 && warp == 0) {
-        MV ta{}, tb{}, td{};
-        if (lane < CL) {
-          const MV* peer = cl.map_shared_rank(&s_seg[0], lane);
-          ta = peer[0];
-          tb = peer[1];
-          td = peer[2];
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          ta = obs_add(ta, obs_shfl(ta, o));
-          tb = obs_add(tb, obs_shfl(tb, o));
-          td = obs_add(td, obs_shfl(td, o));
-        }
-        __syncwarp();
-        if (lane == 0) {
-          s_seg[0] = ta;
-          s_seg[1] = tb;
-          s_seg[2] = td;
-        }
-      }
-      cl.sync();
-    } else {
-      __syncthreads();
-    }
-    if (tid == 0 && slice == 0) {
-      MV* part = reinterpret_cast<MV*>(d.partials);  // one 8-byte slot each
-      part[4 * seg + 0] = s_seg[0];
-      part[4 * seg + 1] = s_seg[1];
-      part[4 * seg + 2] = s_seg[2];
-    }
+    cl.sync();
+  } else {
+    __syncthreads();
+  }
+  if (tid == 0 && slice == 0) {
+    MV* part = reinterpret_cast<MV*>(d.partials);  // 8-byte words
+    part[4 * slot + 0] = s_seg[0];
+    part[4 * slot + 1] = s_seg[1];
+    part[4 * slot + 2] = s_seg[2];
+    // the step it belongs to: slots not written this step are skipped
+    reinterpret_cast<unsigned long long*>(d.partials)[4 * slot + 3] = d.ctrl->step;
   }
   __syncthreads();
-  return status;
 }
 
 // Observables of realisation r, by the CTA that completed its last segment
-// this step: its segments' partials (binary64, or double-binary32 in MIXED)
-// reduced in a fixed order, one row of the ring.
+// this step: the partials of its segment groups written this step (binary64,
+// or double-binary32 in MIXED) reduced in a fixed order, one row of the
+// ring.
 __device__ __forceinline__ double ldcg_obs(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ df ldcg_obs(const df* p) {
   const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
@@ -701,8 +706,11 @@ __device__ void reduce_realisation(const Dev& d, int r) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const Real R = d.rt[r];
   const MV* part = reinterpret_cast<const MV*>(d.partials);
+  const unsigned long long* tag = reinterpret_cast<const unsigned long long*>(d.partials);
+  const unsigned long long step = c->step;
   MV ta{}, tb{}, td{};
   for (int blk = R.seg0 + tid; blk < R.seg0 + R.nseg; blk += NT) {
+    if (__ldcg(&tag[4 * blk + 3]) != step) continue;  // no group started here this step
     ta = obs_add(ta, ldcg_obs(&part[4 * blk + 0]));
     tb = obs_add(tb, ldcg_obs(&part[4 * blk + 1]));
     td = obs_add(td, ldcg_obs(&part[4 * blk + 2]));
@@ -746,24 +754,22 @@ __device__ void reduce_realisation(const Dev& d, int r) {
   __syncthreads();
 }
 
-// Count segment seg as done; the CTA that completes its realisation's last
-// segment reduces that realisation's observables.  Called by every thread of
-// the CTA after the segment's partial is written.
+// Count `count` segments of realisation r as done (their observables are in
+// the partial slots); the CTA that completes the realisation's last segment
+// reduces that realisation's observables.  Called by every thread of the CTA.
 template <bool MIX, int NT>
-__device__ void complete_segment(const Dev& d, int seg) {
+__device__ void complete_group(const Dev& d, int r, int count) {
   __shared__ int s_r;
-  if (d.observe_cap <= 0) return;
   if (threadIdx.x == 0) {
     __threadfence();
-    const int r = d.sreal[seg];
-    s_r = atomicAdd(&d.rdone[r], 1) == d.rt[r].nseg - 1 ? r : -1;
+    s_r = atomicAdd(&d.rdone[r], count) + count == d.rt[r].nseg ? r : -1;
   }
   __syncthreads();
-  const int r = s_r;
+  const int rr = s_r;
   __syncthreads();
-  if (r < 0) return;
+  if (rr < 0) return;
   __threadfence();
-  reduce_realisation<MIX, NT>(d, r);
+  reduce_realisation<MIX, NT>(d, rr);
 }
 
 // End of a fused step (one thread, after every segment is done).
@@ -787,18 +793,44 @@ __global__ void __launch_bounds__(Fast::kT, 3) k_step1d(Dev d, cudaGraphConditio
   Ctrl* c = d.ctrl;
   const int sc = c->scur;
   const long long Dc = (c->dmax >> d.cshift) + 2;
+  const bool observe = d.observe_cap > 0;
+  // Observables: the segments this CTA completes in a row for one
+  // realisation form a group, accumulated per thread and flushed once into
+  // the group's first slot (the group's other slots keep an older step tag
+  // and are skipped).
+  __shared__ ObsAcc<MIX> s_obs[Fast::kT];
+  ObsAcc<MIX>& obs = s_obs[threadIdx.x];
+  obs = ObsAcc<MIX>{};
+  int gslot = -1, greal = -1, gcount = 0;
   int seg = blockIdx.x;
   SegScalars cur = {};
   if (seg < d.nseg) cur = load_seg(d, sc, Dc, seg);
   for (; seg < d.nseg; seg += gridDim.x) {
     SegScalars nxt = {};
     if (seg + (int)gridDim.x < d.nseg) nxt = load_seg(d, sc, Dc, seg + gridDim.x);
-    const int st = fused_segment<MIX, Fast, 1>(d, seg, smem, cur, 0, 1, true);
-    if (st == kSegOk)
-      complete_segment<MIX, Fast::kT>(d, seg);
-    else if (threadIdx.x == 0)
+    const int r = d.sreal[seg];
+    if (observe && gcount > 0 && r != greal) {  // a new realisation ends the group
+      flush_obs<MIX, Fast::kT, 1>(d, gslot, 0, obs);
+      complete_group<MIX, Fast::kT>(d, greal, gcount);
+      gcount = 0;
+    }
+    const int st = fused_segment<MIX, Fast, 1>(d, seg, smem, cur, 0, 1, true, obs);
+    if (st == kSegOk) {
+      if (observe) {
+        if (gcount == 0) {
+          gslot = seg;
+          greal = r;
+        }
+        ++gcount;
+      }
+    } else if (threadIdx.x == 0) {
       d.ovlist[atomicAdd(&c->nov, 1)] = seg;
+    }
     cur = nxt;
+  }
+  if (observe && gcount > 0) {
+    flush_obs<MIX, Fast::kT, 1>(d, gslot, 0, obs);
+    complete_group<MIX, Fast::kT>(d, greal, gcount);
   }
   if (threadIdx.x == 0) {
     __threadfence();
@@ -836,11 +868,16 @@ __global__ void __launch_bounds__(Big::kT, 1)
   const int ncl = gridDim.x / CL;
   for (int q = cid; q < nov; q += ncl) {
     const int seg = d.ovlist[q];
+    __shared__ ObsAcc<MIX> s_obs[Big::kT];
+    ObsAcc<MIX>& obs = s_obs[threadIdx.x];
+    obs = ObsAcc<MIX>{};
     const int st =
-        fused_segment<MIX, Big, CL>(d, seg, smem, load_seg(d, sc, Dc, seg), rank, CL, false);
-    if (st == kSegOk) {
-      if (rank == 0) complete_segment<MIX, Big::kT>(d, seg);
-    } else if (threadIdx.x == 0 && atomicExch(&c->overflow, 1) == 0) {
+        fused_segment<MIX, Big, CL>(d, seg, smem, load_seg(d, sc, Dc, seg), rank, CL, false, obs);
+    if (d.observe_cap > 0 && st == kSegOk) {
+      flush_obs<MIX, Big::kT, CL>(d, seg, rank, obs);
+      if (rank == 0) complete_group<MIX, Big::kT>(d, d.sreal[seg], 1);
+    }
+    if (st != kSegOk && threadIdx.x == 0 && atomicExch(&c->overflow, 1) == 0) {
       c->ov_reason = st;
       c->ov_seg = seg;
     }

@@ -182,6 +182,53 @@ __device__ __forceinline__ kahan acc_warp_sum(kahan v) {
   return v;
 }
 
+// Per-thread observables accumulators (sum A, sum B, sum (A - B) over the
+// particles a thread updates): binary64 sums, or in MIXED compensated sums
+// of the double-binary32 masses (each part added with Knuth's two-sum, the
+// rounding errors and low parts collected in a second term).
+template <bool MIX>
+struct ObsAcc;
+template <>
+struct ObsAcc<false> {
+  double a = 0.0, b = 0.0, d = 0.0;
+  __device__ __forceinline__ void add(double A, double B) {
+    a += A;
+    b += B;
+    d += A - B;
+  }
+  __device__ __forceinline__ void merge(const ObsAcc& o) {
+    a += o.a;
+    b += o.b;
+    d += o.d;
+  }
+  __device__ __forceinline__ double va() const { return a; }
+  __device__ __forceinline__ double vb() const { return b; }
+  __device__ __forceinline__ double vd() const { return d; }
+};
+template <>
+struct ObsAcc<true> {
+  kahan a{0.f, 0.f}, b{0.f, 0.f}, d{0.f, 0.f};
+  static __device__ __forceinline__ void put(kahan& k, float hi, float lo) {
+    const df e = two_sum(k.s, hi);
+    k.s = e.hi;
+    k.c = __fadd_rn(k.c, __fadd_rn(e.lo, lo));
+  }
+  __device__ __forceinline__ void add(df A, df B) {
+    put(a, A.hi, A.lo);
+    put(b, B.hi, B.lo);
+    put(d, A.hi, A.lo);
+    put(d, -B.hi, -B.lo);
+  }
+  __device__ __forceinline__ void merge(const ObsAcc& o) {
+    put(a, o.a.s, o.a.c);
+    put(b, o.b.s, o.b.c);
+    put(d, o.d.s, o.d.c);
+  }
+  __device__ __forceinline__ df va() const { return fast_two_sum(a.s, a.c); }
+  __device__ __forceinline__ df vb() const { return fast_two_sum(b.s, b.c); }
+  __device__ __forceinline__ df vd() const { return fast_two_sum(d.s, d.c); }
+};
+
 // Observables arithmetic: sums in the precision's own format (binary64 or
 // double-binary32), converted to binary64 per CTA.
 __device__ __forceinline__ double obs_add(double a, double b) { return a + b; }

@@ -573,7 +573,10 @@ class Server:
         return mt_server_info(self.s, rid)
 
     def result(self, rid: int):
-        r = self.params[rid]
+        r = self.params.get(rid)
+        if r is None:  # unknown here: let the server report it
+            mt_server_result(self.s, rid, None, None, None, 0)
+            raise MtError(MT_ERR_INVALID, f"unknown request {rid}")
         A = np.empty(int(r.n))
         B = np.empty(int(r.n))
         cap = int(r.observe_cap)
