@@ -277,6 +277,19 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
     __syncthreads();
   }
   __syncthreads();
+  if (tid == 0 && s_nbig > 1) {
+    // dense bins in ascending order (atomics filled the list in any order)
+    const int nb = s_nbig < kBigMax ? s_nbig : kBigMax;
+    for (int a = 1; a < nb; ++a) {
+      const int v = s_big[a];
+      int b = a - 1;
+      while (b >= 0 && s_big[b] > v) {
+        s_big[b + 1] = s_big[b];
+        --b;
+      }
+      s_big[b + 1] = v;
+    }
+  }
   if (active && s_bad) {
     status = kSegDense;
     active = false;
@@ -347,19 +360,37 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
         for (int i = tid; i < len; i += NT)
           key[i] = ((unsigned long long)(sx[lo + i] - blo) << 31) | (unsigned int)sid[lo + i];
         __syncthreads();
-        unsigned long long mk[E];
         int rk[E];
+        if constexpr (NT > 256) {
+          // second tier: a warp per record, lanes striding the keys
+          int* srank = reinterpret_cast<int*>(sr);  // free until the row sums
+          for (int i = warp; i < len; i += NT / 32) {
+            const unsigned long long mki = key[i];
+            int cnt = 0;
+            for (int q = lane; q < len; q += 32) cnt += key[q] < mki ? 1 : 0;
+            cnt = __reduce_add_sync(0xffffffffu, cnt);
+            if (lane == 0) srank[i] = cnt;
+          }
+          __syncthreads();
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int i = tid + e * NT;
-          mk[e] = i < len ? key[i] : ~0ULL;
-          rk[e] = 0;
-        }
+          for (int e = 0; e < E; ++e) {
+            const int i = tid + e * NT;
+            rk[e] = i < len ? srank[i] : 0;
+          }
+        } else {
+          unsigned long long mk[E];
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int i = tid + e * NT;
+            mk[e] = i < len ? key[i] : ~0ULL;
+            rk[e] = 0;
+          }
 #pragma unroll 4
-        for (int q = 0; q < len; ++q) {
-          const unsigned long long kq = key[q];
+          for (int q = 0; q < len; ++q) {
+            const unsigned long long kq = key[q];
 #pragma unroll
-          for (int e = 0; e < E; ++e) rk[e] += kq < mk[e] ? 1 : 0;
+            for (int e = 0; e < E; ++e) rk[e] += kq < mk[e] ? 1 : 0;
+          }
         }
         long long vx[E];
         int vid[E];
@@ -456,9 +487,14 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
       const int j = dlist[k];
       const long long x = sx[j];
       const int lo = lower_at_least(sx, m, x - S), hi = lower_at_least(sx, m, x + S + 1);
-      T r = T(0);
-      for (int q = lo + lane; q < hi; q += 32) r += W::near(d, x > sx[q] ? x - sx[q] : sx[q] - x);
-      r = warp_sum(r);
+      T r0 = T(0), r1 = T(0);  // two chains per lane
+      int q = lo + lane;
+      for (; q + 32 < hi; q += 64) {
+        r0 += W::near(d, x > sx[q] ? x - sx[q] : sx[q] - x);
+        r1 += W::near(d, x > sx[q + 32] ? x - sx[q + 32] : sx[q + 32] - x);
+      }
+      if (q < hi) r0 += W::near(d, x > sx[q] ? x - sx[q] : sx[q] - x);
+      const T r = warp_sum(r0 + r1);
       if (lane == 0) sr[j] = MIX ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
     }
   }
@@ -535,14 +571,30 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
       MV A = MS::load(sA, j), B = MS::load(sB, j);
       typename MS::Acc dA{}, dB{};
       const int lo = lower_at_least(sx, m, x - S), hi = lower_at_least(sx, m, x + S + 1);
-      for (int q = lo + lane; q < hi; q += 32) {
-        if (q == j) continue;
+      typename MS::Acc eA{}, eB{};  // second chain per lane
+      int q = lo + lane;
+      for (; q + 32 < hi; q += 64) {
+        if (q != j) {
+          const T P =
+              normalised<T>(d.norm, W::near(d, x > sx[q] ? x - sx[q] : sx[q] - x), ip, sr[q]);
+          MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
+          MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
+        }
+        const int q2 = q + 32;
+        if (q2 != j) {
+          const T P =
+              normalised<T>(d.norm, W::near(d, x > sx[q2] ? x - sx[q2] : sx[q2] - x), ip, sr[q2]);
+          MS::acc(eA, P, MS::diff(MS::load(sA, q2), A));
+          MS::acc(eB, P, MS::diff(MS::load(sB, q2), B));
+        }
+      }
+      if (q < hi && q != j) {
         const T P = normalised<T>(d.norm, W::near(d, x > sx[q] ? x - sx[q] : sx[q] - x), ip, sr[q]);
         MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
         MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
       }
-      dA = acc_warp_sum(dA);
-      dB = acc_warp_sum(dB);
+      dA = acc_warp_sum(acc_merge(dA, eA));
+      dB = acc_warp_sum(acc_merge(dB, eB));
       if (lane == 0) {
         MS::update(A, B, dA, dB, d.react);
         const long long o = out0 + (j - w0);

@@ -170,6 +170,11 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 __device__ __forceinline__ double acc_warp_sum(double v) { return warp_sum(v); }
+__device__ __forceinline__ double acc_merge(double a, double b) { return a + b; }
+__device__ __forceinline__ kahan acc_merge(kahan a, kahan b) {
+  const df e = two_sum(a.s, b.s);
+  return {e.hi, __fadd_rn(__fadd_rn(a.c, b.c), e.lo)};
+}
 __device__ __forceinline__ kahan acc_warp_sum(kahan v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
