@@ -278,7 +278,8 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
   }
   __syncthreads();
   if (tid == 0 && s_nbig > 1) {
-    // dense bins in ascending order (atomics filled the list in any order)
+    // dense bins in ascending order (atomics filled the list in any order;
+    // the CTAs of a cluster must visit them in the same order)
     const int nb = s_nbig < kBigMax ? s_nbig : kBigMax;
     for (int a = 1; a < nb; ++a) {
       const int v = s_big[a];
@@ -356,27 +357,59 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
     for (int t = 0; t < nbig; ++t) {
       const int lo = bstart[s_big[t]], len = bstart[s_big[t] + 1] - lo;
       if (len <= kRankMax && sh2 <= 32) {
+        if constexpr (CL > 1) {
+          // a bin's records sit in scatter order, which differs between the
+          // cluster's CTAs: all take the first CTA's arrangement
+          cg::cluster_group cl = cg::this_cluster();
+          cl.sync();
+          if (slice != 0) {
+            for (int i = tid; i < len; i += NT) {
+              sx[lo + i] = *cl.map_shared_rank(&sx[lo + i], 0u);
+              sid[lo + i] = *cl.map_shared_rank(&sid[lo + i], 0u);
+              sA[lo + i] = *cl.map_shared_rank(&sA[lo + i], 0u);
+              sB[lo + i] = *cl.map_shared_rank(&sB[lo + i], 0u);
+            }
+          }
+          __syncthreads();
+        }
         const long long blo = wlo + ((long long)s_big[t] << sh2);
         for (int i = tid; i < len; i += NT)
           key[i] = ((unsigned long long)(sx[lo + i] - blo) << 31) | (unsigned int)sid[lo + i];
         __syncthreads();
         int rk[E];
-        if constexpr (NT > 256) {
-          // second tier: a warp per record, lanes striding the keys
+        long long vx[E];
+        int vid[E];
+        unsigned long long va[E], vb[E];
+        if constexpr (CL > 1) {
+          // second tier: the cluster's CTAs rank every CL-th record each (a
+          // warp per record, lanes striding the keys) and read the other
+          // ranks from their peers' shared memory (same arrangement, same
+          // dense-bin order in every CTA)
           int* srank = reinterpret_cast<int*>(sr);  // free until the row sums
-          for (int i = warp; i < len; i += NT / 32) {
+          cg::cluster_group cl = cg::this_cluster();
+          const int nmine = (len - slice + CL - 1) / CL;
+          for (int k = warp; k < nmine; k += NT / 32) {
+            const int i = slice + k * CL;
             const unsigned long long mki = key[i];
             int cnt = 0;
             for (int q = lane; q < len; q += 32) cnt += key[q] < mki ? 1 : 0;
             cnt = __reduce_add_sync(0xffffffffu, cnt);
             if (lane == 0) srank[i] = cnt;
           }
-          __syncthreads();
+          cl.sync();
 #pragma unroll
           for (int e = 0; e < E; ++e) {
             const int i = tid + e * NT;
-            rk[e] = i < len ? srank[i] : 0;
+            if (i < len) {
+              const unsigned int owner = (unsigned int)(i % CL);
+              rk[e] = *cl.map_shared_rank(&srank[i], owner);
+              vx[e] = sx[lo + i];
+              vid[e] = sid[lo + i];
+              va[e] = sA[lo + i];
+              vb[e] = sB[lo + i];
+            }
           }
+          cl.sync();  // every peer has read this CTA's ranks
         } else {
           unsigned long long mk[E];
 #pragma unroll
@@ -391,21 +424,18 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
 #pragma unroll
             for (int e = 0; e < E; ++e) rk[e] += kq < mk[e] ? 1 : 0;
           }
-        }
-        long long vx[E];
-        int vid[E];
-        unsigned long long va[E], vb[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int i = lo + tid + e * NT;
-          if (tid + e * NT < len) {
-            vx[e] = sx[i];
-            vid[e] = sid[i];
-            va[e] = sA[i];
-            vb[e] = sB[i];
+          for (int e = 0; e < E; ++e) {
+            const int i = lo + tid + e * NT;
+            if (tid + e * NT < len) {
+              vx[e] = sx[i];
+              vid[e] = sid[i];
+              va[e] = sA[i];
+              vb[e] = sB[i];
+            }
           }
+          __syncthreads();
         }
-        __syncthreads();
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           if (tid + e * NT < len) {
