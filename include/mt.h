@@ -96,7 +96,10 @@ typedef struct mt_params {
   int32_t observe_cap;  /* steps kept in the observables ring; 0 = off */
   int32_t cell_shift;   /* log2 of the cell width in ticks; 0 = choose */
   int32_t seg_target;   /* 1-d cell search: particles per segment of the
-                           one-kernel step, in [16, 1024]; 0 = choose */
+                           one-kernel step, in [16, 1024]; 0 = choose (the
+                           largest that fits the staging, lowered so the
+                           segments fill whole waves of the step's resident
+                           CTAs on the current device) */
   int32_t reserved;     /* 0 */
 } mt_params;
 

@@ -72,6 +72,20 @@ int default_frac_bits(const mt_params& p) {
   return k;
 }
 
+// Multiprocessors of the current device (0 without one), read once.
+int device_sms() {
+  static int cached = -1;
+  if (cached < 0) {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 0;
+    cudaGetLastError();
+    cached = n;
+  }
+  return cached;
+}
+
 int ceil_log2(long long v) {  // smallest c with 2^c >= v (v >= 1)
   int c = 0;
   while (c < 62 && (1LL << c) < v) ++c;
@@ -229,6 +243,15 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
       if (p.seg_target < 16 || p.seg_target > kFusedCap)
         return fail(MT_ERR_INVALID, "seg_target must be 0 or in [16, %d]", kFusedCap);
       T = p.seg_target;
+    } else if (T >= 64) {
+      // whole waves: the step's persistent CTAs (kFusedCtasPerSm per SM of
+      // the current device) each take the same number of segments
+      const long long slots = (long long)kFusedCtasPerSm * device_sms();
+      if (slots > 0) {
+        const long long waves = (p.n + T * slots - 1) / (T * slots);
+        T = (p.n + waves * slots - 1) / (waves * slots);
+        if (T < 64) T = 64;
+      }
     }
     if (T >= 16 && (T >= 64 || p.seg_target != 0)) {
       D.fused = true;

@@ -165,6 +165,8 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
   const long long xlo = c0 << wsh, xhi = c1 << wsh;  // own cells in ticks
   int sh2 = wsh;
   while (sh2 < 62 && ((whi - wlo) >> sh2) >= NB) ++sh2;
+  // bins the window spans (bins are cells unless the window has >= NB cells)
+  const int nb = whi > wlo ? (int)(((whi - 1 - wlo) >> sh2) + 1) : 1;
   int status = kSegOk;
   bool active = c0 < c1;
   if (active && L > CAP) {
@@ -181,7 +183,7 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
     s_nd = 0;
     s_nd2 = 0;
   }
-  for (int b = tid; b <= NB; b += NT) bstart[b] = 0;
+  for (int b = tid; b <= nb; b += NT) bstart[b] = 0;
   __syncthreads();
 
   // ---- 1-2: stage and move ------------------------------------------------
@@ -246,7 +248,7 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
     int sum = 0, work = 0;
 #pragma unroll
     for (int j = 0; j < BPT; ++j) {
-      v[j] = bstart[1 + tid * BPT + j];
+      v[j] = tid * BPT + j < nb ? bstart[1 + tid * BPT + j] : 0;
       sum += v[j];
       work += v[j] * v[j];
       if (v[j] > kBinMax) {
@@ -270,8 +272,12 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
     for (int w = 0; w < warp; ++w) run += s_scan[w];
 #pragma unroll
     for (int j = 0; j < BPT; ++j) {
-      run += v[j];
-      bstart[1 + tid * BPT + j] = run;
+      const int b = tid * BPT + j;
+      if (b < nb) {
+        bcur[b] = run;  // scatter cursor: the bin's first slot
+        run += v[j];
+        bstart[1 + b] = run;
+      }
     }
   } else {
     __syncthreads();
@@ -299,8 +305,6 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
     status = kSegHeavy;
     active = false;
   }
-  for (int b = tid; b < NB; b += NT) bcur[b] = bstart[b];
-  __syncthreads();
   if (active) {
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
@@ -315,7 +319,7 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
   }
   __syncthreads();
   if (active) {
-    for (int b = tid; b < NB; b += NT) {
+    for (int b = tid; b < nb; b += NT) {
       const int lo = bstart[b], hi = bstart[b + 1];
       if (hi - lo > kBinMax) continue;  // dense bin: sorted below by the whole CTA
       for (int i = lo + 1; i < hi; ++i) {
@@ -480,7 +484,7 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
   }
 
   // ---- 5: row sums, then exchange and reaction for own particles ----------
-  const int m = bstart[NB];
+  const int m = bstart[nb];
   const int w0 = s_w0, w1 = s_w1;
   const long long out0 = o0 + s_lt;
   const long long S = d.S;
@@ -868,7 +872,7 @@ __device__ __forceinline__ void fused_advance(const Dev& d) {
 // segments; each segment's boundary scalars are loaded while the previous
 // segment is processed.
 template <bool MIX>
-__global__ void __launch_bounds__(Fast::kT, 3) k_step1d(Dev d, cudaGraphConditionalHandle cond,
+__global__ void __launch_bounds__(Fast::kT, kFusedCtasPerSm) k_step1d(Dev d, cudaGraphConditionalHandle cond,
                                                          int use_cond) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ bool s_last;
@@ -1119,7 +1123,7 @@ cudaError_t fused_configure() {
 cudaError_t launch_fused_step(const Dev& d, int precision, cudaGraphConditionalHandle cond,
                               int use_cond, cudaStream_t s) {
   const size_t sm = tier_smem<Fast>(precision);
-  const int g = d.nseg < 3 * d.nsm ? d.nseg : 3 * d.nsm;
+  const int g = d.nseg < kFusedCtasPerSm * d.nsm ? d.nseg : kFusedCtasPerSm * d.nsm;
   if (precision == MT_MIXED)
     k_step1d<true><<<g, Fast::kT, sm, s>>>(d, cond, use_cond);
   else
