@@ -84,6 +84,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble object")
     ap.add_argument("--no-precision", action="store_true", help="skip the precision report")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving object")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the paper's accuracy problem")
+    ap.add_argument("--no-dense", action="store_true", help="skip the paper-density workload")
     ap.add_argument("--serve-requests", type=int, default=64, help="requests in the serving run")
     return ap.parse_args()
 
@@ -494,6 +496,116 @@ def serve_run(local: int, count: int, pool_gb: float = 8.0, max_active: int = 16
             "makespan_s": span, "wall_s": wall, "pool_peak_bytes": int(st.pool_peak)}
 
 
+SFU_EX2_PER_SM_CLK = 16  # MUFU ex2 results per SM per clock (4 quadrants x 4)
+
+
+def dense_run(local: int, steps: int = 10, sm_mhz: float | None = None):
+    """The paper's own density (Sec. 6): N = 1e6 on [0, 5000] (200 particles
+    per unit length, about 270 neighbours within the cutoff), D = 1 split,
+    dt = 0.1, segregated C1/C2, MIXED.  This regime is bound by the
+    exponentials (4 per unordered pair: two passes, both sides), reported
+    against the SFU's ex2 rate from its unit count and clock."""
+    import numpy as np
+    import torch
+
+    from paper_1811_05474_gb300 import mt, synth
+
+    dev = torch.device("cuda", local)
+    n, Ld = 10 ** 6, 5000.0
+    p = mt.mt_params_init(n=n, L=(Ld,), D_mt=0.5, D_rw=0.5, dt=0.1, react=0,
+                          precision=mt.MT_MIXED, seed=3)
+    sim = mt.Simulation(p, device=dev)
+    x = synth.uniform_positions(n, Ld, seed=9)
+    c1, c2 = synth.segregated_masses(x, Ld)
+    sim.upload(x, c1, c2)
+    sim.run(3)
+    sim.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(sim.stream)
+    sim.run(steps)
+    e1.record(sim.stream)
+    sim.sync()
+    ms = e0.elapsed_time(e1) / steps
+    npairs = mt.mt_read_pairs(sim.h, None, None, 0)
+    mt.mt_set_profiling(sim.h, True)
+    sim.run(1)
+    kernels = mt.mt_read_profile(sim.h)
+    sim.close()
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = sm_mhz or 2070.0
+    peak = nsm * SFU_EX2_PER_SM_CLK * mhz * 1e6
+    exps = 4.0 * npairs
+    return {"workload": "paper_sec6_density_1d_n1e6_L5000_D1_dt0.1_mixed", "steps": steps,
+            "ms_per_step": ms, "particle_steps_per_s": n / (ms * 1e-3),
+            "pairs_per_step": npairs, "pair_interactions_per_s": npairs / (ms * 1e-3),
+            "search": "cell list (general pipeline: the staging of the one-kernel step does not "
+                      "fit this density)",
+            "kernels": [{"name": k, "ms": v} for k, v in kernels],
+            "roofline": {"bound": "sfu", "achieved": exps / (ms * 1e-3), "peak": peak,
+                         "unit": "exp/s", "frac": exps / (ms * 1e-3) / peak,
+                         "peak_kind": f"derived: {nsm} SMs x {SFU_EX2_PER_SM_CLK} ex2/clk x {mhz:.0f} MHz"}}
+
+
+def accuracy_run(local: int):
+    """The paper's accuracy test problem (Sec. 3): 75 realisations at each
+    N in {500, 1000, 2500, 5000, 10000, 25000}, all in one batch handle,
+    100 steps of dt = 0.1 on [0, 50] with D = 1 split between transfer and
+    walk, C1 and C2 transferred without reaction; error of C1 against the
+    exact step solution at t = 10 (mean RMSE per N), fitted D, and the
+    conservation of C1.  FP64 and MIXED with symmetric normalisation, and
+    MIXED with the literal row normalisation (which does not conserve)."""
+    import numpy as np
+    import torch
+
+    from paper_1811_05474_gb300 import accuracy as acc
+    from paper_1811_05474_gb300 import mt
+
+    dev = torch.device("cuda", local)
+    ns, ins = [], []
+    for n in acc.SIZES:
+        for r in range(acc.REALISATIONS):
+            ns.append(n)
+            ins.append(acc.inputs(n, 100000 * (1 + acc.SIZES.index(n)) + r))
+    x = np.concatenate([i[0][0] for i in ins])[None, :]
+    c1 = np.concatenate([i[1] for i in ins])
+    c2 = np.concatenate([i[2] for i in ins])
+    b = mt.make_batch(ns, [acc.L] * len(ns))
+    kw = acc.params_kw()
+    out = {"workload": "paper_sec3_L50_D1_dt0.1_t10_segregated", "realisations_per_N": acc.REALISATIONS,
+           "sizes": list(acc.SIZES), "particles": int(sum(ns)), "steps": acc.STEPS}
+    for name, prec, norm in (("fp64_sym", mt.MT_FP64, mt.MT_NORM_SYM),
+                             ("mixed_sym", mt.MT_MIXED, mt.MT_NORM_SYM),
+                             ("mixed_row", mt.MT_MIXED, mt.MT_NORM_ROW)):
+        p = mt.mt_params_init(dim=1, L=(1.0,), D_mt=kw["D_mt"], D_rw=kw["D_rw"], dt=kw["dt"],
+                              react=0, precision=prec, norm=norm, seed=2024)
+        sim = mt.Simulation(p, device=dev, batch=b)
+        sim.upload(x, c1, c2)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(sim.stream)
+        sim.run(acc.STEPS)
+        e1.record(sim.stream)
+        sim.sync()
+        ms = e0.elapsed_time(e1)
+        xs = np.split(sim.positions()[0], np.cumsum(ns)[:-1])
+        g1 = np.split(sim.masses()[0], np.cumsum(ns)[:-1])
+        sim.close()
+        per = {}
+        k = 0
+        for n in acc.SIZES:
+            R = acc.REALISATIONS
+            e = [acc.rmse(xs[k + r], g1[k + r]) for r in range(R)]
+            cons = max(abs(g1[k + r].sum() - ins[k + r][1].sum()) for r in range(R))
+            per[str(n)] = {"rmse_mean": float(np.mean(e)), "rmse_sd": float(np.std(e)),
+                           "fitted_D": acc.fitted_d(xs[k:k + R], g1[k:k + R]),
+                           "max_abs_change_sum_C1": float(cons)}
+            k += R
+        out[name] = {"per_N": per, "gpu_ms": ms,
+                     "particle_steps_per_s": sum(ns) * acc.STEPS / (ms * 1e-3)}
+    return out
+
+
 def precision_report(local: int, steps: int):
     """MIXED against the FP64 GPU path on the headline workload: both run
     `steps` steps from the same state with the same random walk (positions
@@ -640,6 +752,12 @@ def main():
     serving = None
     if not args.no_serve and rank == 0:
         serving = serve_run(local, args.serve_requests)
+    accuracy = None
+    if not args.no_accuracy and rank == 0:
+        accuracy = accuracy_run(local)
+    dense = None
+    if not args.no_dense and rank == 0:
+        dense = dense_run(local, sm_mhz=clocks.get("sm_mhz") if clocks else None)
     if ws > 1:
         t = torch.tensor([e2e["value"]], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MIN)
@@ -697,6 +815,8 @@ def main():
         "fp64": fp64,
         "batched": batched,
         "serving": serving,
+        "accuracy": accuracy,
+        "paper_density": dense,
         "precision": precision,
         "mean_A_last_step": main_run["mean_A_last"],
     }
