@@ -86,6 +86,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving object")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the paper's accuracy problem")
     ap.add_argument("--no-dense", action="store_true", help="skip the paper-density workload")
+    ap.add_argument("--no-brute", action="store_true", help="skip the all-pairs forms")
     ap.add_argument("--serve-requests", type=int, default=64, help="requests in the serving run")
     return ap.parse_args()
 
@@ -547,6 +548,59 @@ def dense_run(local: int, steps: int = 10, sm_mhz: float | None = None):
                          "peak_kind": f"derived: {nsm} SMs x {SFU_EX2_PER_SM_CLK} ex2/clk x {mhz:.0f} MHz"}}
 
 
+def brute_run(local: int, n: int = 100000, steps: int = 2, sm_mhz: float | None = None):
+    """The all-pairs forms at the N = 1e5 workload's shape (1-d, [0, 1e5],
+    MIXED): the full matrix (every pair's exponential, the paper's
+    reference) and the cutoff brute force (every pair tested).  Per pass:
+    kernel time, pairs per second, and for the full matrix the exponentials
+    per second against the SFU's ex2 rate."""
+    import torch
+
+    from paper_1811_05474_gb300 import mt, synth
+
+    dev = torch.device("cuda", local)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = sm_mhz or 2070.0
+    peak = nsm * SFU_EX2_PER_SM_CLK * mhz * 1e6
+    x = synth.uniform_positions(n, float(n), seed=0)
+    A, B = synth.uniform_masses(n, seed=0)
+    out = {"workload": f"1d_uniform_n{n}_L{n}_D0.1_dt1_mixed", "steps": steps}
+    for name, search in (("full_matrix", mt.MT_SEARCH_FULL), ("brute_cutoff", mt.MT_SEARCH_BRUTE)):
+        p = mt.mt_params_init(n=n, L=(float(n),), search=search, precision=mt.MT_MIXED, seed=1)
+        sim = mt.Simulation(p, device=dev)
+        sim.upload(x, A, B)
+        sim.run(1)
+        sim.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(sim.stream)
+        sim.run(steps)
+        e1.record(sim.stream)
+        sim.sync()
+        ms = e0.elapsed_time(e1) / steps
+        mt.mt_set_profiling(sim.h, True)
+        sim.run(1)
+        prof = dict(mt.mt_read_profile(sim.h))
+        sim.close()
+        pairs = float(n) * n
+        rk, xk = ("rowsum_full", "exchange_full") if search == mt.MT_SEARCH_FULL else \
+                 ("rowsum_brute", "exchange_brute")
+        r = {"ms_per_step": ms, "pair_evaluations_per_step": 2 * pairs,
+             "pairs_per_s": 2 * pairs / (ms * 1e-3),
+             "rowsum_ms": prof.get(rk), "exchange_ms": prof.get(xk)}
+        if search == mt.MT_SEARCH_FULL:
+            # one exponential per ordered pair in each pass (self included)
+            rate = pairs / (prof[rk] * 1e-3)
+            r["rowsum_roofline"] = {"bound": "sfu", "achieved": rate, "peak": peak, "unit": "exp/s",
+                                    "frac": rate / peak,
+                                    "peak_kind": f"derived: {nsm} SMs x {SFU_EX2_PER_SM_CLK} ex2/clk x {mhz:.0f} MHz"}
+            rate = pairs / (prof[xk] * 1e-3)
+            r["exchange_roofline"] = {"bound": "sfu", "achieved": rate, "peak": peak, "unit": "exp/s",
+                                      "frac": rate / peak}
+        out[name] = r
+    return out
+
+
 def accuracy_run(local: int):
     """The paper's accuracy test problem (Sec. 3): 75 realisations at each
     N in {500, 1000, 2500, 5000, 10000, 25000}, all in one batch handle,
@@ -755,6 +809,9 @@ def main():
     accuracy = None
     if not args.no_accuracy and rank == 0:
         accuracy = accuracy_run(local)
+    brute = None
+    if not args.no_brute and rank == 0:
+        brute = brute_run(local, sm_mhz=clocks.get("sm_mhz") if clocks else None)
     dense = None
     if not args.no_dense and rank == 0:
         dense = dense_run(local, sm_mhz=clocks.get("sm_mhz") if clocks else None)
@@ -817,6 +874,7 @@ def main():
         "serving": serving,
         "accuracy": accuracy,
         "paper_density": dense,
+        "brute_force": brute,
         "precision": precision,
         "mean_A_last_step": main_run["mean_A_last"],
     }

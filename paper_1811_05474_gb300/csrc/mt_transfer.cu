@@ -57,7 +57,7 @@ __device__ void finish_step(const Dev& d, typename Mass<MIX>::V a, typename Mass
     __syncthreads();
     if (threadIdx.x == 0) {
       MV ta = s_part[0][0], tb = s_part[0][1], td = s_part[0][2];
-      for (int w = 1; w < kThreads / 32; ++w) {
+      for (int w = 1; w < (int)(blockDim.x / 32); ++w) {
         ta = obs_add(ta, s_part[w][0]);
         tb = obs_add(tb, s_part[w][1]);
         td = obs_add(td, s_part[w][2]);
@@ -95,7 +95,7 @@ __device__ void finish_step(const Dev& d, typename Mass<MIX>::V a, typename Mass
     __syncthreads();
     if (threadIdx.x == 0) {
       ta = tb = td = 0;
-      for (int w = 0; w < kThreads / 32; ++w) {
+      for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
         ta += s_tot[w][0];
         tb += s_tot[w][1];
         td += s_tot[w][2];
@@ -328,6 +328,11 @@ __global__ void __launch_bounds__(kThreads) k_exchange_cell2(Dev d) {
 // All pairs, j-particles staged through shared memory in tiles.  Particles
 // keep their caller order (no sort); masses ping-pong between buffers.
 
+// |dx| <= S in one unsigned comparison (1-d)
+__device__ __forceinline__ bool within1(long long dx, long long S) {
+  return (unsigned long long)(dx + S) <= (unsigned long long)(2 * S);
+}
+
 template <bool MIX, bool CUT, int DIM>
 __global__ void __launch_bounds__(kThreads) k_rowsum_brute(Dev d) {
   using W = Weight<MIX, DIM>;
@@ -353,7 +358,7 @@ __global__ void __launch_bounds__(kThreads) k_rowsum_brute(Dev d) {
         const long long dx = s_x[jj] - x;
         const long long dy = DIM == 2 ? s_y[jj] - y : 0;
         if (CUT) {
-          if (DIM == 1 ? (dx > d.S || -dx > d.S) : !in_range2(dx, dy, d.S)) continue;
+          if (DIM == 1 ? !within1(dx, d.S) : !in_range2(dx, dy, d.S)) continue;
         }
         r += W::eval(d, dx, dy);
       }
@@ -406,7 +411,7 @@ __global__ void __launch_bounds__(kThreads) k_exchange_brute(Dev d) {
         const long long dx = s_x[jj] - x;
         const long long dy = DIM == 2 ? s_y[jj] - y : 0;
         if (CUT) {
-          if (DIM == 1 ? (dx > d.S || -dx > d.S) : !in_range2(dx, dy, d.S)) continue;
+          if (DIM == 1 ? !within1(dx, d.S) : !in_range2(dx, dy, d.S)) continue;
         }
         const T P = normalised<T>(d.norm, W::eval(d, dx, dy), ip, s_ri[jj]);
         MS::acc(dA, P, MS::diff(s_a[jj], A));
