@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--ncu", action="store_true",
                     help="profiling mode: upload, W graph steps, then K direct steps, nothing else")
     ap.add_argument("--n", type=int, default=N, help="particles (profiling mode only)")
+    ap.add_argument("--ncu-search", default="cell", choices=["cell", "full"],
+                    help="profiling mode: the cell list (headline) or the full matrix")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble object")
     ap.add_argument("--no-precision", action="store_true", help="skip the precision report")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving object")
@@ -733,8 +735,9 @@ def run_ncu(args):
     n = args.n
     Ln = float(n) * (L / N)
     prec = mt.MT_MIXED if args.precision == "mixed" else mt.MT_FP64
+    search = mt.MT_SEARCH_FULL if args.ncu_search == "full" else mt.MT_SEARCH_CELL
     p = mt.mt_params_init(n=n, L=(Ln,), v=(V, 0.0), D_mt=D, D_rw=D, dt=DT, precision=prec,
-                          seed=2024, observe_cap=args.steps + args.warmup)
+                          search=search, seed=2024, observe_cap=args.steps + args.warmup)
     sim = mt.Simulation(p)
     sim.upload(synth.uniform_positions(n, Ln, seed=0), *synth.uniform_masses(n, seed=0))
     sim.run(args.warmup)
