@@ -26,7 +26,7 @@
 //      the next step's segment boundaries that fall in its output range.
 //
 // Two tiers.  k_step1d stages up to 1024 particles per CTA (256 threads, a
-// persistent grid of 3 CTAs per SM).  A segment that does not fit, or whose
+// persistent grid of 4 CTAs per SM).  A segment that does not fit, or whose
 // pair work is heavy (a dense cluster), is queued; a CUDA-graph conditional
 // node then runs k_step1d_big over the queue: a cluster of 8 CTAs (512
 // threads, up to 4096 staged particles each) per segment, splitting its row
@@ -70,86 +70,7 @@ size_t tier_smem(int precision) {
   return (size_t)TR::kCap * (8 + 8 + 8 + 4 + r) + (size_t)(2 * TR::kBins + 1) * 4;
 }
 
-// ---- bulk prefetch of the next segment's positions and ids --------------
-// The first tier copies the old positions X[a0, a0 + L) and ids of the next
-// segment into shared memory while it works on the current one: one thread
-// issues two bulk asynchronous copies (cp.async.bulk) completing on an
-// mbarrier.  A bulk copy needs 16-byte aligned addresses and a size that is
-// a multiple of 16 bytes, so each range is widened to 16-byte boundaries
-// (the extra words lie inside the workspace: arrays are padded to 256
-// bytes); element e of the segment is then at pfX[(a0 & 1) + e] and
-// pfI[(a0 & 3) + e].
-// widened ranges: X up to L + 2 words, ids up to L + 6 words
-constexpr int kPfCap = kFusedCap + 8;
-static_assert(kPfCap * 8 % 16 == 0 && kPfCap * 12 % 16 == 0, "16-byte aligned regions");
-constexpr size_t kPfBytes = (size_t)kPfCap * (8 + 4) + 16;  // X, ids, mbarrier
-
-size_t fast_smem_bytes(int precision) {
-  return (tier_smem<Fast>(precision) + 15) / 16 * 16 + kPfBytes;
-}
-
-size_t fused_smem_bytes(int precision) { return fast_smem_bytes(precision); }
-
-template <typename TR, bool MIX>
-__device__ constexpr size_t tier_smem_dev() {
-  return (size_t)TR::kCap * (8 + 8 + 8 + 4 + (MIX ? 4 : 8)) + (size_t)(2 * TR::kBins + 1) * 4;
-}
-
-struct Prefetch {
-  long long* X;            // [kPfCap]
-  int* id;                 // [kPfCap]
-  unsigned long long* bar; // mbarrier
-  unsigned int phase;      // parity of the next completion to wait for
-  bool pending;            // a copy has been issued and not yet waited for
-};
-
-__device__ __forceinline__ unsigned int smem_addr(const void* p) {
-  return (unsigned int)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ bool pf_fits(long long L) { return L > 0 && L <= kFusedCap; }
-
-// One thread: copy the positions and ids of staged slots [a0, a0 + L).
-__device__ __forceinline__ void pf_issue(const Dev& d, const Prefetch& pf, int xc, long long a0,
-                                         long long L) {
-  const long long x0 = a0 & ~1LL, x1 = (a0 + L + 1) & ~1LL;  // 8-byte words, 16-byte aligned
-  const long long i0 = a0 & ~3LL, i1 = (a0 + L + 3) & ~3LL;  // 4-byte words
-  const unsigned int bx = (unsigned int)((x1 - x0) * 8), bi = (unsigned int)((i1 - i0) * 4);
-  const unsigned int bar = smem_addr(pf.bar);
-  // the buffer was last read through the generic proxy
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bx + bi)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(pf.X)),
-      "l"(d.X[xc] + x0), "r"(bx), "r"(bar)
-      : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(pf.id)),
-      "l"(d.id[xc] + i0), "r"(bi), "r"(bar)
-      : "memory");
-}
-
-// All threads: wait for the issued copy (bounded).  False if it gave up.
-__device__ __forceinline__ bool pf_wait(Prefetch& pf) {
-  const unsigned int bar = smem_addr(pf.bar);
-  bool ok = false;
-  for (long long it = 0; it < kSpinLimit && !ok; ++it) {
-    unsigned int done;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(done)
-        : "r"(bar), "r"(pf.phase)
-        : "memory");
-    ok = done != 0;
-  }
-  pf.phase ^= 1u;
-  pf.pending = false;
-  return ok;
-}
-
+size_t fused_smem_bytes(int precision) { return tier_smem<Fast>(precision); }
 
 __device__ __forceinline__ long long lmin(long long a, long long b) { return a < b ? a : b; }
 __device__ __forceinline__ long long lmax(long long a, long long b) { return a > b ? a : b; }
@@ -212,8 +133,7 @@ __device__ __forceinline__ SegScalars load_seg(const Dev& d, int sc, long long D
 // segment does not fit this tier (then nothing of it has been written).
 template <bool MIX, typename TR, int CL>
 __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const SegScalars& g,
-                             int slice, int nslice, bool route_heavy, ObsAcc<MIX>& obs_sum,
-                             Prefetch* pf = nullptr, const SegScalars* next = nullptr) {
+                             int slice, int nslice, bool route_heavy, ObsAcc<MIX>& obs_sum) {
   using W = Weight<MIX, 1>;
   using T = typename W::T;
   using MS = Mass<MIX>;
@@ -267,20 +187,12 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
   __syncthreads();
 
   // ---- 1-2: stage and move ------------------------------------------------
-  // (first tier: positions and ids from the prefetch buffer)
+  // Registers keep only the new position and bin of each staged particle;
+  // its id and masses are read again (cache hits) when it is scattered.
   const long long* Xs = Xo + a0;
   const int* Is = Io + a0;
-  if (pf) {
-    if (pf->pending && !pf_wait(*pf)) {
-      if (tid == 0) raise_error(c, kErrTimeout, seg);
-      active = false;
-    }
-    Xs = pf->X + (a0 & 1);
-    Is = pf->id + (a0 & 3);
-  }
   long long rx[PER];
-  int rid[PER], rbin[PER];
-  unsigned long long ra[PER], rb[PER];
+  int rbin[PER];
   if (active) {
     const unsigned long long step = c->step;
     const float* noise = c->noise;
@@ -307,9 +219,6 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
         const long long x =
             base + reflect(Xs[e] - base + d.drift[0] + float_to_ll_rn(__fmul_rn(d.bq, z)), R->Lq);
         rx[k] = x;
-        rid[k] = id;
-        ra[k] = Mo[slot];
-        rb[k] = Mo[d.n + slot];
         lt = slot >= o0 && slot < o1 && x < xlo;
         if (x >= wlo && x < whi) {
           const int b = (int)((x - wlo) >> sh2);
@@ -401,19 +310,15 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
     for (int k = 0; k < PER; ++k) {
       if (rbin[k] >= 0) {
         const int slot = atomicAdd(&bcur[rbin[k]], 1);
+        const long long e = tid + (long long)k * NT;
         sx[slot] = rx[k];
-        sid[slot] = rid[k];
-        sA[slot] = ra[k];
-        sB[slot] = rb[k];
+        sid[slot] = Is[e];
+        sA[slot] = Mo[a0 + e];
+        sB[slot] = Mo[d.n + a0 + e];
       }
     }
   }
   __syncthreads();
-  if (pf && next && pf_fits(next->L)) {
-    // the prefetch buffer has been read: fetch the next segment into it
-    if (tid == 0) pf_issue(d, *pf, xc, next->a0, next->L);
-    pf->pending = true;
-  }
   if (active) {
     for (int b = tid; b < nb; b += NT) {
       const int lo = bstart[b], hi = bstart[b + 1];
@@ -983,29 +888,10 @@ __global__ void __launch_bounds__(Fast::kT, kFusedCtasPerSm) k_step1d(Dev d, cud
   __shared__ ObsAcc<MIX> s_obs[Fast::kT];
   ObsAcc<MIX>& obs = s_obs[threadIdx.x];
   obs = ObsAcc<MIX>{};
-  // prefetch buffer after the staging area
-  unsigned char* pfb = smem + (tier_smem_dev<Fast, MIX>() + 15) / 16 * 16;
-  Prefetch pf;
-  pf.X = reinterpret_cast<long long*>(pfb);
-  pf.id = reinterpret_cast<int*>(pfb + (size_t)kPfCap * 8);
-  pf.bar = reinterpret_cast<unsigned long long*>(pfb + (size_t)kPfCap * 12);
-  pf.phase = 0;
-  pf.pending = false;
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(pf.bar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
   int gslot = -1, greal = -1, gcount = 0;
   int seg = blockIdx.x;
   SegScalars cur = {};
-  if (seg < d.nseg) {
-    cur = load_seg(d, sc, Dc, seg);
-    if (pf_fits(cur.L)) {
-      if (threadIdx.x == 0) pf_issue(d, pf, c->xcur, cur.a0, cur.L);
-      pf.pending = true;
-    }
-  }
+  if (seg < d.nseg) cur = load_seg(d, sc, Dc, seg);
   for (; seg < d.nseg; seg += gridDim.x) {
     SegScalars nxt = {};
     const bool has_next = seg + (int)gridDim.x < d.nseg;
@@ -1016,8 +902,7 @@ __global__ void __launch_bounds__(Fast::kT, kFusedCtasPerSm) k_step1d(Dev d, cud
       complete_group<MIX, Fast::kT>(d, greal, gcount);
       gcount = 0;
     }
-    const int st = fused_segment<MIX, Fast, 1>(d, seg, smem, cur, 0, 1, true, obs, &pf,
-                                               has_next ? &nxt : nullptr);
+    const int st = fused_segment<MIX, Fast, 1>(d, seg, smem, cur, 0, 1, true, obs);
     if (st == kSegOk) {
       if (observe) {
         if (gcount == 0) {
@@ -1035,7 +920,6 @@ __global__ void __launch_bounds__(Fast::kT, kFusedCtasPerSm) k_step1d(Dev d, cud
     flush_obs<MIX, Fast::kT, 1>(d, gslot, 0, obs);
     complete_group<MIX, Fast::kT>(d, greal, gcount);
   }
-  if (pf.pending && !pf_wait(pf) && threadIdx.x == 0) raise_error(c, kErrTimeout, -1);
   if (threadIdx.x == 0) {
     __threadfence();
     s_last = atomicAdd(&c->done, 1u) == gridDim.x - 1;
@@ -1222,10 +1106,10 @@ static int max_active_clusters(int precision) {
 cudaError_t fused_configure() {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_step1d<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)fast_smem_bytes(MT_MIXED))) != cudaSuccess)
+                                (int)tier_smem<Fast>(MT_MIXED))) != cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(k_step1d<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)fast_smem_bytes(MT_FP64))) != cudaSuccess)
+                                (int)tier_smem<Fast>(MT_FP64))) != cudaSuccess)
     return e;
   if ((e = configure_big<true, 8>(MT_MIXED)) != cudaSuccess) return e;
   if ((e = configure_big<false, 8>(MT_FP64)) != cudaSuccess) return e;
@@ -1240,7 +1124,7 @@ cudaError_t fused_configure() {
 
 cudaError_t launch_fused_step(const Dev& d, int precision, cudaGraphConditionalHandle cond,
                               int use_cond, cudaStream_t s) {
-  const size_t sm = fast_smem_bytes(precision);
+  const size_t sm = tier_smem<Fast>(precision);
   const int g = d.nseg < kFusedCtasPerSm * d.nsm ? d.nseg : kFusedCtasPerSm * d.nsm;
   if (precision == MT_MIXED)
     k_step1d<true><<<g, Fast::kT, sm, s>>>(d, cond, use_cond);

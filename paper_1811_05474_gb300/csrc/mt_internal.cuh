@@ -17,7 +17,7 @@ constexpr int kBigSortCap = 2048;      // cells up to this size sort in shared m
 constexpr int kBruteTile = 256;        // j-particles staged per tile, brute force
 constexpr long long kSpinLimit = 1LL << 22;  // bounded waits (scan look-back)
 constexpr int kFusedCap = 1024;        // particles one fused-step CTA stages
-constexpr int kFusedCtasPerSm = 3;     // resident CTAs per SM of the fused step
+constexpr int kFusedCtasPerSm = 4;     // resident CTAs per SM of the fused step
 
 // Device error codes (Ctrl::err); the first one raised is kept.
 enum : int { kErrNone = 0, kErrIndex = 1, kErrTimeout = 2, kErrInput = 3 };
