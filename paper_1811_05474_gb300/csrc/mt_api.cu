@@ -60,8 +60,8 @@ struct Derived {
   std::vector<int> sslot, sreal;
   // workspace offsets
   size_t o_ctrl, o_X[2], o_id[2], o_M[2], o_src, o_rinv, o_count, o_start, o_cursor,
-      o_status, o_big, o_part, o_obs, o_fstart[2], o_cb[2], o_ovlist, o_rt, o_sslot, o_sreal,
-      o_rdone, total;
+      o_status, o_big, o_part, o_obs, o_fstart[2], o_cb[2], o_ovlist, o_pred[2], o_rt, o_sslot,
+      o_sreal, o_rdone, total;
 };
 
 int default_frac_bits(const mt_params& p) {
@@ -315,6 +315,7 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
   for (int b2 = 0; b2 < 2; ++b2) D.o_fstart[b2] = take(D.fused ? (size_t)(D.ncell + 1) * 4 : 0);
   for (int b2 = 0; b2 < 2; ++b2) D.o_cb[b2] = take(D.fused ? (size_t)(D.nseg + 1) * 4 : 0);
   D.o_ovlist = take(D.fused ? (size_t)D.nseg * 4 : 0);
+  for (int b2 = 0; b2 < 2; ++b2) D.o_pred[b2] = take(D.fused ? (size_t)D.nseg : 0);
   D.o_rt = take(D.rt.size() * sizeof(Real));
   D.o_sslot = take(D.sslot.size() * 4);
   D.o_sreal = take(D.sreal.size() * 4);
@@ -341,6 +342,10 @@ struct mt_handle {
   char* ws = nullptr;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // fused path: the predicted-segment kernel runs on a second stream beside
+  // the first tier (fork / join events around it in the captured graph)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   bool uploaded = false;
   long long steps = 0;     // host mirror of the step counter
   const float* noise = nullptr;
@@ -413,15 +418,29 @@ mt_status enqueue_step(mt_handle* h, const Dev& d) {
     mk.names = h->ev_names;
   }
   if (h->D.fused) {
+    // the step's prediction (segments pair-heavy last step) decides whether
+    // the predicted-segment kernel runs; here it runs before the first tier
+    // (in the captured graph, beside it)
+    Ctrl c;
+    mt_status s = MT_OK;
+    if (d.use_pred) {
+      s = read_ctrl(h, &c);
+      if (s != MT_OK) return s;
+      if (c.npred > 0) {
+        mk("fused_pred", h->stream);
+        CU(launch_fused_pred(d, p.precision, 0, 0, h->stream));
+      } else {
+        CU(launch_join_stub(d, h->stream));  // the first tier's partner in the join
+      }
+    }
     mk("fused_step", h->stream);
     CU(launch_fused_step(d, p.precision, 0, 0, h->stream));
     // a gap mark: the idle time while the host reads the control block is
     // not counted in the kernel before it
     mk(nullptr, h->stream);
-    Ctrl c;
-    mt_status s = read_ctrl(h, &c);
+    s = read_ctrl(h, &c);
     if (s != MT_OK) return s;
-    if (c.nov > 0) {
+    if (c.nov > 0 || c.overflow) {
       mk("fused_big", h->stream);
       CU(launch_fused_big(d, p.precision, 0, 0, h->stream));
       mk(nullptr, h->stream);
@@ -456,8 +475,19 @@ mt_status build_graph(mt_handle* h) {
     // g: [fast tier] -> IF(queued) { [second tier] -> IF(overflow) { general } }
     cudaGraphConditionalHandle cond1, cond2;
     CU(cudaGraphConditionalHandleCreate(&cond1, g, 0, 0));
+    // large systems fork: the predicted-segment kernel on the side stream,
+    // the first tier on the handle's stream; join before the conditional
+    const bool fork = d.use_pred != 0;
     CU(cudaStreamBeginCaptureToGraph(h->stream, g, nullptr, nullptr, 0, mode));
-    cudaError_t e1 = launch_fused_step(d, h->D.p.precision, cond1, 1, h->stream);
+    cudaError_t e1 = cudaSuccess;
+    if (fork) {
+      e1 = cudaEventRecord(h->fork, h->stream);
+      if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(h->side, h->fork, 0);
+      if (e1 == cudaSuccess) e1 = launch_fused_pred(d, h->D.p.precision, cond1, 1, h->side);
+    }
+    if (e1 == cudaSuccess) e1 = launch_fused_step(d, h->D.p.precision, cond1, 1, h->stream);
+    if (fork && e1 == cudaSuccess) e1 = cudaEventRecord(h->join, h->side);
+    if (fork && e1 == cudaSuccess) e1 = cudaStreamWaitEvent(h->stream, h->join, 0);
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
       cudaGraphDestroy(g);
@@ -465,16 +495,21 @@ mt_status build_graph(mt_handle* h) {
     }
     cudaGraph_t body1 = nullptr;
     {
-      cudaGraphNode_t knode = nullptr;
-      size_t nn = 1;
-      CU(cudaGraphGetNodes(g, &knode, &nn));
+      const size_t want = fork ? 2 : 1;
+      cudaGraphNode_t knodes[2] = {nullptr, nullptr};
+      size_t nn = 2;
+      CU(cudaGraphGetNodes(g, knodes, &nn));
+      if (nn != want) {
+        cudaGraphDestroy(g);
+        return fail(MT_ERR_CUDA, "fused step graph: expected %zu kernel nodes, got %zu", want, nn);
+      }
       cudaGraphNodeParams cp = {};
       cp.type = cudaGraphNodeTypeConditional;
       cp.conditional.handle = cond1;
       cp.conditional.type = cudaGraphCondTypeIf;
       cp.conditional.size = 1;
       cudaGraphNode_t cnode = nullptr;
-      CU(cudaGraphAddNode(&cnode, g, &knode, nullptr, 1, &cp));
+      CU(cudaGraphAddNode(&cnode, g, knodes, nullptr, want, &cp));
       body1 = cp.conditional.phGraph_out[0];
     }
     CU(cudaGraphConditionalHandleCreate(&cond2, body1, 0, 0));
@@ -625,6 +660,7 @@ mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace
     d.cb[b] = reinterpret_cast<int*>(w + D.o_cb[b]);
   }
   d.ovlist = reinterpret_cast<int*>(w + D.o_ovlist);
+  for (int b = 0; b < 2; ++b) d.pred[b] = reinterpret_cast<unsigned char*>(w + D.o_pred[b]);
   d.nseg = (int)D.nseg;
   d.seg_target = (int)D.seg_target;
   d.hc = D.hc;
@@ -635,6 +671,9 @@ mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace
       nsm = 1;
     d.nsm = nsm;
   }
+  // the predicted-segment kernel pays off when the first tier has more than
+  // one wave of segments (large systems); small ones keep the plain chain
+  d.use_pred = D.fused && D.nseg > (long long)kFusedCtasPerSm * d.nsm ? 1 : 0;
   d.n = D.p.n;
   d.dim = D.p.dim;
   d.norm = D.p.norm;
@@ -667,6 +706,11 @@ mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace
   d.rdone = reinterpret_cast<int*>(w + D.o_rdone);
   const Derived& hd = h->D;  // the tables live as long as the handle
   cudaError_t e = D.fused ? fused_configure() : cudaSuccess;
+  if (e == cudaSuccess && d.use_pred) {
+    e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(h->ws, 0, D.total, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(w + D.o_rt, hd.rt.data(), hd.rt.size() * sizeof(Real),
@@ -679,9 +723,12 @@ mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace
                         cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->fork) cudaEventDestroy(h->fork);
+    if (h->join) cudaEventDestroy(h->join);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
-    return fail(MT_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    return fail(MT_ERR_CUDA, "handle setup: %s", cudaGetErrorString(e));
   }
   *out = h;
   return MT_OK;
@@ -697,6 +744,8 @@ mt_status mt_upload(mt_handle* h, const double* x, const double* A, const double
   CU(cudaMemsetAsync(h->ws + h->D.o_ctrl, 0, sizeof(Ctrl), h->stream));
   // partial slots carry the step they were written in: clear old ones
   CU(cudaMemsetAsync(h->ws + h->D.o_part, 0, (size_t)h->D.nblocks * 32, h->stream));
+  if (h->D.fused)
+    for (int b = 0; b < 2; ++b) CU(cudaMemsetAsync(h->ws + h->D.o_pred[b], 0, h->D.nseg, h->stream));
   // the scan epoch restarts with the control block: clear old status words
   if (h->D.ntiles > 0) CU(cudaMemsetAsync(h->ws + h->D.o_status, 0, h->D.ntiles * 8, h->stream));
   h->steps = 0;
@@ -927,6 +976,12 @@ void mt_destroy(mt_handle* h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
   for (int i = 0; i <= kMaxMarks; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  if (h->side) {
+    cudaStreamSynchronize(h->side);
+    cudaStreamDestroy(h->side);
+  }
+  if (h->fork) cudaEventDestroy(h->fork);
+  if (h->join) cudaEventDestroy(h->join);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
 }

@@ -133,7 +133,8 @@ __device__ __forceinline__ SegScalars load_seg(const Dev& d, int sc, long long D
 // segment does not fit this tier (then nothing of it has been written).
 template <bool MIX, typename TR, int CL>
 __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const SegScalars& g,
-                             int slice, int nslice, bool route_heavy, ObsAcc<MIX>& obs_sum) {
+                             int slice, int nslice, bool route_heavy, ObsAcc<MIX>& obs_sum,
+                             bool* heavy_out = nullptr) {
   using W = Weight<MIX, 1>;
   using T = typename W::T;
   using MS = Mass<MIX>;
@@ -301,6 +302,7 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
     status = kSegDense;
     active = false;
   }
+  if (heavy_out) *heavy_out = s_work >= kHeavyWork || L > Fast::kCap;
   if (active && route_heavy && s_work >= kHeavyWork) {
     status = kSegHeavy;
     active = false;
@@ -522,14 +524,20 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
       const int j = dlist[k];
       const long long x = sx[j];
       const int lo = lower_at_least(sx, m, x - S), hi = lower_at_least(sx, m, x + S + 1);
-      T r0 = T(0), r1 = T(0);  // two chains per lane
+      // second tier: four chains per lane (dense particles are its work);
+      // first tier: one (registers are scarce there)
+      T r0 = T(0), r1 = T(0), r2 = T(0), r3 = T(0);
       int q = lo + lane;
-      for (; q + 32 < hi; q += 64) {
-        r0 += W::near(d, x > sx[q] ? x - sx[q] : sx[q] - x);
-        r1 += W::near(d, x > sx[q + 32] ? x - sx[q + 32] : sx[q + 32] - x);
+      if constexpr (CL > 1) {
+        for (; q + 96 < hi; q += 128) {
+          r0 += W::near(d, x > sx[q] ? x - sx[q] : sx[q] - x);
+          r1 += W::near(d, x > sx[q + 32] ? x - sx[q + 32] : sx[q + 32] - x);
+          r2 += W::near(d, x > sx[q + 64] ? x - sx[q + 64] : sx[q + 64] - x);
+          r3 += W::near(d, x > sx[q + 96] ? x - sx[q + 96] : sx[q + 96] - x);
+        }
       }
-      if (q < hi) r0 += W::near(d, x > sx[q] ? x - sx[q] : sx[q] - x);
-      const T r = warp_sum(r0 + r1);
+      for (; q < hi; q += 32) r0 += W::near(d, x > sx[q] ? x - sx[q] : sx[q] - x);
+      const T r = warp_sum((r0 + r1) + (r2 + r3));
       if (lane == 0) sr[j] = MIX ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
     }
   }
@@ -606,30 +614,32 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
       MV A = MS::load(sA, j), B = MS::load(sB, j);
       typename MS::Acc dA{}, dB{};
       const int lo = lower_at_least(sx, m, x - S), hi = lower_at_least(sx, m, x + S + 1);
-      typename MS::Acc eA{}, eB{};  // second chain per lane
+      // second tier: four chains per lane (q, q + 32, q + 64, q + 96),
+      // merged at the end; first tier: one
+      typename MS::Acc cA[4] = {}, cB[4] = {};
+      auto pair = [&](int qq, int ch) {
+        if (qq == j) return;
+        const T P =
+            normalised<T>(d.norm, W::near(d, x > sx[qq] ? x - sx[qq] : sx[qq] - x), ip, sr[qq]);
+        MS::acc(cA[ch], P, MS::diff(MS::load(sA, qq), A));
+        MS::acc(cB[ch], P, MS::diff(MS::load(sB, qq), B));
+      };
       int q = lo + lane;
-      for (; q + 32 < hi; q += 64) {
-        if (q != j) {
-          const T P =
-              normalised<T>(d.norm, W::near(d, x > sx[q] ? x - sx[q] : sx[q] - x), ip, sr[q]);
-          MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
-          MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
+      if constexpr (CL > 1) {
+        for (; q + 96 < hi; q += 128) {
+          pair(q, 0);
+          pair(q + 32, 1);
+          pair(q + 64, 2);
+          pair(q + 96, 3);
         }
-        const int q2 = q + 32;
-        if (q2 != j) {
-          const T P =
-              normalised<T>(d.norm, W::near(d, x > sx[q2] ? x - sx[q2] : sx[q2] - x), ip, sr[q2]);
-          MS::acc(eA, P, MS::diff(MS::load(sA, q2), A));
-          MS::acc(eB, P, MS::diff(MS::load(sB, q2), B));
-        }
+        for (; q < hi; q += 32) pair(q, 0);
+        dA = acc_warp_sum(acc_merge(acc_merge(cA[0], cA[1]), acc_merge(cA[2], cA[3])));
+        dB = acc_warp_sum(acc_merge(acc_merge(cB[0], cB[1]), acc_merge(cB[2], cB[3])));
+      } else {
+        for (; q < hi; q += 32) pair(q, 0);
+        dA = acc_warp_sum(cA[0]);
+        dB = acc_warp_sum(cB[0]);
       }
-      if (q < hi && q != j) {
-        const T P = normalised<T>(d.norm, W::near(d, x > sx[q] ? x - sx[q] : sx[q] - x), ip, sr[q]);
-        MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
-        MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
-      }
-      dA = acc_warp_sum(acc_merge(dA, eA));
-      dB = acc_warp_sum(acc_merge(dB, eB));
       if (lane == 0) {
         MS::update(A, B, dA, dB, d.react);
         const long long o = out0 + (j - w0);
@@ -796,11 +806,25 @@ __device__ void reduce_realisation(const Dev& d, int r) {
   const unsigned long long* tag = reinterpret_cast<const unsigned long long*>(d.partials);
   const unsigned long long step = c->step;
   MV ta{}, tb{}, td{};
-  for (int blk = R.seg0 + tid; blk < R.seg0 + R.nseg; blk += NT) {
-    if (__ldcg(&tag[4 * blk + 3]) != step) continue;  // no group started here this step
-    ta = obs_add(ta, ldcg_obs(&part[4 * blk + 0]));
-    tb = obs_add(tb, ldcg_obs(&part[4 * blk + 1]));
-    td = obs_add(td, ldcg_obs(&part[4 * blk + 2]));
+  // slots in chunks of 4 per thread: the tag loads of a chunk are issued
+  // together (they are independent), then the chunk's live slots are added
+  // in slot order
+  constexpr int U = 4;
+  for (int b0 = R.seg0 + tid; b0 < R.seg0 + R.nseg; b0 += NT * U) {
+    unsigned long long tg[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int blk = b0 + u * NT;
+      tg[u] = blk < R.seg0 + R.nseg ? __ldcg(&tag[4 * blk + 3]) : ~step;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int blk = b0 + u * NT;
+      if (tg[u] != step) continue;  // no group started here this step
+      ta = obs_add(ta, ldcg_obs(&part[4 * blk + 0]));
+      tb = obs_add(tb, ldcg_obs(&part[4 * blk + 1]));
+      td = obs_add(td, ldcg_obs(&part[4 * blk + 2]));
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -867,6 +891,30 @@ __device__ __forceinline__ void fused_advance(const Dev& d) {
   c->mcur ^= 1;
   c->scur ^= 1;
   c->fallback = 0;
+  c->npred = c->npred_next;
+  c->npred_next = 0;
+}
+
+// The first tier and the predicted-segment kernel run side by side; the
+// last CTA of each calls this (one thread).  The second caller decides the
+// step: advance it, or (segments newly queued, or a predicted segment that
+// did not fit) raise the graph condition for the second tier.  Without the
+// predicted-segment kernel (small systems) the first tier decides alone.
+__device__ __forceinline__ void join_step(const Dev& d, cudaGraphConditionalHandle cond,
+                                          int use_cond) {
+  Ctrl* c = d.ctrl;
+  __threadfence();
+  if (d.use_pred && atomicAdd(&c->kjoin, 1u) != 1u) return;  // the first of two
+  __threadfence();
+  const int nov = atomicAdd(&c->nov, 0);
+  const int ov = atomicAdd(&c->overflow, 0);
+  const bool more = nov > 0 || ov != 0;
+  if (!more) fused_advance(d);
+  if (more) c->big_steps += 1;
+  if (nov > c->ov_value) c->ov_value = nov;  // largest queue seen (diagnostic)
+  c->kjoin = 0;
+  c->seg_ctr = 0;
+  if (use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
 }
 
 // First tier: a persistent grid (a few CTAs per SM) looping over the
@@ -889,32 +937,51 @@ __global__ void __launch_bounds__(Fast::kT, kFusedCtasPerSm) k_step1d(Dev d, cud
   ObsAcc<MIX>& obs = s_obs[threadIdx.x];
   obs = ObsAcc<MIX>{};
   int gslot = -1, greal = -1, gcount = 0;
+  const unsigned char* pcur = d.pred[sc];
+  unsigned char* pnext = d.pred[sc ^ 1];
+  // Segments: the first wave by CTA index, then one ticket at a time (drawn
+  // while the current one is processed, so its scalars load meanwhile).
+  // Segments predicted pair-heavy belong to the predicted-segment kernel.
+  // (two ticket words: a skipped segment has no barrier of its own before
+  // the next ticket is written)
+  __shared__ int s_ticket[2];
+  int par = 0;
   int seg = blockIdx.x;
   SegScalars cur = {};
   if (seg < d.nseg) cur = load_seg(d, sc, Dc, seg);
-  for (; seg < d.nseg; seg += gridDim.x) {
+  while (seg < d.nseg) {
+    if (threadIdx.x == 0) s_ticket[par] = (int)gridDim.x + atomicAdd(&c->seg_ctr, 1);
+    __syncthreads();
+    const int next = s_ticket[par];
+    par ^= 1;
     SegScalars nxt = {};
-    const bool has_next = seg + (int)gridDim.x < d.nseg;
-    if (has_next) nxt = load_seg(d, sc, Dc, seg + gridDim.x);
-    const int r = d.sreal[seg];
-    if (observe && gcount > 0 && r != greal) {  // a new realisation ends the group
-      flush_obs<MIX, Fast::kT, 1>(d, gslot, 0, obs);
-      complete_group<MIX, Fast::kT>(d, greal, gcount);
-      gcount = 0;
-    }
-    const int st = fused_segment<MIX, Fast, 1>(d, seg, smem, cur, 0, 1, true, obs);
-    if (st == kSegOk) {
-      if (observe) {
-        if (gcount == 0) {
-          gslot = seg;
-          greal = r;
-        }
-        ++gcount;
+    if (next < d.nseg) nxt = load_seg(d, sc, Dc, next);
+    if (!d.use_pred || !pcur[seg]) {
+      const int r = d.sreal[seg];
+      if (observe && gcount > 0 && r != greal) {  // a new realisation ends the group
+        flush_obs<MIX, Fast::kT, 1>(d, gslot, 0, obs);
+        complete_group<MIX, Fast::kT>(d, greal, gcount);
+        gcount = 0;
       }
-    } else if (threadIdx.x == 0) {
-      d.ovlist[atomicAdd(&c->nov, 1)] = seg;
+      const int st = fused_segment<MIX, Fast, 1>(d, seg, smem, cur, 0, 1, true, obs);
+      if (st == kSegOk) {
+        if (observe) {
+          if (gcount == 0) {
+            gslot = seg;
+            greal = r;
+          }
+          ++gcount;
+        }
+      } else if (threadIdx.x == 0) {
+        d.ovlist[atomicAdd(&c->nov, 1)] = seg;
+      }
+      if (threadIdx.x == 0) {
+        pnext[seg] = st == kSegOk ? 0 : 1;
+        if (st != kSegOk) atomicAdd(&c->npred_next, 1);
+      }
     }
     cur = nxt;
+    seg = next;
   }
   if (observe && gcount > 0) {
     flush_obs<MIX, Fast::kT, 1>(d, gslot, 0, obs);
@@ -926,14 +993,88 @@ __global__ void __launch_bounds__(Fast::kT, kFusedCtasPerSm) k_step1d(Dev d, cud
   }
   __syncthreads();
   if (!s_last) return;
-  __threadfence();
-  const int nov = atomicAdd(&c->nov, 0);
   if (threadIdx.x == 0) {
-    if (nov == 0) fused_advance(d);
-    if (nov > 0) c->big_steps += 1;
-    if (nov > c->ov_value) c->ov_value = nov;  // largest queue seen (diagnostic)
-    if (use_cond) cudaGraphSetConditional(cond, nov > 0 ? 1u : 0u);
     c->done = 0;
+    join_step(d, cond, use_cond);
+  }
+}
+
+// The predicted-segment kernel: one thread-block cluster takes the segments
+// that were pair-heavy last step (the layer piled against a wall stays in
+// the same segment from step to step), at the same time as the first tier
+// works on the rest.  All CTAs of the cluster list the predicted segments
+// in index order (an ordered compaction per chunk of indices) and process
+// them one after another like the second tier; each records whether its
+// segment is still heavy for the next step's prediction.
+template <bool MIX, int CL>
+__global__ void __launch_bounds__(Big::kT, 1)
+    k_step1d_pred(Dev d, cudaGraphConditionalHandle cond, int use_cond) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ bool s_last;
+  __shared__ int s_warp[Big::kT / 32];
+  __shared__ int s_list[Big::kT];
+  __shared__ int s_nlist;
+  Ctrl* c = d.ctrl;
+  const int sc = c->scur;
+  const long long Dc = (c->dmax >> d.cshift) + 2;
+  const int rank = blockIdx.x % CL;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned char* pcur = d.pred[sc];
+  unsigned char* pnext = d.pred[sc ^ 1];
+  __shared__ ObsAcc<MIX> s_obs[Big::kT];
+  ObsAcc<MIX>& obs = s_obs[tid];
+  if (blockIdx.x < CL && c->npred > 0) {  // the first cluster does the work
+    for (int base = 0; base < d.nseg; base += Big::kT) {
+      const int sidx = base + tid;
+      const bool f = sidx < d.nseg && pcur[sidx] != 0;
+      const unsigned int bal = __ballot_sync(0xffffffffu, f);
+      if (lane == 0) s_warp[warp] = __popc(bal);
+      __syncthreads();
+      if (tid == 0) {
+        int run = 0;
+        for (int w = 0; w < Big::kT / 32; ++w) {
+          const int v = s_warp[w];
+          s_warp[w] = run;
+          run += v;
+        }
+        s_nlist = run;
+      }
+      __syncthreads();
+      if (f) s_list[s_warp[warp] + __popc(bal & ((1u << lane) - 1u))] = sidx;
+      __syncthreads();
+      const int nl = s_nlist;
+      for (int k = 0; k < nl; ++k) {
+        const int seg = s_list[k];
+        obs = ObsAcc<MIX>{};
+        bool heavy = true;
+        const int st = fused_segment<MIX, Big, CL>(d, seg, smem, load_seg(d, sc, Dc, seg), rank,
+                                                   CL, false, obs, &heavy);
+        if (st == kSegOk) {
+          if (d.observe_cap > 0) {
+            flush_obs<MIX, Big::kT, CL>(d, seg, rank, obs);
+            if (rank == 0) complete_group<MIX, Big::kT>(d, d.sreal[seg], 1);
+          }
+        } else if (tid == 0 && atomicExch(&c->overflow, 1) == 0) {
+          c->ov_reason = st;
+          c->ov_seg = seg;
+        }
+        if (tid == 0 && rank == 0) {
+          pnext[seg] = heavy ? 1 : 0;
+          if (heavy) atomicAdd(&c->npred_next, 1);
+        }
+      }
+      __syncthreads();  // s_list is rewritten for the next chunk
+    }
+  }
+  if (tid == 0) {
+    __threadfence();
+    s_last = atomicAdd(&c->gdone, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  if (tid == 0) {
+    c->gdone = 0;
+    join_step(d, cond, use_cond);
   }
 }
 
@@ -1039,6 +1180,8 @@ __global__ void k_fused_flip(Dev d, int flip) {
   if (flip) d.ctrl->scur ^= 1;
   d.ctrl->fallback = 0;
   d.ctrl->nov = 0;
+  d.ctrl->npred = d.ctrl->npred_next;
+  d.ctrl->npred_next = 0;
 }
 
 // Largest |rint(b xi)| over an injected noise buffer -> Ctrl::dmax.
@@ -1072,6 +1215,10 @@ __global__ void k_set_dmax(Dev d, long long v) { d.ctrl->dmax = v; }
 // resident (non-portable size), else 8.
 static int g_big_cluster = 8;
 
+// Highest launch priority of the device (the predicted-segment kernel's
+// CTAs should take their SMs before the first tier fills them).
+static int g_top_priority = 0;
+
 template <bool MIX, int CL>
 static cudaError_t configure_big(int precision) {
   auto k = k_step1d_big<MIX, CL>;
@@ -1079,6 +1226,12 @@ static cudaError_t configure_big(int precision) {
                                        (int)tier_smem<Big>(precision));
   if (e == cudaSuccess && CL > 8)
     e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  auto kp = k_step1d_pred<MIX, CL>;
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tier_smem<Big>(precision));
+  if (e == cudaSuccess && CL > 8)
+    e = cudaFuncSetAttribute(kp, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;
 }
 
@@ -1119,6 +1272,9 @@ cudaError_t fused_configure() {
       max_active_clusters<true, 16>(MT_MIXED) >= 1 && max_active_clusters<false, 16>(MT_FP64) >= 1)
     g_big_cluster = 16;
   cudaGetLastError();  // a refused non-portable size leaves the 8-CTA choice
+  int lo = 0, hi = 0;
+  if (cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess) g_top_priority = hi;
+  cudaGetLastError();
   return cudaSuccess;
 }
 
@@ -1160,6 +1316,43 @@ cudaError_t launch_fused_big(const Dev& d, int precision, cudaGraphConditionalHa
                                  : launch_big<false, 16>(d, precision, cond, use_cond, s);
   return precision == MT_MIXED ? launch_big<true, 8>(d, precision, cond, use_cond, s)
                                : launch_big<false, 8>(d, precision, cond, use_cond, s);
+}
+
+template <bool MIX, int CL>
+static cudaError_t launch_pred(const Dev& d, int precision, cudaGraphConditionalHandle cond,
+                               int use_cond, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributePriority;
+  at[1].val.priority = g_top_priority;
+  cfg.gridDim = dim3((unsigned int)CL);  // one cluster
+  cfg.blockDim = dim3(Big::kT);
+  cfg.dynamicSmemBytes = tier_smem<Big>(precision);
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, k_step1d_pred<MIX, CL>, d, cond, use_cond);
+}
+
+cudaError_t launch_fused_pred(const Dev& d, int precision, cudaGraphConditionalHandle cond,
+                              int use_cond, cudaStream_t s) {
+  if (g_big_cluster == 16)
+    return precision == MT_MIXED ? launch_pred<true, 16>(d, precision, cond, use_cond, s)
+                                 : launch_pred<false, 16>(d, precision, cond, use_cond, s);
+  return precision == MT_MIXED ? launch_pred<true, 8>(d, precision, cond, use_cond, s)
+                               : launch_pred<false, 8>(d, precision, cond, use_cond, s);
+}
+
+// Direct launches without a predicted segment: the join's second arrival.
+__global__ void k_join_stub(Dev d) { join_step(d, 0, 0); }
+
+cudaError_t launch_join_stub(const Dev& d, cudaStream_t s) {
+  k_join_stub<<<1, 1, 0, s>>>(d);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fused_prep(const Dev& d, int flip, cudaStream_t s) {

@@ -47,7 +47,11 @@ struct Ctrl {
   unsigned long long fallbacks; // steps the general pipeline redid since upload
   unsigned long long big_steps; // steps that needed the second fused tier
   int nov;                      // segments queued for the second tier this step
-  int pad1;
+  int seg_ctr;                  // first-tier segments handed out beyond the first wave
+  unsigned int gdone;           // CTAs of the predicted-segment kernel finished
+  unsigned int kjoin;           // of the two concurrent fused kernels, how many are done
+  int npred;                    // segments predicted pair-heavy for this step
+  int npred_next;               // ... counted during this step for the next
 };
 
 // One realisation of a batch (a single system is a batch of one).  Batched
@@ -84,6 +88,8 @@ struct Dev {
   int* fstart[2];           // [ncell + 1] cell starts of the sorted state (fused path)
   int* cb[2];               // [nseg + 1] first cell of each fused segment
   int* ovlist;              // [nseg] segments queued for the second fused tier
+  unsigned char* pred[2];   // [nseg] segments predicted pair-heavy (by scur parity)
+  int use_pred;             // 1: the predicted-segment kernel runs beside the first tier
   long long n;
   int dim;
   int norm;                 // MT_NORM_*
@@ -302,6 +308,9 @@ size_t fused_smem_bytes(int precision);
 cudaError_t fused_configure();  // opt in to the large dynamic shared memory
 cudaError_t launch_fused_step(const Dev& d, int precision, cudaGraphConditionalHandle cond,
                               int use_cond, cudaStream_t s);
+cudaError_t launch_fused_pred(const Dev& d, int precision, cudaGraphConditionalHandle cond,
+                              int use_cond, cudaStream_t s);  // predicted heavy segments
+cudaError_t launch_join_stub(const Dev& d, cudaStream_t s);
 cudaError_t launch_fused_big(const Dev& d, int precision, cudaGraphConditionalHandle cond,
                              int use_cond, cudaStream_t s);
 cudaError_t launch_fused_prep(const Dev& d, int flip, cudaStream_t s);  // start/cb from d.start

@@ -157,7 +157,7 @@ def test_batch_with_dense_realisation_uses_second_tier(cluster):
     sim.set_noise(None)
     sim.step()
     names = [k for k, _ in mt.mt_read_profile(sim.h)]
-    assert names[:2] == ["fused_step", "fused_big"]
+    assert "fused_step" in names and ("fused_pred" in names or "fused_big" in names)
     if cluster == 5000:
         assert "observables" in names  # the general pipeline redid the step
     obs = sim.observables()

@@ -393,11 +393,14 @@ def test_fused_tiers_on_clustered_segments(cluster, tiers):
     mt.mt_set_profiling(sim.h, True)
     sim.step()
     names = [k for k, _ in mt.mt_read_profile(sim.h)]
-    assert names[:len(tiers)] == tiers
+    # the heavy segment goes to a cluster kernel: the predicted-segment
+    # kernel (it was heavy last step) or the second tier (newly heavy)
+    assert "fused_step" in names
+    assert ("fused_pred" in names) or ("fused_big" in names)
     if "move" in tiers:
         assert names[-1] == "fused_prep"
     else:
-        assert len(names) == len(tiers)
+        assert "move" not in names
 
 
 def test_fused_segments_many_steps_with_drift_and_walls():
@@ -440,7 +443,12 @@ def test_fused_dense_bins_sorted_in_place(cluster, tiers):
     run_both(sim, x, A, B, 3, pairs=True)
     mt.mt_set_profiling(sim.h, True)
     sim.step()
-    assert [k for k, _ in mt.mt_read_profile(sim.h)] == tiers
+    names = [k for k, _ in mt.mt_read_profile(sim.h)]
+    if tiers == ["fused_step"]:
+        assert names == ["fused_step"]
+    else:  # a cluster kernel took the pair-heavy segment
+        assert "fused_step" in names and ("fused_pred" in names or "fused_big" in names)
+        assert "move" not in names
 
 
 @pytest.mark.parametrize("precision", [mt.MT_FP64, mt.MT_MIXED])
