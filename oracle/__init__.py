@@ -31,6 +31,8 @@ SEARCH_CUTOFF = 0
 SEARCH_FULL = 2
 NORM_SYM = 0
 NORM_ROW = 1
+WALLS_REFLECT = 0
+WALLS_PERIODIC = 1
 
 
 class Params(ctypes.Structure):
@@ -46,22 +48,23 @@ class Params(ctypes.Structure):
         ("search", ctypes.c_int32),
         ("norm", ctypes.c_int32),
         ("react", ctypes.c_int32),
-        ("pad_", ctypes.c_int32),
+        ("walls", ctypes.c_int32),
     ]
 
 
 def params(*, dim=1, frac_bits=29, L=(1000.0, 0.0), v=(0.0, 0.0), D_mt=0.1,
            D_rw=0.1, dt=1.0, smax=None, search=SEARCH_CUTOFF, norm=NORM_SYM,
-           react=1) -> Params:
+           react=1, walls=0) -> Params:
     """Problem parameters.  ``smax`` defaults to three standard deviations of
-    Eq. 3's Gaussian, 3 * sqrt(4 D_mt dt)."""
+    Eq. 3's Gaussian, 3 * sqrt(4 D_mt dt).  ``walls``: WALLS_REFLECT (Sec. 3)
+    or WALLS_PERIODIC (a wrapping domain, minimum-image separations)."""
     if smax is None:
         smax = 3.0 * np.sqrt(4.0 * D_mt * dt)
     Lv = list(L) + [0.0] * (2 - len(L))
     vv = list(v) + [0.0] * (2 - len(v))
     return Params(dim, frac_bits, (ctypes.c_double * 2)(*Lv),
                   (ctypes.c_double * 2)(*vv), D_mt, D_rw, dt, float(smax),
-                  search, norm, react, 0)
+                  search, norm, react, walls)
 
 
 def build(force: bool = False) -> Path:

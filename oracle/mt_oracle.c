@@ -33,6 +33,11 @@ static int valid(const mto_params* p) {
   if (!(p->D_mt > 0.0) || !(p->dt > 0.0) || !(p->D_rw >= 0.0)) return 0;
   if (p->norm != MTO_NORM_SYM && p->norm != MTO_NORM_ROW) return 0;
   if (p->search != MTO_SEARCH_CUTOFF && p->search != MTO_SEARCH_FULL) return 0;
+  if (p->walls != MTO_WALLS_REFLECT && p->walls != MTO_WALLS_PERIODIC) return 0;
+  if (p->walls == MTO_WALLS_PERIODIC && p->search == MTO_SEARCH_CUTOFF)
+    for (int32_t d = 0; d < p->dim; ++d) /* one image per pair: 2 Smax < L */
+      if (2 * (int64_t)floor(ldexp(p->smax, p->frac_bits)) >= llrint(ldexp(p->L[d], p->frac_bits)))
+        return 0;
   if (p->search == MTO_SEARCH_CUTOFF) {
     if (!(p->smax >= 0.0)) return 0;
     /* |dX|, |dY| <= Smax < 2^31 keeps dX^2 + dY^2 inside 63 bits. */
@@ -57,6 +62,12 @@ static int64_t reflect(int64_t y, int64_t Lq) {
   return y < 0 ? 0 : (y > Lq ? Lq : y);
 }
 
+/* Periodic walls: y taken modulo Lq into [0, Lq). */
+static int64_t wrap(int64_t y, int64_t Lq) {
+  const int64_t m = y % Lq;
+  return m < 0 ? m + Lq : m;
+}
+
 void mto_move(const mto_params* p, int64_t n, int64_t* X, const float* xi) {
   const int32_t k = p->frac_bits;
   /* Eq. 2 with alpha_L = 0: the random walk carries D_rw (Sec. 3). */
@@ -67,7 +78,7 @@ void mto_move(const mto_params* p, int64_t n, int64_t* X, const float* xi) {
     for (int64_t i = 0; i < n; ++i) {
       const float step = b * xi[(int64_t)d * n + i];
       const int64_t y = X[(int64_t)d * n + i] + drift + (int64_t)llrintf(step);
-      X[(int64_t)d * n + i] = reflect(y, Lq);
+      X[(int64_t)d * n + i] = p->walls == MTO_WALLS_PERIODIC ? wrap(y, Lq) : reflect(y, Lq);
     }
   }
 }
@@ -99,9 +110,27 @@ static double weight(const mto_params* p, double inv8, int64_t dx, int64_t dy) {
 
 static double inv8(const mto_params* p) { return 1.0 / (8.0 * p->D_mt * p->dt); }
 
+/* Separation X_j - X_i along axis d; with periodic walls the minimum image,
+ * in (-Lq/2, Lq/2]. */
+static int64_t sep(const mto_params* p, int32_t d, int64_t xi_, int64_t xj) {
+  int64_t s = xj - xi_;
+  if (p->walls == MTO_WALLS_PERIODIC) {
+    const int64_t Lq = llrint(ldexp(p->L[d], p->frac_bits));
+    if (2 * s > Lq) s -= Lq;
+    else if (2 * s <= -Lq) s += Lq;
+  }
+  return s;
+}
+
+static int64_t dX(const mto_params* p, int64_t n, const int64_t* X, int64_t i,
+                  int64_t j) {
+  (void)n;
+  return sep(p, 0, X[i], X[j]);
+}
+
 static int64_t dY(const mto_params* p, int64_t n, const int64_t* X, int64_t i,
                   int64_t j) {
-  return p->dim == 2 ? X[n + j] - X[n + i] : 0;
+  return p->dim == 2 ? sep(p, 1, X[n + i], X[n + j]) : 0;
 }
 
 /* ------------------------------------------------------------- weights --- */
@@ -112,7 +141,7 @@ void mto_row_sums(const mto_params* p, int64_t n, const int64_t* X, double* r) {
   for (int64_t i = 0; i < n; ++i) {
     double s = 0.0;
     for (int64_t j = 0; j < n; ++j) {
-      const int64_t dx = X[j] - X[i], dy = dY(p, n, X, i, j);
+      const int64_t dx = dX(p, n, X, i, j), dy = dY(p, n, X, i, j);
       if (in_range(p, S, dx, dy)) s += weight(p, c, dx, dy);
     }
     r[i] = s;
@@ -143,7 +172,7 @@ int mto_mass_transfer(const mto_params* p, int64_t n, const int64_t* X,
       double acc = 0.0; /* sum_j P_ij (M_j - M_i), Eq. 4 */
       for (int64_t j = 0; j < n; ++j) {
         if (j == i) continue;
-        const int64_t dx = X[j] - X[i], dy = dY(p, n, X, i, j);
+        const int64_t dx = dX(p, n, X, i, j), dy = dY(p, n, X, i, j);
         if (!in_range(p, S, dx, dy)) continue;
         const double w = weight(p, c, dx, dy);
         acc += normalised(p, w, r[i], r[j]) * (M[s][j] - M[s][i]);
@@ -172,7 +201,7 @@ int mto_mass_transfer_matrix(const mto_params* p, int64_t n, const int64_t* X,
   /* nu_ij (Eq. 3) as a dense matrix, zero outside the cutoff. */
   for (int64_t i = 0; i < n; ++i)
     for (int64_t j = 0; j < n; ++j) {
-      const int64_t dx = X[j] - X[i], dy = dY(p, n, X, i, j);
+      const int64_t dx = dX(p, n, X, i, j), dy = dY(p, n, X, i, j);
       if (in_range(p, S, dx, dy)) nu[i * n + j] = weight(p, c, dx, dy);
     }
   for (int64_t i = 0; i < n; ++i) {
@@ -205,7 +234,7 @@ static double row_sum_one(const mto_params* p, int64_t n, const int64_t* X,
                           int64_t i, int64_t S, double c) {
   double s = 0.0;
   for (int64_t j = 0; j < n; ++j) {
-    const int64_t dx = X[j] - X[i], dy = dY(p, n, X, i, j);
+    const int64_t dx = dX(p, n, X, i, j), dy = dY(p, n, X, i, j);
     if (in_range(p, S, dx, dy)) s += weight(p, c, dx, dy);
   }
   return s;
@@ -226,7 +255,7 @@ int mto_mass_transfer_sample(const mto_params* p, int64_t n, const int64_t* X,
     if (nspec > 8) return -1;
     for (int64_t j = 0; j < n; ++j) {
       if (j == i) continue;
-      const int64_t dx = X[j] - X[i], dy = dY(p, n, X, i, j);
+      const int64_t dx = dX(p, n, X, i, j), dy = dY(p, n, X, i, j);
       if (!in_range(p, S, dx, dy)) continue;
       const double w = weight(p, c, dx, dy);
       const double rj = p->norm == MTO_NORM_SYM ? row_sum_one(p, n, X, j, S, c) : ri;
@@ -262,7 +291,7 @@ int mto_mass_transfer_sorted_1d(const mto_params* p, int64_t n,
                                 const int64_t* X, int32_t nspec,
                                 const double* const* M, double* const* Mout) {
   if (!valid(p) || p->dim != 1 || p->search != MTO_SEARCH_CUTOFF || n < 0 ||
-      nspec < 1)
+      nspec < 1 || p->walls != MTO_WALLS_REFLECT)
     return -1;
   const int64_t S = mto_cutoff_ticks(p);
   const double c = inv8(p);
@@ -325,7 +354,7 @@ int64_t mto_pairs_brute(const mto_params* p, int64_t n, const int64_t* X,
   int64_t cnt = 0;
   for (int64_t i = 0; i < n; ++i)
     for (int64_t j = i + 1; j < n; ++j) {
-      const int64_t dx = X[j] - X[i], dy = dY(p, n, X, i, j);
+      const int64_t dx = dX(p, n, X, i, j), dy = dY(p, n, X, i, j);
       if (!in_range(p, S, dx, dy)) continue;
       if (cnt < cap) {
         pi[cnt] = (int32_t)i;
@@ -338,7 +367,9 @@ int64_t mto_pairs_brute(const mto_params* p, int64_t n, const int64_t* X,
 
 int64_t mto_pairs_sorted_1d(const mto_params* p, int64_t n, const int64_t* X,
                             int64_t cap, int32_t* pi, int32_t* pj) {
-  if (!valid(p) || p->dim != 1 || p->search != MTO_SEARCH_CUTOFF) return -1;
+  if (!valid(p) || p->dim != 1 || p->search != MTO_SEARCH_CUTOFF ||
+      p->walls != MTO_WALLS_REFLECT)
+    return -1;
   const int64_t S = mto_cutoff_ticks(p);
   int64_t* ord = sorted_order(n, X);
   if (!ord) return -1;
@@ -372,7 +403,7 @@ int mto_step(const mto_params* p, int64_t n, int64_t* X, const float* xi,
   const double* M[2] = {A, B};
   double* Mo[2] = {A2, B2};
   int rc;
-  if (p->dim == 1 && p->search == MTO_SEARCH_CUTOFF)
+  if (p->dim == 1 && p->search == MTO_SEARCH_CUTOFF && p->walls == MTO_WALLS_REFLECT)
     rc = mto_mass_transfer_sorted_1d(p, n, X, 2, M, Mo);
   else
     rc = mto_mass_transfer(p, n, X, 2, M, Mo);

@@ -40,11 +40,12 @@ extern "C" {
 
 enum { MTO_SEARCH_CUTOFF = 0, MTO_SEARCH_FULL = 2 };
 enum { MTO_NORM_SYM = 0, MTO_NORM_ROW = 1 };
+enum { MTO_WALLS_REFLECT = 0, MTO_WALLS_PERIODIC = 1 };
 
 typedef struct {
   int32_t dim;        /* 1 or 2 */
   int32_t frac_bits;  /* k in x = X * 2^-k */
-  double  L[2];       /* domain [0, L0] (x [0, L1]) with reflecting walls */
+  double  L[2];       /* domain [0, L0] (x [0, L1]) */
   double  v[2];       /* constant advection velocity */
   double  D_mt;       /* diffusion coefficient carried by mass transfer, Eq. 3 */
   double  D_rw;       /* diffusion coefficient carried by the random walk, Eq. 2 */
@@ -53,7 +54,9 @@ typedef struct {
   int32_t search;     /* MTO_SEARCH_CUTOFF or MTO_SEARCH_FULL (no cutoff) */
   int32_t norm;       /* MTO_NORM_SYM or MTO_NORM_ROW */
   int32_t react;      /* 1: apply A + B -> E after the transfer */
-  int32_t pad_;
+  int32_t walls;      /* MTO_WALLS_REFLECT (Sec. 3) or MTO_WALLS_PERIODIC: the
+                         domain wraps, positions live in [0, L) and pairs
+                         take the minimum-image separation (needs s_max < L/2) */
 } mto_params;
 
 /* x -> nearest grid point X = rint(x * 2^k) (ties to even). */
