@@ -75,6 +75,7 @@ enum { MT_SEARCH_CELL = 0, MT_SEARCH_BRUTE = 1, MT_SEARCH_FULL = 2 };
 enum { MT_FP64 = 0, MT_MIXED = 1 };
 enum { MT_NORM_SYM = 0, MT_NORM_ROW = 1 };
 enum { MT_MEM_HOST = 0, MT_MEM_DEVICE = 1 };
+enum { MT_WALLS_REFLECT = 0, MT_WALLS_PERIODIC = 1 };
 
 typedef struct mt_params {
   int32_t dim;          /* 1 or 2 */
@@ -100,7 +101,12 @@ typedef struct mt_params {
                            largest that fits the staging, lowered so the
                            segments fill whole waves of the step's resident
                            CTAs on the current device) */
-  int32_t reserved;     /* 0 */
+  int32_t walls;        /* MT_WALLS_REFLECT (Sec. 3, default) or
+                           MT_WALLS_PERIODIC: the domain wraps, positions
+                           live in [0, L) and pairs take the minimum-image
+                           separation; needs s_max < L/2 per axis; 1-d with
+                           any search, 2-d with MT_SEARCH_BRUTE or FULL;
+                           single systems only */
 } mt_params;
 
 /* A batch: count independent 1-d realisations (the ensembles of repeated

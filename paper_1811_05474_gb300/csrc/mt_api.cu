@@ -151,6 +151,12 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
     return fail(MT_ERR_INVALID, "unknown norm %d", p.norm);
   if (p.react != 0 && p.react != 1) return fail(MT_ERR_INVALID, "react must be 0 or 1");
   if (p.observe_cap < 0) return fail(MT_ERR_INVALID, "observe_cap must be >= 0");
+  if (p.walls != MT_WALLS_REFLECT && p.walls != MT_WALLS_PERIODIC)
+    return fail(MT_ERR_INVALID, "unknown walls %d", p.walls);
+  const bool periodic = p.walls == MT_WALLS_PERIODIC;
+  if (periodic && b) return fail(MT_ERR_INVALID, "batches use reflecting walls");
+  if (periodic && p.dim == 2 && p.search == MT_SEARCH_CELL)
+    return fail(MT_ERR_INVALID, "periodic walls in 2-d need MT_SEARCH_BRUTE or MT_SEARCH_FULL");
   if (p.frac_bits == 0) p.frac_bits = default_frac_bits(p);
   const int k = p.frac_bits;
   if (k < 1 || k > 62) return fail(MT_ERR_INVALID, "frac_bits must be in [1, 62] (got %d)", k);
@@ -170,6 +176,10 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
     return fail(MT_ERR_INVALID, "sqrt(2 D_rw dt) 2^frac_bits is too large for the grid");
   D.bq = (float)bw;
   D.S = (long long)std::floor(std::ldexp(p.cutoff, k));
+  if (periodic && p.search != MT_SEARCH_FULL)
+    for (int a = 0; a < p.dim; ++a)
+      if (2 * D.S >= D.Lq[a])
+        return fail(MT_ERR_INVALID, "periodic walls need the cutoff below L[%d]/2", a);
   // cell grid
   std::vector<long long> lq;  // batch: each realisation's length in ticks
   double lq_sum = (double)D.Lq[0];
@@ -229,7 +239,7 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
   // Fused 1-d step: segments of seg_target particles staged with a halo of
   // hc cells (2 Smax) and the displacement bound; pick the largest target
   // (<= 1024) whose expected staging, with 50% headroom, fits kFusedCap.
-  if (p.search == MT_SEARCH_CELL && p.dim == 1 && p.n > 0) {
+  if (p.search == MT_SEARCH_CELL && p.dim == 1 && p.n > 0 && !periodic) {
     const long long w = 1LL << D.cshift;
     D.hc = (2 * D.S + w - 1) / w + 1;
     double dr = std::fabs((double)D.drift[0]);
@@ -674,6 +684,7 @@ mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace
   // the predicted-segment kernel pays off when the first tier has more than
   // one wave of segments (large systems); small ones keep the plain chain
   d.use_pred = D.fused && D.nseg > (long long)kFusedCtasPerSm * d.nsm ? 1 : 0;
+  d.periodic = D.p.walls == MT_WALLS_PERIODIC ? 1 : 0;
   d.n = D.p.n;
   d.dim = D.p.dim;
   d.norm = D.p.norm;

@@ -90,6 +90,7 @@ struct Dev {
   int* ovlist;              // [nseg] segments queued for the second fused tier
   unsigned char* pred[2];   // [nseg] segments predicted pair-heavy (by scur parity)
   int use_pred;             // 1: the predicted-segment kernel runs beside the first tier
+  int periodic;             // 1: periodic walls (wrap, minimum-image separations)
   long long n;
   int dim;
   int norm;                 // MT_NORM_*
@@ -144,6 +145,20 @@ __device__ __forceinline__ long long reflect(long long y, long long Lq) {
       return y;
   }
   return y < 0 ? 0 : (y > Lq ? Lq : y);
+}
+
+// Periodic walls: y modulo Lq into [0, Lq).
+__device__ __forceinline__ long long wrap(long long y, long long Lq) {
+  const long long m = y % Lq;
+  return m < 0 ? m + Lq : m;
+}
+
+// Periodic walls: the minimum-image separation of two positions in [0, Lq),
+// in (-Lq/2, Lq/2].
+__device__ __forceinline__ long long min_image(long long s, long long Lq) {
+  if (2 * s > Lq) return s - Lq;
+  if (2 * s <= -Lq) return s + Lq;
+  return s;
 }
 
 __device__ __forceinline__ long long cell_of(const Dev& d, long long x, long long y) {

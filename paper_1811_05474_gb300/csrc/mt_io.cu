@@ -34,7 +34,9 @@ __global__ void k_upload(Dev d, const double* x, const double* A, const double* 
       raise_error(c, kErrInput, i);
     } else {
       X = __double2ll_rn(v * pow2k);
-      if (X > Lq) {
+      if (d.periodic && X == Lq) {
+        X = 0;  // L is the same point as 0
+      } else if (X > Lq) {
         raise_error(c, kErrInput, i);
         X = Lq;
       }
@@ -132,8 +134,21 @@ __global__ void k_pairs_walk(Dev d, int* pi, int* pj, long long cap) {
   const long long* X = d.X[xc];
   const int* id = d.id[xc];
   const long long x = X[p];
-  for (long long q = p + 1; q < d.n; ++q) {
-    if (X[q] - x > d.S) break;
+  if (!d.periodic) {
+    for (long long q = p + 1; q < d.n; ++q) {
+      if (X[q] - x > d.S) break;
+      emit(d, id[p], id[q], pi, pj, cap);
+    }
+    return;
+  }
+  // periodic: walk right around the ring (each pair is found from the
+  // particle that has the other on its right within Smax)
+  for (long long k = 1; k < d.n; ++k) {
+    long long q = p + k;
+    q = q >= d.n ? q - d.n : q;
+    long long D = X[q] - x;
+    D = D < 0 ? D + d.Lq[0] : D;
+    if (D > d.S) break;
     emit(d, id[p], id[q], pi, pj, cap);
   }
 }
@@ -174,12 +189,13 @@ __global__ void k_pairs_brute(Dev d, int* pi, int* pj, long long cap) {
   const int* id = d.id[xc];
   const long long x = X[p], y = d.dim == 2 ? X[d.n + p] : 0;
   for (long long q = p + 1; q < d.n; ++q) {
-    const long long dx = X[q] - x;
+    long long dx = X[q] - x;
+    if (d.periodic) dx = min_image(dx, d.Lq[0]);
     bool ok;
     if (d.dim == 1)
       ok = dx <= d.S && -dx <= d.S;
     else
-      ok = in_range2_io(dx, X[d.n + q] - y, d.S);
+      ok = in_range2_io(dx, d.periodic ? min_image(X[d.n + q] - y, d.Lq[1]) : X[d.n + q] - y, d.S);
     if (ok) emit(d, id[p], id[q], pi, pj, cap);
   }
 }

@@ -47,7 +47,9 @@ __global__ void __launch_bounds__(kThreads) k_move(Dev d) {
     for (int a = 0; a < DIM; ++a) {
       // Eq. 2 on the grid: drift + rint(b * xi), then the wall mirror.
       const long long step = float_to_ll_rn(__fmul_rn(d.bq, z[a]));
-      if (a == 0)
+      if (d.periodic)  // single systems only: base = 0
+        pos[a] = wrap(pos[a] + d.drift[a] + step, a == 0 ? R->Lq : d.Lq[a]);
+      else if (a == 0)
         pos[0] = base + reflect(pos[0] - base + d.drift[0] + step, R->Lq);
       else
         pos[a] = reflect(pos[a] + d.drift[a] + step, d.Lq[a]);

@@ -186,15 +186,32 @@ __global__ void __launch_bounds__(kThreads) k_rowsum_walk(Dev d) {
   const long long* Xs = d.X[xc ^ 1];
   const long long x = Xs[p];
   T r = T(1);  // self: nu_pp = 1
-  for (long long q = p - 1; q >= 0; --q) {
-    const long long D = x - Xs[q];
-    if (D > d.S) break;
-    r += W::eval(d, D, 0);
-  }
-  for (long long q = p + 1; q < d.n; ++q) {
-    const long long D = Xs[q] - x;
-    if (D > d.S) break;
-    r += W::eval(d, D, 0);
+  if (!d.periodic) {
+    for (long long q = p - 1; q >= 0; --q) {
+      const long long D = x - Xs[q];
+      if (D > d.S) break;
+      r += W::eval(d, D, 0);
+    }
+    for (long long q = p + 1; q < d.n; ++q) {
+      const long long D = Xs[q] - x;
+      if (D > d.S) break;
+      r += W::eval(d, D, 0);
+    }
+  } else {
+    // periodic: the walks continue around the ring (2 Smax < L, so no slot
+    // is reached from both sides)
+    for (long long k = 1; k < d.n; ++k) {
+      const long long q = p - k < 0 ? p - k + d.n : p - k;
+      const long long D = wrap(x - Xs[q], d.Lq[0]);
+      if (D > d.S) break;
+      r += W::eval(d, D, 0);
+    }
+    for (long long k = 1; k < d.n; ++k) {
+      const long long q = p + k >= d.n ? p + k - d.n : p + k;
+      const long long D = wrap(Xs[q] - x, d.Lq[0]);
+      if (D > d.S) break;
+      r += W::eval(d, D, 0);
+    }
   }
   store_rinv<MIX>(d, p, r);
   // gather id and masses into the sorted slots (stage buffer)
@@ -222,19 +239,35 @@ __global__ void __launch_bounds__(kThreads) k_exchange_walk(Dev d) {
     A = MS::load(Min, p);
     B = MS::load(Min, d.n + p);
     typename MS::Acc dA{}, dB{};
-    for (long long q = p - 1; q >= 0; --q) {
-      const long long D = x - Xs[q];
-      if (D > d.S) break;
+    auto pair = [&](long long q, long long D) {
       const T P = normalised<T>(d.norm, W::eval(d, D, 0), ip, load_rinv<MIX>(d, q));
       MS::acc(dA, P, MS::diff(MS::load(Min, q), A));
       MS::acc(dB, P, MS::diff(MS::load(Min, d.n + q), B));
-    }
-    for (long long q = p + 1; q < d.n; ++q) {
-      const long long D = Xs[q] - x;
-      if (D > d.S) break;
-      const T P = normalised<T>(d.norm, W::eval(d, D, 0), ip, load_rinv<MIX>(d, q));
-      MS::acc(dA, P, MS::diff(MS::load(Min, q), A));
-      MS::acc(dB, P, MS::diff(MS::load(Min, d.n + q), B));
+    };
+    if (!d.periodic) {
+      for (long long q = p - 1; q >= 0; --q) {
+        const long long D = x - Xs[q];
+        if (D > d.S) break;
+        pair(q, D);
+      }
+      for (long long q = p + 1; q < d.n; ++q) {
+        const long long D = Xs[q] - x;
+        if (D > d.S) break;
+        pair(q, D);
+      }
+    } else {
+      for (long long k = 1; k < d.n; ++k) {
+        const long long q = p - k < 0 ? p - k + d.n : p - k;
+        const long long D = wrap(x - Xs[q], d.Lq[0]);
+        if (D > d.S) break;
+        pair(q, D);
+      }
+      for (long long k = 1; k < d.n; ++k) {
+        const long long q = p + k >= d.n ? p + k - d.n : p + k;
+        const long long D = wrap(Xs[q] - x, d.Lq[0]);
+        if (D > d.S) break;
+        pair(q, D);
+      }
     }
     MS::update(A, B, dA, dB, d.react);
     MS::store(d.M[mc], p, A);
@@ -355,8 +388,12 @@ __global__ void __launch_bounds__(kThreads) k_rowsum_brute(Dev d) {
     const int jn = (int)min((long long)kBruteTile, d.n - j0);
     if (valid) {
       for (int jj = 0; jj < jn; ++jj) {
-        const long long dx = s_x[jj] - x;
-        const long long dy = DIM == 2 ? s_y[jj] - y : 0;
+        long long dx = s_x[jj] - x;
+        long long dy = DIM == 2 ? s_y[jj] - y : 0;
+        if (d.periodic) {
+          dx = min_image(dx, d.Lq[0]);
+          if (DIM == 2) dy = min_image(dy, d.Lq[1]);
+        }
         if (CUT) {
           if (DIM == 1 ? !within1(dx, d.S) : !in_range2(dx, dy, d.S)) continue;
         }
@@ -408,8 +445,12 @@ __global__ void __launch_bounds__(kThreads) k_exchange_brute(Dev d) {
     if (valid) {
       for (int jj = 0; jj < jn; ++jj) {
         if (j0 + jj == p) continue;
-        const long long dx = s_x[jj] - x;
-        const long long dy = DIM == 2 ? s_y[jj] - y : 0;
+        long long dx = s_x[jj] - x;
+        long long dy = DIM == 2 ? s_y[jj] - y : 0;
+        if (d.periodic) {
+          dx = min_image(dx, d.Lq[0]);
+          if (DIM == 2) dy = min_image(dy, d.Lq[1]);
+        }
         if (CUT) {
           if (DIM == 1 ? !within1(dx, d.S) : !in_range2(dx, dy, d.S)) continue;
         }

@@ -27,6 +27,7 @@ MT_SEARCH_CELL, MT_SEARCH_BRUTE, MT_SEARCH_FULL = 0, 1, 2
 MT_FP64, MT_MIXED = 0, 1
 MT_NORM_SYM, MT_NORM_ROW = 0, 1
 MT_MEM_HOST, MT_MEM_DEVICE = 0, 1
+MT_WALLS_REFLECT, MT_WALLS_PERIODIC = 0, 1
 
 
 class mt_params(ctypes.Structure):
@@ -49,7 +50,7 @@ class mt_params(ctypes.Structure):
         ("observe_cap", ctypes.c_int32),
         ("cell_shift", ctypes.c_int32),
         ("seg_target", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("walls", ctypes.c_int32),
     ]
 
 

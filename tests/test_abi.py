@@ -152,3 +152,22 @@ def test_seg_target_is_validated_and_kept():
         mt.mt_resolve(mt.mt_params_init(n=100000, L=(1e5,), seg_target=8))
     # no one-kernel step for 2-d or brute force
     assert mt.mt_resolve(mt.mt_params_init(dim=2, n=100, L=(10.0, 10.0))).seg_target == 0
+
+
+def test_periodic_walls_rules():
+    r = mt.mt_resolve(mt.mt_params_init(n=1000, L=(1000.0,), walls=mt.MT_WALLS_PERIODIC))
+    assert r.walls == mt.MT_WALLS_PERIODIC and r.seg_target == 0  # general pipeline
+    for bad in (dict(dim=2, n=100, L=(10.0, 10.0)),                 # 2-d cell list
+                dict(n=10, L=(3.0,)),                                # cutoff >= L / 2
+                dict(n=10, L=(100.0,), search=mt.MT_SEARCH_BRUTE, cutoff=60.0),
+                dict(n=10, L=(100.0,), walls=7)):
+        kw = dict(walls=mt.MT_WALLS_PERIODIC)
+        kw.update(bad)
+        with pytest.raises(mt.MtError) as e:
+            mt.mt_resolve(mt.mt_params_init(**kw))
+        assert e.value.status == mt.MT_ERR_INVALID
+    mt.mt_resolve(mt.mt_params_init(dim=2, n=100, L=(10.0, 10.0), search=mt.MT_SEARCH_BRUTE,
+                                    walls=mt.MT_WALLS_PERIODIC))
+    with pytest.raises(mt.MtError):
+        mt.mt_batch_resolve(mt.mt_params_init(dim=1, L=(1.0,), walls=mt.MT_WALLS_PERIODIC),
+                            mt.make_batch([10], [10.0]))

@@ -1,0 +1,86 @@
+"""Periodic walls on the GPU against the oracle: the wrapping move, minimum-
+image pairs and weights, for the 1-d cell list (general pipeline) and the
+all-pairs forms in 1-d and 2-d."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1811_05474_gb300 import mt, synth
+
+from .test_gpu_parity import TOL, assert_masses
+
+pytestmark = pytest.mark.gpu
+
+
+def make(n, L, dim, search, precision, v=(0.7, -0.4), D_rw=0.3):
+    Ls = tuple(L) if dim == 2 else (float(L),)
+    p = mt.mt_params_init(dim=dim, n=n, L=Ls, v=v[:dim] if dim == 2 else (v[0],), D_rw=D_rw,
+                          search=search, precision=precision, walls=mt.MT_WALLS_PERIODIC,
+                          observe_cap=8)
+    return mt.Simulation(p)
+
+
+def oracle_of(sim):
+    r = sim.params
+    return O.params(dim=r.dim, frac_bits=r.frac_bits, L=tuple(r.L)[: r.dim], v=tuple(r.v)[: r.dim],
+                    D_mt=r.D_mt, D_rw=r.D_rw, dt=r.dt, smax=r.cutoff,
+                    search=O.SEARCH_FULL if r.search == mt.MT_SEARCH_FULL else O.SEARCH_CUTOFF,
+                    norm=r.norm, react=r.react, walls=O.WALLS_PERIODIC)
+
+
+CASES = [
+    (3000, 2000.0, 1, mt.MT_SEARCH_CELL, 12),
+    (500, 300.0, 1, mt.MT_SEARCH_BRUTE, 6),
+    (500, 300.0, 1, mt.MT_SEARCH_FULL, 3),
+    (400, (30.0, 20.0), 2, mt.MT_SEARCH_BRUTE, 6),
+    (300, (20.0, 12.0), 2, mt.MT_SEARCH_FULL, 3),
+]
+
+
+@pytest.mark.parametrize("n,L,dim,search,steps", CASES)
+@pytest.mark.parametrize("precision", [mt.MT_FP64, mt.MT_MIXED])
+def test_periodic_matches_oracle(n, L, dim, search, steps, precision):
+    sim = make(n, L, dim, search, precision)
+    assert sim.params.seg_target == 0  # no one-kernel step with periodic walls
+    po = oracle_of(sim)
+    k = int(sim.params.frac_bits)
+    x = synth.uniform_positions(n, L, dim=dim, seed=n + dim)
+    A, B = synth.uniform_masses(n, seed=n)
+    sim.upload(x, A, B)
+    X = O.quantize(x.reshape(dim, -1), k)
+    a, b = A.copy(), B.copy()
+    xi = synth.normals(steps, dim, n, seed=77)
+    Lq = [O.quantize(np.array([[v]]), k)[0, 0] for v in (L if dim == 2 else (L,))]
+    for s in range(steps):
+        sim.set_noise(xi[s])
+        sim.step()
+        X, a, b = O.step(po, X, xi[s], a, b)
+        T = sim.ticks()
+        assert np.array_equal(T, X), f"positions at step {s}"
+        for ax in range(dim):
+            assert T[ax].min() >= 0 and T[ax].max() < Lq[ax]
+    ga, gb = sim.masses()
+    assert_masses(ga, a, TOL[precision], "A")
+    assert_masses(gb, b, TOL[precision], "B")
+    if search != mt.MT_SEARCH_FULL:
+        gi, gj = sim.pairs()
+        oi, oj = O.pairs_brute(po, X)
+        got = set(zip(gi.tolist(), gj.tolist()))
+        assert len(got) == len(gi) and got == set(zip(oi.tolist(), oj.tolist()))
+
+
+def test_periodic_pair_across_the_wall():
+    """Two particles 0.2 apart through the wall exchange mass like an
+    interior pair; with reflecting walls they do not interact."""
+    x = np.array([[19.9, 0.1]])
+    A = np.array([1.0, 0.0])
+    B = np.array([0.0, 1.0])
+    out = []
+    for walls in (mt.MT_WALLS_PERIODIC, mt.MT_WALLS_REFLECT):
+        p = mt.mt_params_init(n=2, L=(20.0,), D_rw=0.0, react=0, walls=walls)
+        sim = mt.Simulation(p)
+        sim.upload(x, A, B)
+        sim.step()
+        out.append(sim.masses()[0])
+    assert 0.0 < out[0][1] < 0.5
+    assert out[1][1] == 0.0
