@@ -93,6 +93,26 @@ def parse():
     return ap.parse_args()
 
 
+def rank_reduce(vals, op: str, device=None):
+    """All-reduce a list of floats over the ranks of the default process
+    group ('max', 'min' or 'sum'); any backend (NCCL on GPUs, gloo in the
+    CPU tests)."""
+    import torch
+    import torch.distributed as tdist
+
+    ops = {"max": tdist.ReduceOp.MAX, "min": tdist.ReduceOp.MIN, "sum": tdist.ReduceOp.SUM}
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=ops[op])
+    return [float(v) for v in t.tolist()]
+
+
+def replicas_value(particles_per_rank: int, steps: int, max_total_ms: float, ranks: int) -> float:
+    """Whole-job particle-steps/s of independent replicas (one realisation
+    per rank, no data exchanged): all ranks' work over the slowest rank's
+    timed region."""
+    return ranks * particles_per_rank * steps / (max_total_ms * 1e-3)
+
+
 def dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -784,9 +804,7 @@ def main():
     main_run = gpu_run(args, args.precision, args.steps, max(args.warmup, 3), local, rank, sampler)
     total_ms = main_run["total_ms"]
     if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = rank_reduce([total_ms], "max", device="cuda")[0]
         torch.distributed.barrier()
     clocks = sampler.stop()
     fp64 = None
@@ -819,9 +837,8 @@ def main():
     if not args.no_dense and rank == 0:
         dense = dense_run(local, sm_mhz=clocks.get("sm_mhz") if clocks else None)
     if ws > 1:
-        t = torch.tensor([e2e["value"]], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MIN)
-        e2e["value"] = float(t.item()) * ws
+        # the slowest replica's rate times the replicas
+        e2e["value"] = rank_reduce([e2e["value"]], "min", device="cuda")[0] * ws
     if rank != 0:
         if ws > 1:
             torch.distributed.barrier()
@@ -829,7 +846,7 @@ def main():
         return 0
 
     K = args.steps
-    value = ws * N * K / (total_ms * 1e-3)
+    value = replicas_value(N, K, total_ms, ws)
     ms_step = total_ms / K
     kernels = main_run["kernels"]
     ksum = sum(k["ms_per_step"] for k in kernels)
