@@ -89,6 +89,7 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true", help="skip the paper's accuracy problem")
     ap.add_argument("--no-dense", action="store_true", help="skip the paper-density workload")
     ap.add_argument("--no-brute", action="store_true", help="skip the all-pairs forms")
+    ap.add_argument("--no-species", action="store_true", help="skip the species-count sweep")
     ap.add_argument("--serve-requests", type=int, default=64, help="requests in the serving run")
     return ap.parse_args()
 
@@ -570,6 +571,49 @@ def dense_run(local: int, steps: int = 10, sm_mhz: float | None = None):
                          "peak_kind": f"derived: {nsm} SMs x {SFU_EX2_PER_SM_CLK} ex2/clk x {mhz:.0f} MHz"}}
 
 
+def species_run(local: int, steps: int = 50, counts=(2, 3, 4, 6, 8)):
+    """Cost against the species count (Sec. 2: linear in it) at the N = 1e6
+    workload's shape (1-d, [0, 1e6], MIXED): two species run the one-kernel
+    step; more run the multi-kernel pipeline, whose row sums and A/B pass
+    are shared and each further pair of species adds one exchange pass with
+    the same weights."""
+    import torch
+
+    from paper_1811_05474_gb300 import mt, synth
+
+    dev = torch.device("cuda", local)
+    n, Ld = 10 ** 6, 1.0e6
+    x = synth.uniform_positions(n, Ld, seed=13)
+    A, B = synth.uniform_masses(n, seed=13)
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    fsum = torch.empty((), dtype=torch.int64, device=dev)
+
+    def flush_l2(s):
+        with torch.cuda.stream(s):
+            flush.zero_()
+            torch.sum(flush.view(torch.int64), dim=0, out=fsum)
+
+    rows = []
+    for S in counts:
+        p = mt.mt_params_init(n=n, L=(Ld,), v=(0.5,), precision=mt.MT_MIXED, species=S, seed=5)
+        sim = mt.Simulation(p, device=dev)
+        sim.upload(x, A, B)
+        for s in range(2, S):
+            sim.set_species(s, A if s % 2 == 0 else B)
+        ms = timed_steps(sim, steps, 3, flush_l2) / steps
+        mt.mt_set_profiling(sim.h, True)
+        sim.run(1)
+        kernels = mt.mt_read_profile(sim.h)
+        path = "one-kernel step" if sim.params.seg_target > 0 else "multi-kernel pipeline"
+        sim.close()
+        rows.append({"species": S, "path": path, "ms_per_step": ms,
+                     "particle_steps_per_s": n / (ms * 1e-3),
+                     "kernels": [{"name": k, "ms": v} for k, v in kernels]})
+    return {"workload": "1d_uniform_n1e6_L1e6_v0.5_D0.1_dt1_cutoff3sigma_mixed", "steps": steps,
+            "l2": "flushed between timed steps (512 MiB write, then read)",
+            "per_species_count": rows}
+
+
 def brute_run(local: int, n: int = 100000, steps: int = 2, sm_mhz: float | None = None):
     """The all-pairs forms at the N = 1e5 workload's shape (1-d, [0, 1e5],
     MIXED): the full matrix (every pair's exponential, the paper's
@@ -836,6 +880,9 @@ def main():
     dense = None
     if not args.no_dense and rank == 0:
         dense = dense_run(local, sm_mhz=clocks.get("sm_mhz") if clocks else None)
+    species = None
+    if not args.no_species and rank == 0:
+        species = species_run(local)
     if ws > 1:
         # the slowest replica's rate times the replicas
         e2e["value"] = rank_reduce([e2e["value"]], "min", device="cuda")[0] * ws
@@ -895,6 +942,7 @@ def main():
         "accuracy": accuracy,
         "paper_density": dense,
         "brute_force": brute,
+        "species": species,
         "precision": precision,
         "mean_A_last_step": main_run["mean_A_last"],
     }

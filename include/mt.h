@@ -107,7 +107,18 @@ typedef struct mt_params {
                            separation; needs s_max < L/2 per axis; 1-d with
                            any search, 2-d with MT_SEARCH_BRUTE or FULL;
                            single systems only */
+  int32_t species;      /* chemical species each particle carries: 0 or 2 =
+                           A and B; 3 .. MT_MAX_SPECIES adds species 2, 3,
+                           ... moved by the same transfer (Sec. 1.1: one
+                           system of Eq. 4 per species, all with the same
+                           weights; cost linear in the species count).  Only
+                           A and B react; the others are conservative.
+                           More than 2: single systems only, and the step
+                           runs as the multi-kernel pipeline */
+  int32_t reserved;     /* 0 */
 } mt_params;
+
+#define MT_MAX_SPECIES 8
 
 /* A batch: count independent 1-d realisations (the ensembles of repeated
  * simulations behind the paper's averaged results, Sec. 3 and Sec. 6.1)
@@ -229,7 +240,8 @@ mt_status mt_server_create(const mt_server_config* cfg, void* pool, size_t pool_
 
 /* Queue a request: params p, host arrays x (dim*n), A, B (n), steps to run.
  * *id receives its identifier.  A request whose footprint exceeds the whole
- * pool is refused (MT_ERR_WORKSPACE). */
+ * pool is refused (MT_ERR_WORKSPACE); one with more than two species is
+ * refused (MT_ERR_INVALID). */
 mt_status mt_server_submit(mt_server* s, const mt_params* p, const double* x, const double* A,
                            const double* B, int64_t steps, int64_t* id);
 
@@ -264,6 +276,16 @@ void mt_server_destroy(mt_server* s);
  * arrays are copied before the call returns. */
 mt_status mt_upload(mt_handle* h, const double* x, const double* A,
                     const double* B, int32_t mem);
+
+/* Species s of a state with p->species > 2 (any s in [0, species); 0 is A
+ * and 1 is B): set it from n doubles in the caller's particle order (host or
+ * device memory, per mem), or read it back the same way.  mt_upload sets
+ * A and B and zeroes species 2 and up; call mt_set_species after it and
+ * between steps.  Both wait for the stream when mem is MT_MEM_HOST.  Errors:
+ * MT_ERR_INVALID for s out of range or a NULL array, MT_ERR_STATE before
+ * mt_upload. */
+mt_status mt_set_species(mt_handle* h, int32_t s, const double* M, int32_t mem);
+mt_status mt_read_species(mt_handle* h, int32_t s, double* M, int32_t mem);
 
 /* Random-walk noise for the following steps: a device pointer to dim*n
  * floats, axis-major and indexed by the caller's particle order, read by

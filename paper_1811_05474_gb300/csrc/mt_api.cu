@@ -153,6 +153,12 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
   if (p.observe_cap < 0) return fail(MT_ERR_INVALID, "observe_cap must be >= 0");
   if (p.walls != MT_WALLS_REFLECT && p.walls != MT_WALLS_PERIODIC)
     return fail(MT_ERR_INVALID, "unknown walls %d", p.walls);
+  if (p.species == 0) p.species = 2;
+  if (p.species < 2 || p.species > MT_MAX_SPECIES)
+    return fail(MT_ERR_INVALID, "species must be 0 or in [2, %d] (got %d)", MT_MAX_SPECIES,
+                p.species);
+  if (p.species > 2 && b) return fail(MT_ERR_INVALID, "batches carry two species");
+  if (p.reserved != 0) return fail(MT_ERR_INVALID, "reserved must be 0");
   const bool periodic = p.walls == MT_WALLS_PERIODIC;
   if (periodic && b) return fail(MT_ERR_INVALID, "batches use reflecting walls");
   if (periodic && p.dim == 2 && p.search == MT_SEARCH_CELL)
@@ -239,7 +245,7 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
   // Fused 1-d step: segments of seg_target particles staged with a halo of
   // hc cells (2 Smax) and the displacement bound; pick the largest target
   // (<= 1024) whose expected staging, with 50% headroom, fits kFusedCap.
-  if (p.search == MT_SEARCH_CELL && p.dim == 1 && p.n > 0 && !periodic) {
+  if (p.search == MT_SEARCH_CELL && p.dim == 1 && p.n > 0 && !periodic && p.species == 2) {
     const long long w = 1LL << D.cshift;
     D.hc = (2 * D.S + w - 1) / w + 1;
     double dr = std::fabs((double)D.drift[0]);
@@ -312,7 +318,7 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
   D.o_ctrl = take(sizeof(Ctrl));
   for (int b2 = 0; b2 < 2; ++b2) D.o_X[b2] = take((size_t)p.dim * n * 8);
   for (int b2 = 0; b2 < 2; ++b2) D.o_id[b2] = take(n * 4);
-  for (int b2 = 0; b2 < 2; ++b2) D.o_M[b2] = take(2 * n * 8);
+  for (int b2 = 0; b2 < 2; ++b2) D.o_M[b2] = take((size_t)p.species * n * 8);
   D.o_src = take(n * 4);
   D.o_rinv = take(n * 8);
   D.o_count = take((size_t)D.ncell * 4);
@@ -685,6 +691,7 @@ mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace
   // one wave of segments (large systems); small ones keep the plain chain
   d.use_pred = D.fused && D.nseg > (long long)kFusedCtasPerSm * d.nsm ? 1 : 0;
   d.periodic = D.p.walls == MT_WALLS_PERIODIC ? 1 : 0;
+  d.nspec = D.p.species;
   d.n = D.p.n;
   d.dim = D.p.dim;
   d.norm = D.p.norm;
@@ -849,6 +856,42 @@ mt_status mt_read_masses(mt_handle* h, double* A, double* B, int32_t mem) {
     CU(cudaMemcpyAsync(B, stage + n, n * 8, cudaMemcpyDeviceToHost, h->stream));
   }
   return check_device(h);
+}
+
+static mt_status species_io(mt_handle* h, int32_t sp, double* out, const double* in,
+                            int32_t mem) {
+  if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
+  if (!h->uploaded) return fail(MT_ERR_STATE, "no state uploaded");
+  if (mem != MT_MEM_HOST && mem != MT_MEM_DEVICE) return fail(MT_ERR_INVALID, "bad mem kind");
+  if (sp < 0 || sp >= h->D.p.species)
+    return fail(MT_ERR_INVALID, "species %d out of range [0, %d)", sp, h->D.p.species);
+  const size_t n = (size_t)h->D.p.n;
+  if (n == 0) return check_device(h);
+  if (!out && !in) return fail(MT_ERR_INVALID, "species array is NULL");
+  if (mem == MT_MEM_DEVICE) {
+    CU(launch_species_io(h->dev, sp, out, in, h->D.p.precision, h->stream));
+    return MT_OK;
+  }
+  Ctrl c;
+  const mt_status s = read_ctrl(h, &c);
+  if (s != MT_OK) return s;
+  double* stage = reinterpret_cast<double*>(h->dev.M[c.mcur ^ 1]);
+  if (in) {
+    CU(cudaMemcpyAsync(stage, in, n * 8, cudaMemcpyHostToDevice, h->stream));
+    CU(launch_species_io(h->dev, sp, nullptr, stage, h->D.p.precision, h->stream));
+  } else {
+    CU(launch_species_io(h->dev, sp, stage, nullptr, h->D.p.precision, h->stream));
+    CU(cudaMemcpyAsync(out, stage, n * 8, cudaMemcpyDeviceToHost, h->stream));
+  }
+  return check_device(h);
+}
+
+mt_status mt_set_species(mt_handle* h, int32_t s, const double* M, int32_t mem) {
+  return species_io(h, s, nullptr, M, mem);
+}
+
+mt_status mt_read_species(mt_handle* h, int32_t s, double* M, int32_t mem) {
+  return species_io(h, s, M, nullptr, mem);
 }
 
 static mt_status read_pos(mt_handle* h, double* x, long long* X, int32_t mem) {

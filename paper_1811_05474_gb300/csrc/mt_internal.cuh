@@ -91,6 +91,7 @@ struct Dev {
   unsigned char* pred[2];   // [nseg] segments predicted pair-heavy (by scur parity)
   int use_pred;             // 1: the predicted-segment kernel runs beside the first tier
   int periodic;             // 1: periodic walls (wrap, minimum-image separations)
+  int nspec;                // species per particle (masses hold nspec * n words)
   long long n;
   int dim;
   int norm;                 // MT_NORM_*
@@ -145,6 +146,16 @@ __device__ __forceinline__ long long reflect(long long y, long long Lq) {
       return y;
   }
   return y < 0 ? 0 : (y > Lq ? Lq : y);
+}
+
+// Every species of the particle in slot s of buffer mc moves to slot p of
+// the other buffer.
+__device__ __forceinline__ void gather_masses(const Dev& d, int mc, long long p, long long s) {
+  const unsigned long long* in = d.M[mc];
+  unsigned long long* out = d.M[mc ^ 1];
+  out[p] = in[s];
+  out[d.n + p] = in[d.n + s];
+  for (int k = 2; k < d.nspec; ++k) out[k * d.n + p] = in[k * d.n + s];
 }
 
 // Periodic walls: y modulo Lq into [0, Lq).
@@ -315,6 +326,9 @@ cudaError_t launch_upload(const Dev& d, const double* x, const double* A,
                           const double* B, int precision, cudaStream_t s);
 cudaError_t launch_read_masses(const Dev& d, double* A, double* B, int precision,
                                cudaStream_t s);
+// in != NULL: species sp <- in[n] (caller's order); else out[n] <- species sp
+cudaError_t launch_species_io(const Dev& d, int sp, double* out, const double* in, int precision,
+                              cudaStream_t s);
 cudaError_t launch_read_positions(const Dev& d, double* x, long long* X, cudaStream_t s);
 cudaError_t launch_pairs(const Dev& d, int search, int* pi, int* pj, long long cap,
                          cudaStream_t s);

@@ -53,6 +53,7 @@ __global__ void k_upload(Dev d, const double* x, const double* A, const double* 
     f64_store(d.M[mc], i, A[i]);
     f64_store(d.M[mc], d.n + i, B[i]);
   }
+  for (int k = 2; k < d.nspec; ++k) d.M[mc][k * d.n + i] = 0ULL;  // +0 in both formats
 }
 
 cudaError_t launch_upload(const Dev& d, const double* x, const double* A, const double* B,
@@ -88,6 +89,42 @@ cudaError_t launch_read_masses(const Dev& d, double* A, double* B, int precision
                                cudaStream_t s) {
   k_read_masses<<<blocks_for(d.n, kThreads), kThreads, 0, s>>>(d, A, B,
                                                                precision == MT_MIXED);
+  return cudaGetLastError();
+}
+
+// One species in the caller's order: v[caller index] <-> slot p of the
+// current mass buffer.
+__global__ void k_species_io(Dev d, int sp, double* out, const double* in, int mixed) {
+  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (p >= d.n) return;
+  const int xc = d.ctrl->xcur, mc = d.ctrl->mcur;
+  const int idp = d.id[xc][p];
+  const long long id = idp < 0 || (idp >> d.lbits) >= d.nreal ? -1 : caller_index(d, idp);
+  if (id < 0 || id >= d.n) {
+    raise_error(d.ctrl, kErrIndex, p);
+    return;
+  }
+  unsigned long long* M = d.M[mc] + (long long)sp * d.n;
+  if (in) {
+    const double v = in[id];
+    if (mixed) {
+      const float h = __double2float_rn(v);
+      df_store(M, p, {h, __double2float_rn(v - (double)h)});
+    } else {
+      f64_store(M, p, v);
+    }
+  } else if (mixed) {
+    const df v = df_load(M, p);
+    out[id] = (double)v.hi + (double)v.lo;
+  } else {
+    out[id] = f64_load(M, p);
+  }
+}
+
+cudaError_t launch_species_io(const Dev& d, int sp, double* out, const double* in, int precision,
+                              cudaStream_t s) {
+  k_species_io<<<blocks_for(d.n, kThreads), kThreads, 0, s>>>(d, sp, out, in,
+                                                              precision == MT_MIXED);
   return cudaGetLastError();
 }
 

@@ -311,8 +311,7 @@ __global__ void __launch_bounds__(kThreads) k_permute(Dev d) {
   const int xc = d.ctrl->xcur, mc = d.ctrl->mcur;
   const int s = d.src[p];
   d.id[xc ^ 1][p] = d.id[xc][s];
-  d.M[mc ^ 1][p] = d.M[mc][s];
-  d.M[mc ^ 1][d.n + p] = d.M[mc][d.n + s];
+  gather_masses(d, mc, p, s);
 }
 
 __global__ void k_flip(Dev d, int fx, int fm) {

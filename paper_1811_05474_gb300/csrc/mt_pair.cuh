@@ -134,6 +134,21 @@ struct Mass<true> {
   static __device__ __forceinline__ double to_double(df v) { return (double)v.hi + (double)v.lo; }
 };
 
+// The two mass arrays one exchange pass works on (word offsets into a mass
+// buffer of nspec * n words): A and B, or the extra species sp and sp + 1;
+// when sp is the last species the second array repeats it and is not
+// stored.
+struct SpeciesPair {
+  long long oa, ob;
+  bool store_b;
+};
+template <bool TR>
+__device__ __forceinline__ SpeciesPair species_pair(const Dev& d, int sp) {
+  if (!TR) return {0, d.n, true};
+  const bool two = sp + 1 < d.nspec;
+  return {(long long)sp * d.n, (long long)(two ? sp + 1 : sp) * d.n, two};
+}
+
 template <bool MIX>
 __device__ __forceinline__ void store_rinv(const Dev& d, long long p, typename Weight<MIX, 1>::T r) {
   if (MIX)

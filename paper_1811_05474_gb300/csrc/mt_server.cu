@@ -257,6 +257,8 @@ mt_status mt_server_submit(mt_server* s, const mt_params* p, const double* x, co
   mt_params r;
   mt_status st = mt_resolve(p, &r);
   if (st != MT_OK) return st;
+  if (r.species != 2)
+    return err(MT_ERR_INVALID, "mt_server_submit: requests carry two species (A and B)");
   const size_t n = (size_t)r.n, m = (size_t)r.dim * n;
   if (n > 0 && (!x || !A || !B)) return err(MT_ERR_INVALID, "mt_server_submit: x, A, B required");
   const size_t fp = footprint_of(*p);

@@ -217,12 +217,15 @@ __global__ void __launch_bounds__(kThreads) k_rowsum_walk(Dev d) {
   // gather id and masses into the sorted slots (stage buffer)
   const int s = d.src[p];
   d.id[xc ^ 1][p] = d.id[xc][s];
-  d.M[mc ^ 1][p] = d.M[mc][s];
-  d.M[mc ^ 1][d.n + p] = d.M[mc][d.n + s];
+  gather_masses(d, mc, p, s);
 }
 
-template <bool MIX>
-__global__ void __launch_bounds__(kThreads) k_exchange_walk(Dev d) {
+// TR = false: species A and B (species 0, 1), then the reaction, the
+// observables and the end of the step.  TR = true: the extra species sp and
+// sp + 1 (sp alone when it is the last), conservative, run before the A/B
+// pass of the same step.
+template <bool MIX, bool TR>
+__global__ void __launch_bounds__(kThreads) k_exchange_walk(Dev d, int sp) {
   using W = Weight<MIX, 1>;
   using T = typename W::T;
   using MS = Mass<MIX>;
@@ -230,19 +233,21 @@ __global__ void __launch_bounds__(kThreads) k_exchange_walk(Dev d) {
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
   const bool valid = p < d.n;
   const int xc = d.ctrl->xcur, mc = d.ctrl->mcur;
+  const SpeciesPair sq = species_pair<TR>(d, sp);
   MV A{}, B{};
   if (valid) {
     const long long* Xs = d.X[xc ^ 1];
-    const unsigned long long* Min = d.M[mc ^ 1];
+    const unsigned long long* MA = d.M[mc ^ 1] + sq.oa;
+    const unsigned long long* MB = d.M[mc ^ 1] + sq.ob;
     const long long x = Xs[p];
     const T ip = load_rinv<MIX>(d, p);
-    A = MS::load(Min, p);
-    B = MS::load(Min, d.n + p);
+    A = MS::load(MA, p);
+    B = MS::load(MB, p);
     typename MS::Acc dA{}, dB{};
     auto pair = [&](long long q, long long D) {
       const T P = normalised<T>(d.norm, W::eval(d, D, 0), ip, load_rinv<MIX>(d, q));
-      MS::acc(dA, P, MS::diff(MS::load(Min, q), A));
-      MS::acc(dB, P, MS::diff(MS::load(Min, d.n + q), B));
+      MS::acc(dA, P, MS::diff(MS::load(MA, q), A));
+      MS::acc(dB, P, MS::diff(MS::load(MB, q), B));
     };
     if (!d.periodic) {
       for (long long q = p - 1; q >= 0; --q) {
@@ -269,11 +274,11 @@ __global__ void __launch_bounds__(kThreads) k_exchange_walk(Dev d) {
         pair(q, D);
       }
     }
-    MS::update(A, B, dA, dB, d.react);
-    MS::store(d.M[mc], p, A);
-    MS::store(d.M[mc], d.n + p, B);
+    MS::update(A, B, dA, dB, TR ? 0 : d.react);
+    MS::store(d.M[mc] + sq.oa, p, A);
+    if (sq.store_b) MS::store(d.M[mc] + sq.ob, p, B);
   }
-  finish_step<MIX>(d, A, B, valid, 1, 0);
+  if (!TR) finish_step<MIX>(d, A, B, valid, 1, 0);
 }
 
 // =============================================================== 2-d cells ==
@@ -282,7 +287,8 @@ template <bool MIX, bool EXCHANGE>
 __device__ __forceinline__ void cell2_loop(const Dev& d, const long long* Xs, long long p,
                                            long long x, long long y,
                                            typename Weight<MIX, 2>::T& r,
-                                           const unsigned long long* Min,
+                                           const unsigned long long* MA,
+                                           const unsigned long long* MB,
                                            typename Weight<MIX, 2>::T ip,
                                            typename Mass<MIX>::V A, typename Mass<MIX>::V B,
                                            typename Mass<MIX>::Acc& dA,
@@ -307,8 +313,8 @@ __device__ __forceinline__ void cell2_loop(const Dev& d, const long long* Xs, lo
         r += w;
       } else if (q != p) {
         const T P = normalised<T>(d.norm, w, ip, load_rinv<MIX>(d, q));
-        MS::acc(dA, P, MS::diff(MS::load(Min, q), A));
-        MS::acc(dB, P, MS::diff(MS::load(Min, d.n + q), B));
+        MS::acc(dA, P, MS::diff(MS::load(MA, q), A));
+        MS::acc(dB, P, MS::diff(MS::load(MB, q), B));
       }
     }
   }
@@ -324,37 +330,39 @@ __global__ void __launch_bounds__(kThreads) k_rowsum_cell2(Dev d) {
   T r = T(0);
   typename Mass<MIX>::Acc dummy{};
   typename Mass<MIX>::V z{};
-  cell2_loop<MIX, false>(d, Xs, p, Xs[p], Xs[d.n + p], r, nullptr, T(0), z, z, dummy, dummy);
+  cell2_loop<MIX, false>(d, Xs, p, Xs[p], Xs[d.n + p], r, nullptr, nullptr, T(0), z, z, dummy,
+                         dummy);
   store_rinv<MIX>(d, p, r);
   const int s = d.src[p];
   d.id[xc ^ 1][p] = d.id[xc][s];
-  d.M[mc ^ 1][p] = d.M[mc][s];
-  d.M[mc ^ 1][d.n + p] = d.M[mc][d.n + s];
+  gather_masses(d, mc, p, s);
 }
 
-template <bool MIX>
-__global__ void __launch_bounds__(kThreads) k_exchange_cell2(Dev d) {
+template <bool MIX, bool TR>
+__global__ void __launch_bounds__(kThreads) k_exchange_cell2(Dev d, int sp) {
   using T = typename Weight<MIX, 2>::T;
   using MS = Mass<MIX>;
   using MV = typename MS::V;
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
   const bool valid = p < d.n;
   const int xc = d.ctrl->xcur, mc = d.ctrl->mcur;
+  const SpeciesPair sq = species_pair<TR>(d, sp);
   MV A{}, B{};
   if (valid) {
     const long long* Xs = d.X[xc ^ 1];
-    const unsigned long long* Min = d.M[mc ^ 1];
-    A = MS::load(Min, p);
-    B = MS::load(Min, d.n + p);
+    const unsigned long long* MA = d.M[mc ^ 1] + sq.oa;
+    const unsigned long long* MB = d.M[mc ^ 1] + sq.ob;
+    A = MS::load(MA, p);
+    B = MS::load(MB, p);
     T r = T(0);
     typename MS::Acc dA{}, dB{};
-    cell2_loop<MIX, true>(d, Xs, p, Xs[p], Xs[d.n + p], r, Min, load_rinv<MIX>(d, p), A, B,
+    cell2_loop<MIX, true>(d, Xs, p, Xs[p], Xs[d.n + p], r, MA, MB, load_rinv<MIX>(d, p), A, B,
                           dA, dB);
-    MS::update(A, B, dA, dB, d.react);
-    MS::store(d.M[mc], p, A);
-    MS::store(d.M[mc], d.n + p, B);
+    MS::update(A, B, dA, dB, TR ? 0 : d.react);
+    MS::store(d.M[mc] + sq.oa, p, A);
+    if (sq.store_b) MS::store(d.M[mc] + sq.ob, p, B);
   }
-  finish_step<MIX>(d, A, B, valid, 1, 0);
+  if (!TR) finish_step<MIX>(d, A, B, valid, 1, 0);
 }
 
 // ============================================================ brute force ==
@@ -405,8 +413,8 @@ __global__ void __launch_bounds__(kThreads) k_rowsum_brute(Dev d) {
   if (valid) store_rinv<MIX>(d, p, r);
 }
 
-template <bool MIX, bool CUT, int DIM>
-__global__ void __launch_bounds__(kThreads) k_exchange_brute(Dev d) {
+template <bool MIX, bool CUT, int DIM, bool TR>
+__global__ void __launch_bounds__(kThreads) k_exchange_brute(Dev d, int sp) {
   using W = Weight<MIX, DIM>;
   using T = typename W::T;
   using MS = Mass<MIX>;
@@ -420,14 +428,16 @@ __global__ void __launch_bounds__(kThreads) k_exchange_brute(Dev d) {
   const bool valid = p < d.n;
   const int mc = d.ctrl->mcur;
   const long long* X = d.X[d.ctrl->xcur];
-  const unsigned long long* Min = d.M[mc];
+  const SpeciesPair sq = species_pair<TR>(d, sp);
+  const unsigned long long* MA = d.M[mc] + sq.oa;
+  const unsigned long long* MB = d.M[mc] + sq.ob;
   const long long x = valid ? X[p] : 0;
   const long long y = (valid && DIM == 2) ? X[d.n + p] : 0;
   MV A{}, B{};
   T ip = T(0);
   if (valid) {
-    A = MS::load(Min, p);
-    B = MS::load(Min, d.n + p);
+    A = MS::load(MA, p);
+    B = MS::load(MB, p);
     ip = load_rinv<MIX>(d, p);
   }
   typename MS::Acc dA{}, dB{};
@@ -437,8 +447,8 @@ __global__ void __launch_bounds__(kThreads) k_exchange_brute(Dev d) {
       s_x[threadIdx.x] = X[j];
       if (DIM == 2) s_y[threadIdx.x] = X[d.n + j];
       s_ri[threadIdx.x] = load_rinv<MIX>(d, j);
-      s_a[threadIdx.x] = MS::load(Min, j);
-      s_b[threadIdx.x] = MS::load(Min, d.n + j);
+      s_a[threadIdx.x] = MS::load(MA, j);
+      s_b[threadIdx.x] = MS::load(MB, j);
     }
     __syncthreads();
     const int jn = (int)min((long long)kBruteTile, d.n - j0);
@@ -462,15 +472,33 @@ __global__ void __launch_bounds__(kThreads) k_exchange_brute(Dev d) {
     __syncthreads();
   }
   if (valid) {
-    MS::update(A, B, dA, dB, d.react);
-    MS::store(d.M[mc ^ 1], p, A);
-    MS::store(d.M[mc ^ 1], d.n + p, B);
+    MS::update(A, B, dA, dB, TR ? 0 : d.react);
+    MS::store(d.M[mc ^ 1] + sq.oa, p, A);
+    if (sq.store_b) MS::store(d.M[mc ^ 1] + sq.ob, p, B);
   }
-  finish_step<MIX>(d, A, B, valid, 0, 1);
+  if (!TR) finish_step<MIX>(d, A, B, valid, 0, 1);
 }
 
 // --------------------------------------------------------------- launch --
 
+template <bool MIX, bool TR>
+static void launch_exchange_brute(const Dev& d, bool cut, unsigned int g, cudaStream_t s,
+                                  int sp) {
+  if (cut) {
+    if (d.dim == 1)
+      k_exchange_brute<MIX, true, 1, TR><<<g, kThreads, 0, s>>>(d, sp);
+    else
+      k_exchange_brute<MIX, true, 2, TR><<<g, kThreads, 0, s>>>(d, sp);
+  } else {
+    if (d.dim == 1)
+      k_exchange_brute<MIX, false, 1, TR><<<g, kThreads, 0, s>>>(d, sp);
+    else
+      k_exchange_brute<MIX, false, 2, TR><<<g, kThreads, 0, s>>>(d, sp);
+  }
+}
+
+// The extra species' passes (pairs 2-3, 4-5, ...) run between the row sums
+// and the A/B pass, which ends the step.
 template <bool MIX>
 static void transfer_t(const Dev& d, int search, cudaStream_t s, Marker& mk) {
   const unsigned int g = (unsigned int)((d.n + kThreads - 1) / kThreads);
@@ -478,36 +506,42 @@ static void transfer_t(const Dev& d, int search, cudaStream_t s, Marker& mk) {
     if (d.dim == 1) {
       mk("rowsum_walk", s);
       k_rowsum_walk<MIX><<<g, kThreads, 0, s>>>(d);
+      for (int sp = 2; sp < d.nspec; sp += 2) {
+        mk("exchange_walk_species", s);
+        k_exchange_walk<MIX, true><<<g, kThreads, 0, s>>>(d, sp);
+      }
       mk("exchange_walk", s);
-      k_exchange_walk<MIX><<<g, kThreads, 0, s>>>(d);
+      k_exchange_walk<MIX, false><<<g, kThreads, 0, s>>>(d, 0);
     } else {
       mk("rowsum_cell2", s);
       k_rowsum_cell2<MIX><<<g, kThreads, 0, s>>>(d);
+      for (int sp = 2; sp < d.nspec; sp += 2) {
+        mk("exchange_cell2_species", s);
+        k_exchange_cell2<MIX, true><<<g, kThreads, 0, s>>>(d, sp);
+      }
       mk("exchange_cell2", s);
-      k_exchange_cell2<MIX><<<g, kThreads, 0, s>>>(d);
+      k_exchange_cell2<MIX, false><<<g, kThreads, 0, s>>>(d, 0);
     }
-  } else if (search == MT_SEARCH_BRUTE) {
-    mk("rowsum_brute", s);
-    if (d.dim == 1)
-      k_rowsum_brute<MIX, true, 1><<<g, kThreads, 0, s>>>(d);
-    else
-      k_rowsum_brute<MIX, true, 2><<<g, kThreads, 0, s>>>(d);
-    mk("exchange_brute", s);
-    if (d.dim == 1)
-      k_exchange_brute<MIX, true, 1><<<g, kThreads, 0, s>>>(d);
-    else
-      k_exchange_brute<MIX, true, 2><<<g, kThreads, 0, s>>>(d);
   } else {
-    mk("rowsum_full", s);
-    if (d.dim == 1)
-      k_rowsum_brute<MIX, false, 1><<<g, kThreads, 0, s>>>(d);
-    else
-      k_rowsum_brute<MIX, false, 2><<<g, kThreads, 0, s>>>(d);
-    mk("exchange_full", s);
-    if (d.dim == 1)
-      k_exchange_brute<MIX, false, 1><<<g, kThreads, 0, s>>>(d);
-    else
-      k_exchange_brute<MIX, false, 2><<<g, kThreads, 0, s>>>(d);
+    const bool cut = search == MT_SEARCH_BRUTE;
+    mk(cut ? "rowsum_brute" : "rowsum_full", s);
+    if (cut) {
+      if (d.dim == 1)
+        k_rowsum_brute<MIX, true, 1><<<g, kThreads, 0, s>>>(d);
+      else
+        k_rowsum_brute<MIX, true, 2><<<g, kThreads, 0, s>>>(d);
+    } else {
+      if (d.dim == 1)
+        k_rowsum_brute<MIX, false, 1><<<g, kThreads, 0, s>>>(d);
+      else
+        k_rowsum_brute<MIX, false, 2><<<g, kThreads, 0, s>>>(d);
+    }
+    for (int sp = 2; sp < d.nspec; sp += 2) {
+      mk(cut ? "exchange_brute_species" : "exchange_full_species", s);
+      launch_exchange_brute<MIX, true>(d, cut, g, s, sp);
+    }
+    mk(cut ? "exchange_brute" : "exchange_full", s);
+    launch_exchange_brute<MIX, false>(d, cut, g, s, 0);
   }
 }
 

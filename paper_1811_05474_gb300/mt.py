@@ -28,6 +28,7 @@ MT_FP64, MT_MIXED = 0, 1
 MT_NORM_SYM, MT_NORM_ROW = 0, 1
 MT_MEM_HOST, MT_MEM_DEVICE = 0, 1
 MT_WALLS_REFLECT, MT_WALLS_PERIODIC = 0, 1
+MT_MAX_SPECIES = 8
 
 
 class mt_params(ctypes.Structure):
@@ -51,6 +52,8 @@ class mt_params(ctypes.Structure):
         ("cell_shift", ctypes.c_int32),
         ("seg_target", ctypes.c_int32),
         ("walls", ctypes.c_int32),
+        ("species", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -142,6 +145,8 @@ def lib(path: Path | None = None):
         "mt_run": [H, i64],
         "mt_sync": [H],
         "mt_read_masses": [H, _vp, _vp, i32],
+        "mt_set_species": [H, i32, _vp, i32],
+        "mt_read_species": [H, i32, _vp, i32],
         "mt_read_positions": [H, _vp, i32],
         "mt_read_ticks": [H, _vp, i32],
         "mt_read_observables": [H, _vp, i64, ctypes.POINTER(i64)],
@@ -304,6 +309,14 @@ def mt_sync(h) -> None:
 
 def mt_read_masses(h, A_ptr, B_ptr, mem: int) -> None:
     check(lib().mt_read_masses(h, A_ptr, B_ptr, mem))
+
+
+def mt_set_species(h, s: int, M_ptr, mem: int) -> None:
+    check(lib().mt_set_species(h, s, M_ptr, mem))
+
+
+def mt_read_species(h, s: int, M_ptr, mem: int) -> None:
+    check(lib().mt_read_species(h, s, M_ptr, mem))
 
 
 def mt_read_positions(h, x_ptr, mem: int) -> None:
@@ -477,6 +490,16 @@ class Simulation:
         B = np.empty(self.n, dtype=np.float64)
         mt_read_masses(self.h, _ptr(A), _ptr(B), MT_MEM_HOST)
         return A, B
+
+    def set_species(self, s: int, M: np.ndarray) -> None:
+        M = np.ascontiguousarray(M, dtype=np.float64)
+        assert M.shape == (self.n,)
+        mt_set_species(self.h, s, _ptr(M), MT_MEM_HOST)
+
+    def species(self, s: int) -> np.ndarray:
+        M = np.empty(self.n, dtype=np.float64)
+        mt_read_species(self.h, s, _ptr(M), MT_MEM_HOST)
+        return M
 
     def positions(self) -> np.ndarray:
         x = np.empty((self.dim, self.n), dtype=np.float64)

@@ -171,3 +171,21 @@ def test_periodic_walls_rules():
     with pytest.raises(mt.MtError):
         mt.mt_batch_resolve(mt.mt_params_init(dim=1, L=(1.0,), walls=mt.MT_WALLS_PERIODIC),
                             mt.make_batch([10], [10.0]))
+
+
+def test_species_rules():
+    r = mt.mt_resolve(mt.mt_params_init(n=1000, L=(1000.0,)))
+    assert r.species == 2 and r.seg_target > 0  # default: A and B, one-kernel step
+    r4 = mt.mt_resolve(mt.mt_params_init(n=1000, L=(1000.0,), species=4))
+    assert r4.species == 4 and r4.seg_target == 0  # multi-kernel pipeline
+    w3 = mt.mt_workspace_bytes(mt.mt_params_init(n=10000, L=(1e4,), species=3))
+    w6 = mt.mt_workspace_bytes(mt.mt_params_init(n=10000, L=(1e4,), species=6))
+    assert abs((w6 - w3) - 2 * 3 * 10000 * 8) <= 512  # two buffers, three more species
+    mt.mt_resolve(mt.mt_params_init(n=10, species=mt.MT_MAX_SPECIES))
+    for bad in (dict(species=1), dict(species=mt.MT_MAX_SPECIES + 1), dict(species=-2),
+                dict(reserved=3)):
+        with pytest.raises(mt.MtError) as e:
+            mt.mt_resolve(mt.mt_params_init(n=10, **bad))
+        assert e.value.status == mt.MT_ERR_INVALID
+    with pytest.raises(mt.MtError):
+        mt.mt_batch_resolve(_batch_params(species=3), mt.make_batch([10], [10.0]))

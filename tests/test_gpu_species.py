@@ -1,0 +1,131 @@
+"""More than two species on the GPU against the oracle (Sec. 1.1: the same
+transfer weights act on every species; only A and B react): the 1-d and 2-d
+cell lists and the all-pairs forms, FP64 and MIXED, an odd and an even count
+of extra species, reflecting and periodic walls."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1811_05474_gb300 import mt, synth
+
+from .test_gpu_parity import TOL, assert_masses
+from .test_oracle_species import oracle_step_species, species_masses
+
+pytestmark = pytest.mark.gpu
+
+
+def make(n, L, dim, search, precision, S, walls=mt.MT_WALLS_REFLECT, react=1):
+    Ls = tuple(L) if dim == 2 else (float(L),)
+    v = (0.4, -0.3)[:dim]
+    p = mt.mt_params_init(dim=dim, n=n, L=Ls, v=v, D_rw=0.2, D_mt=0.15, search=search,
+                          precision=precision, species=S, walls=walls, react=react,
+                          observe_cap=8)
+    return mt.Simulation(p)
+
+
+def oracle_of(sim):
+    r = sim.params
+    return O.params(dim=r.dim, frac_bits=r.frac_bits, L=tuple(r.L)[: r.dim], v=tuple(r.v)[: r.dim],
+                    D_mt=r.D_mt, D_rw=r.D_rw, dt=r.dt, smax=r.cutoff,
+                    search=O.SEARCH_FULL if r.search == mt.MT_SEARCH_FULL else O.SEARCH_CUTOFF,
+                    norm=r.norm, react=r.react, walls=r.walls)
+
+
+CASES = [  # n, L, dim, search, S, steps
+    (5000, 4000.0, 1, mt.MT_SEARCH_CELL, 3, 10),
+    (3000, 2000.0, 1, mt.MT_SEARCH_CELL, 8, 6),
+    (2000, (150.0, 120.0), 2, mt.MT_SEARCH_CELL, 5, 6),
+    (600, 500.0, 1, mt.MT_SEARCH_BRUTE, 4, 5),
+    (400, (30.0, 25.0), 2, mt.MT_SEARCH_BRUTE, 3, 4),
+    (400, 300.0, 1, mt.MT_SEARCH_FULL, 5, 3),
+]
+
+
+def run_both(sim, n, L, dim, S, steps, seed):
+    po = oracle_of(sim)
+    k = int(sim.params.frac_bits)
+    x = synth.uniform_positions(n, L, dim=dim, seed=seed)
+    Ms = species_masses(n, S, seed=seed + 1)
+    sim.upload(x, Ms[0], Ms[1])
+    for s in range(2, S):
+        sim.set_species(s, Ms[s])
+    X = O.quantize(x.reshape(dim, -1), k)
+    cur = [m.copy() for m in Ms]
+    xi = synth.normals(steps, dim, n, seed=seed + 2)
+    for s in range(steps):
+        sim.set_noise(xi[s])
+        sim.step()
+        X, cur = oracle_step_species(po, X, xi[s], cur)
+        assert np.array_equal(sim.ticks(), X), f"positions at step {s}"
+    return Ms, cur
+
+
+@pytest.mark.parametrize("n,L,dim,search,S,steps", CASES)
+@pytest.mark.parametrize("precision", [mt.MT_FP64, mt.MT_MIXED])
+def test_species_match_oracle(n, L, dim, search, S, steps, precision):
+    sim = make(n, L, dim, search, precision, S)
+    assert sim.params.species == S and sim.params.seg_target == 0
+    _, cur = run_both(sim, n, L, dim, S, steps, seed=n + S)
+    for s in range(S):
+        assert_masses(sim.species(s), cur[s], TOL[precision], f"species {s}")
+    ga, gb = sim.masses()
+    assert np.array_equal(ga, sim.species(0)) and np.array_equal(gb, sim.species(1))
+    # A and B's observables are those of the two-species step
+    obs = sim.observables()
+    assert abs(obs[-1][0] - cur[0].sum()) <= 1e-9 * n
+
+
+def test_species_with_periodic_walls():
+    n, L, S = 3000, 2500.0, 4
+    sim = make(n, L, 1, mt.MT_SEARCH_CELL, mt.MT_FP64, S, walls=mt.MT_WALLS_PERIODIC, react=0)
+    Ms, cur = run_both(sim, n, L, 1, S, 8, seed=21)
+    for s in range(S):
+        got = sim.species(s)
+        assert_masses(got, cur[s], TOL[mt.MT_FP64], f"species {s}")
+        assert abs(got.sum() - Ms[s].sum()) <= 1e-10 * n
+
+
+def test_two_species_path_unchanged_and_species_io():
+    """species = 2 keeps the one-kernel step; species 0 and 1 read and set
+    through the species calls are A and B; setting a species between steps
+    takes effect at the next step."""
+    n, L = 4000, 4000.0
+    x = synth.uniform_positions(n, L, seed=5)
+    A, B = synth.uniform_masses(n, seed=5)
+    p2 = mt.mt_params_init(n=n, L=(L,), precision=mt.MT_FP64)
+    s2 = mt.Simulation(p2)
+    assert s2.params.seg_target > 0
+    s2.upload(x, A, B)
+    s2.run(3)
+    p3 = mt.mt_params_init(n=n, L=(L,), precision=mt.MT_FP64, species=3)
+    s3 = mt.Simulation(p3)
+    s3.upload(x, A, B)
+    assert np.array_equal(s3.species(2), np.zeros(n))  # upload zeroes the extra species
+    s3.run(3)
+    a2, b2 = s2.masses()
+    a3, b3 = s3.masses()
+    assert_masses(a3, a2, 1e-12, "A")
+    assert_masses(b3, b2, 1e-12, "B")
+    # set A through the species call; a second handle with the same A agrees
+    newA = np.linspace(0.0, 1.0, n)
+    s3.set_species(0, newA)
+    assert np.array_equal(s3.species(0), newA)
+    s2.set_species(0, newA)
+    s3.run(2)
+    s2.run(2)
+    assert_masses(s3.masses()[0], s2.masses()[0], 1e-12, "A after set")
+    with pytest.raises(mt.MtError):
+        s3.set_species(3, newA)
+    with pytest.raises(mt.MtError):
+        s2.species(2)
+    s2.close()
+    s3.close()
+
+
+def test_server_refuses_more_species():
+    p = mt.mt_params_init(n=100, L=(100.0,), species=3)
+    srv = mt.Server(pool_bytes=2 ** 24, max_active=1, chunk_steps=4)
+    with pytest.raises(mt.MtError) as e:
+        srv.submit(p, np.linspace(1, 99, 100), np.ones(100), np.zeros(100), 3)
+    assert e.value.status == mt.MT_ERR_INVALID
+    srv.close()
