@@ -115,7 +115,17 @@ typedef struct mt_params {
                            A and B react; the others are conservative.
                            More than 2: single systems only, and the step
                            runs as the multi-kernel pipeline */
-  int32_t reserved;     /* 0 */
+  int32_t stored_p;     /* 0: weights computed where they are used (two
+                           passes, each pair's weight evaluated in both).
+                           1 or more: the SPaM form (Sec. 6: the sparse
+                           transfer matrix is stored and applied by sparse
+                           matrix-vector products): each step stores nu_ij
+                           once per unordered pair, in a band of b entries
+                           per particle (its right neighbours in sorted
+                           order), and both passes read it; 1 chooses b from
+                           the mean density with headroom, b >= 2 sets it.
+                           Entries past the band are recomputed, so any b is
+                           correct.  1-d MT_SEARCH_CELL, single systems */
 } mt_params;
 
 #define MT_MAX_SPECIES 8

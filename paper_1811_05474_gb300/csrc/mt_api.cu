@@ -61,7 +61,8 @@ struct Derived {
   // workspace offsets
   size_t o_ctrl, o_X[2], o_id[2], o_M[2], o_src, o_rinv, o_count, o_start, o_cursor,
       o_status, o_big, o_part, o_obs, o_fstart[2], o_cb[2], o_ovlist, o_pred[2], o_rt, o_sslot,
-      o_sreal, o_rdone, total;
+      o_sreal, o_rdone, o_cnt, o_band, total;
+  long long band = 0;  // SPaM band entries per particle (0: off)
 };
 
 int default_frac_bits(const mt_params& p) {
@@ -158,7 +159,9 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
     return fail(MT_ERR_INVALID, "species must be 0 or in [2, %d] (got %d)", MT_MAX_SPECIES,
                 p.species);
   if (p.species > 2 && b) return fail(MT_ERR_INVALID, "batches carry two species");
-  if (p.reserved != 0) return fail(MT_ERR_INVALID, "reserved must be 0");
+  if (p.stored_p < 0) return fail(MT_ERR_INVALID, "stored_p must be >= 0");
+  if (p.stored_p > 0 && (p.dim != 1 || p.search != MT_SEARCH_CELL || b))
+    return fail(MT_ERR_INVALID, "stored_p needs a single 1-d system with MT_SEARCH_CELL");
   const bool periodic = p.walls == MT_WALLS_PERIODIC;
   if (periodic && b) return fail(MT_ERR_INVALID, "batches use reflecting walls");
   if (periodic && p.dim == 2 && p.search == MT_SEARCH_CELL)
@@ -245,7 +248,8 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
   // Fused 1-d step: segments of seg_target particles staged with a halo of
   // hc cells (2 Smax) and the displacement bound; pick the largest target
   // (<= 1024) whose expected staging, with 50% headroom, fits kFusedCap.
-  if (p.search == MT_SEARCH_CELL && p.dim == 1 && p.n > 0 && !periodic && p.species == 2) {
+  if (p.search == MT_SEARCH_CELL && p.dim == 1 && p.n > 0 && !periodic && p.species == 2 &&
+      p.stored_p == 0) {
     const long long w = 1LL << D.cshift;
     D.hc = (2 * D.S + w - 1) / w + 1;
     double dr = std::fabs((double)D.drift[0]);
@@ -276,6 +280,15 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
     }
   }
   if (!D.fused) p.seg_target = 0;
+  // SPaM band: right neighbours kept per particle; the mean count with
+  // headroom for the Poisson spread of a uniform density
+  if (p.stored_p == 1) {
+    const double mean = (double)D.S * (double)p.n / (double)D.Lq[0];
+    const double b = std::ceil(1.25 * mean + 4.0 * std::sqrt(mean) + 8.0);
+    p.stored_p = (int32_t)std::min(b, 1.0e6);
+  }
+  if (p.stored_p > 0 && p.stored_p > p.n) p.stored_p = (int32_t)std::max<long long>(p.n, 2);
+  D.band = p.stored_p;
   // realisation table and fused segments (each realisation's own, so its
   // particles' slot range [off, off + n) is split at off + j T)
   {
@@ -335,6 +348,8 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
   D.o_rt = take(D.rt.size() * sizeof(Real));
   D.o_sslot = take(D.sslot.size() * 4);
   D.o_sreal = take(D.sreal.size() * 4);
+  D.o_cnt = take(D.band > 0 ? n * 4 : 0);
+  D.o_band = take(D.band > 0 ? (size_t)D.band * n * (p.precision == MT_MIXED ? 4 : 8) : 0);
   D.o_rdone = take((size_t)D.nreal * 4);
   D.total = o;
   D.p = p;
@@ -692,6 +707,9 @@ mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace
   d.use_pred = D.fused && D.nseg > (long long)kFusedCtasPerSm * d.nsm ? 1 : 0;
   d.periodic = D.p.walls == MT_WALLS_PERIODIC ? 1 : 0;
   d.nspec = D.p.species;
+  d.band_cap = (int)D.band;
+  d.cnt = reinterpret_cast<int*>(w + D.o_cnt);
+  d.band = w + D.o_band;
   d.n = D.p.n;
   d.dim = D.p.dim;
   d.norm = D.p.norm;

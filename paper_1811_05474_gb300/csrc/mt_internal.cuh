@@ -92,6 +92,9 @@ struct Dev {
   int use_pred;             // 1: the predicted-segment kernel runs beside the first tier
   int periodic;             // 1: periodic walls (wrap, minimum-image separations)
   int nspec;                // species per particle (masses hold nspec * n words)
+  int band_cap;             // SPaM form: stored weights per particle (0: off)
+  int* cnt;                 // [n] SPaM: right neighbours of each sorted slot
+  void* band;               // [band_cap][n] SPaM: nu(p, p + k) at (k - 1) n + p
   long long n;
   int dim;
   int norm;                 // MT_NORM_*

@@ -281,6 +281,127 @@ __global__ void __launch_bounds__(kThreads) k_exchange_walk(Dev d, int sp) {
   if (!TR) finish_step<MIX>(d, A, B, valid, 1, 0);
 }
 
+// ================================================== 1-d SPaM (stored P) ==
+// The SPaM form of Sec. 6: the nonzero weights of the step's transfer
+// matrix are stored and both passes read them, so each unordered pair's
+// exponential is evaluated once.  In sorted order the nonzeros of row p are
+// the contiguous slots around p; the band keeps nu(p, p + k), k = 1 ..
+// min(cnt_p, band_cap), at (k - 1) n + p, so a warp's reads of one k are
+// contiguous from either end of the pair (row p reads its right neighbours
+// at p, row p + k its left neighbour at p).  Weights past the band are
+// recomputed from the positions.
+//   band_build   right neighbours: nu stored, right part of r_p, cnt_p;
+//                gathers ids and masses into the sorted slots
+//   band_rowsum  left part of r_p from the band -> 1 / r_p
+//   band_exchange  Eq. 4 / 7 with the stored weights
+
+template <typename T>
+__device__ __forceinline__ T* band_of(const Dev& d) {
+  return static_cast<T*>(d.band);
+}
+
+// Slot k steps to the right (left for k < 0) of p, around the ring when the
+// walls are periodic (the walk never needs more than n - 1 steps).
+__device__ __forceinline__ long long ring(const Dev& d, long long p, long long k) {
+  long long q = p + k;
+  if (d.periodic) q = q < 0 ? q + d.n : (q >= d.n ? q - d.n : q);
+  return q;
+}
+
+template <bool MIX>
+__global__ void __launch_bounds__(kThreads) k_band_build(Dev d) {
+  using W = Weight<MIX, 1>;
+  using T = typename W::T;
+  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (p >= d.n) return;
+  const int xc = d.ctrl->xcur, mc = d.ctrl->mcur;
+  const long long* Xs = d.X[xc ^ 1];
+  const long long x = Xs[p];
+  T* band = band_of<T>(d);
+  const long long kmax = d.periodic ? d.n - 1 : d.n - 1 - p;
+  T r = T(0);
+  long long k = 1;
+  for (; k <= kmax; ++k) {
+    const long long q = ring(d, p, k);
+    const long long D = d.periodic ? wrap(Xs[q] - x, d.Lq[0]) : Xs[q] - x;
+    if (D > d.S) break;
+    const T w = W::eval(d, D, 0);
+    if (k <= d.band_cap) band[(k - 1) * d.n + p] = w;
+    r += w;
+  }
+  d.cnt[p] = (int)(k - 1);
+  static_cast<T*>(d.rinv)[p] = r;  // right part of r_p, completed by band_rowsum
+  const int s = d.src[p];
+  d.id[xc ^ 1][p] = d.id[xc][s];
+  gather_masses(d, mc, p, s);
+}
+
+template <bool MIX>
+__global__ void __launch_bounds__(kThreads) k_band_rowsum(Dev d) {
+  using W = Weight<MIX, 1>;
+  using T = typename W::T;
+  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (p >= d.n) return;
+  const long long* Xs = d.X[d.ctrl->xcur ^ 1];
+  const T* band = band_of<T>(d);
+  T r = T(1) + static_cast<const T*>(d.rinv)[p];  // self, right part
+  const long long kmax = d.periodic ? d.n - 1 : p;
+  for (long long k = 1; k <= kmax; ++k) {
+    const long long q = ring(d, p, -k);
+    if (k > d.cnt[q]) break;  // p is past q's right neighbours
+    r += k <= d.band_cap ? band[(k - 1) * d.n + q]
+                         : W::eval(d, d.periodic ? wrap(Xs[p] - Xs[q], d.Lq[0]) : Xs[p] - Xs[q], 0);
+  }
+  store_rinv<MIX>(d, p, r);
+}
+
+template <bool MIX, bool TR>
+__global__ void __launch_bounds__(kThreads) k_band_exchange(Dev d, int sp) {
+  using W = Weight<MIX, 1>;
+  using T = typename W::T;
+  using MS = Mass<MIX>;
+  using MV = typename MS::V;
+  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const bool valid = p < d.n;
+  const int xc = d.ctrl->xcur, mc = d.ctrl->mcur;
+  const SpeciesPair sq = species_pair<TR>(d, sp);
+  MV A{}, B{};
+  if (valid) {
+    const long long* Xs = d.X[xc ^ 1];
+    const unsigned long long* MA = d.M[mc ^ 1] + sq.oa;
+    const unsigned long long* MB = d.M[mc ^ 1] + sq.ob;
+    const T* band = band_of<T>(d);
+    const T ip = load_rinv<MIX>(d, p);
+    A = MS::load(MA, p);
+    B = MS::load(MB, p);
+    typename MS::Acc dA{}, dB{};
+    auto pair = [&](long long q, T w) {
+      const T P = normalised<T>(d.norm, w, ip, load_rinv<MIX>(d, q));
+      MS::acc(dA, P, MS::diff(MS::load(MA, q), A));
+      MS::acc(dB, P, MS::diff(MS::load(MB, q), B));
+    };
+    const long long kl = d.periodic ? d.n - 1 : p;
+    for (long long k = 1; k <= kl; ++k) {
+      const long long q = ring(d, p, -k);
+      if (k > d.cnt[q]) break;
+      pair(q, k <= d.band_cap
+                  ? band[(k - 1) * d.n + q]
+                  : W::eval(d, d.periodic ? wrap(Xs[p] - Xs[q], d.Lq[0]) : Xs[p] - Xs[q], 0));
+    }
+    const long long kr = d.cnt[p];
+    for (long long k = 1; k <= kr; ++k) {
+      const long long q = ring(d, p, k);
+      pair(q, k <= d.band_cap
+                  ? band[(k - 1) * d.n + p]
+                  : W::eval(d, d.periodic ? wrap(Xs[q] - Xs[p], d.Lq[0]) : Xs[q] - Xs[p], 0));
+    }
+    MS::update(A, B, dA, dB, TR ? 0 : d.react);
+    MS::store(d.M[mc] + sq.oa, p, A);
+    if (sq.store_b) MS::store(d.M[mc] + sq.ob, p, B);
+  }
+  if (!TR) finish_step<MIX>(d, A, B, valid, 1, 0);
+}
+
 // =============================================================== 2-d cells ==
 
 template <bool MIX, bool EXCHANGE>
@@ -503,7 +624,18 @@ template <bool MIX>
 static void transfer_t(const Dev& d, int search, cudaStream_t s, Marker& mk) {
   const unsigned int g = (unsigned int)((d.n + kThreads - 1) / kThreads);
   if (search == MT_SEARCH_CELL) {
-    if (d.dim == 1) {
+    if (d.dim == 1 && d.band_cap > 0) {
+      mk("band_build", s);
+      k_band_build<MIX><<<g, kThreads, 0, s>>>(d);
+      mk("band_rowsum", s);
+      k_band_rowsum<MIX><<<g, kThreads, 0, s>>>(d);
+      for (int sp = 2; sp < d.nspec; sp += 2) {
+        mk("band_exchange_species", s);
+        k_band_exchange<MIX, true><<<g, kThreads, 0, s>>>(d, sp);
+      }
+      mk("band_exchange", s);
+      k_band_exchange<MIX, false><<<g, kThreads, 0, s>>>(d, 0);
+    } else if (d.dim == 1) {
       mk("rowsum_walk", s);
       k_rowsum_walk<MIX><<<g, kThreads, 0, s>>>(d);
       for (int sp = 2; sp < d.nspec; sp += 2) {

@@ -53,7 +53,7 @@ class mt_params(ctypes.Structure):
         ("seg_target", ctypes.c_int32),
         ("walls", ctypes.c_int32),
         ("species", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("stored_p", ctypes.c_int32),
     ]
 
 

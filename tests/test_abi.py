@@ -183,9 +183,30 @@ def test_species_rules():
     assert abs((w6 - w3) - 2 * 3 * 10000 * 8) <= 512  # two buffers, three more species
     mt.mt_resolve(mt.mt_params_init(n=10, species=mt.MT_MAX_SPECIES))
     for bad in (dict(species=1), dict(species=mt.MT_MAX_SPECIES + 1), dict(species=-2),
-                dict(reserved=3)):
+                dict(stored_p=-1)):
         with pytest.raises(mt.MtError) as e:
             mt.mt_resolve(mt.mt_params_init(n=10, **bad))
         assert e.value.status == mt.MT_ERR_INVALID
     with pytest.raises(mt.MtError):
         mt.mt_batch_resolve(_batch_params(species=3), mt.make_batch([10], [10.0]))
+
+
+def test_stored_p_rules():
+    # the band follows the mean density: 1.9 right neighbours per particle here
+    r = mt.mt_resolve(mt.mt_params_init(n=100000, L=(1e5,), stored_p=1))
+    assert 8 <= r.stored_p <= 32 and r.seg_target == 0
+    dense = mt.mt_resolve(mt.mt_params_init(n=100000, L=(500.0,), D_mt=0.5, dt=0.1, stored_p=1))
+    mean = dense.cutoff * 100000 / 500.0
+    assert mean * 1.2 <= dense.stored_p <= mean * 1.6 + 16
+    assert mt.mt_resolve(mt.mt_params_init(n=1000, L=(1e3,), stored_p=40)).stored_p == 40
+    assert mt.mt_resolve(mt.mt_params_init(n=10, L=(1e3,), stored_p=40)).stored_p == 10
+    base = mt.mt_workspace_bytes(mt.mt_params_init(n=10000, L=(1e4,), stored_p=0, species=3))
+    w = mt.mt_workspace_bytes(mt.mt_params_init(n=10000, L=(1e4,), stored_p=20, species=3))
+    assert abs((w - base) - (10000 * 4 + 20 * 10000 * 8)) <= 512  # counts + FP64 band
+    for bad in (dict(dim=2, L=(10.0, 10.0)), dict(search=mt.MT_SEARCH_BRUTE),
+                dict(search=mt.MT_SEARCH_FULL)):
+        with pytest.raises(mt.MtError) as e:
+            mt.mt_resolve(mt.mt_params_init(n=10, stored_p=1, **bad))
+        assert e.value.status == mt.MT_ERR_INVALID
+    with pytest.raises(mt.MtError):
+        mt.mt_batch_resolve(_batch_params(stored_p=1), mt.make_batch([10], [10.0]))
