@@ -81,8 +81,9 @@ def parse():
     ap.add_argument("--ncu", action="store_true",
                     help="profiling mode: upload, W graph steps, then K direct steps, nothing else")
     ap.add_argument("--n", type=int, default=N, help="particles (profiling mode only)")
-    ap.add_argument("--ncu-search", default="cell", choices=["cell", "full"],
-                    help="profiling mode: the cell list (headline) or the full matrix")
+    ap.add_argument("--ncu-search", default="cell", choices=["cell", "full", "dense", "dense_spam"],
+                    help="profiling mode: the cell list (headline), the full matrix, or the "
+                         "paper's density on the fly or in the SPaM form")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble object")
     ap.add_argument("--no-precision", action="store_true", help="skip the precision report")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving object")
@@ -523,52 +524,73 @@ def serve_run(local: int, count: int, pool_gb: float = 8.0, max_active: int = 16
 SFU_EX2_PER_SM_CLK = 16  # MUFU ex2 results per SM per clock (4 quadrants x 4)
 
 
-def dense_run(local: int, steps: int = 10, sm_mhz: float | None = None):
+def dense_run(local: int, steps: int = 10, sm_mhz: float | None = None, peak_gbs: float = 0.0):
     """The paper's own density (Sec. 6): N = 1e6 on [0, 5000] (200 particles
     per unit length, about 270 neighbours within the cutoff), D = 1 split,
-    dt = 0.1, segregated C1/C2, MIXED.  This regime is bound by the
-    exponentials (4 per unordered pair: two passes, both sides), reported
-    against the SFU's ex2 rate from its unit count and clock."""
-    import numpy as np
+    dt = 0.1, segregated C1/C2, MIXED, in two forms.  On the fly, each pass
+    evaluates its weights (4 exponentials per unordered pair: two passes,
+    both sides), reported against the SFU's ex2 rate from its unit count and
+    clock.  The SPaM form (Sec. 6's stored sparse matrix) evaluates each
+    pair's weight once, stores it in the band and reads it back in both
+    passes, reported against HBM: the band's bytes written once and read by
+    each of the two passes."""
     import torch
 
     from paper_1811_05474_gb300 import mt, synth
 
     dev = torch.device("cuda", local)
     n, Ld = 10 ** 6, 5000.0
-    p = mt.mt_params_init(n=n, L=(Ld,), D_mt=0.5, D_rw=0.5, dt=0.1, react=0,
-                          precision=mt.MT_MIXED, seed=3)
-    sim = mt.Simulation(p, device=dev)
     x = synth.uniform_positions(n, Ld, seed=9)
     c1, c2 = synth.segregated_masses(x, Ld)
-    sim.upload(x, c1, c2)
-    sim.run(3)
-    sim.sync()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(sim.stream)
-    sim.run(steps)
-    e1.record(sim.stream)
-    sim.sync()
-    ms = e0.elapsed_time(e1) / steps
-    npairs = mt.mt_read_pairs(sim.h, None, None, 0)
-    mt.mt_set_profiling(sim.h, True)
-    sim.run(1)
-    kernels = mt.mt_read_profile(sim.h)
-    sim.close()
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    fsum = torch.empty((), dtype=torch.int64, device=dev)
+
+    def flush_l2(s):
+        with torch.cuda.stream(s):
+            flush.zero_()
+            torch.sum(flush.view(torch.int64), dim=0, out=fsum)
+
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = sm_mhz or 2070.0
-    peak = nsm * SFU_EX2_PER_SM_CLK * mhz * 1e6
-    exps = 4.0 * npairs
-    return {"workload": "paper_sec6_density_1d_n1e6_L5000_D1_dt0.1_mixed", "steps": steps,
-            "ms_per_step": ms, "particle_steps_per_s": n / (ms * 1e-3),
-            "pairs_per_step": npairs, "pair_interactions_per_s": npairs / (ms * 1e-3),
-            "search": "cell list (general pipeline: the staging of the one-kernel step does not "
-                      "fit this density)",
-            "kernels": [{"name": k, "ms": v} for k, v in kernels],
-            "roofline": {"bound": "sfu", "achieved": exps / (ms * 1e-3), "peak": peak,
-                         "unit": "exp/s", "frac": exps / (ms * 1e-3) / peak,
-                         "peak_kind": f"derived: {nsm} SMs x {SFU_EX2_PER_SM_CLK} ex2/clk x {mhz:.0f} MHz"}}
+    sfu_peak = nsm * SFU_EX2_PER_SM_CLK * mhz * 1e6
+    out = {"workload": "paper_sec6_density_1d_n1e6_L5000_D1_dt0.1_mixed", "steps": steps,
+           "l2": "flushed between timed steps (512 MiB write, then read)"}
+    for form, stored in (("on_the_fly", 0), ("spam", 1)):
+        p = mt.mt_params_init(n=n, L=(Ld,), D_mt=0.5, D_rw=0.5, dt=0.1, react=0,
+                              precision=mt.MT_MIXED, seed=3, stored_p=stored)
+        sim = mt.Simulation(p, device=dev)
+        sim.upload(x, c1, c2)
+        ms = timed_steps(sim, steps, 3, flush_l2) / steps
+        npairs = mt.mt_read_pairs(sim.h, None, None, 0)
+        mt.mt_set_profiling(sim.h, True)
+        sim.run(1)
+        kernels = mt.mt_read_profile(sim.h)
+        band = int(sim.params.stored_p)
+        sim.close()
+        r = {"ms_per_step": ms, "particle_steps_per_s": n / (ms * 1e-3),
+             "pairs_per_step": npairs, "pair_interactions_per_s": npairs / (ms * 1e-3),
+             "kernels": [{"name": k, "ms": v} for k, v in kernels]}
+        if stored:
+            t = sum(v for k, v in kernels if k.startswith("band"))
+            bb = 3.0 * 4.0 * npairs  # band: written once, read by both passes (binary32)
+            r["band_per_particle"] = band
+            r["exponentials_per_step"] = npairs
+            r["roofline"] = {"bound": "hbm", "kernels": "band_build + band_rowsum + band_exchange",
+                             "achieved": bb / (t * 1e-3) / 1e9, "peak": peak_gbs, "unit": "GB/s",
+                             "frac": bb / (t * 1e-3) / 1e9 / peak_gbs if peak_gbs else None,
+                             "algo_bytes_per_step": bb,
+                             "note": "band bytes only (3 x 4 B per unordered pair); "
+                                     "per-particle arrays add about 0.1 GB"}
+        else:
+            exps = 4.0 * npairs
+            r["exponentials_per_step"] = exps
+            r["roofline"] = {"bound": "sfu", "achieved": exps / (ms * 1e-3), "peak": sfu_peak,
+                             "unit": "exp/s", "frac": exps / (ms * 1e-3) / sfu_peak,
+                             "peak_kind": f"derived: {nsm} SMs x {SFU_EX2_PER_SM_CLK} ex2/clk x "
+                                          f"{mhz:.0f} MHz"}
+        out[form] = r
+    del flush
+    return out
 
 
 def species_run(local: int, steps: int = 50, counts=(2, 3, 4, 6, 8)):
@@ -797,13 +819,22 @@ def run_ncu(args):
     from paper_1811_05474_gb300 import mt, synth
 
     n = args.n
-    Ln = float(n) * (L / N)
     prec = mt.MT_MIXED if args.precision == "mixed" else mt.MT_FP64
-    search = mt.MT_SEARCH_FULL if args.ncu_search == "full" else mt.MT_SEARCH_CELL
-    p = mt.mt_params_init(n=n, L=(Ln,), v=(V, 0.0), D_mt=D, D_rw=D, dt=DT, precision=prec,
-                          search=search, seed=2024, observe_cap=args.steps + args.warmup)
-    sim = mt.Simulation(p)
-    sim.upload(synth.uniform_positions(n, Ln, seed=0), *synth.uniform_masses(n, seed=0))
+    if args.ncu_search.startswith("dense"):
+        # the paper's density (200 per unit length, D = 1 split, dt = 0.1)
+        Ln = float(n) * 5000.0 / 1e6
+        p = mt.mt_params_init(n=n, L=(Ln,), D_mt=0.5, D_rw=0.5, dt=0.1, react=0, precision=prec,
+                              seed=3, stored_p=1 if args.ncu_search == "dense_spam" else 0)
+        x = synth.uniform_positions(n, Ln, seed=9)
+        sim = mt.Simulation(p)
+        sim.upload(x, *synth.segregated_masses(x, Ln))
+    else:
+        Ln = float(n) * (L / N)
+        search = mt.MT_SEARCH_FULL if args.ncu_search == "full" else mt.MT_SEARCH_CELL
+        p = mt.mt_params_init(n=n, L=(Ln,), v=(V, 0.0), D_mt=D, D_rw=D, dt=DT, precision=prec,
+                              search=search, seed=2024, observe_cap=args.steps + args.warmup)
+        sim = mt.Simulation(p)
+        sim.upload(synth.uniform_positions(n, Ln, seed=0), *synth.uniform_masses(n, seed=0))
     sim.run(args.warmup)
     # direct launches (ncu does not profile kernels inside graphs that
     # contain conditional nodes)
@@ -879,7 +910,7 @@ def main():
         brute = brute_run(local, sm_mhz=clocks.get("sm_mhz") if clocks else None)
     dense = None
     if not args.no_dense and rank == 0:
-        dense = dense_run(local, sm_mhz=clocks.get("sm_mhz") if clocks else None)
+        dense = dense_run(local, sm_mhz=clocks.get("sm_mhz") if clocks else None, peak_gbs=peak)
     species = None
     if not args.no_species and rank == 0:
         species = species_run(local)

@@ -63,6 +63,7 @@ struct Derived {
       o_status, o_big, o_part, o_obs, o_fstart[2], o_cb[2], o_ovlist, o_pred[2], o_rt, o_sslot,
       o_sreal, o_rdone, o_cnt, o_band, total;
   long long band = 0;  // SPaM band entries per particle (0: off)
+  bool tile = false;   // dense 1-d: tiled transfer passes
 };
 
 int default_frac_bits(const mt_params& p) {
@@ -289,6 +290,10 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
   }
   if (p.stored_p > 0 && p.stored_p > p.n) p.stored_p = (int32_t)std::max<long long>(p.n, 2);
   D.band = p.stored_p;
+  // dense 1-d neighbourhoods (>= kTileMinNeighbours a side on average) walk
+  // shared-memory tiles instead of per-particle global-memory walks
+  if (p.search == MT_SEARCH_CELL && p.dim == 1 && !periodic && D.band == 0 && p.n > 0)
+    D.tile = (double)D.S * (double)p.n / lq_sum >= kTileMinNeighbours;
   // realisation table and fused segments (each realisation's own, so its
   // particles' slot range [off, off + n) is split at off + j T)
   {
@@ -348,8 +353,10 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
   D.o_rt = take(D.rt.size() * sizeof(Real));
   D.o_sslot = take(D.sslot.size() * 4);
   D.o_sreal = take(D.sreal.size() * 4);
-  D.o_cnt = take(D.band > 0 ? n * 4 : 0);
-  D.o_band = take(D.band > 0 ? (size_t)D.band * n * (p.precision == MT_MIXED ? 4 : 8) : 0);
+  D.o_cnt = take(D.band > 0 ? 2 * n * 4 : 0);
+  D.o_band = take(D.band > 0 ? (size_t)D.band * ((n + 31) / 32 * 32) *
+                                   (p.precision == MT_MIXED ? 4 : 8)
+                             : 0);
   D.o_rdone = take((size_t)D.nreal * 4);
   D.total = o;
   D.p = p;
@@ -708,6 +715,7 @@ mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace
   d.periodic = D.p.walls == MT_WALLS_PERIODIC ? 1 : 0;
   d.nspec = D.p.species;
   d.band_cap = (int)D.band;
+  d.tile = D.tile ? 1 : 0;
   d.cnt = reinterpret_cast<int*>(w + D.o_cnt);
   d.band = w + D.o_band;
   d.n = D.p.n;

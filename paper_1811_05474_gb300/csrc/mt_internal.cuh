@@ -16,6 +16,7 @@ constexpr int kSmallCell = 32;         // cells up to this size sort in one thre
 constexpr int kBigSortCap = 2048;      // cells up to this size sort in shared memory
 constexpr int kBruteTile = 256;        // j-particles staged per tile, brute force
 constexpr long long kSpinLimit = 1LL << 22;  // bounded waits (scan look-back)
+constexpr double kTileMinNeighbours = 32.0;  // mean neighbours a side for tiled passes
 constexpr int kFusedCap = 1024;        // particles one fused-step CTA stages
 constexpr int kFusedCtasPerSm = 4;     // resident CTAs per SM of the fused step
 
@@ -93,8 +94,9 @@ struct Dev {
   int periodic;             // 1: periodic walls (wrap, minimum-image separations)
   int nspec;                // species per particle (masses hold nspec * n words)
   int band_cap;             // SPaM form: stored weights per particle (0: off)
-  int* cnt;                 // [n] SPaM: right neighbours of each sorted slot
-  void* band;               // [band_cap][n] SPaM: nu(p, p + k) at (k - 1) n + p
+  int tile;                 // 1: dense 1-d transfer passes over shared-memory tiles
+  int* cnt;                 // [2][n] SPaM: right, then left neighbours of each slot
+  void* band;               // SPaM: nu(p, p + k), k <= band_cap, in tiles of 32 slots
   long long n;
   int dim;
   int norm;                 // MT_NORM_*

@@ -34,7 +34,7 @@ struct Weight<false, DIM> {
     }
     return exp(-__dmul_rn(s2, d.inv8));
   }
-  // 1-d, 0 <= D <= Smax < 2^30
+  // 1-d, |D| <= Smax < 2^30 (the same value as eval(d, D, 0))
   static __device__ __forceinline__ double near(const Dev& d, long long D) {
     const double sx = __dmul_rn((double)(int)D, d.scale);
     return exp(-__dmul_rn(__dmul_rn(sx, sx), d.inv8));
@@ -53,7 +53,7 @@ struct Weight<true, DIM> {
     }
     return __expf(-__fmul_rn(s2, d.inv8f));
   }
-  // 1-d, 0 <= D <= Smax < 2^30
+  // 1-d, |D| <= Smax < 2^30 (the same value as eval(d, D, 0))
   static __device__ __forceinline__ float near(const Dev& d, long long D) {
     const float f = __int2float_rn((int)D);
     return __expf(-__fmul_rn(__fmul_rn(f, f), d.inv8f));
@@ -148,6 +148,31 @@ __device__ __forceinline__ SpeciesPair species_pair(const Dev& d, int sp) {
   const bool two = sp + 1 < d.nspec;
   return {(long long)sp * d.n, (long long)(two ? sp + 1 : sp) * d.n, two};
 }
+
+// Row sum r_i over a dense neighbourhood (hundreds to thousands of terms):
+// binary64, or in MIXED a binary32 sum with each addition's rounding error
+// (Knuth's two-sum) collected in a second term, so the sum keeps about twice
+// binary32's precision however many weights it adds.
+template <bool MIX>
+struct RowSum;
+template <>
+struct RowSum<false> {
+  double r;
+  __device__ __forceinline__ explicit RowSum(double v) : r(v) {}
+  __device__ __forceinline__ void add(double w) { r += w; }
+  __device__ __forceinline__ double value() const { return r; }
+};
+template <>
+struct RowSum<true> {
+  float s, c;
+  __device__ __forceinline__ explicit RowSum(float v) : s(v), c(0.0f) {}
+  __device__ __forceinline__ void add(float w) {
+    const df e = two_sum(s, w);
+    s = e.hi;
+    c = __fadd_rn(c, e.lo);
+  }
+  __device__ __forceinline__ float value() const { return __fadd_rn(s, c); }
+};
 
 template <bool MIX>
 __device__ __forceinline__ void store_rinv(const Dev& d, long long p, typename Weight<MIX, 1>::T r) {

@@ -281,31 +281,187 @@ __global__ void __launch_bounds__(kThreads) k_exchange_walk(Dev d, int sp) {
   if (!TR) finish_step<MIX>(d, A, B, valid, 1, 0);
 }
 
+// |dx| <= S in one unsigned comparison (1-d)
+__device__ __forceinline__ bool within1(long long dx, long long S) {
+  return (unsigned long long)(dx + S) <= (unsigned long long)(2 * S);
+}
+
+// ======================================================= 1-d dense tiles ==
+// Dense neighbourhoods (tens to thousands of neighbours per particle): a CTA
+// takes 256 consecutive sorted slots; the slots any of them can pair with
+// form one contiguous range (from the cell starts of x_first - Smax and
+// x_last + Smax), staged through shared memory in chunks of kTileChunk.
+// Each warp walks its own sub-range of the chunk with every lane reading the
+// same slot (a shared-memory broadcast), so a pair costs one broadcast load
+// per operand instead of a load per lane, and the loop has no
+// data-dependent exit.  Each lane tests its own cutoff.
+
+constexpr int kTileChunk = 512;
+
+// Candidate range [lo, hi) of the sorted slots that can pair with x in
+// [xa, xb] (whole cells, so a superset of the exact range).
+__device__ __forceinline__ void tile_range(const Dev& d, long long xa, long long xb,
+                                           long long& lo, long long& hi) {
+  lo = d.start[cell_of(d, xa - d.S, 0)];
+  hi = d.start[cell_of(d, xb + d.S, 0) + 1];
+}
+
+template <bool MIX>
+__global__ void __launch_bounds__(kThreads) k_rowsum_tile(Dev d) {
+  using W = Weight<MIX, 1>;
+  using T = typename W::T;
+  __shared__ long long s_x[kTileChunk];
+  const long long b0 = (long long)blockIdx.x * kThreads;
+  const long long b1 = min(b0 + (long long)kThreads, d.n);
+  const int xc = d.ctrl->xcur, mc = d.ctrl->mcur;
+  const long long* Xs = d.X[xc ^ 1];
+  long long lo, hi, wlo, whi;
+  tile_range(d, Xs[b0], Xs[b1 - 1], lo, hi);
+  const long long w0 = b0 + (threadIdx.x & ~31);
+  const long long w1 = min(w0 + 32, b1);
+  const bool wact = w0 < b1;
+  if (wact) tile_range(d, Xs[w0], Xs[w1 - 1], wlo, whi);
+  const long long p = b0 + threadIdx.x;
+  const bool valid = p < b1;
+  const long long x = valid ? Xs[p] : 0;
+  // two independent sums (even and odd candidates) halve the dependent
+  // chain of compensated additions
+  RowSum<MIX> r0(T(1)), r1(T(0));  // self
+  for (long long c0 = lo; c0 < hi; c0 += kTileChunk) {
+    const int nc = (int)min((long long)kTileChunk, hi - c0);
+    for (int i = threadIdx.x; i < nc; i += kThreads) s_x[i] = Xs[c0 + i];
+    __syncthreads();
+    if (wact) {
+      const int j0 = (int)(max(wlo, c0) - c0), j1 = (int)(min(whi, c0 + nc) - c0);
+      const int self = (int)(p - c0);
+      int j = j0;
+#pragma unroll 2
+      for (; j + 1 < j1; j += 2) {
+        const long long D0 = s_x[j] - x, D1 = s_x[j + 1] - x;
+        if (j != self && within1(D0, d.S)) r0.add(W::near(d, D0));
+        if (j + 1 != self && within1(D1, d.S)) r1.add(W::near(d, D1));
+      }
+      if (j < j1) {
+        const long long D = s_x[j] - x;
+        if (j != self && within1(D, d.S)) r0.add(W::near(d, D));
+      }
+    }
+    __syncthreads();
+  }
+  if (!valid) return;
+  r0.add(r1.value());
+  store_rinv<MIX>(d, p, r0.value());
+  const int s = d.src[p];
+  d.id[xc ^ 1][p] = d.id[xc][s];
+  gather_masses(d, mc, p, s);
+}
+
+template <bool MIX, bool TR>
+__global__ void __launch_bounds__(kThreads) k_exchange_tile(Dev d, int sp) {
+  using W = Weight<MIX, 1>;
+  using T = typename W::T;
+  using MS = Mass<MIX>;
+  using MV = typename MS::V;
+  __shared__ long long s_x[kTileChunk];
+  __shared__ T s_r[kTileChunk];
+  __shared__ MV s_a[kTileChunk];
+  __shared__ MV s_b[kTileChunk];
+  const long long b0 = (long long)blockIdx.x * kThreads;
+  const long long b1 = min(b0 + (long long)kThreads, d.n);
+  const int xc = d.ctrl->xcur, mc = d.ctrl->mcur;
+  const SpeciesPair sq = species_pair<TR>(d, sp);
+  const long long* Xs = d.X[xc ^ 1];
+  const unsigned long long* MA = d.M[mc ^ 1] + sq.oa;
+  const unsigned long long* MB = d.M[mc ^ 1] + sq.ob;
+  long long lo, hi, wlo, whi;
+  tile_range(d, Xs[b0], Xs[b1 - 1], lo, hi);
+  const long long w0 = b0 + (threadIdx.x & ~31);
+  const long long w1 = min(w0 + 32, b1);
+  const bool wact = w0 < b1;
+  if (wact) tile_range(d, Xs[w0], Xs[w1 - 1], wlo, whi);
+  const long long p = b0 + threadIdx.x;
+  const bool valid = p < b1;
+  const long long x = valid ? Xs[p] : 0;
+  MV A{}, B{};
+  T ip = T(0);
+  if (valid) {
+    A = MS::load(MA, p);
+    B = MS::load(MB, p);
+    ip = load_rinv<MIX>(d, p);
+  }
+  // two accumulator sets (even and odd candidates) halve the dependent
+  // chain of compensated additions
+  typename MS::Acc dA{}, dB{}, dA1{}, dB1{};
+  for (long long c0 = lo; c0 < hi; c0 += kTileChunk) {
+    const int nc = (int)min((long long)kTileChunk, hi - c0);
+    for (int i = threadIdx.x; i < nc; i += kThreads) {
+      s_x[i] = Xs[c0 + i];
+      s_r[i] = load_rinv<MIX>(d, c0 + i);
+      s_a[i] = MS::load(MA, c0 + i);
+      s_b[i] = MS::load(MB, c0 + i);
+    }
+    __syncthreads();
+    if (wact) {
+      const int j0 = (int)(max(wlo, c0) - c0), j1 = (int)(min(whi, c0 + nc) - c0);
+      const int self = (int)(p - c0);
+      auto pair = [&](int j, typename MS::Acc& a, typename MS::Acc& b) {
+        const long long D = s_x[j] - x;
+        if (j != self && within1(D, d.S)) {
+          const T P = normalised<T>(d.norm, W::near(d, D), ip, s_r[j]);
+          MS::acc(a, P, MS::diff(s_a[j], A));
+          MS::acc(b, P, MS::diff(s_b[j], B));
+        }
+      };
+      int j = j0;
+      for (; j + 1 < j1; j += 2) {
+        pair(j, dA, dB);
+        pair(j + 1, dA1, dB1);
+      }
+      if (j < j1) pair(j, dA, dB);
+    }
+    __syncthreads();
+  }
+  dA = acc_merge(dA, dA1);
+  dB = acc_merge(dB, dB1);
+  if (valid) {
+    MS::update(A, B, dA, dB, TR ? 0 : d.react);
+    MS::store(d.M[mc] + sq.oa, p, A);
+    if (sq.store_b) MS::store(d.M[mc] + sq.ob, p, B);
+  }
+  if (!TR) finish_step<MIX>(d, A, B, valid, 1, 0);
+}
+
 // ================================================== 1-d SPaM (stored P) ==
 // The SPaM form of Sec. 6: the nonzero weights of the step's transfer
 // matrix are stored and both passes read them, so each unordered pair's
 // exponential is evaluated once.  In sorted order the nonzeros of row p are
-// the contiguous slots around p; the band keeps nu(p, p + k), k = 1 ..
-// min(cnt_p, band_cap), at (k - 1) n + p, so a warp's reads of one k are
-// contiguous from either end of the pair (row p reads its right neighbours
-// at p, row p + k its left neighbour at p).  Weights past the band are
-// recomputed from the positions.
-//   band_build   right neighbours: nu stored, right part of r_p, cnt_p;
-//                gathers ids and masses into the sorted slots
-//   band_rowsum  left part of r_p from the band -> 1 / r_p
+// the contiguous slots around p: cnt_l(p) to the left and cnt_r(p) to the
+// right.  The band keeps nu(p, p + k), k = 1 .. min(cnt_r(p), band_cap), in
+// tiles of 32 slots: entry (p, k) is at ((p / 32) band_cap + k - 1) 32 +
+// p % 32, so a warp reading its right neighbours streams one contiguous
+// block, and reading its left neighbours (entries (p - k, k)) streams two
+// adjacent ones.  Weights past the band are recomputed from the positions.
+//   band_build     right neighbours: nu stored, right part of r_p, cnt_r;
+//                  left count cnt_l; ids and masses into the sorted slots
+//   band_rowsum    left part of r_p from the band -> 1 / r_p
 //   band_exchange  Eq. 4 / 7 with the stored weights
 
-template <typename T>
-__device__ __forceinline__ T* band_of(const Dev& d) {
-  return static_cast<T*>(d.band);
+__device__ __forceinline__ long long band_at(const Dev& d, long long q, long long k) {
+  return (((q >> 5) * d.band_cap) + (k - 1)) * 32 + (q & 31);
 }
 
 // Slot k steps to the right (left for k < 0) of p, around the ring when the
-// walls are periodic (the walk never needs more than n - 1 steps).
+// walls are periodic (a walk never takes more than n - 1 steps).
 __device__ __forceinline__ long long ring(const Dev& d, long long p, long long k) {
   long long q = p + k;
   if (d.periodic) q = q < 0 ? q + d.n : (q >= d.n ? q - d.n : q);
   return q;
+}
+
+// Tick distance from slot q up to slot p (p to the right of q).
+__device__ __forceinline__ long long gap(const Dev& d, const long long* Xs, long long q,
+                                         long long p) {
+  return d.periodic ? wrap(Xs[p] - Xs[q], d.Lq[0]) : Xs[p] - Xs[q];
 }
 
 template <bool MIX>
@@ -316,21 +472,23 @@ __global__ void __launch_bounds__(kThreads) k_band_build(Dev d) {
   if (p >= d.n) return;
   const int xc = d.ctrl->xcur, mc = d.ctrl->mcur;
   const long long* Xs = d.X[xc ^ 1];
-  const long long x = Xs[p];
-  T* band = band_of<T>(d);
-  const long long kmax = d.periodic ? d.n - 1 : d.n - 1 - p;
-  T r = T(0);
+  T* band = static_cast<T*>(d.band);
+  RowSum<MIX> r(T(0));
   long long k = 1;
-  for (; k <= kmax; ++k) {
-    const long long q = ring(d, p, k);
-    const long long D = d.periodic ? wrap(Xs[q] - x, d.Lq[0]) : Xs[q] - x;
+  const long long kr = d.periodic ? d.n - 1 : d.n - 1 - p;
+  for (; k <= kr; ++k) {
+    const long long D = gap(d, Xs, p, ring(d, p, k));
     if (D > d.S) break;
     const T w = W::eval(d, D, 0);
-    if (k <= d.band_cap) band[(k - 1) * d.n + p] = w;
-    r += w;
+    if (k <= d.band_cap) band[band_at(d, p, k)] = w;
+    r.add(w);
   }
   d.cnt[p] = (int)(k - 1);
-  static_cast<T*>(d.rinv)[p] = r;  // right part of r_p, completed by band_rowsum
+  const long long kl = d.periodic ? d.n - 1 : p;
+  for (k = 1; k <= kl; ++k)
+    if (gap(d, Xs, ring(d, p, -k), p) > d.S) break;
+  d.cnt[d.n + p] = (int)(k - 1);
+  static_cast<T*>(d.rinv)[p] = r.value();  // right part of r_p, completed by band_rowsum
   const int s = d.src[p];
   d.id[xc ^ 1][p] = d.id[xc][s];
   gather_masses(d, mc, p, s);
@@ -342,17 +500,18 @@ __global__ void __launch_bounds__(kThreads) k_band_rowsum(Dev d) {
   using T = typename W::T;
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (p >= d.n) return;
-  const long long* Xs = d.X[d.ctrl->xcur ^ 1];
-  const T* band = band_of<T>(d);
-  T r = T(1) + static_cast<const T*>(d.rinv)[p];  // self, right part
-  const long long kmax = d.periodic ? d.n - 1 : p;
-  for (long long k = 1; k <= kmax; ++k) {
-    const long long q = ring(d, p, -k);
-    if (k > d.cnt[q]) break;  // p is past q's right neighbours
-    r += k <= d.band_cap ? band[(k - 1) * d.n + q]
-                         : W::eval(d, d.periodic ? wrap(Xs[p] - Xs[q], d.Lq[0]) : Xs[p] - Xs[q], 0);
+  const T* band = static_cast<const T*>(d.band);
+  RowSum<MIX> r(T(1));  // self
+  r.add(static_cast<const T*>(d.rinv)[p]);  // right part
+  const int kl = d.cnt[d.n + p];
+  const int kb = kl < d.band_cap ? kl : d.band_cap;
+#pragma unroll 4
+  for (int k = 1; k <= kb; ++k) r.add(band[band_at(d, ring(d, p, -k), k)]);
+  if (kl > kb) {
+    const long long* Xs = d.X[d.ctrl->xcur ^ 1];
+    for (int k = kb + 1; k <= kl; ++k) r.add(W::eval(d, gap(d, Xs, ring(d, p, -k), p), 0));
   }
-  store_rinv<MIX>(d, p, r);
+  store_rinv<MIX>(d, p, r.value());
 }
 
 template <bool MIX, bool TR>
@@ -370,7 +529,7 @@ __global__ void __launch_bounds__(kThreads) k_band_exchange(Dev d, int sp) {
     const long long* Xs = d.X[xc ^ 1];
     const unsigned long long* MA = d.M[mc ^ 1] + sq.oa;
     const unsigned long long* MB = d.M[mc ^ 1] + sq.ob;
-    const T* band = band_of<T>(d);
+    const T* band = static_cast<const T*>(d.band);
     const T ip = load_rinv<MIX>(d, p);
     A = MS::load(MA, p);
     B = MS::load(MB, p);
@@ -380,20 +539,23 @@ __global__ void __launch_bounds__(kThreads) k_band_exchange(Dev d, int sp) {
       MS::acc(dA, P, MS::diff(MS::load(MA, q), A));
       MS::acc(dB, P, MS::diff(MS::load(MB, q), B));
     };
-    const long long kl = d.periodic ? d.n - 1 : p;
-    for (long long k = 1; k <= kl; ++k) {
+    const int kl = d.cnt[d.n + p], kr = d.cnt[p];
+    const int bl = kl < d.band_cap ? kl : d.band_cap;
+    const int br = kr < d.band_cap ? kr : d.band_cap;
+#pragma unroll 2
+    for (int k = 1; k <= bl; ++k) {
       const long long q = ring(d, p, -k);
-      if (k > d.cnt[q]) break;
-      pair(q, k <= d.band_cap
-                  ? band[(k - 1) * d.n + q]
-                  : W::eval(d, d.periodic ? wrap(Xs[p] - Xs[q], d.Lq[0]) : Xs[p] - Xs[q], 0));
+      pair(q, band[band_at(d, q, k)]);
     }
-    const long long kr = d.cnt[p];
-    for (long long k = 1; k <= kr; ++k) {
+    for (int k = bl + 1; k <= kl; ++k) {
+      const long long q = ring(d, p, -k);
+      pair(q, W::eval(d, gap(d, Xs, q, p), 0));
+    }
+#pragma unroll 2
+    for (int k = 1; k <= br; ++k) pair(ring(d, p, k), band[band_at(d, p, k)]);
+    for (int k = br + 1; k <= kr; ++k) {
       const long long q = ring(d, p, k);
-      pair(q, k <= d.band_cap
-                  ? band[(k - 1) * d.n + p]
-                  : W::eval(d, d.periodic ? wrap(Xs[q] - Xs[p], d.Lq[0]) : Xs[q] - Xs[p], 0));
+      pair(q, W::eval(d, gap(d, Xs, p, q), 0));
     }
     MS::update(A, B, dA, dB, TR ? 0 : d.react);
     MS::store(d.M[mc] + sq.oa, p, A);
@@ -489,11 +651,6 @@ __global__ void __launch_bounds__(kThreads) k_exchange_cell2(Dev d, int sp) {
 // ============================================================ brute force ==
 // All pairs, j-particles staged through shared memory in tiles.  Particles
 // keep their caller order (no sort); masses ping-pong between buffers.
-
-// |dx| <= S in one unsigned comparison (1-d)
-__device__ __forceinline__ bool within1(long long dx, long long S) {
-  return (unsigned long long)(dx + S) <= (unsigned long long)(2 * S);
-}
 
 template <bool MIX, bool CUT, int DIM>
 __global__ void __launch_bounds__(kThreads) k_rowsum_brute(Dev d) {
@@ -635,6 +792,15 @@ static void transfer_t(const Dev& d, int search, cudaStream_t s, Marker& mk) {
       }
       mk("band_exchange", s);
       k_band_exchange<MIX, false><<<g, kThreads, 0, s>>>(d, 0);
+    } else if (d.dim == 1 && d.tile) {
+      mk("rowsum_tile", s);
+      k_rowsum_tile<MIX><<<g, kThreads, 0, s>>>(d);
+      for (int sp = 2; sp < d.nspec; sp += 2) {
+        mk("exchange_tile_species", s);
+        k_exchange_tile<MIX, true><<<g, kThreads, 0, s>>>(d, sp);
+      }
+      mk("exchange_tile", s);
+      k_exchange_tile<MIX, false><<<g, kThreads, 0, s>>>(d, 0);
     } else if (d.dim == 1) {
       mk("rowsum_walk", s);
       k_rowsum_walk<MIX><<<g, kThreads, 0, s>>>(d);

@@ -202,7 +202,7 @@ def test_stored_p_rules():
     assert mt.mt_resolve(mt.mt_params_init(n=10, L=(1e3,), stored_p=40)).stored_p == 10
     base = mt.mt_workspace_bytes(mt.mt_params_init(n=10000, L=(1e4,), stored_p=0, species=3))
     w = mt.mt_workspace_bytes(mt.mt_params_init(n=10000, L=(1e4,), stored_p=20, species=3))
-    assert abs((w - base) - (10000 * 4 + 20 * 10000 * 8)) <= 512  # counts + FP64 band
+    assert abs((w - base) - (2 * 10000 * 4 + 20 * 10016 * 8)) <= 512  # counts + FP64 band
     for bad in (dict(dim=2, L=(10.0, 10.0)), dict(search=mt.MT_SEARCH_BRUTE),
                 dict(search=mt.MT_SEARCH_FULL)):
         with pytest.raises(mt.MtError) as e:

@@ -1,0 +1,96 @@
+"""Dense 1-d neighbourhoods (the paper's densities, Sec. 3 and Sec. 6: hundreds
+to thousands of neighbours per particle) on the GPU: the transfer passes
+over shared-memory tiles, against the oracle for single systems, batches,
+more species, and a density whose neighbourhoods span many staged chunks."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1811_05474_gb300 import mt, synth
+
+from .test_gpu_parity import TOL, assert_masses
+from .test_oracle_species import oracle_step_species, species_masses
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_of(r):
+    return O.params(frac_bits=r.frac_bits, L=(r.L[0],), v=(r.v[0],), D_mt=r.D_mt, D_rw=r.D_rw,
+                    dt=r.dt, smax=r.cutoff, norm=r.norm, react=r.react)
+
+
+def profile_names(sim):
+    mt.mt_set_profiling(sim.h, True)
+    sim.step()
+    names = [k for k, _ in mt.mt_read_profile(sim.h)]
+    mt.mt_set_profiling(sim.h, False)
+    return names
+
+
+@pytest.mark.parametrize("n,L,S,steps", [
+    (20000, 100.0, 2, 3),     # 200 per unit length: ~270 neighbours a side
+    (12000, 6.0, 2, 2),       # 2000 per unit length: ~2700 a side, many chunks
+    (9000, 45.0, 3, 3),       # three species
+])
+@pytest.mark.parametrize("precision", [mt.MT_FP64, mt.MT_MIXED])
+def test_dense_tiles_match_oracle(n, L, S, steps, precision):
+    p = mt.mt_params_init(n=n, L=(L,), v=(0.05,), D_mt=0.5, D_rw=0.5, dt=0.1,
+                          precision=precision, species=S, observe_cap=4)
+    sim = mt.Simulation(p)
+    assert sim.params.seg_target == 0
+    po = oracle_of(sim.params)
+    k = int(sim.params.frac_bits)
+    x = synth.uniform_positions(n, L, seed=n)
+    Ms = species_masses(n, S, seed=n + 1)
+    sim.upload(x, Ms[0], Ms[1])
+    for s in range(2, S):
+        sim.set_species(s, Ms[s])
+    X = O.quantize(x.reshape(1, -1), k)
+    cur = [m.copy() for m in Ms]
+    xi = synth.normals(steps + 1, 1, n, seed=4)
+    for s in range(steps):
+        sim.set_noise(xi[s])
+        sim.step()
+        X, cur = oracle_step_species(po, X, xi[s], cur)
+        assert np.array_equal(sim.ticks(), X), f"positions at step {s}"
+    for s in range(S):
+        assert_masses(sim.species(s), cur[s], TOL[precision], f"species {s}")
+    sim.set_noise(xi[steps])
+    names = profile_names(sim)
+    assert "rowsum_tile" in names and "exchange_tile" in names
+    assert "rowsum_walk" not in names
+
+
+@pytest.mark.parametrize("precision", [mt.MT_FP64, mt.MT_MIXED])
+def test_dense_tiles_in_a_batch(precision):
+    """Realisations at the paper's density side by side: the tiles never
+    pair particles of different realisations."""
+    ns = [3000, 1700, 4100, 2500]
+    Ls = [15.0, 8.5, 20.5, 12.5]
+    p = mt.mt_params_init(dim=1, L=(1.0,), D_mt=0.5, D_rw=0.5, dt=0.1, react=1,
+                          precision=precision, frac_bits=29)
+    sim = mt.Simulation(p, batch=mt.make_batch(ns, Ls))
+    assert sim.params.seg_target == 0
+    xs = [synth.uniform_positions(n, L, seed=50 + i) for i, (n, L) in enumerate(zip(ns, Ls))]
+    As = [synth.uniform_masses(n, seed=60 + i) for i, n in enumerate(ns)]
+    sim.upload(np.concatenate([x[0] for x in xs])[None, :], np.concatenate([a for a, _ in As]),
+               np.concatenate([b for _, b in As]))
+    xi = synth.normals(3, 1, sum(ns), seed=8)
+    cur = []
+    for i, (n, L) in enumerate(zip(ns, Ls)):
+        po = O.params(frac_bits=29, L=(L,), D_mt=0.5, D_rw=0.5, dt=0.1, react=1)
+        cur.append([O.quantize(xs[i], 29), As[i][0].copy(), As[i][1].copy(), po])
+    offs = np.cumsum([0] + ns)
+    for s in range(3):
+        sim.set_noise(xi[s])
+        sim.step()
+        for i, c in enumerate(cur):
+            c[0], c[1], c[2] = O.step(c[3], c[0], xi[s][:, offs[i]:offs[i + 1]], c[1], c[2])
+    T = sim.ticks()[0]
+    ga, gb = sim.masses()
+    for i, c in enumerate(cur):
+        sl = slice(offs[i], offs[i + 1])
+        assert np.array_equal(T[sl], c[0][0])
+        assert_masses(ga[sl], c[1], TOL[precision], f"A of realisation {i}")
+        assert_masses(gb[sl], c[2], TOL[precision], f"B of realisation {i}")
+    assert "rowsum_tile" in profile_names(sim)
