@@ -215,6 +215,9 @@ __device__ __forceinline__ kahan acc_merge(kahan a, kahan b) {
   const df e = two_sum(a.s, b.s);
   return {e.hi, __fadd_rn(__fadd_rn(a.c, b.c), e.lo)};
 }
+// Exact halving of a flux sum (a power-of-two scaling of both terms).
+__device__ __forceinline__ double acc_half(double a) { return 0.5 * a; }
+__device__ __forceinline__ kahan acc_half(kahan a) { return {0.5f * a.s, 0.5f * a.c}; }
 __device__ __forceinline__ kahan acc_warp_sum(kahan v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

@@ -288,64 +288,95 @@ __device__ __forceinline__ bool within1(long long dx, long long S) {
 
 // ======================================================= 1-d dense tiles ==
 // Dense neighbourhoods (tens to thousands of neighbours per particle): a CTA
-// takes 256 consecutive sorted slots; the slots any of them can pair with
-// form one contiguous range (from the cell starts of x_first - Smax and
-// x_last + Smax), staged through shared memory in chunks of kTileChunk.
-// Each warp walks its own sub-range of the chunk with every lane reading the
-// same slot (a shared-memory broadcast), so a pair costs one broadcast load
-// per operand instead of a load per lane, and the loop has no
-// data-dependent exit.  Each lane tests its own cutoff.
+// takes 256 consecutive sorted slots.  Each particle first finds its exact
+// neighbour slots [jl, jr) (itself included) from the cell starts; the
+// union over the CTA is one contiguous range, staged through shared memory
+// in chunks of kTileChunk.  Each warp walks the union of its lanes' ranges
+// with every lane reading the same slot (a shared-memory broadcast) and
+// keeping the pair when the slot lies in its own range: an index test, no
+// branch, and no data-dependent exit.  Inside the cutoff |dX| < 2^30, so the
+// separation is the difference of the positions' low 32-bit words.  The
+// particle itself adds nu_pp = 1 to r_p and an exact zero flux.
 
 constexpr int kTileChunk = 512;
 
-// Candidate range [lo, hi) of the sorted slots that can pair with x in
-// [xa, xb] (whole cells, so a superset of the exact range).
-__device__ __forceinline__ void tile_range(const Dev& d, long long xa, long long xb,
-                                           long long& lo, long long& hi) {
-  lo = d.start[cell_of(d, xa - d.S, 0)];
-  hi = d.start[cell_of(d, xb + d.S, 0) + 1];
+// Exact neighbour slots [jl, jr) of the particle at x: every sorted slot q
+// with |X_q - x| <= Smax.  The bounds lie in the cells of x -/+ Smax.
+__device__ __forceinline__ void exact_range(const Dev& d, const long long* Xs, long long x,
+                                            long long& jl, long long& jr) {
+  long long c = cell_of(d, x - d.S, 0);
+  long long q = d.start[c], e = d.start[c + 1];
+  while (q < e && Xs[q] < x - d.S) ++q;
+  jl = q;
+  c = cell_of(d, x + d.S, 0);
+  q = d.start[c];
+  e = d.start[c + 1];
+  while (q < e && Xs[q] <= x + d.S) ++q;
+  jr = q;
+}
+
+// The CTA's and the warp's candidate ranges from the lanes' exact ranges.
+struct TileRanges {
+  long long lo, hi;    // CTA: union of its particles' ranges
+  long long wlo, whi;  // warp: union of its lanes' ranges (empty if no lane is valid)
+};
+__device__ __forceinline__ TileRanges tile_ranges(long long jl, long long jr, long long b0,
+                                                  long long b1, long long* s_lohi) {
+  const long long p = b0 + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const long long w0 = b0 + (threadIdx.x & ~31);
+  const int last = w0 < b1 ? (int)min(31LL, b1 - 1 - w0) : 0;
+  TileRanges t;
+  t.wlo = __shfl_sync(0xffffffffu, jl, 0);
+  t.whi = __shfl_sync(0xffffffffu, jr, last);
+  if (w0 >= b1) t.wlo = t.whi = 0;
+  if (p == b0) s_lohi[0] = jl;
+  if (p == b1 - 1) s_lohi[1] = jr;
+  (void)lane;
+  __syncthreads();
+  t.lo = s_lohi[0];
+  t.hi = s_lohi[1];
+  return t;
 }
 
 template <bool MIX>
 __global__ void __launch_bounds__(kThreads) k_rowsum_tile(Dev d) {
   using W = Weight<MIX, 1>;
   using T = typename W::T;
-  __shared__ long long s_x[kTileChunk];
+  __shared__ unsigned int s_x[kTileChunk];
+  __shared__ long long s_lohi[2];
   const long long b0 = (long long)blockIdx.x * kThreads;
   const long long b1 = min(b0 + (long long)kThreads, d.n);
   const int xc = d.ctrl->xcur, mc = d.ctrl->mcur;
   const long long* Xs = d.X[xc ^ 1];
-  long long lo, hi, wlo, whi;
-  tile_range(d, Xs[b0], Xs[b1 - 1], lo, hi);
-  const long long w0 = b0 + (threadIdx.x & ~31);
-  const long long w1 = min(w0 + 32, b1);
-  const bool wact = w0 < b1;
-  if (wact) tile_range(d, Xs[w0], Xs[w1 - 1], wlo, whi);
   const long long p = b0 + threadIdx.x;
   const bool valid = p < b1;
   const long long x = valid ? Xs[p] : 0;
+  long long jl = 0, jr = 0;
+  if (valid) exact_range(d, Xs, x, jl, jr);
+  const TileRanges t = tile_ranges(jl, jr, b0, b1, s_lohi);
+  const unsigned int x32 = (unsigned int)x;
   // two independent sums (even and odd candidates) halve the dependent
   // chain of compensated additions
-  RowSum<MIX> r0(T(1)), r1(T(0));  // self
-  for (long long c0 = lo; c0 < hi; c0 += kTileChunk) {
-    const int nc = (int)min((long long)kTileChunk, hi - c0);
-    for (int i = threadIdx.x; i < nc; i += kThreads) s_x[i] = Xs[c0 + i];
+  RowSum<MIX> r0(T(0)), r1(T(0));
+  for (long long c0 = t.lo; c0 < t.hi; c0 += kTileChunk) {
+    const int nc = (int)min((long long)kTileChunk, t.hi - c0);
+    for (int i = threadIdx.x; i < nc; i += kThreads) s_x[i] = (unsigned int)Xs[c0 + i];
     __syncthreads();
-    if (wact) {
-      const int j0 = (int)(max(wlo, c0) - c0), j1 = (int)(min(whi, c0 + nc) - c0);
-      const int self = (int)(p - c0);
-      int j = j0;
+    const int j0 = (int)(max(t.wlo, c0) - c0), j1 = (int)(min(t.whi, c0 + nc) - c0);
+    const int ql = (int)(jl - c0);
+    const unsigned int qn = (unsigned int)(jr - jl);
+    auto term = [&](int j) {
+      const T w = W::near(d, (int)(s_x[j] - x32));
+      return (unsigned int)(j - ql) < qn ? w : T(0);
+    };
+    int j = j0;
 #pragma unroll 2
-      for (; j + 1 < j1; j += 2) {
-        const long long D0 = s_x[j] - x, D1 = s_x[j + 1] - x;
-        if (j != self && within1(D0, d.S)) r0.add(W::near(d, D0));
-        if (j + 1 != self && within1(D1, d.S)) r1.add(W::near(d, D1));
-      }
-      if (j < j1) {
-        const long long D = s_x[j] - x;
-        if (j != self && within1(D, d.S)) r0.add(W::near(d, D));
-      }
+    for (; j + 1 < j1; j += 2) {
+      r0.add(term(j));
+      r1.add(term(j + 1));
     }
+    if (j < j1) r0.add(term(j));
     __syncthreads();
   }
   if (!valid) return;
@@ -362,10 +393,11 @@ __global__ void __launch_bounds__(kThreads) k_exchange_tile(Dev d, int sp) {
   using T = typename W::T;
   using MS = Mass<MIX>;
   using MV = typename MS::V;
-  __shared__ long long s_x[kTileChunk];
+  __shared__ unsigned int s_x[kTileChunk];
   __shared__ T s_r[kTileChunk];
   __shared__ MV s_a[kTileChunk];
   __shared__ MV s_b[kTileChunk];
+  __shared__ long long s_lohi[2];
   const long long b0 = (long long)blockIdx.x * kThreads;
   const long long b1 = min(b0 + (long long)kThreads, d.n);
   const int xc = d.ctrl->xcur, mc = d.ctrl->mcur;
@@ -373,15 +405,17 @@ __global__ void __launch_bounds__(kThreads) k_exchange_tile(Dev d, int sp) {
   const long long* Xs = d.X[xc ^ 1];
   const unsigned long long* MA = d.M[mc ^ 1] + sq.oa;
   const unsigned long long* MB = d.M[mc ^ 1] + sq.ob;
-  long long lo, hi, wlo, whi;
-  tile_range(d, Xs[b0], Xs[b1 - 1], lo, hi);
-  const long long w0 = b0 + (threadIdx.x & ~31);
-  const long long w1 = min(w0 + 32, b1);
-  const bool wact = w0 < b1;
-  if (wact) tile_range(d, Xs[w0], Xs[w1 - 1], wlo, whi);
   const long long p = b0 + threadIdx.x;
   const bool valid = p < b1;
   const long long x = valid ? Xs[p] : 0;
+  long long jl = 0, jr = 0;
+  if (valid) exact_range(d, Xs, x, jl, jr);
+  const TileRanges t = tile_ranges(jl, jr, b0, b1, s_lohi);
+  const unsigned int x32 = (unsigned int)x;
+  // SYM: P = w (1/r_p + 1/r_q) / 2 is formed as 2P = w (1/r_p + 1/r_q) and
+  // the sums are halved at the end; ROW: P = w / r_p (the staged 1/r_q is
+  // 0).  Halving is exact, so the result is the same as with P.
+  const bool sym = d.norm != MT_NORM_ROW;
   MV A{}, B{};
   T ip = T(0);
   if (valid) {
@@ -392,37 +426,38 @@ __global__ void __launch_bounds__(kThreads) k_exchange_tile(Dev d, int sp) {
   // two accumulator sets (even and odd candidates) halve the dependent
   // chain of compensated additions
   typename MS::Acc dA{}, dB{}, dA1{}, dB1{};
-  for (long long c0 = lo; c0 < hi; c0 += kTileChunk) {
-    const int nc = (int)min((long long)kTileChunk, hi - c0);
+  for (long long c0 = t.lo; c0 < t.hi; c0 += kTileChunk) {
+    const int nc = (int)min((long long)kTileChunk, t.hi - c0);
     for (int i = threadIdx.x; i < nc; i += kThreads) {
-      s_x[i] = Xs[c0 + i];
-      s_r[i] = load_rinv<MIX>(d, c0 + i);
+      s_x[i] = (unsigned int)Xs[c0 + i];
+      s_r[i] = sym ? load_rinv<MIX>(d, c0 + i) : T(0);
       s_a[i] = MS::load(MA, c0 + i);
       s_b[i] = MS::load(MB, c0 + i);
     }
     __syncthreads();
-    if (wact) {
-      const int j0 = (int)(max(wlo, c0) - c0), j1 = (int)(min(whi, c0 + nc) - c0);
-      const int self = (int)(p - c0);
-      auto pair = [&](int j, typename MS::Acc& a, typename MS::Acc& b) {
-        const long long D = s_x[j] - x;
-        if (j != self && within1(D, d.S)) {
-          const T P = normalised<T>(d.norm, W::near(d, D), ip, s_r[j]);
-          MS::acc(a, P, MS::diff(s_a[j], A));
-          MS::acc(b, P, MS::diff(s_b[j], B));
-        }
-      };
-      int j = j0;
-      for (; j + 1 < j1; j += 2) {
-        pair(j, dA, dB);
-        pair(j + 1, dA1, dB1);
-      }
-      if (j < j1) pair(j, dA, dB);
+    const int j0 = (int)(max(t.wlo, c0) - c0), j1 = (int)(min(t.whi, c0 + nc) - c0);
+    const int ql = (int)(jl - c0);
+    const unsigned int qn = (unsigned int)(jr - jl);
+    auto pair = [&](int j, typename MS::Acc& a, typename MS::Acc& b) {
+      const T w = W::near(d, (int)(s_x[j] - x32));
+      const T P2 = (unsigned int)(j - ql) < qn ? w * (ip + s_r[j]) : T(0);
+      MS::acc(a, P2, MS::diff(s_a[j], A));
+      MS::acc(b, P2, MS::diff(s_b[j], B));
+    };
+    int j = j0;
+    for (; j + 1 < j1; j += 2) {
+      pair(j, dA, dB);
+      pair(j + 1, dA1, dB1);
     }
+    if (j < j1) pair(j, dA, dB);
     __syncthreads();
   }
   dA = acc_merge(dA, dA1);
   dB = acc_merge(dB, dB1);
+  if (sym) {
+    dA = acc_half(dA);
+    dB = acc_half(dB);
+  }
   if (valid) {
     MS::update(A, B, dA, dB, TR ? 0 : d.react);
     MS::store(d.M[mc] + sq.oa, p, A);
