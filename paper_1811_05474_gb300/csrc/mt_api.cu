@@ -165,8 +165,6 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
     return fail(MT_ERR_INVALID, "stored_p needs a single 1-d system with MT_SEARCH_CELL");
   const bool periodic = p.walls == MT_WALLS_PERIODIC;
   if (periodic && b) return fail(MT_ERR_INVALID, "batches use reflecting walls");
-  if (periodic && p.dim == 2 && p.search == MT_SEARCH_CELL)
-    return fail(MT_ERR_INVALID, "periodic walls in 2-d need MT_SEARCH_BRUTE or MT_SEARCH_FULL");
   if (p.frac_bits == 0) p.frac_bits = default_frac_bits(p);
   const int k = p.frac_bits;
   if (k < 1 || k > 62) return fail(MT_ERR_INVALID, "frac_bits must be in [1, 62] (got %d)", k);

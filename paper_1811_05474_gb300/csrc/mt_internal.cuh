@@ -186,6 +186,56 @@ __device__ __forceinline__ long long cell_of(const Dev& d, long long x, long lon
   return ky * d.ncx + kx;
 }
 
+// 2-d cell list (cells wider than Smax): the cells of one axis that can hold
+// a neighbour of coordinate v.  Reflecting walls: the cell of v and the two
+// beside it.  Periodic walls: the cells covering [v - Smax, v + Smax], in two
+// pieces when the interval wraps (merged into every cell when they meet, so
+// no cell is visited twice).  [a0, a1] and [b0, b1] (b0 > b1: no second).
+struct CellSpan {
+  long long a0, a1, b0, b1;
+};
+__device__ __forceinline__ CellSpan axis_cells(const Dev& d, long long v, long long Lq,
+                                               long long nc) {
+  auto cell = [&](long long u) {
+    const long long k = u >> d.cshift;
+    return k < 0 ? 0 : (k >= nc ? nc - 1 : k);
+  };
+  CellSpan s{0, -1, 0, -1};
+  if (!d.periodic) {
+    const long long k = cell(v);
+    s.a0 = k > 0 ? k - 1 : 0;
+    s.a1 = k + 1 < nc ? k + 1 : nc - 1;
+    return s;
+  }
+  const long long lo = v - d.S, hi = v + d.S;
+  if (lo < 0) {
+    s = {0, cell(hi), cell(lo + Lq), nc - 1};
+  } else if (hi >= Lq) {
+    s = {0, cell(hi - Lq), cell(lo), nc - 1};
+  } else {
+    s.a0 = cell(lo);
+    s.a1 = cell(hi);
+  }
+  if (s.b0 <= s.b1 && s.a1 >= s.b0 - 1) s = {0, nc - 1, 0, -1};
+  return s;
+}
+
+// Calls f(q0, q1) for each run [q0, q1) of sorted slots (one per cell row
+// and x piece) that can hold a neighbour of (x, y).
+template <class F>
+__device__ __forceinline__ void cells2_visit(const Dev& d, long long x, long long y, F&& f) {
+  const CellSpan cx = axis_cells(d, x, d.Lq[0], d.ncx);
+  const CellSpan cy = axis_cells(d, y, d.Lq[1], d.ncy);
+  for (int iy = 0; iy < 2; ++iy) {
+    const long long r0 = iy ? cy.b0 : cy.a0, r1 = iy ? cy.b1 : cy.a1;
+    for (long long row = r0; row <= r1; ++row)
+      for (int ix = 0; ix < 2; ++ix) {
+        const long long k0 = ix ? cx.b0 : cx.a0, k1 = ix ? cx.b1 : cx.a1;
+        if (k0 <= k1) f((int)d.start[row * d.ncx + k0], (int)d.start[row * d.ncx + k1 + 1]);
+      }
+  }
+}
+
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): 10 rounds of the
 // 2x(32x32->64) multiply / xor network with Weyl key schedule.
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned int k0, unsigned int k1) {

@@ -204,18 +204,17 @@ __global__ void k_pairs_cell2(Dev d, int* pi, int* pj, long long cap) {
   const long long* X = d.X[xc];
   const int* id = d.id[xc];
   const long long x = X[p], y = X[d.n + p];
-  long long kx = x >> d.cshift, ky = y >> d.cshift;
-  kx = kx >= d.ncx ? d.ncx - 1 : kx;
-  ky = ky >= d.ncy ? d.ncy - 1 : ky;
-  const long long kx0 = kx > 0 ? kx - 1 : 0;
-  const long long kx1 = kx + 1 < d.ncx ? kx + 1 : d.ncx - 1;
-  for (long long row = ky - 1; row <= ky + 1; ++row) {
-    if (row < 0 || row >= d.ncy) continue;
-    const int q0 = d.start[row * d.ncx + kx0];
-    const int q1 = d.start[row * d.ncx + kx1 + 1];
-    for (int q = q0; q < q1; ++q)
-      if (q > p && in_range2_io(X[q] - x, X[d.n + q] - y, d.S)) emit(d, id[p], id[q], pi, pj, cap);
-  }
+  cells2_visit(d, x, y, [&](int q0, int q1) {
+    for (int q = q0; q < q1; ++q) {
+      if (q <= p) continue;
+      long long dx = X[q] - x, dy = X[d.n + q] - y;
+      if (d.periodic) {
+        dx = min_image(dx, d.Lq[0]);
+        dy = min_image(dy, d.Lq[1]);
+      }
+      if (in_range2_io(dx, dy, d.S)) emit(d, id[p], id[q], pi, pj, cap);
+    }
+  });
 }
 
 __global__ void k_pairs_brute(Dev d, int* pi, int* pj, long long cap) {

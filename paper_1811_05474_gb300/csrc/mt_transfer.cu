@@ -614,17 +614,13 @@ __device__ __forceinline__ void cell2_loop(const Dev& d, const long long* Xs, lo
   using W = Weight<MIX, 2>;
   using T = typename W::T;
   using MS = Mass<MIX>;
-  long long kx = x >> d.cshift, ky = y >> d.cshift;
-  kx = kx >= d.ncx ? d.ncx - 1 : kx;
-  ky = ky >= d.ncy ? d.ncy - 1 : ky;
-  const long long kx0 = kx > 0 ? kx - 1 : 0;
-  const long long kx1 = kx + 1 < d.ncx ? kx + 1 : d.ncx - 1;
-  for (long long row = ky - 1; row <= ky + 1; ++row) {
-    if (row < 0 || row >= d.ncy) continue;
-    const int q0 = d.start[row * d.ncx + kx0];
-    const int q1 = d.start[row * d.ncx + kx1 + 1];
+  cells2_visit(d, x, y, [&](int q0, int q1) {
     for (int q = q0; q < q1; ++q) {
-      const long long dx = Xs[q] - x, dy = Xs[d.n + q] - y;
+      long long dx = Xs[q] - x, dy = Xs[d.n + q] - y;
+      if (d.periodic) {
+        dx = min_image(dx, d.Lq[0]);
+        dy = min_image(dy, d.Lq[1]);
+      }
       if (!in_range2(dx, dy, d.S)) continue;
       const T w = W::eval(d, dx, dy);
       if (!EXCHANGE) {
@@ -635,7 +631,7 @@ __device__ __forceinline__ void cell2_loop(const Dev& d, const long long* Xs, lo
         MS::acc(dB, P, MS::diff(MS::load(MB, q), B));
       }
     }
-  }
+  });
 }
 
 template <bool MIX>

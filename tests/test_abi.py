@@ -157,7 +157,8 @@ def test_seg_target_is_validated_and_kept():
 def test_periodic_walls_rules():
     r = mt.mt_resolve(mt.mt_params_init(n=1000, L=(1000.0,), walls=mt.MT_WALLS_PERIODIC))
     assert r.walls == mt.MT_WALLS_PERIODIC and r.seg_target == 0  # general pipeline
-    for bad in (dict(dim=2, n=100, L=(10.0, 10.0)),                 # 2-d cell list
+    mt.mt_resolve(mt.mt_params_init(dim=2, n=100, L=(10.0, 10.0), walls=mt.MT_WALLS_PERIODIC))
+    for bad in (dict(dim=2, n=100, L=(10.0, 3.0)),                  # cutoff >= L[1] / 2
                 dict(n=10, L=(3.0,)),                                # cutoff >= L / 2
                 dict(n=10, L=(100.0,), search=mt.MT_SEARCH_BRUTE, cutoff=60.0),
                 dict(n=10, L=(100.0,), walls=7)):

@@ -1,6 +1,7 @@
 """Periodic walls on the GPU against the oracle: the wrapping move, minimum-
-image pairs and weights, for the 1-d cell list (general pipeline) and the
-all-pairs forms in 1-d and 2-d."""
+image pairs and weights, for the cell lists (1-d general pipeline; 2-d with
+wrapped cell neighbourhoods, including partial last cells and grids of two
+cells a side) and the all-pairs forms in 1-d and 2-d."""
 import numpy as np
 import pytest
 
@@ -33,6 +34,9 @@ CASES = [
     (500, 300.0, 1, mt.MT_SEARCH_BRUTE, 6),
     (500, 300.0, 1, mt.MT_SEARCH_FULL, 3),
     (400, (30.0, 20.0), 2, mt.MT_SEARCH_BRUTE, 6),
+    (3000, (120.0, 90.0), 2, mt.MT_SEARCH_CELL, 8),
+    (500, (9.0, 7.1), 2, mt.MT_SEARCH_CELL, 6),    # a few cells a side, partial last cells
+    (300, (4.0, 3.9), 2, mt.MT_SEARCH_CELL, 4),    # two cells a side: the wrapped pieces meet
     (300, (20.0, 12.0), 2, mt.MT_SEARCH_FULL, 3),
 ]
 
