@@ -299,6 +299,7 @@ __device__ __forceinline__ bool within1(long long dx, long long S) {
 // particle itself adds nu_pp = 1 to r_p and an exact zero flux.
 
 constexpr int kTileChunk = 512;
+constexpr int kTileGroup = 16;  // row-sum terms added plainly before compensation
 
 // Exact neighbour slots [jl, jr) of the particle at x: every sorted slot q
 // with |X_q - x| <= Smax.  The bounds lie in the cells of x -/+ Smax.
@@ -356,9 +357,11 @@ __global__ void __launch_bounds__(kThreads) k_rowsum_tile(Dev d) {
   if (valid) exact_range(d, Xs, x, jl, jr);
   const TileRanges t = tile_ranges(jl, jr, b0, b1, s_lohi);
   const unsigned int x32 = (unsigned int)x;
-  // two independent sums (even and odd candidates) halve the dependent
-  // chain of compensated additions
-  RowSum<MIX> r0(T(0)), r1(T(0));
+  // The weights are summed plainly in groups of kTileGroup candidates (two
+  // chains) and each group's sum enters a compensated sum: the group sums'
+  // rounding (at most kTileGroup terms of at most 1) stays near binary32's
+  // precision relative to r_p, at a plain addition per weight.
+  RowSum<MIX> r(T(0));
   for (long long c0 = t.lo; c0 < t.hi; c0 += kTileChunk) {
     const int nc = (int)min((long long)kTileChunk, t.hi - c0);
     for (int i = threadIdx.x; i < nc; i += kThreads) s_x[i] = (unsigned int)Xs[c0 + i];
@@ -371,17 +374,22 @@ __global__ void __launch_bounds__(kThreads) k_rowsum_tile(Dev d) {
       return (unsigned int)(j - ql) < qn ? w : T(0);
     };
     int j = j0;
-#pragma unroll 2
-    for (; j + 1 < j1; j += 2) {
-      r0.add(term(j));
-      r1.add(term(j + 1));
+    for (; j + kTileGroup <= j1; j += kTileGroup) {
+      T g0 = T(0), g1 = T(0);
+#pragma unroll
+      for (int k = 0; k < kTileGroup; k += 2) {
+        g0 += term(j + k);
+        g1 += term(j + k + 1);
+      }
+      r.add(g0 + g1);
     }
-    if (j < j1) r0.add(term(j));
+    T g = T(0);
+    for (; j < j1; ++j) g += term(j);
+    r.add(g);
     __syncthreads();
   }
   if (!valid) return;
-  r0.add(r1.value());
-  store_rinv<MIX>(d, p, r0.value());
+  store_rinv<MIX>(d, p, r.value());
   const int s = d.src[p];
   d.id[xc ^ 1][p] = d.id[xc][s];
   gather_masses(d, mc, p, s);
