@@ -61,11 +61,20 @@ ALGO_BYTES = {
 CSRC = os.path.join(ROOT, "paper_1811_05474_gb300", "csrc")
 
 
-def source_hash() -> str:
+# The translation unit of the one-kernel step (its kernels' code).
+FUSED_SOURCES = ("paper_1811_05474_gb300/csrc/mt_fused.cu", "paper_1811_05474_gb300/csrc/mt_pair.cuh",
+                 "paper_1811_05474_gb300/csrc/mt_internal.cuh", "include/mt.h")
+
+
+def source_hash(files=None) -> str:
+    """Hash of the given sources (paths relative to the repository), or of
+    every file under csrc/."""
+    if files is None:
+        files = [os.path.relpath(os.path.join(CSRC, f), ROOT) for f in sorted(os.listdir(CSRC))]
     h = hashlib.sha256()
-    for f in sorted(os.listdir(CSRC)):
-        with open(os.path.join(CSRC, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(os.path.basename(f).encode() + fh.read())
     return h.hexdigest()[:16]
 
 
@@ -798,17 +807,17 @@ def load_peaks():
 
 def load_traffic(kernel: str):
     """dram bytes per launch from a committed ncu summary, if it was taken on
-    the current sources."""
+    the kernel's current sources (the hash of its translation unit)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             t = json.load(f)
-    except (OSError, ValueError):
+        k = t["kernels"][kernel]
+        if k["source_hash"] != source_hash(k["sources"]):
+            return None
+        return float(k["bytes"])
+    except (OSError, ValueError, KeyError, TypeError):
         return None
-    if t.get("source_hash") != source_hash():
-        return None
-    v = t.get("kernels", {}).get(kernel)
-    return float(v) if v is not None else None
 
 
 def run_ncu(args):
