@@ -805,6 +805,32 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def load_issue(kernel: str, launch_ms: float, sm_mhz: float | None):
+    """The kernel's instruction-issue rate: warp instructions per launch from
+    the committed ncu capture (if taken on the kernel's current sources) over
+    the event-timed launch duration, against the issue peak of one warp
+    instruction per clock per SM sub-partition (4 per SM)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            k = json.load(f)["kernels"][kernel]
+        if k["source_hash"] != source_hash(k["sources"]):
+            return None
+        inst = float(k["warp_instructions"])
+    except (OSError, ValueError, KeyError, TypeError):
+        return None
+    import torch
+
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = sm_mhz or 2070.0
+    achieved = inst / (launch_ms * 1e-3)
+    peak = nsm * 4 * mhz * 1e6
+    return {"bound": "issue", "kernel": kernel, "achieved": achieved, "peak": peak,
+            "unit": "warp instructions/s", "frac": achieved / peak,
+            "warp_instructions_per_launch": inst,
+            "peak_kind": f"derived: {nsm} SMs x 4 issue slots/clk x {mhz:.0f} MHz"}
+
+
 def load_traffic(kernel: str):
     """dram bytes per launch from a committed ncu summary, if it was taken on
     the kernel's current sources (the hash of its translation unit)."""
@@ -971,6 +997,7 @@ def main():
                      "traffic": load_traffic(dom["name"])},
         "path_roofline": {"bound": "hbm", "achieved": path_achieved, "peak": peak, "unit": "GB/s",
                           "frac": path_achieved / peak, "algo_bytes_per_step": step_bytes},
+        "issue_roofline": load_issue(dom["name"], dom["ms"], clocks.get("sm_mhz") if clocks else None),
         "kernels": kernels,
         "gpu_launches": int(round(K * main_run["launches_per_step"])),
         "clocks": clocks,
