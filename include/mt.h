@@ -296,6 +296,23 @@ mt_status mt_upload(mt_handle* h, const double* x, const double* A,
 mt_status mt_set_species(mt_handle* h, int32_t s, const double* M, int32_t mem);
 mt_status mt_read_species(mt_handle* h, int32_t s, double* M, int32_t mem);
 
+/* Checkpoint and resume.  mt_save writes the handle's whole device state
+ * (positions, ids, masses, step counter, observables, the step's internal
+ * tables) and its resolved parameters to the file at path; it waits for the
+ * stream.  mt_checkpoint_params reads the parameters back from such a file,
+ * to create a handle for it (same parameters: mt_create, or mt_batch_create
+ * with the same batch).  mt_load restores the state into such a handle; the
+ * handle then continues exactly as the saved one would have (the
+ * counter-based random walk is keyed by the step counter, which the state
+ * holds), bit for bit on the same device kind.  The handle's own noise
+ * source (mt_set_noise) replaces the saved one.  Errors: MT_ERR_STATE
+ * (mt_save before mt_upload); MT_ERR_INVALID (unreadable or foreign file, or
+ * a handle with other resolved parameters or realisations; the device state
+ * is then unchanged). */
+mt_status mt_save(mt_handle* h, const char* path);
+mt_status mt_checkpoint_params(const char* path, mt_params* p);
+mt_status mt_load(mt_handle* h, const char* path);
+
 /* Random-walk noise for the following steps: a device pointer to dim*n
  * floats, axis-major and indexed by the caller's particle order, read by
  * every mt_step until it is replaced; NULL returns to the built-in

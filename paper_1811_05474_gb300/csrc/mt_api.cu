@@ -1046,6 +1046,119 @@ const char* mt_profile_name(const mt_handle* h, int32_t idx) {
   return "";
 }
 
+// ------------------------------------------------------------ checkpoint --
+// File: kCkptMagic, format version, sizeof(mt_params), the resolved
+// parameters, the host step count, the realisation table's size and bytes,
+// the workspace's size and bytes (little-endian, as on both host
+// architectures).  The workspace holds the whole device state (positions,
+// ids, masses, cell starts, segment tables, the step counter, the
+// observables ring and the tiers' scheduling flags), so a handle that takes
+// it back continues exactly as the saved one would have.  The only pointer
+// in it, the noise source, is replaced by the loading handle's own.
+
+namespace {
+constexpr char kCkptMagic[8] = {'M', 'T', 'C', 'K', 'P', 'T', '0', '1'};
+constexpr uint32_t kCkptVersion = 1;
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version;
+  uint32_t params_bytes;
+  mt_params p;
+  int64_t steps;
+  uint64_t rt_bytes;
+  uint64_t ws_bytes;
+};
+
+bool same_params(const mt_params& a, const mt_params& b) {
+  return std::memcmp(&a, &b, sizeof(mt_params)) == 0;
+}
+
+mt_status read_header(FILE* f, CkptHeader* hd) {
+  if (std::fread(hd, sizeof(CkptHeader), 1, f) != 1)
+    return fail(MT_ERR_INVALID, "checkpoint: short header");
+  if (std::memcmp(hd->magic, kCkptMagic, sizeof kCkptMagic) != 0)
+    return fail(MT_ERR_INVALID, "checkpoint: not a checkpoint file");
+  if (hd->version != kCkptVersion || hd->params_bytes != sizeof(mt_params))
+    return fail(MT_ERR_INVALID, "checkpoint: format version %u not supported", hd->version);
+  return MT_OK;
+}
+}  // namespace
+
+mt_status mt_save(mt_handle* h, const char* path) {
+  if (!h || !path) return fail(MT_ERR_INVALID, "mt_save: NULL argument");
+  if (!h->uploaded) return fail(MT_ERR_STATE, "mt_save before mt_upload");
+  mt_status s = check_device(h);  // waits for the stream
+  if (s != MT_OK) return s;
+  if (h->side) CU(cudaStreamSynchronize(h->side));
+  std::vector<char> ws(h->D.total);
+  if (!ws.empty()) CU(cudaMemcpy(ws.data(), h->ws, ws.size(), cudaMemcpyDeviceToHost));
+  CkptHeader hd;
+  std::memset(&hd, 0, sizeof hd);
+  std::memcpy(hd.magic, kCkptMagic, sizeof kCkptMagic);
+  hd.version = kCkptVersion;
+  hd.params_bytes = sizeof(mt_params);
+  hd.p = h->D.p;
+  hd.steps = h->steps;
+  hd.rt_bytes = h->D.rt.size() * sizeof(Real);
+  hd.ws_bytes = ws.size();
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(MT_ERR_INVALID, "mt_save: cannot open %s", path);
+  bool ok = std::fwrite(&hd, sizeof hd, 1, f) == 1;
+  if (ok && hd.rt_bytes) ok = std::fwrite(h->D.rt.data(), hd.rt_bytes, 1, f) == 1;
+  if (ok && hd.ws_bytes) ok = std::fwrite(ws.data(), hd.ws_bytes, 1, f) == 1;
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return fail(MT_ERR_INVALID, "mt_save: write to %s failed", path);
+  return MT_OK;
+}
+
+mt_status mt_checkpoint_params(const char* path, mt_params* p) {
+  if (!path || !p) return fail(MT_ERR_INVALID, "mt_checkpoint_params: NULL argument");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(MT_ERR_INVALID, "checkpoint: cannot open %s", path);
+  CkptHeader hd;
+  const mt_status s = read_header(f, &hd);
+  std::fclose(f);
+  if (s != MT_OK) return s;
+  *p = hd.p;
+  return MT_OK;
+}
+
+mt_status mt_load(mt_handle* h, const char* path) {
+  if (!h || !path) return fail(MT_ERR_INVALID, "mt_load: NULL argument");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(MT_ERR_INVALID, "checkpoint: cannot open %s", path);
+  CkptHeader hd;
+  mt_status s = read_header(f, &hd);
+  std::vector<char> rt, ws;
+  if (s == MT_OK) {
+    if (!same_params(hd.p, h->D.p) || hd.ws_bytes != h->D.total ||
+        hd.rt_bytes != h->D.rt.size() * sizeof(Real))
+      s = fail(MT_ERR_INVALID, "mt_load: the checkpoint was saved by a handle with other parameters");
+  }
+  if (s == MT_OK) {
+    rt.resize(hd.rt_bytes);
+    ws.resize(hd.ws_bytes);
+    if ((hd.rt_bytes && std::fread(rt.data(), hd.rt_bytes, 1, f) != 1) ||
+        (hd.ws_bytes && std::fread(ws.data(), hd.ws_bytes, 1, f) != 1))
+      s = fail(MT_ERR_INVALID, "mt_load: truncated checkpoint");
+    else if (hd.rt_bytes && std::memcmp(rt.data(), h->D.rt.data(), hd.rt_bytes) != 0)
+      s = fail(MT_ERR_INVALID, "mt_load: the checkpoint holds other realisations");
+  }
+  std::fclose(f);
+  if (s != MT_OK) return s;
+  CU(cudaStreamSynchronize(h->stream));
+  if (h->side) CU(cudaStreamSynchronize(h->side));
+  if (!ws.empty()) CU(cudaMemcpy(h->ws, ws.data(), ws.size(), cudaMemcpyHostToDevice));
+  h->steps = hd.steps;
+  h->uploaded = true;
+  // the saved noise pointer belongs to the saving process: use this handle's
+  CU(cudaMemcpyAsync(&h->dev.ctrl->noise, &h->noise, sizeof(h->noise), cudaMemcpyHostToDevice,
+                     h->stream));
+  if (h->D.p.n > 0) CU(launch_noise_bound(h->dev, h->noise, h->stream));
+  return check_device(h);
+}
+
 const char* mt_last_error(void) { return g_err.c_str(); }
 
 void mt_destroy(mt_handle* h) {

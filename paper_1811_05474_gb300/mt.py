@@ -146,6 +146,9 @@ def lib(path: Path | None = None):
         "mt_sync": [H],
         "mt_read_masses": [H, _vp, _vp, i32],
         "mt_set_species": [H, i32, _vp, i32],
+        "mt_save": [H, ctypes.c_char_p],
+        "mt_checkpoint_params": [ctypes.c_char_p, P],
+        "mt_load": [H, ctypes.c_char_p],
         "mt_read_species": [H, i32, _vp, i32],
         "mt_read_positions": [H, _vp, i32],
         "mt_read_ticks": [H, _vp, i32],
@@ -313,6 +316,20 @@ def mt_read_masses(h, A_ptr, B_ptr, mem: int) -> None:
 
 def mt_set_species(h, s: int, M_ptr, mem: int) -> None:
     check(lib().mt_set_species(h, s, M_ptr, mem))
+
+
+def mt_save(h, path: str) -> None:
+    check(lib().mt_save(h, str(path).encode()))
+
+
+def mt_checkpoint_params(path: str) -> mt_params:
+    p = mt_params()
+    check(lib().mt_checkpoint_params(str(path).encode(), ctypes.byref(p)))
+    return p
+
+
+def mt_load(h, path: str) -> None:
+    check(lib().mt_load(h, str(path).encode()))
 
 
 def mt_read_species(h, s: int, M_ptr, mem: int) -> None:
@@ -500,6 +517,12 @@ class Simulation:
         M = np.empty(self.n, dtype=np.float64)
         mt_read_species(self.h, s, _ptr(M), MT_MEM_HOST)
         return M
+
+    def save(self, path) -> None:
+        mt_save(self.h, path)
+
+    def load(self, path) -> None:
+        mt_load(self.h, path)
 
     def positions(self) -> np.ndarray:
         x = np.empty((self.dim, self.n), dtype=np.float64)

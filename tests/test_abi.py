@@ -211,3 +211,14 @@ def test_stored_p_rules():
         assert e.value.status == mt.MT_ERR_INVALID
     with pytest.raises(mt.MtError):
         mt.mt_batch_resolve(_batch_params(stored_p=1), mt.make_batch([10], [10.0]))
+
+
+def test_checkpoint_params_rejects_foreign_files(tmp_path):
+    with pytest.raises(mt.MtError) as e:
+        mt.mt_checkpoint_params(tmp_path / "missing.ckpt")
+    assert e.value.status == mt.MT_ERR_INVALID
+    junk = tmp_path / "junk.ckpt"
+    junk.write_bytes(b"not a checkpoint" * 20)
+    with pytest.raises(mt.MtError) as e:
+        mt.mt_checkpoint_params(junk)
+    assert e.value.status == mt.MT_ERR_INVALID
