@@ -31,6 +31,8 @@ def profile_names(sim):
     (20000, 100.0, 2, 3),     # 200 per unit length: ~270 neighbours a side
     (12000, 6.0, 2, 2),       # 2000 per unit length: ~2700 a side, many chunks
     (9000, 45.0, 3, 3),       # three species
+    (77, 0.4, 2, 3),          # one partial CTA, every particle within reach of every other
+    (1000, 3.3, 2, 3),        # four CTAs, a ragged last one
 ])
 @pytest.mark.parametrize("precision", [mt.MT_FP64, mt.MT_MIXED])
 def test_dense_tiles_match_oracle(n, L, S, steps, precision):

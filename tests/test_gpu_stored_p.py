@@ -36,6 +36,8 @@ CASES = [  # n, L, D_mt, dt, stored_p, walls, S, steps
     (8000, 6000.0, 0.1, 1.0, 1, mt.MT_WALLS_PERIODIC, 2, 8),
     (8000, 6000.0, 0.1, 1.0, 3, mt.MT_WALLS_PERIODIC, 3, 6),
     (5000, 40.0, 0.5, 0.1, 1, mt.MT_WALLS_REFLECT, 5, 3),
+    (77, 0.4, 0.5, 0.1, 1, mt.MT_WALLS_REFLECT, 2, 3),        # all within reach, band = n
+    (1000, 700.0, 0.1, 1.0, 1, mt.MT_WALLS_PERIODIC, 2, 4),   # ragged last warp tile
 ]
 
 
