@@ -153,13 +153,18 @@ __device__ __forceinline__ long long reflect(long long y, long long Lq) {
   return y < 0 ? 0 : (y > Lq ? Lq : y);
 }
 
-// Every species of the particle in slot s of buffer mc moves to slot p of
-// the other buffer.
+// A and B of the particle in slot s of buffer mc move to slot p of the
+// other buffer (species 2 and up: gather_species, in a pass of their own so
+// the transfer kernels keep their registers).
 __device__ __forceinline__ void gather_masses(const Dev& d, int mc, long long p, long long s) {
   const unsigned long long* in = d.M[mc];
   unsigned long long* out = d.M[mc ^ 1];
   out[p] = in[s];
   out[d.n + p] = in[d.n + s];
+}
+__device__ __forceinline__ void gather_species(const Dev& d, int mc, long long p, long long s) {
+  const unsigned long long* in = d.M[mc];
+  unsigned long long* out = d.M[mc ^ 1];
   for (int k = 2; k < d.nspec; ++k) out[k * d.n + p] = in[k * d.n + s];
 }
 

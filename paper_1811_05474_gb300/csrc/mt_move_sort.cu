@@ -312,6 +312,7 @@ __global__ void __launch_bounds__(kThreads) k_permute(Dev d) {
   const int s = d.src[p];
   d.id[xc ^ 1][p] = d.id[xc][s];
   gather_masses(d, mc, p, s);
+  gather_species(d, mc, p, s);
 }
 
 __global__ void k_flip(Dev d, int fx, int fm) {

@@ -609,40 +609,70 @@ __global__ void __launch_bounds__(kThreads) k_band_exchange(Dev d, int sp) {
 
 // =============================================================== 2-d cells ==
 
-template <bool MIX, bool EXCHANGE>
-__device__ __forceinline__ void cell2_loop(const Dev& d, const long long* Xs, long long p,
-                                           long long x, long long y,
-                                           typename Weight<MIX, 2>::T& r,
-                                           const unsigned long long* MA,
-                                           const unsigned long long* MB,
-                                           typename Weight<MIX, 2>::T ip,
-                                           typename Mass<MIX>::V A, typename Mass<MIX>::V B,
-                                           typename Mass<MIX>::Acc& dA,
-                                           typename Mass<MIX>::Acc& dB) {
+// One run [q0, q1) of candidate slots for the particle in slot p at (x, y).
+template <bool MIX, bool EXCHANGE, bool PER>
+__device__ __forceinline__ void cell2_run(const Dev& d, const long long* Xs, long long p,
+                                          long long x, long long y, int q0, int q1,
+                                          typename Weight<MIX, 2>::T& r,
+                                          const unsigned long long* M,
+                                          typename Weight<MIX, 2>::T ip,
+                                          typename Mass<MIX>::V A, typename Mass<MIX>::V B,
+                                          typename Mass<MIX>::Acc& dA,
+                                          typename Mass<MIX>::Acc& dB, long long ob) {
   using W = Weight<MIX, 2>;
   using T = typename W::T;
   using MS = Mass<MIX>;
-  cells2_visit(d, x, y, [&](int q0, int q1) {
-    for (int q = q0; q < q1; ++q) {
-      long long dx = Xs[q] - x, dy = Xs[d.n + q] - y;
-      if (d.periodic) {
-        dx = min_image(dx, d.Lq[0]);
-        dy = min_image(dy, d.Lq[1]);
-      }
-      if (!in_range2(dx, dy, d.S)) continue;
-      const T w = W::eval(d, dx, dy);
-      if (!EXCHANGE) {
-        r += w;
-      } else if (q != p) {
-        const T P = normalised<T>(d.norm, w, ip, load_rinv<MIX>(d, q));
-        MS::acc(dA, P, MS::diff(MS::load(MA, q), A));
-        MS::acc(dB, P, MS::diff(MS::load(MB, q), B));
-      }
+  for (int q = q0; q < q1; ++q) {
+    long long dx = Xs[q] - x, dy = Xs[d.n + q] - y;
+    if (PER) {
+      dx = min_image(dx, d.Lq[0]);
+      dy = min_image(dy, d.Lq[1]);
     }
-  });
+    if (!in_range2(dx, dy, d.S)) continue;
+    const T w = W::eval(d, dx, dy);
+    if (!EXCHANGE) {
+      r += w;
+    } else if (q != p) {
+      const T P = normalised<T>(d.norm, w, ip, load_rinv<MIX>(d, q));
+      MS::acc(dA, P, MS::diff(MS::load(M, q), A));
+      MS::acc(dB, P, MS::diff(MS::load(M, ob + q), B));
+    }
+  }
 }
 
-template <bool MIX>
+// All candidates of the particle in slot p: the 3 x 3 block of cells around
+// its cell (reflecting walls), or the wrapped cell spans (periodic).  M:
+// the first species' masses; the second's are ob words further.
+template <bool MIX, bool EXCHANGE, bool PER>
+__device__ __forceinline__ void cell2_loop(const Dev& d, const long long* Xs, long long p,
+                                           long long x, long long y,
+                                           typename Weight<MIX, 2>::T& r,
+                                           const unsigned long long* M,
+                                           typename Weight<MIX, 2>::T ip,
+                                           typename Mass<MIX>::V A, typename Mass<MIX>::V B,
+                                           typename Mass<MIX>::Acc& dA,
+                                           typename Mass<MIX>::Acc& dB, long long ob) {
+  if (PER) {
+    cells2_visit(d, x, y, [&](int q0, int q1) {
+      cell2_run<MIX, EXCHANGE, true>(d, Xs, p, x, y, q0, q1, r, M, ip, A, B, dA, dB, ob);
+    });
+    return;
+  }
+  long long kx = x >> d.cshift, ky = y >> d.cshift;
+  kx = kx >= d.ncx ? d.ncx - 1 : kx;
+  ky = ky >= d.ncy ? d.ncy - 1 : ky;
+  const long long kx0 = kx > 0 ? kx - 1 : 0;
+  const long long kx1 = kx + 1 < d.ncx ? kx + 1 : d.ncx - 1;
+  for (long long row = ky - 1; row <= ky + 1; ++row) {
+    if (row < 0 || row >= d.ncy) continue;
+    cell2_run<MIX, EXCHANGE, false>(d, Xs, p, x, y, d.start[row * d.ncx + kx0],
+                                    d.start[row * d.ncx + kx1 + 1], r, M, ip, A, B, dA, dB, ob);
+  }
+}
+
+// PER: periodic walls (wrapped cell spans, minimum-image separations), a
+// separate instantiation so the reflecting kernels keep their registers.
+template <bool MIX, bool PER>
 __global__ void __launch_bounds__(kThreads) k_rowsum_cell2(Dev d) {
   using T = typename Weight<MIX, 2>::T;
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
@@ -652,15 +682,15 @@ __global__ void __launch_bounds__(kThreads) k_rowsum_cell2(Dev d) {
   T r = T(0);
   typename Mass<MIX>::Acc dummy{};
   typename Mass<MIX>::V z{};
-  cell2_loop<MIX, false>(d, Xs, p, Xs[p], Xs[d.n + p], r, nullptr, nullptr, T(0), z, z, dummy,
-                         dummy);
+  cell2_loop<MIX, false, PER>(d, Xs, p, Xs[p], Xs[d.n + p], r, nullptr, T(0), z, z, dummy,
+                              dummy, 0);
   store_rinv<MIX>(d, p, r);
   const int s = d.src[p];
   d.id[xc ^ 1][p] = d.id[xc][s];
   gather_masses(d, mc, p, s);
 }
 
-template <bool MIX, bool TR>
+template <bool MIX, bool TR, bool PER>
 __global__ void __launch_bounds__(kThreads) k_exchange_cell2(Dev d, int sp) {
   using T = typename Weight<MIX, 2>::T;
   using MS = Mass<MIX>;
@@ -678,8 +708,8 @@ __global__ void __launch_bounds__(kThreads) k_exchange_cell2(Dev d, int sp) {
     B = MS::load(MB, p);
     T r = T(0);
     typename MS::Acc dA{}, dB{};
-    cell2_loop<MIX, true>(d, Xs, p, Xs[p], Xs[d.n + p], r, MA, MB, load_rinv<MIX>(d, p), A, B,
-                          dA, dB);
+    cell2_loop<MIX, true, PER>(d, Xs, p, Xs[p], Xs[d.n + p], r, MA, load_rinv<MIX>(d, p), A, B,
+                               dA, dB, sq.ob - sq.oa);
     MS::update(A, B, dA, dB, TR ? 0 : d.react);
     MS::store(d.M[mc] + sq.oa, p, A);
     if (sq.store_b) MS::store(d.M[mc] + sq.ob, p, B);
@@ -796,7 +826,30 @@ __global__ void __launch_bounds__(kThreads) k_exchange_brute(Dev d, int sp) {
   if (!TR) finish_step<MIX>(d, A, B, valid, 0, 1);
 }
 
+// Species 2 and up into the sorted slots (the row-sum pass moved A and B).
+__global__ void __launch_bounds__(kThreads) k_gather_species(Dev d) {
+  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (p >= d.n) return;
+  gather_species(d, d.ctrl->mcur, p, d.src[p]);
+}
+
 // --------------------------------------------------------------- launch --
+
+template <bool MIX, bool PER>
+static void cell2_passes(const Dev& d, unsigned int g, cudaStream_t s, Marker& mk) {
+  mk("rowsum_cell2", s);
+  k_rowsum_cell2<MIX, PER><<<g, kThreads, 0, s>>>(d);
+  if (d.nspec > 2) {
+    mk("gather_species", s);
+    k_gather_species<<<g, kThreads, 0, s>>>(d);
+  }
+  for (int sp = 2; sp < d.nspec; sp += 2) {
+    mk("exchange_cell2_species", s);
+    k_exchange_cell2<MIX, true, PER><<<g, kThreads, 0, s>>>(d, sp);
+  }
+  mk("exchange_cell2", s);
+  k_exchange_cell2<MIX, false, PER><<<g, kThreads, 0, s>>>(d, 0);
+}
 
 template <bool MIX, bool TR>
 static void launch_exchange_brute(const Dev& d, bool cut, unsigned int g, cudaStream_t s,
@@ -825,6 +878,10 @@ static void transfer_t(const Dev& d, int search, cudaStream_t s, Marker& mk) {
       k_band_build<MIX><<<g, kThreads, 0, s>>>(d);
       mk("band_rowsum", s);
       k_band_rowsum<MIX><<<g, kThreads, 0, s>>>(d);
+      if (d.nspec > 2) {
+        mk("gather_species", s);
+        k_gather_species<<<g, kThreads, 0, s>>>(d);
+      }
       for (int sp = 2; sp < d.nspec; sp += 2) {
         mk("band_exchange_species", s);
         k_band_exchange<MIX, true><<<g, kThreads, 0, s>>>(d, sp);
@@ -834,6 +891,10 @@ static void transfer_t(const Dev& d, int search, cudaStream_t s, Marker& mk) {
     } else if (d.dim == 1 && d.tile) {
       mk("rowsum_tile", s);
       k_rowsum_tile<MIX><<<g, kThreads, 0, s>>>(d);
+      if (d.nspec > 2) {
+        mk("gather_species", s);
+        k_gather_species<<<g, kThreads, 0, s>>>(d);
+      }
       for (int sp = 2; sp < d.nspec; sp += 2) {
         mk("exchange_tile_species", s);
         k_exchange_tile<MIX, true><<<g, kThreads, 0, s>>>(d, sp);
@@ -843,21 +904,20 @@ static void transfer_t(const Dev& d, int search, cudaStream_t s, Marker& mk) {
     } else if (d.dim == 1) {
       mk("rowsum_walk", s);
       k_rowsum_walk<MIX><<<g, kThreads, 0, s>>>(d);
+      if (d.nspec > 2) {
+        mk("gather_species", s);
+        k_gather_species<<<g, kThreads, 0, s>>>(d);
+      }
       for (int sp = 2; sp < d.nspec; sp += 2) {
         mk("exchange_walk_species", s);
         k_exchange_walk<MIX, true><<<g, kThreads, 0, s>>>(d, sp);
       }
       mk("exchange_walk", s);
       k_exchange_walk<MIX, false><<<g, kThreads, 0, s>>>(d, 0);
+    } else if (d.periodic) {
+      cell2_passes<MIX, true>(d, g, s, mk);
     } else {
-      mk("rowsum_cell2", s);
-      k_rowsum_cell2<MIX><<<g, kThreads, 0, s>>>(d);
-      for (int sp = 2; sp < d.nspec; sp += 2) {
-        mk("exchange_cell2_species", s);
-        k_exchange_cell2<MIX, true><<<g, kThreads, 0, s>>>(d, sp);
-      }
-      mk("exchange_cell2", s);
-      k_exchange_cell2<MIX, false><<<g, kThreads, 0, s>>>(d, 0);
+      cell2_passes<MIX, false>(d, g, s, mk);
     }
   } else {
     const bool cut = search == MT_SEARCH_BRUTE;

@@ -19,11 +19,13 @@ def assert_same(a, b):
     """Positions and masses bit for bit; the observables (sums over the
     particles) to rounding: on the one-kernel step with more than one wave of
     segments their grouping into per-CTA partial sums follows the dynamic
-    segment schedule."""
+    segment schedule, so each sum may move by a few ulp of the sum of its
+    terms' magnitudes (sum (A - B) cancels to far less than that)."""
     for u, v in zip(a[:-1], b[:-1]):
         assert np.array_equal(u, v)
     assert a[-1].shape == b[-1].shape
-    assert np.allclose(a[-1], b[-1], rtol=1e-13, atol=1e-13)
+    n = a[0].shape[-1]
+    assert np.allclose(a[-1], b[-1], rtol=1e-13, atol=1e-14 * n)
 
 
 def clustered(n, L, seed):
