@@ -324,7 +324,6 @@ struct TileRanges {
 __device__ __forceinline__ TileRanges tile_ranges(long long jl, long long jr, long long b0,
                                                   long long b1, long long* s_lohi) {
   const long long p = b0 + threadIdx.x;
-  const int lane = threadIdx.x & 31;
   const long long w0 = b0 + (threadIdx.x & ~31);
   const int last = w0 < b1 ? (int)min(31LL, b1 - 1 - w0) : 0;
   TileRanges t;
@@ -333,7 +332,6 @@ __device__ __forceinline__ TileRanges tile_ranges(long long jl, long long jr, lo
   if (w0 >= b1) t.wlo = t.whi = 0;
   if (p == b0) s_lohi[0] = jl;
   if (p == b1 - 1) s_lohi[1] = jr;
-  (void)lane;
   __syncthreads();
   t.lo = s_lohi[0];
   t.hi = s_lohi[1];
