@@ -96,3 +96,33 @@ def test_dense_tiles_in_a_batch(precision):
         assert_masses(ga[sl], c[1], TOL[precision], f"A of realisation {i}")
         assert_masses(gb[sl], c[2], TOL[precision], f"B of realisation {i}")
     assert "rowsum_tile" in profile_names(sim)
+
+
+@pytest.mark.parametrize("stored_p", [0, 1])
+def test_paper_density_full_size_step(stored_p):
+    """The paper-density workload at full size (N = 1e6 on [0, 5000], ~270
+    neighbours a side, MIXED) in the benchmark's launch configuration (CUDA
+    graph, built-in generator) for 5 steps, on the fly (tiles) and in the
+    SPaM form; then one injected-noise step from the read-back state against
+    the oracle element by element (sorted-window search), C1 and C2
+    conserved."""
+    n, L = 10 ** 6, 5000.0
+    p = mt.mt_params_init(n=n, L=(L,), D_mt=0.5, D_rw=0.5, dt=0.1, react=0,
+                          precision=mt.MT_MIXED, seed=3, stored_p=stored_p)
+    sim = mt.Simulation(p)
+    x = synth.uniform_positions(n, L, seed=9)
+    c1, c2 = synth.segregated_masses(x, L)
+    sim.upload(x, c1, c2)
+    sim.run(5)
+    X0 = sim.ticks()
+    a0, b0 = sim.masses()
+    assert abs(a0.sum() - c1.sum()) <= 1e-9 * n and abs(b0.sum() - c2.sum()) <= 1e-9 * n
+    xi = synth.normals(1, 1, n, seed=77)[0]
+    sim.set_noise(xi)
+    sim.step()
+    X1, a1, b1 = O.step(oracle_of(sim.params), X0, xi, a0, b0)
+    assert np.array_equal(sim.ticks(), X1)
+    ga, gb = sim.masses()
+    assert_masses(ga, a1, TOL[mt.MT_MIXED], "C1")
+    assert_masses(gb, b1, TOL[mt.MT_MIXED], "C2")
+    sim.close()
