@@ -73,3 +73,46 @@ def test_paper_problem_error_against_exact_solution(precision):
     assert 0.85 <= acc.fitted_d(xs[R:], c1[R:]) <= 1.02
     for r in range(2 * R):
         assert abs(c1[r].sum() - ins[r][1].sum()) <= 1e-9 * ns[r]
+
+
+def test_cutoff_width_and_full_matrix_on_the_paper_problem():
+    """75 realisations of N = 500 (the same inputs and built-in walks for
+    each variant): a 2-sigma cutoff damps the transfer visibly against
+    3 sigma (fitted D), and the full matrix, run as one handle per
+    realisation, gives the cell list's RMSE and fitted D."""
+    R, n = acc.REALISATIONS, 500
+    ns = [n] * R
+    ins = [acc.inputs(n, 2000 + r) for r in range(R)]
+    x = np.concatenate([i[0][0] for i in ins])[None, :]
+    c1 = np.concatenate([i[1] for i in ins])
+    c2 = np.concatenate([i[2] for i in ins])
+    sig = np.sqrt(4 * 0.5 * acc.DT)
+    out = {}
+    for name, cutoff in (("3s", 3 * sig), ("2s", 2 * sig)):
+        kw = acc.params_kw()
+        p = mt.mt_params_init(dim=1, L=(1.0,), D_mt=kw["D_mt"], D_rw=kw["D_rw"], dt=kw["dt"],
+                              react=0, precision=mt.MT_MIXED, frac_bits=29, seed=17, cutoff=cutoff)
+        sim = mt.Simulation(p, batch=mt.make_batch(ns, [acc.L] * R))
+        sim.upload(x, c1, c2)
+        sim.run(acc.STEPS)
+        out[name] = (split(sim.positions()[0], ns), split(sim.masses()[0], ns))
+        sim.close()
+    xs, cs = [], []
+    for r in range(R):
+        kw = acc.params_kw()
+        p = mt.mt_params_init(n=n, L=(acc.L,), D_mt=kw["D_mt"], D_rw=kw["D_rw"], dt=kw["dt"], react=0,
+                              precision=mt.MT_MIXED, frac_bits=29, seed=17, realisation=r,
+                              search=mt.MT_SEARCH_FULL)
+        sim = mt.Simulation(p)
+        sim.upload(ins[r][0], ins[r][1], ins[r][2])
+        sim.run(acc.STEPS)
+        xs.append(sim.positions()[0])
+        cs.append(sim.masses()[0])
+        sim.close()
+    out["full"] = (xs, cs)
+    d = {k: acc.fitted_d(*v) for k, v in out.items()}
+    e = {k: np.mean([acc.rmse(a, b) for a, b in zip(*v)]) for k, v in out.items()}
+    assert d["2s"] < d["3s"] - 0.05
+    assert abs(d["full"] - d["3s"]) < 0.03
+    assert e["2s"] > e["3s"]
+    assert abs(e["full"] - e["3s"]) < 0.1 * e["3s"]

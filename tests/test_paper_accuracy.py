@@ -64,3 +64,23 @@ def test_symmetric_normalisation_conserves_row_does_not(sym500):
     x, c1, _ = run(500, 0, norm=O.NORM_ROW)
     _, c10, _ = acc.inputs(500, 0)
     assert abs(c1.sum() - c10.sum()) > 1e-3
+
+
+def test_narrower_pad_damps_more_and_full_matrix_agrees(sym500):
+    """Sec. 5's observations with the same inputs and walks: a 2-sigma cutoff
+    truncates more of Eq. 3's kernel than 3 sigma and damps the transfer
+    visibly (fitted D well below), while the full matrix (no cutoff) gives
+    the 3-sigma result within a few per cent."""
+    sig = np.sqrt(4 * 0.5 * acc.DT)
+    d3 = acc.fitted_d([r[0] for r in sym500], [r[1] for r in sym500])
+    two = [run(500, s, smax=2 * sig) for s in range(8)]
+    full = [run(500, s, search=O.SEARCH_FULL) for s in range(8)]
+    d2 = acc.fitted_d([r[0] for r in two], [r[1] for r in two])
+    dfull = acc.fitted_d([r[0] for r in full], [r[1] for r in full])
+    assert d2 < d3 - 0.05
+    assert abs(dfull - d3) < 0.03
+    e3 = np.mean([acc.rmse(x, c) for x, c, _ in sym500])
+    e2 = np.mean([acc.rmse(x, c) for x, c, _ in two])
+    efull = np.mean([acc.rmse(x, c) for x, c, _ in full])
+    assert e2 > e3
+    assert abs(efull - e3) < 0.1 * e3
