@@ -349,6 +349,16 @@ mt_status mt_read_ticks(mt_handle* h, int64_t* X, int32_t mem);
 mt_status mt_read_observables(mt_handle* h, double* out, int64_t cap,
                               int64_t* count);
 
+/* The observables of the last rows steps enqueued (1 <= rows <= min(steps
+ * enqueued, observe_cap)), oldest first, in mt_read_observables' layout,
+ * copied to out (host or device memory) by copies enqueued on the handle's
+ * stream behind those steps; the call does not wait (with page-locked host
+ * memory the copies are asynchronous too).  out holds the rows once the
+ * stream has reached the copies (mt_sync, or an event recorded after the
+ * call).  The copies run in stream order, so no later step overwrites a
+ * row before it is copied. */
+mt_status mt_copy_observables_async(mt_handle* h, double* out, int64_t rows);
+
 /* Pairs {i, j} (caller's particle indices, i < j) within the cutoff at the
  * current positions, as the handle's search finds them.  pi, pj: device
  * pointers with room for cap entries (may be NULL when cap = 0); *count

@@ -972,6 +972,23 @@ mt_status mt_read_observables(mt_handle* h, double* out, int64_t cap, int64_t* c
   return MT_OK;
 }
 
+mt_status mt_copy_observables_async(mt_handle* h, double* out, int64_t rows) {
+  if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
+  const long long ocap = h->D.p.observe_cap;
+  const long long have = h->steps < ocap ? h->steps : ocap;
+  if (rows < 1 || rows > have)
+    return fail(MT_ERR_INVALID, "rows must be in [1, %lld] (steps enqueued, observe_cap)", have);
+  if (!out) return fail(MT_ERR_INVALID, "out is NULL");
+  const size_t width = (size_t)h->D.nreal * 4;  // doubles per row
+  const long long r0 = (h->steps - rows) % ocap;  // ring row of the oldest step copied
+  const long long n1 = r0 + rows <= ocap ? rows : ocap - r0;
+  CU(cudaMemcpyAsync(out, h->dev.obs + width * r0, width * 8 * n1, cudaMemcpyDefault, h->stream));
+  if (n1 < rows)
+    CU(cudaMemcpyAsync(out + width * n1, h->dev.obs, width * 8 * (rows - n1), cudaMemcpyDefault,
+                       h->stream));
+  return MT_OK;
+}
+
 mt_status mt_read_pairs(mt_handle* h, int32_t* pi, int32_t* pj, int64_t cap, int64_t* count) {
   if (!h || !count) return fail(MT_ERR_INVALID, "handle or count is NULL");
   if (!h->uploaded) return fail(MT_ERR_STATE, "no state uploaded");

@@ -7,6 +7,8 @@ set must be identical, and the masses must agree to 1e-12 (FP64) or 1e-6
 m_ref = 0.5 is the mean initial mass (late-time values after the reaction
 cancel towards zero).
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -481,3 +483,29 @@ def test_workload2_n1e5_1000_steps_oracle_on_strided_steps(precision):
     obs = sim.observables()
     assert obs.shape == (1000, 4)
     np.testing.assert_allclose(obs[-1, 2], np.sum(A - B), rtol=0, atol=1e-10 * np.sum(A + B))
+
+
+def test_async_observables_copy_matches_synchronous_read():
+    """Rows copied behind each step into page-locked host memory (no wait
+    between steps) equal the synchronous read; several rows across the
+    ring's wrap; bad row counts refused."""
+    import torch
+
+    n, L = 5000, 5000.0
+    sim = make(n, L, precision=mt.MT_MIXED, seed=4, observe_cap=5)
+    sim.upload(synth.uniform_positions(n, L, seed=4), *synth.uniform_masses(n, seed=4))
+    rows = torch.zeros((12, 4), dtype=torch.float64).pin_memory().numpy()
+    for s in range(12):
+        sim.run(1)
+        mt.mt_copy_observables_async(sim.h, rows[s:].ctypes.data_as(ctypes.c_void_p), 1)
+    sim.sync()
+    assert np.array_equal(rows[-5:], sim.observables())
+    wrap = np.zeros((4, 4))
+    sim.run(3)  # the ring's newest row is now at index 0 again after a wrap
+    mt.mt_copy_observables_async(sim.h, wrap.ctypes.data_as(ctypes.c_void_p), 4)
+    sim.sync()
+    assert np.array_equal(wrap, sim.observables()[-4:])
+    for bad in (0, 6):
+        with pytest.raises(mt.MtError):
+            mt.mt_copy_observables_async(sim.h, wrap.ctypes.data_as(ctypes.c_void_p), bad)
+    sim.close()
