@@ -50,7 +50,7 @@ struct Derived {
   float bq = 0.f;
   int cshift = 0;
   long long ncx = 1, ncy = 1, ncell = 0;
-  long long nbig_cap = 0, nblocks = 0, ntiles = 0;
+  long long nbig_cap = 0, ntiles = 0;
   // fused 1-d step (one kernel per step) and its tiling
   bool fused = false;
   long long seg_target = 0, nseg = 0, hc = 0;
@@ -58,10 +58,12 @@ struct Derived {
   int nreal = 1, lbits = 31;
   std::vector<Real> rt;
   std::vector<int> sslot, sreal;
+  std::vector<int> ochunk;  // first slot of each observables chunk (+ n)
+  std::vector<int> ochr;    // realisation of each chunk
   // workspace offsets
   size_t o_ctrl, o_X[2], o_id[2], o_M[2], o_src, o_rinv, o_count, o_start, o_cursor,
-      o_status, o_big, o_part, o_obs, o_fstart[2], o_cb[2], o_ovlist, o_pred[2], o_rt, o_sslot,
-      o_sreal, o_rdone, o_cnt, o_band, total;
+      o_status, o_big, o_obs, o_fstart[2], o_cb[2], o_ovlist, o_pred[2], o_rt, o_sslot,
+      o_sreal, o_ochunk, o_opart, o_ochr, o_ocnt, o_cnt, o_band, total;
   long long band = 0;  // SPaM band entries per particle (0: off)
   bool tile = false;   // dense 1-d: tiled transfer passes
 };
@@ -242,8 +244,6 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
     p.cell_shift = 0;
   }
   D.nbig_cap = p.n / (kSmallCell + 1) + 1;
-  D.nblocks = (p.n + kThreads - 1) / kThreads;
-  if (D.nblocks < 1) D.nblocks = 1;
   // Fused 1-d step: segments of seg_target particles staged with a halo of
   // hc cells (2 Smax) and the displacement bound; pick the largest target
   // (<= 1024) whose expected staging, with 50% headroom, fits kFusedCap.
@@ -312,6 +312,12 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
         D.sslot.push_back((int)(off + j * T));
         D.sreal.push_back(r);
       }
+      R.ch0 = (int)D.ochunk.size();
+      for (long long j = 0; j < R.n; j += kObsChunk) {
+        D.ochunk.push_back((int)(off + j));
+        D.ochr.push_back(r);
+      }
+      R.nch = (int)D.ochunk.size() - R.ch0;
       if (b) cb += (lq[r] >> D.cshift) + 1 + gapc;
       off += R.n;
       D.rt.push_back(R);
@@ -319,7 +325,7 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
     D.nseg = (long long)D.sslot.size();
     D.sslot.push_back((int)p.n);
     if (D.sreal.empty()) D.sreal.push_back(0);
-    if (D.fused) D.nblocks = D.nblocks > D.nseg ? D.nblocks : D.nseg;  // partial slots
+    D.ochunk.push_back((int)p.n);
   }
   if (b) p.L[0] = std::ldexp((double)D.Lq[0], -k);
   D.ntiles = (D.ncell + kScanTile - 1) / kScanTile;
@@ -342,7 +348,6 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
   D.o_cursor = take((size_t)D.ncell * 4);
   D.o_status = take((size_t)D.ntiles * 8);
   D.o_big = take((size_t)D.nbig_cap * 4);
-  D.o_part = take((size_t)D.nblocks * 4 * 8);
   D.o_obs = take((size_t)p.observe_cap * D.nreal * 4 * 8);
   for (int b2 = 0; b2 < 2; ++b2) D.o_fstart[b2] = take(D.fused ? (size_t)(D.ncell + 1) * 4 : 0);
   for (int b2 = 0; b2 < 2; ++b2) D.o_cb[b2] = take(D.fused ? (size_t)(D.nseg + 1) * 4 : 0);
@@ -355,7 +360,10 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
   D.o_band = take(D.band > 0 ? (size_t)D.band * ((n + 31) / 32 * 32) *
                                    (p.precision == MT_MIXED ? 4 : 8)
                              : 0);
-  D.o_rdone = take((size_t)D.nreal * 4);
+  D.o_ochunk = take(D.ochunk.size() * 4);
+  D.o_opart = take((D.ochunk.size() - 1) * 4 * 8);
+  D.o_ochr = take(D.ochr.size() * 4);
+  D.o_ocnt = take((size_t)D.nreal * 4);
   D.total = o;
   D.p = p;
   *out = D;
@@ -430,10 +438,6 @@ mt_status enqueue_general(mt_handle* h, const Dev& d, Marker& mk) {
     CU(launch_move(d, true, false, h->stream));
   }
   CU(launch_transfer(d, p.search, p.precision, h->stream, mk));
-  if (h->D.nreal > 1 && p.observe_cap > 0) {
-    mk("observables", h->stream);
-    CU(launch_real_obs(d, p.precision, h->stream));
-  }
   if (h->D.fused) {
     mk("fused_prep", h->stream);
     CU(launch_fused_prep(d, 1, h->stream));
@@ -491,6 +495,10 @@ mt_status enqueue_step(mt_handle* h, const Dev& d) {
     const mt_status s = enqueue_general(h, d, mk);
     if (s != MT_OK) return s;
   }
+  if (p.observe_cap > 0) {
+    mk("observables", h->stream);
+    CU(launch_obs(d, p.precision, h->stream));
+  }
   if (h->profile) {
     CU(Marker::record(h->ev[mk.count], h->stream));
     h->ev_count = mk.count;
@@ -530,6 +538,7 @@ mt_status build_graph(mt_handle* h) {
       return fail(MT_ERR_CUDA, "graph capture of the fused step failed");
     }
     cudaGraph_t body1 = nullptr;
+    cudaGraphNode_t cnode = nullptr;  // the IF node; the observables follow it
     {
       const size_t want = fork ? 2 : 1;
       cudaGraphNode_t knodes[2] = {nullptr, nullptr};
@@ -544,7 +553,6 @@ mt_status build_graph(mt_handle* h) {
       cp.conditional.handle = cond1;
       cp.conditional.type = cudaGraphCondTypeIf;
       cp.conditional.size = 1;
-      cudaGraphNode_t cnode = nullptr;
       CU(cudaGraphAddNode(&cnode, g, knodes, nullptr, want, &cp));
       body1 = cp.conditional.phGraph_out[0];
     }
@@ -574,9 +582,18 @@ mt_status build_graph(mt_handle* h) {
     s = enqueue_general(h, d, none);
     const cudaError_t e3 = cudaStreamEndCapture(h->stream, &body2);
     if (s == MT_OK && e3 != cudaSuccess) s = fail(MT_ERR_CUDA, "graph capture of the fallback failed");
+    if (s == MT_OK && h->D.p.observe_cap > 0) {
+      CU(cudaStreamBeginCaptureToGraph(h->stream, g, &cnode, nullptr, 1, mode));
+      const cudaError_t e4 = launch_obs(d, h->D.p.precision, h->stream);
+      const cudaError_t e5 = cudaStreamEndCapture(h->stream, &g);
+      if (e4 != cudaSuccess || e5 != cudaSuccess)
+        s = fail(MT_ERR_CUDA, "graph capture of the observables failed");
+    }
   } else {
     CU(cudaStreamBeginCaptureToGraph(h->stream, g, nullptr, nullptr, 0, mode));
     s = enqueue_general(h, d, none);
+    if (s == MT_OK && launch_obs(d, h->D.p.precision, h->stream) != cudaSuccess)
+      s = fail(MT_ERR_CUDA, "observables launch failed");
     const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (s == MT_OK && e != cudaSuccess) s = fail(MT_ERR_CUDA, "graph capture failed");
   }
@@ -689,7 +706,6 @@ mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace
   d.cursor = reinterpret_cast<int*>(w + D.o_cursor);
   d.scan_status = reinterpret_cast<unsigned long long*>(w + D.o_status);
   d.big = reinterpret_cast<int*>(w + D.o_big);
-  d.partials = reinterpret_cast<double*>(w + D.o_part);
   d.obs = reinterpret_cast<double*>(w + D.o_obs);
   for (int b = 0; b < 2; ++b) {
     d.fstart[b] = reinterpret_cast<int*>(w + D.o_fstart[b]);
@@ -738,14 +754,17 @@ mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace
   d.key1 = (unsigned int)(D.p.seed >> 32);
   d.real = (unsigned int)D.p.realisation;
   d.nbig_cap = (int)D.nbig_cap;
-  d.nblocks = (int)D.nblocks;
   d.rt = reinterpret_cast<const Real*>(w + D.o_rt);
   d.nreal = D.nreal;
   d.lbits = D.lbits;
   d.lmask = (int)((1LL << D.lbits) - 1);
   d.sslot = reinterpret_cast<const int*>(w + D.o_sslot);
   d.sreal = reinterpret_cast<const int*>(w + D.o_sreal);
-  d.rdone = reinterpret_cast<int*>(w + D.o_rdone);
+  d.ochunk = reinterpret_cast<int*>(w + D.o_ochunk);
+  d.nochunk = (int)D.ochunk.size() - 1;
+  d.opart = reinterpret_cast<unsigned long long*>(w + D.o_opart);
+  d.ochr = reinterpret_cast<int*>(w + D.o_ochr);
+  d.ocnt = reinterpret_cast<int*>(w + D.o_ocnt);
   const Derived& hd = h->D;  // the tables live as long as the handle
   cudaError_t e = D.fused ? fused_configure() : cudaSuccess;
   if (e == cudaSuccess && d.use_pred) {
@@ -763,6 +782,12 @@ mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(w + D.o_sreal, hd.sreal.data(), hd.sreal.size() * 4,
                         cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(w + D.o_ochunk, hd.ochunk.data(), hd.ochunk.size() * 4,
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && !hd.ochr.empty())
+    e = cudaMemcpyAsync(w + D.o_ochr, hd.ochr.data(), hd.ochr.size() * 4, cudaMemcpyHostToDevice,
+                        h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     if (h->side) cudaStreamDestroy(h->side);
@@ -784,8 +809,7 @@ mt_status mt_upload(mt_handle* h, const double* x, const double* A, const double
   const size_t n = (size_t)p.n;
   if (n > 0 && (!x || !A || !B)) return fail(MT_ERR_INVALID, "x, A and B are required");
   CU(cudaMemsetAsync(h->ws + h->D.o_ctrl, 0, sizeof(Ctrl), h->stream));
-  // partial slots carry the step they were written in: clear old ones
-  CU(cudaMemsetAsync(h->ws + h->D.o_part, 0, (size_t)h->D.nblocks * 32, h->stream));
+  CU(cudaMemsetAsync(h->ws + h->D.o_ocnt, 0, (size_t)h->D.nreal * 4, h->stream));
   if (h->D.fused)
     for (int b = 0; b < 2; ++b) CU(cudaMemsetAsync(h->ws + h->D.o_pred[b], 0, h->D.nseg, h->stream));
   // the scan epoch restarts with the control block: clear old status words

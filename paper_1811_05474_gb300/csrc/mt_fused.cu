@@ -133,7 +133,7 @@ __device__ __forceinline__ SegScalars load_seg(const Dev& d, int sc, long long D
 // segment does not fit this tier (then nothing of it has been written).
 template <bool MIX, typename TR, int CL>
 __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const SegScalars& g,
-                             int slice, int nslice, bool route_heavy, ObsAcc<MIX>& obs_sum,
+                             int slice, int nslice, bool route_heavy,
                              bool* heavy_out = nullptr) {
   using W = Weight<MIX, 1>;
   using T = typename W::T;
@@ -561,7 +561,6 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
   } else {
     __syncthreads();
   }
-  ObsAcc<MIX> obs{};
   if (active) {
     long long* Xn = d.X[xc ^ 1];
     int* In = d.id[xc ^ 1];
@@ -597,7 +596,6 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
         MS::store(Mn, o, A);
         MS::store(Mn, d.n + o, B);
       }
-      if (d.observe_cap > 0) obs.add(A, B);
     }
   }
   __syncthreads();
@@ -649,11 +647,9 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
           MS::store(Mn, o, A);
           MS::store(Mn, d.n + o, B);
         }
-        if (d.observe_cap > 0) obs.add(A, B);
       }
     }
   }
-  if (active && d.observe_cap > 0) obs_sum.merge(obs);
   if (active && slice == 0) {
     // ---- 6: next step's cell starts and segment boundaries ----------------
     int* Sn = d.fstart[sc ^ 1];
@@ -698,191 +694,6 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
   return status;
 }
 
-// Reduce the CTA's (second tier: the cluster's) observables accumulators in
-// fixed shuffle trees -- warps, then warp totals, then the cluster's CTA
-// totals -- into partial slot `slot` (3 words in the precision's own
-// arithmetic, then the step number), and clear them.  Called by every
-// thread (of every CTA of the cluster).
-template <bool MIX, int NT, int CL>
-__device__ void flush_obs(const Dev& d, int slot, int slice, ObsAcc<MIX>& obs) {
-  using MV = typename Mass<MIX>::V;
-  __shared__ MV s_red[3][NT / 32];
-  __shared__ MV s_seg[3];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  MV oa = obs.va(), ob = obs.vb(), od = obs.vd();
-  obs = ObsAcc<MIX>{};
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    oa = obs_add(oa, obs_shfl(oa, o));
-    ob = obs_add(ob, obs_shfl(ob, o));
-    od = obs_add(od, obs_shfl(od, o));
-  }
-  if (lane == 0) {
-    s_red[0][warp] = oa;
-    s_red[1][warp] = ob;
-    s_red[2][warp] = od;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    static_assert(NT / 32 <= 32, "one warp reduces the warp totals");
-    MV ta{}, tb{}, td{};
-    if (lane < NT / 32) {
-      ta = s_red[0][lane];
-      tb = s_red[1][lane];
-      td = s_red[2][lane];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      ta = obs_add(ta, obs_shfl(ta, o));
-      tb = obs_add(tb, obs_shfl(tb, o));
-      td = obs_add(td, obs_shfl(td, o));
-    }
-    if (lane == 0) {
-      s_seg[0] = ta;
-      s_seg[1] = tb;
-      s_seg[2] = td;
-    }
-  }
-  if constexpr (CL > 1) {
-    // the cluster's CTAs hold the sums of their own slices: the first one
-    // gathers them (distributed shared memory, one lane per CTA)
-    static_assert(CL <= 32, "one warp gathers the cluster");
-    cg::cluster_group cl = cg::this_cluster();
-    cl.sync();
-    if (slice == 0 && warp == 0) {
-      MV ta{}, tb{}, td{};
-      if (lane < CL) {
-        const MV* peer = cl.map_shared_rank(&s_seg[0], lane);
-        ta = peer[0];
-        tb = peer[1];
-        td = peer[2];
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        ta = obs_add(ta, obs_shfl(ta, o));
-        tb = obs_add(tb, obs_shfl(tb, o));
-        td = obs_add(td, obs_shfl(td, o));
-      }
-      __syncwarp();
-      if (lane == 0) {
-        s_seg[0] = ta;
-        s_seg[1] = tb;
-        s_seg[2] = td;
-      }
-    }
-    cl.sync();
-  } else {
-    __syncthreads();
-  }
-  if (tid == 0 && slice == 0) {
-    MV* part = reinterpret_cast<MV*>(d.partials);  // 8-byte words
-    part[4 * slot + 0] = s_seg[0];
-    part[4 * slot + 1] = s_seg[1];
-    part[4 * slot + 2] = s_seg[2];
-    // the step it belongs to: slots not written this step are skipped
-    reinterpret_cast<unsigned long long*>(d.partials)[4 * slot + 3] = d.ctrl->step;
-  }
-  __syncthreads();
-}
-
-// Observables of realisation r, by the CTA that completed its last segment
-// this step: the partials of its segment groups written this step (binary64,
-// or double-binary32 in MIXED) reduced in a fixed order, one row of the
-// ring.
-__device__ __forceinline__ double ldcg_obs(const double* p) { return __ldcg(p); }
-__device__ __forceinline__ df ldcg_obs(const df* p) {
-  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
-  return {v.x, v.y};
-}
-
-template <bool MIX, int NT>
-__device__ void reduce_realisation(const Dev& d, int r) {
-  using MV = typename Mass<MIX>::V;
-  __shared__ MV s_tot[NT / 32][3];
-  Ctrl* c = d.ctrl;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const Real R = d.rt[r];
-  const MV* part = reinterpret_cast<const MV*>(d.partials);
-  const unsigned long long* tag = reinterpret_cast<const unsigned long long*>(d.partials);
-  const unsigned long long step = c->step;
-  MV ta{}, tb{}, td{};
-  // slots in chunks of 4 per thread: the tag loads of a chunk are issued
-  // together (they are independent), then the chunk's live slots are added
-  // in slot order
-  constexpr int U = 4;
-  for (int b0 = R.seg0 + tid; b0 < R.seg0 + R.nseg; b0 += NT * U) {
-    unsigned long long tg[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int blk = b0 + u * NT;
-      tg[u] = blk < R.seg0 + R.nseg ? __ldcg(&tag[4 * blk + 3]) : ~step;
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int blk = b0 + u * NT;
-      if (tg[u] != step) continue;  // no group started here this step
-      ta = obs_add(ta, ldcg_obs(&part[4 * blk + 0]));
-      tb = obs_add(tb, ldcg_obs(&part[4 * blk + 1]));
-      td = obs_add(td, ldcg_obs(&part[4 * blk + 2]));
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    ta = obs_add(ta, obs_shfl(ta, o));
-    tb = obs_add(tb, obs_shfl(tb, o));
-    td = obs_add(td, obs_shfl(td, o));
-  }
-  if (lane == 0) {
-    s_tot[warp][0] = ta;
-    s_tot[warp][1] = tb;
-    s_tot[warp][2] = td;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    ta = tb = td = MV{};
-    if (lane < NT / 32) {
-      ta = s_tot[lane][0];
-      tb = s_tot[lane][1];
-      td = s_tot[lane][2];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      ta = obs_add(ta, obs_shfl(ta, o));
-      tb = obs_add(tb, obs_shfl(tb, o));
-      td = obs_add(td, obs_shfl(td, o));
-    }
-  }
-  if (tid == 0) {
-    const long long row = (long long)(c->step % (unsigned long long)d.observe_cap);
-    double* o = d.obs + 4 * (row * d.nreal + r);
-    const double sa = obs_double(ta);
-    o[0] = sa;
-    o[1] = obs_double(tb);
-    o[2] = obs_double(td);
-    o[3] = sa / (double)R.n;
-    d.rdone[r] = 0;
-  }
-  __syncthreads();
-}
-
-// Count `count` segments of realisation r as done (their observables are in
-// the partial slots); the CTA that completes the realisation's last segment
-// reduces that realisation's observables.  Called by every thread of the CTA.
-template <bool MIX, int NT>
-__device__ void complete_group(const Dev& d, int r, int count) {
-  __shared__ int s_r;
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_r = atomicAdd(&d.rdone[r], count) + count == d.rt[r].nseg ? r : -1;
-  }
-  __syncthreads();
-  const int rr = s_r;
-  __syncthreads();
-  if (rr < 0) return;
-  __threadfence();
-  reduce_realisation<MIX, NT>(d, rr);
-}
-
 // End of a fused step (one thread, after every segment is done).
 __device__ __forceinline__ void fused_advance(const Dev& d) {
   Ctrl* c = d.ctrl;
@@ -896,25 +707,39 @@ __device__ __forceinline__ void fused_advance(const Dev& d) {
 }
 
 // The first tier and the predicted-segment kernel run side by side; the
-// last CTA of each calls this (one thread).  The second caller decides the
-// step: advance it, or (segments newly queued, or a predicted segment that
-// did not fit) raise the graph condition for the second tier.  Without the
-// predicted-segment kernel (small systems) the first tier decides alone.
-__device__ __forceinline__ void join_step(const Dev& d, cudaGraphConditionalHandle cond,
-                                          int use_cond) {
+// last CTA of each joins.  join_decide (one thread): 0 for the first of the
+// two to arrive; for the second (or the first tier alone, without the
+// predicted-segment kernel) 1 if the step is complete, 2 if segments were
+// newly queued or a predicted segment did not fit (the second tier runs).
+__device__ __forceinline__ int join_decide(const Dev& d) {
   Ctrl* c = d.ctrl;
   __threadfence();
-  if (d.use_pred && atomicAdd(&c->kjoin, 1u) != 1u) return;  // the first of two
+  if (d.use_pred && atomicAdd(&c->kjoin, 1u) != 1u) return 0;  // the first of two
   __threadfence();
   const int nov = atomicAdd(&c->nov, 0);
   const int ov = atomicAdd(&c->overflow, 0);
-  const bool more = nov > 0 || ov != 0;
+  return nov > 0 || ov != 0 ? 2 : 1;
+}
+
+// The deciding thread: advance the step or raise the graph condition.
+__device__ __forceinline__ void join_finish(const Dev& d, int role,
+                                            cudaGraphConditionalHandle cond, int use_cond) {
+  Ctrl* c = d.ctrl;
+  const bool more = role == 2;
   if (!more) fused_advance(d);
   if (more) c->big_steps += 1;
-  if (nov > c->ov_value) c->ov_value = nov;  // largest queue seen (diagnostic)
+  if (c->nov > c->ov_value) c->ov_value = c->nov;  // largest queue seen (diagnostic)
   c->kjoin = 0;
   c->seg_ctr = 0;
   if (use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
+}
+
+// The end of the first tier or the predicted-segment kernel (thread 0 of
+// its last CTA).
+__device__ __forceinline__ void end_of_tier(const Dev& d, cudaGraphConditionalHandle cond,
+                                            int use_cond) {
+  const int role = join_decide(d);
+  if (role != 0) join_finish(d, role, cond, use_cond);
 }
 
 // First tier: a persistent grid (a few CTAs per SM) looping over the
@@ -928,15 +753,6 @@ __global__ void __launch_bounds__(Fast::kT, kFusedCtasPerSm) k_step1d(Dev d, cud
   Ctrl* c = d.ctrl;
   const int sc = c->scur;
   const long long Dc = (c->dmax >> d.cshift) + 2;
-  const bool observe = d.observe_cap > 0;
-  // Observables: the segments this CTA completes in a row for one
-  // realisation form a group, accumulated per thread and flushed once into
-  // the group's first slot (the group's other slots keep an older step tag
-  // and are skipped).
-  __shared__ ObsAcc<MIX> s_obs[Fast::kT];
-  ObsAcc<MIX>& obs = s_obs[threadIdx.x];
-  obs = ObsAcc<MIX>{};
-  int gslot = -1, greal = -1, gcount = 0;
   const unsigned char* pcur = d.pred[sc];
   unsigned char* pnext = d.pred[sc ^ 1];
   // Segments: the first wave by CTA index, then one ticket at a time (drawn
@@ -957,24 +773,8 @@ __global__ void __launch_bounds__(Fast::kT, kFusedCtasPerSm) k_step1d(Dev d, cud
     SegScalars nxt = {};
     if (next < d.nseg) nxt = load_seg(d, sc, Dc, next);
     if (!d.use_pred || !pcur[seg]) {
-      const int r = d.sreal[seg];
-      if (observe && gcount > 0 && r != greal) {  // a new realisation ends the group
-        flush_obs<MIX, Fast::kT, 1>(d, gslot, 0, obs);
-        complete_group<MIX, Fast::kT>(d, greal, gcount);
-        gcount = 0;
-      }
-      const int st = fused_segment<MIX, Fast, 1>(d, seg, smem, cur, 0, 1, true, obs);
-      if (st == kSegOk) {
-        if (observe) {
-          if (gcount == 0) {
-            gslot = seg;
-            greal = r;
-          }
-          ++gcount;
-        }
-      } else if (threadIdx.x == 0) {
-        d.ovlist[atomicAdd(&c->nov, 1)] = seg;
-      }
+      const int st = fused_segment<MIX, Fast, 1>(d, seg, smem, cur, 0, 1, true);
+      if (st != kSegOk && threadIdx.x == 0) d.ovlist[atomicAdd(&c->nov, 1)] = seg;
       if (threadIdx.x == 0) {
         pnext[seg] = st == kSegOk ? 0 : 1;
         if (st != kSegOk) atomicAdd(&c->npred_next, 1);
@@ -982,10 +782,6 @@ __global__ void __launch_bounds__(Fast::kT, kFusedCtasPerSm) k_step1d(Dev d, cud
     }
     cur = nxt;
     seg = next;
-  }
-  if (observe && gcount > 0) {
-    flush_obs<MIX, Fast::kT, 1>(d, gslot, 0, obs);
-    complete_group<MIX, Fast::kT>(d, greal, gcount);
   }
   if (threadIdx.x == 0) {
     __threadfence();
@@ -995,7 +791,7 @@ __global__ void __launch_bounds__(Fast::kT, kFusedCtasPerSm) k_step1d(Dev d, cud
   if (!s_last) return;
   if (threadIdx.x == 0) {
     c->done = 0;
-    join_step(d, cond, use_cond);
+    end_of_tier(d, cond, use_cond);
   }
 }
 
@@ -1021,8 +817,6 @@ __global__ void __launch_bounds__(Big::kT, 1)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned char* pcur = d.pred[sc];
   unsigned char* pnext = d.pred[sc ^ 1];
-  __shared__ ObsAcc<MIX> s_obs[Big::kT];
-  ObsAcc<MIX>& obs = s_obs[tid];
   if (blockIdx.x < CL && c->npred > 0) {  // the first cluster does the work
     for (int base = 0; base < d.nseg; base += Big::kT) {
       const int sidx = base + tid;
@@ -1045,16 +839,10 @@ __global__ void __launch_bounds__(Big::kT, 1)
       const int nl = s_nlist;
       for (int k = 0; k < nl; ++k) {
         const int seg = s_list[k];
-        obs = ObsAcc<MIX>{};
         bool heavy = true;
         const int st = fused_segment<MIX, Big, CL>(d, seg, smem, load_seg(d, sc, Dc, seg), rank,
-                                                   CL, false, obs, &heavy);
-        if (st == kSegOk) {
-          if (d.observe_cap > 0) {
-            flush_obs<MIX, Big::kT, CL>(d, seg, rank, obs);
-            if (rank == 0) complete_group<MIX, Big::kT>(d, d.sreal[seg], 1);
-          }
-        } else if (tid == 0 && atomicExch(&c->overflow, 1) == 0) {
+                                                   CL, false, &heavy);
+        if (st != kSegOk && tid == 0 && atomicExch(&c->overflow, 1) == 0) {
           c->ov_reason = st;
           c->ov_seg = seg;
         }
@@ -1074,7 +862,7 @@ __global__ void __launch_bounds__(Big::kT, 1)
   if (!s_last) return;
   if (tid == 0) {
     c->gdone = 0;
-    join_step(d, cond, use_cond);
+    end_of_tier(d, cond, use_cond);
   }
 }
 
@@ -1097,15 +885,8 @@ __global__ void __launch_bounds__(Big::kT, 1)
   const int ncl = gridDim.x / CL;
   for (int q = cid; q < nov; q += ncl) {
     const int seg = d.ovlist[q];
-    __shared__ ObsAcc<MIX> s_obs[Big::kT];
-    ObsAcc<MIX>& obs = s_obs[threadIdx.x];
-    obs = ObsAcc<MIX>{};
     const int st =
-        fused_segment<MIX, Big, CL>(d, seg, smem, load_seg(d, sc, Dc, seg), rank, CL, false, obs);
-    if (d.observe_cap > 0 && st == kSegOk) {
-      flush_obs<MIX, Big::kT, CL>(d, seg, rank, obs);
-      if (rank == 0) complete_group<MIX, Big::kT>(d, d.sreal[seg], 1);
-    }
+        fused_segment<MIX, Big, CL>(d, seg, smem, load_seg(d, sc, Dc, seg), rank, CL, false);
     if (st != kSegOk && threadIdx.x == 0 && atomicExch(&c->overflow, 1) == 0) {
       c->ov_reason = st;
       c->ov_seg = seg;
@@ -1138,7 +919,6 @@ __global__ void __launch_bounds__(Big::kT, 1)
 __global__ void k_fused_prep(Dev d, int flip) {
   const int target = d.ctrl->scur ^ flip;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < d.nreal) d.rdone[i] = 0;  // a step the general pipeline redid
   if (i <= d.ncell) {
     d.fstart[target][i] = d.start[i];
     if (i == d.ncell) {
@@ -1347,8 +1127,9 @@ cudaError_t launch_fused_pred(const Dev& d, int precision, cudaGraphConditionalH
                                : launch_pred<false, 8>(d, precision, cond, use_cond, s);
 }
 
-// Direct launches without a predicted segment: the join's second arrival.
-__global__ void k_join_stub(Dev d) { join_step(d, 0, 0); }
+// Direct launches without a predicted segment: the first tier's partner in
+// the join (launched before the first tier, so it arrives first).
+__global__ void k_join_stub(Dev d) { end_of_tier(d, 0, 0); }
 
 cudaError_t launch_join_stub(const Dev& d, cudaStream_t s) {
   k_join_stub<<<1, 1, 0, s>>>(d);

@@ -16,6 +16,7 @@ constexpr int kSmallCell = 32;         // cells up to this size sort in one thre
 constexpr int kBigSortCap = 2048;      // cells up to this size sort in shared memory
 constexpr int kBruteTile = 256;        // j-particles staged per tile, brute force
 constexpr long long kSpinLimit = 1LL << 22;  // bounded waits (scan look-back)
+constexpr int kObsChunk = 2048;  // slots per observables chunk (8 per thread)
 constexpr double kTileMinNeighbours = 32.0;  // mean neighbours a side for tiled passes
 constexpr int kFusedCap = 1024;        // particles one fused-step CTA stages
 constexpr int kFusedCtasPerSm = 4;     // resident CTAs per SM of the fused step
@@ -68,6 +69,8 @@ struct Real {
   unsigned int real;   // Philox counter word of its random walk
   int seg0;            // its first fused segment
   int nseg;            // its fused segments
+  int ch0;             // its first observables chunk
+  int nch;             // its observables chunks
   int pad;
 };
 
@@ -84,7 +87,11 @@ struct Dev {
   int* cursor;              // [ncell] scatter cursor
   unsigned long long* scan_status;  // [ntiles] look-back words
   int* big;                 // [nbig_cap] cells for the large-cell sort
-  double* partials;         // [nblocks][4] per-CTA observables
+  int* ochunk;              // [nochunk + 1] first slot of each observables chunk
+  int nochunk;
+  unsigned long long* opart;  // [nochunk][4] chunk sums (8-byte words)
+  int* ochr;                // [nochunk] realisation of each chunk
+  int* ocnt;                // [nreal] chunks summed this step
   double* obs;              // [observe_cap][4] observables ring
   int* fstart[2];           // [ncell + 1] cell starts of the sorted state (fused path)
   int* cb[2];               // [nseg + 1] first cell of each fused segment
@@ -114,7 +121,6 @@ struct Dev {
   unsigned int key0, key1;  // Philox key (seed)
   unsigned int real;        // realisation counter word
   int nbig_cap;
-  int nblocks;              // CTAs of the per-particle kernels
   int nseg;                 // fused segments (CTAs of the fused step)
   int seg_target;           // particles a fused segment aims for
   int nsm;                  // multiprocessors of the device
@@ -125,7 +131,6 @@ struct Dev {
   int lmask;                // (1 << lbits) - 1
   const int* sslot;         // [nseg + 1] first slot each fused segment aims for
   const int* sreal;         // [nseg] realisation of each fused segment
-  int* rdone;               // [nreal] segments of the step done (observables)
 };
 
 // Caller index of a particle id.
@@ -381,7 +386,8 @@ cudaError_t launch_move(const Dev& d, bool move, bool hist, cudaStream_t s);
 cudaError_t launch_sort(const Dev& d, cudaStream_t s, Marker& mk);  // scan, scatter, cell sort
 cudaError_t launch_permute(const Dev& d, cudaStream_t s);  // gather id/masses after sort, flip
 cudaError_t launch_transfer(const Dev& d, int search, int precision, cudaStream_t s, Marker& mk);
-cudaError_t launch_real_obs(const Dev& d, int precision, cudaStream_t s);  // batches
+// after a step: the observables row of every realisation
+cudaError_t launch_obs(const Dev& d, int precision, cudaStream_t s);
 cudaError_t launch_upload(const Dev& d, const double* x, const double* A,
                           const double* B, int precision, cudaStream_t s);
 cudaError_t launch_read_masses(const Dev& d, double* A, double* B, int precision,

@@ -230,53 +230,6 @@ __device__ __forceinline__ kahan acc_warp_sum(kahan v) {
   return v;
 }
 
-// Per-thread observables accumulators (sum A, sum B, sum (A - B) over the
-// particles a thread updates): binary64 sums, or in MIXED compensated sums
-// of the double-binary32 masses (each part added with Knuth's two-sum, the
-// rounding errors and low parts collected in a second term).
-template <bool MIX>
-struct ObsAcc;
-template <>
-struct ObsAcc<false> {
-  double a = 0.0, b = 0.0, d = 0.0;
-  __device__ __forceinline__ void add(double A, double B) {
-    a += A;
-    b += B;
-    d += A - B;
-  }
-  __device__ __forceinline__ void merge(const ObsAcc& o) {
-    a += o.a;
-    b += o.b;
-    d += o.d;
-  }
-  __device__ __forceinline__ double va() const { return a; }
-  __device__ __forceinline__ double vb() const { return b; }
-  __device__ __forceinline__ double vd() const { return d; }
-};
-template <>
-struct ObsAcc<true> {
-  kahan a{0.f, 0.f}, b{0.f, 0.f}, d{0.f, 0.f};
-  static __device__ __forceinline__ void put(kahan& k, float hi, float lo) {
-    const df e = two_sum(k.s, hi);
-    k.s = e.hi;
-    k.c = __fadd_rn(k.c, __fadd_rn(e.lo, lo));
-  }
-  __device__ __forceinline__ void add(df A, df B) {
-    put(a, A.hi, A.lo);
-    put(b, B.hi, B.lo);
-    put(d, A.hi, A.lo);
-    put(d, -B.hi, -B.lo);
-  }
-  __device__ __forceinline__ void merge(const ObsAcc& o) {
-    put(a, o.a.s, o.a.c);
-    put(b, o.b.s, o.b.c);
-    put(d, o.d.s, o.d.c);
-  }
-  __device__ __forceinline__ df va() const { return fast_two_sum(a.s, a.c); }
-  __device__ __forceinline__ df vb() const { return fast_two_sum(b.s, b.c); }
-  __device__ __forceinline__ df vd() const { return fast_two_sum(d.s, d.c); }
-};
-
 // Observables arithmetic: sums in the precision's own format (binary64 or
 // double-binary32), converted to binary64 per CTA.
 __device__ __forceinline__ double obs_add(double a, double b) { return a + b; }
@@ -291,5 +244,56 @@ __device__ __forceinline__ double obs_double(double v) { return v; }
 __device__ __forceinline__ double obs_double(df v) { return (double)v.hi + (double)v.lo; }
 __device__ __forceinline__ double obs_diff(double a, double b) { return a - b; }
 __device__ __forceinline__ df obs_diff(df a, df b) { return df_sub(a, b); }
+
+// Fixed-order reductions of the observables sums (three values).
+template <typename MV>
+struct Obs3 {
+  MV a, b, d;
+};
+template <typename MV>
+__device__ __forceinline__ Obs3<MV> obs3_add(Obs3<MV> x, Obs3<MV> y) {
+  return {obs_add(x.a, y.a), obs_add(x.b, y.b), obs_add(x.d, y.d)};
+}
+template <typename MV>
+__device__ __forceinline__ Obs3<MV> obs3_warp(Obs3<MV> v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = obs3_add(v, Obs3<MV>{obs_shfl(v.a, o), obs_shfl(v.b, o), obs_shfl(v.d, o)});
+  return v;
+}
+// Block-wide (NT threads): warp trees, then warp 0 over the warp totals;
+// the result is valid in thread 0.  Called by every thread.
+template <typename MV, int NT>
+__device__ __forceinline__ Obs3<MV> obs3_block(Obs3<MV> v, Obs3<MV>* s_w) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = obs3_warp(v);
+  if (lane == 0) s_w[warp] = v;
+  __syncthreads();
+  Obs3<MV> t{};
+  if (warp == 0) {
+    if (lane < NT / 32) t = s_w[lane];
+    t = obs3_warp(t);
+  }
+  __syncthreads();
+  return t;
+}
+
+__device__ __forceinline__ double ldcg_obs(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ df ldcg_obs(const df* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return {v.x, v.y};
+}
+
+template <typename MV>
+__device__ __forceinline__ void obs_row(const Dev& d, long long row, int r, long long n,
+                                        Obs3<MV> t) {
+  double* o = d.obs + 4 * (row * d.nreal + r);
+  const double a = obs_double(t.a);
+  o[0] = a;
+  o[1] = obs_double(t.b);
+  o[2] = obs_double(t.d);
+  o[3] = a / (double)n;
+}
+
 
 }  // namespace mt

@@ -20,157 +20,101 @@
 namespace mt {
 
 // ------------------------------------------- step epilogue (last CTA) --
-// Per-CTA partial observables -> the last CTA to finish reduces them in a
-// fixed order, appends a row to the ring, advances the step counter and
-// flips the buffer selectors.  Deterministic: no floating-point atomics.
-// Per-particle sums stay in the precision's own arithmetic (binary64, or
-// double-binary32 in MIXED); only per-CTA totals are converted to binary64.
-
-template <bool MIX>
-__device__ void finish_step(const Dev& d, typename Mass<MIX>::V a, typename Mass<MIX>::V b,
-                            bool valid, int flip_x, int flip_m) {
-  using MV = typename Mass<MIX>::V;
-  __shared__ MV s_part[kThreads / 32][3];
-  __shared__ double s_tot[kThreads / 32][3];
+// The last CTA of a step's final pass advances the step counter and flips
+// the buffer selectors.  Called by every thread.
+__device__ void finish_step(const Dev& d, int flip_x, int flip_m) {
   __shared__ bool s_last;
   Ctrl* c = d.ctrl;
-  const bool observe = d.observe_cap > 0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (observe) {
-    MV sa{}, sb{}, sd{};
-    if (valid) {
-      sa = a;
-      sb = b;
-      sd = obs_diff(a, b);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      sa = obs_add(sa, obs_shfl(sa, o));
-      sb = obs_add(sb, obs_shfl(sb, o));
-      sd = obs_add(sd, obs_shfl(sd, o));
-    }
-    if (lane == 0) {
-      s_part[warp][0] = sa;
-      s_part[warp][1] = sb;
-      s_part[warp][2] = sd;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      MV ta = s_part[0][0], tb = s_part[0][1], td = s_part[0][2];
-      for (int w = 1; w < (int)(blockDim.x / 32); ++w) {
-        ta = obs_add(ta, s_part[w][0]);
-        tb = obs_add(tb, s_part[w][1]);
-        td = obs_add(td, s_part[w][2]);
-      }
-      d.partials[4 * blockIdx.x + 0] = obs_double(ta);
-      d.partials[4 * blockIdx.x + 1] = obs_double(tb);
-      d.partials[4 * blockIdx.x + 2] = obs_double(td);
-    }
-  }
   if (threadIdx.x == 0) {
     __threadfence();
     s_last = atomicAdd(&c->done, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!s_last) return;
+  if (!s_last || threadIdx.x != 0) return;
   __threadfence();
-  if (observe && d.nreal == 1) {  // batches: k_real_obs after the step
-    double ta = 0, tb = 0, td = 0;
-    for (unsigned int blk = threadIdx.x; blk < gridDim.x; blk += blockDim.x) {
-      ta += __ldcg(&d.partials[4 * blk + 0]);
-      tb += __ldcg(&d.partials[4 * blk + 1]);
-      td += __ldcg(&d.partials[4 * blk + 2]);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      ta += __shfl_down_sync(0xffffffffu, ta, o);
-      tb += __shfl_down_sync(0xffffffffu, tb, o);
-      td += __shfl_down_sync(0xffffffffu, td, o);
-    }
-    if (lane == 0) {
-      s_tot[warp][0] = ta;
-      s_tot[warp][1] = tb;
-      s_tot[warp][2] = td;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      ta = tb = td = 0;
-      for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
-        ta += s_tot[w][0];
-        tb += s_tot[w][1];
-        td += s_tot[w][2];
-      }
-      const long long row = (long long)(c->step % (unsigned long long)d.observe_cap);
-      d.obs[4 * row + 0] = ta;
-      d.obs[4 * row + 1] = tb;
-      d.obs[4 * row + 2] = td;
-      d.obs[4 * row + 3] = d.n > 0 ? ta / (double)d.n : 0.0;
-    }
-  }
-  if (threadIdx.x == 0) {
-    c->step += 1;
-    c->xcur ^= flip_x;
-    c->mcur ^= flip_m;
-    c->done = 0;
-  }
+  c->step += 1;
+  c->xcur ^= flip_x;
+  c->mcur ^= flip_m;
+  c->done = 0;
 }
 
-// Observables of each realisation of a batch after a step of the general
-// pipeline: one CTA per realisation sums the masses of its slot range (the
-// state is sorted, so realisation r holds slots [off, off + n)) in the
-// precision's arithmetic, in a fixed order.
+// ------------------------------------------------------------ observables --
+// After every step (every path): sum A, sum B, sum (A - B) and mean A of each
+// realisation, one ring row per step.  Each realisation's slot range is cut
+// into fixed chunks of kObsChunk slots (the state keeps a realisation's
+// particles in its own range); a CTA sums one chunk -- each thread its
+// strided slots in order, then fixed shuffle trees -- in the precision's
+// own arithmetic (binary64, or double-binary32 in MIXED), and the CTA that
+// completes a realisation's last chunk adds its chunk sums (thread-strided
+// in order, then the block tree).  The result depends on
+// the state only, not on how the step was scheduled.
+
 template <bool MIX>
-__global__ void __launch_bounds__(kThreads) k_real_obs(Dev d) {
+__global__ void __launch_bounds__(kThreads) k_obs(Dev d) {
   using MS = Mass<MIX>;
   using MV = typename MS::V;
-  __shared__ MV s_part[kThreads / 32][3];
-  const int r = blockIdx.x;
-  const Real R = d.rt[r];
-  const Ctrl* c = d.ctrl;
+  constexpr int kPer = kObsChunk / kThreads;  // slots per thread
+  __shared__ Obs3<MV> s_w[kThreads / 32];
+  __shared__ bool s_last;
+  Ctrl* c = d.ctrl;
+  const int ch = blockIdx.x;
   const unsigned long long* M = d.M[c->mcur];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  MV sa{}, sb{}, sd{};
-  for (long long p = R.off + threadIdx.x; p < R.off + R.n; p += kThreads) {
-    const MV a = MS::load(M, p), b = MS::load(M, d.n + p);
-    sa = obs_add(sa, a);
-    sb = obs_add(sb, b);
-    sd = obs_add(sd, obs_diff(a, b));
-  }
+  // this thread's slots: loaded together, then added in slot order
+  const long long a0 = d.ochunk[ch], a1 = d.ochunk[ch + 1];
+  MV va[kPer], vb[kPer];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    sa = obs_add(sa, obs_shfl(sa, o));
-    sb = obs_add(sb, obs_shfl(sb, o));
-    sd = obs_add(sd, obs_shfl(sd, o));
+  for (int k = 0; k < kPer; ++k) {
+    const long long p = a0 + threadIdx.x + (long long)k * kThreads;
+    va[k] = p < a1 ? MS::load(M, p) : MV{};
+    vb[k] = p < a1 ? MS::load(M, d.n + p) : MV{};
   }
-  if (lane == 0) {
-    s_part[warp][0] = sa;
-    s_part[warp][1] = sb;
-    s_part[warp][2] = sd;
+  Obs3<MV> v{};
+#pragma unroll
+  for (int k = 0; k < kPer; ++k)
+    v = obs3_add(v, Obs3<MV>{va[k], vb[k], obs_diff(va[k], vb[k])});
+  const Obs3<MV> t = obs3_block<MV, kThreads>(v, s_w);
+  MV* part = reinterpret_cast<MV*>(d.opart);  // 8-byte words, 4 per chunk
+  const int r = d.ochr[ch];
+  const Real R = d.rt[r];
+  if (threadIdx.x == 0) {
+    part[4 * ch + 0] = t.a;
+    part[4 * ch + 1] = t.b;
+    part[4 * ch + 2] = t.d;
+    __threadfence();
+    s_last = atomicAdd(&d.ocnt[r], 1) + 1 == R.nch;
   }
   __syncthreads();
+  if (!s_last) return;
+  // the realisation's last chunk: thread t adds its chunks t, t + 256, ...
+  // in order (four in flight), then the block tree
+  __threadfence();
+  auto get = [&](int k) {
+    return Obs3<MV>{ldcg_obs(&part[4 * k + 0]), ldcg_obs(&part[4 * k + 1]),
+                    ldcg_obs(&part[4 * k + 2])};
+  };
+  const int k1 = R.ch0 + R.nch;
+  Obs3<MV> u{};
+  int k = R.ch0 + threadIdx.x;
+  for (; k + 3 * kThreads < k1; k += 4 * kThreads) {
+    const Obs3<MV> p0 = get(k), p1 = get(k + kThreads), p2 = get(k + 2 * kThreads),
+                   p3 = get(k + 3 * kThreads);
+    u = obs3_add(obs3_add(obs3_add(obs3_add(u, p0), p1), p2), p3);
+  }
+  for (; k < k1; k += kThreads) u = obs3_add(u, get(k));
+  u = obs3_block<MV, kThreads>(u, s_w);
   if (threadIdx.x == 0) {
-    MV ta = s_part[0][0], tb = s_part[0][1], td = s_part[0][2];
-    for (int w = 1; w < kThreads / 32; ++w) {
-      ta = obs_add(ta, s_part[w][0]);
-      tb = obs_add(tb, s_part[w][1]);
-      td = obs_add(td, s_part[w][2]);
-    }
     const long long row = (long long)((c->step - 1) % (unsigned long long)d.observe_cap);
-    double* o = d.obs + 4 * (row * d.nreal + r);
-    const double a = obs_double(ta);
-    o[0] = a;
-    o[1] = obs_double(tb);
-    o[2] = obs_double(td);
-    o[3] = a / (double)R.n;
+    obs_row(d, row, r, R.n, u);
+    d.ocnt[r] = 0;
   }
 }
 
-cudaError_t launch_real_obs(const Dev& d, int precision, cudaStream_t s) {
-  if (d.observe_cap <= 0 || d.nreal <= 1) return cudaSuccess;
+cudaError_t launch_obs(const Dev& d, int precision, cudaStream_t s) {
+  if (d.observe_cap <= 0 || d.nochunk <= 0) return cudaSuccess;
   if (precision == MT_MIXED)
-    k_real_obs<true><<<d.nreal, kThreads, 0, s>>>(d);
+    k_obs<true><<<d.nochunk, kThreads, 0, s>>>(d);
   else
-    k_real_obs<false><<<d.nreal, kThreads, 0, s>>>(d);
+    k_obs<false><<<d.nochunk, kThreads, 0, s>>>(d);
   return cudaGetLastError();
 }
 
@@ -278,7 +222,7 @@ __global__ void __launch_bounds__(kThreads) k_exchange_walk(Dev d, int sp) {
     MS::store(d.M[mc] + sq.oa, p, A);
     if (sq.store_b) MS::store(d.M[mc] + sq.ob, p, B);
   }
-  if (!TR) finish_step<MIX>(d, A, B, valid, 1, 0);
+  if (!TR) finish_step(d, 1, 0);
 }
 
 // |dx| <= S in one unsigned comparison (1-d)
@@ -469,7 +413,7 @@ __global__ void __launch_bounds__(kThreads) k_exchange_tile(Dev d, int sp) {
     MS::store(d.M[mc] + sq.oa, p, A);
     if (sq.store_b) MS::store(d.M[mc] + sq.ob, p, B);
   }
-  if (!TR) finish_step<MIX>(d, A, B, valid, 1, 0);
+  if (!TR) finish_step(d, 1, 0);
 }
 
 // ================================================== 1-d SPaM (stored P) ==
@@ -602,7 +546,7 @@ __global__ void __launch_bounds__(kThreads) k_band_exchange(Dev d, int sp) {
     MS::store(d.M[mc] + sq.oa, p, A);
     if (sq.store_b) MS::store(d.M[mc] + sq.ob, p, B);
   }
-  if (!TR) finish_step<MIX>(d, A, B, valid, 1, 0);
+  if (!TR) finish_step(d, 1, 0);
 }
 
 // =============================================================== 2-d cells ==
@@ -712,7 +656,7 @@ __global__ void __launch_bounds__(kThreads) k_exchange_cell2(Dev d, int sp) {
     MS::store(d.M[mc] + sq.oa, p, A);
     if (sq.store_b) MS::store(d.M[mc] + sq.ob, p, B);
   }
-  if (!TR) finish_step<MIX>(d, A, B, valid, 1, 0);
+  if (!TR) finish_step(d, 1, 0);
 }
 
 // ============================================================ brute force ==
@@ -821,7 +765,7 @@ __global__ void __launch_bounds__(kThreads) k_exchange_brute(Dev d, int sp) {
     MS::store(d.M[mc ^ 1] + sq.oa, p, A);
     if (sq.store_b) MS::store(d.M[mc ^ 1] + sq.ob, p, B);
   }
-  if (!TR) finish_step<MIX>(d, A, B, valid, 0, 1);
+  if (!TR) finish_step(d, 0, 1);
 }
 
 // Species 2 and up into the sorted slots (the row-sum pass moved A and B).

@@ -199,6 +199,27 @@ def test_bitwise_deterministic(precision):
         assert np.array_equal(u, w)
 
 
+def test_observables_bitwise_deterministic_on_a_large_system():
+    """More than one wave of segments (the first tier takes them by ticket)
+    and the predicted-segment kernel beside it: two runs give the same
+    observables bit for bit, and equal to the sums of the masses read back."""
+    n, L = 400000, 4.0e5
+    x = synth.uniform_positions(n, L, seed=12)
+    x[0, :4000] = np.random.default_rng(12).uniform(0.0, 4.0, 4000)
+    A, B = synth.uniform_masses(n, seed=12)
+    outs = []
+    for _ in range(2):
+        sim = make(n, L, precision=mt.MT_MIXED, seed=5, v=(0.5, 0.0), observe_cap=40)
+        assert sim.params.seg_target > 0
+        sim.upload(x, A, B)
+        sim.run(30)
+        outs.append((sim.observables(), *sim.masses()))
+        sim.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    a, b = outs[0][1], outs[0][2]
+    np.testing.assert_allclose(outs[0][0][-1], O.observables(a, b), rtol=1e-12, atol=1e-8)
+
+
 def test_run_graph_equals_step_loop():
     n, L = 5000, 5000.0
     x = synth.uniform_positions(n, L, seed=12)
