@@ -343,9 +343,11 @@ mt_status mt_read_ticks(mt_handle* h, int64_t* X, int32_t mem);
 
 /* Observables of the last min(steps, cap, observe_cap) steps, oldest first,
  * 4 doubles each: sum A, sum B, sum (A - B), mean A after the step (a batch
- * handle: 4 per realisation, realisation 0 first).  out: host memory for
- * 4*cap doubles (4*count*cap for a batch).  *count receives the rows
- * written. */
+ * handle: 4 per realisation, realisation 0 first).  The sums are taken after
+ * every step over fixed chunks of the state in a fixed order, in the
+ * precision's arithmetic (binary64, or double-binary32 in MIXED), so they are
+ * bitwise reproducible.  out: host memory for 4*cap doubles (4*count*cap for
+ * a batch).  *count receives the rows written. */
 mt_status mt_read_observables(mt_handle* h, double* out, int64_t cap,
                               int64_t* count);
 
