@@ -49,6 +49,40 @@ __device__ void finish_step(const Dev& d, int flip_x, int flip_m) {
 // in order, then the block tree).  The result depends on
 // the state only, not on how the step was scheduled.
 
+// A thread's sums over its slots, in slot order: binary64, or in MIXED
+// Sum2-style compensated sums of the double-binary32 masses (each high part
+// added with Knuth's two-sum, the rounding errors and the low parts collected
+// in a second term; as accurate here as double-binary32 additions, at a third
+// of the operations).
+template <bool MIX>
+struct ThreadObs;
+template <>
+struct ThreadObs<false> {
+  Obs3<double> v{};
+  __device__ __forceinline__ void add(double a, double b) {
+    v = obs3_add(v, Obs3<double>{a, b, a - b});
+  }
+  __device__ __forceinline__ Obs3<double> value() const { return v; }
+};
+template <>
+struct ThreadObs<true> {
+  kahan a{0.f, 0.f}, b{0.f, 0.f}, d{0.f, 0.f};
+  static __device__ __forceinline__ void put(kahan& k, float hi, float lo) {
+    const df e = two_sum(k.s, hi);
+    k.s = e.hi;
+    k.c = __fadd_rn(k.c, __fadd_rn(e.lo, lo));
+  }
+  __device__ __forceinline__ void add(df A, df B) {
+    put(a, A.hi, A.lo);
+    put(b, B.hi, B.lo);
+    put(d, A.hi, A.lo);
+    put(d, -B.hi, -B.lo);
+  }
+  __device__ __forceinline__ Obs3<df> value() const {
+    return {fast_two_sum(a.s, a.c), fast_two_sum(b.s, b.c), fast_two_sum(d.s, d.c)};
+  }
+};
+
 template <bool MIX>
 __global__ void __launch_bounds__(kThreads) k_obs(Dev d) {
   using MS = Mass<MIX>;
@@ -68,11 +102,10 @@ __global__ void __launch_bounds__(kThreads) k_obs(Dev d) {
     va[k] = p < a1 ? MS::load(M, p) : MV{};
     vb[k] = p < a1 ? MS::load(M, d.n + p) : MV{};
   }
-  Obs3<MV> v{};
+  ThreadObs<MIX> acc;
 #pragma unroll
-  for (int k = 0; k < kPer; ++k)
-    v = obs3_add(v, Obs3<MV>{va[k], vb[k], obs_diff(va[k], vb[k])});
-  const Obs3<MV> t = obs3_block<MV, kThreads>(v, s_w);
+  for (int k = 0; k < kPer; ++k) acc.add(va[k], vb[k]);
+  const Obs3<MV> t = obs3_block<MV, kThreads>(acc.value(), s_w);
   MV* part = reinterpret_cast<MV*>(d.opart);  // 8-byte words, 4 per chunk
   const int r = d.ochr[ch];
   const Real R = d.rt[r];
