@@ -112,8 +112,8 @@ typedef struct mt_params {
                            system of Eq. 4 per species, all with the same
                            weights; cost linear in the species count).  Only
                            A and B react; the others are conservative.
-                           More than 2: single systems only, and the step
-                           runs as the multi-kernel pipeline */
+                           More than 2: the step runs as the multi-kernel
+                           pipeline */
   int32_t stored_p;     /* 0: weights computed where they are used (two
                            passes, each pair's weight evaluated in both).
                            1 or more: the SPaM form (Sec. 6: the sparse

@@ -161,7 +161,6 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
   if (p.species < 2 || p.species > MT_MAX_SPECIES)
     return fail(MT_ERR_INVALID, "species must be 0 or in [2, %d] (got %d)", MT_MAX_SPECIES,
                 p.species);
-  if (p.species > 2 && b) return fail(MT_ERR_INVALID, "batches carry two species");
   if (p.stored_p < 0) return fail(MT_ERR_INVALID, "stored_p must be >= 0");
   if (p.stored_p > 0 && (p.dim != 1 || p.search != MT_SEARCH_CELL || b))
     return fail(MT_ERR_INVALID, "stored_p needs a single 1-d system with MT_SEARCH_CELL");

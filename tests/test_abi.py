@@ -188,8 +188,9 @@ def test_species_rules():
         with pytest.raises(mt.MtError) as e:
             mt.mt_resolve(mt.mt_params_init(n=10, **bad))
         assert e.value.status == mt.MT_ERR_INVALID
-    with pytest.raises(mt.MtError):
-        mt.mt_batch_resolve(_batch_params(species=3), mt.make_batch([10], [10.0]))
+    # a batch with more species runs the multi-kernel pipeline
+    rb = mt.mt_batch_resolve(_batch_params(species=3), mt.make_batch([100, 50], [100.0, 50.0]))
+    assert rb.species == 3 and rb.seg_target == 0
 
 
 def test_stored_p_rules():

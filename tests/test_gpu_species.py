@@ -129,3 +129,46 @@ def test_server_refuses_more_species():
         srv.submit(p, np.linspace(1, 99, 100), np.ones(100), np.zeros(100), 3)
     assert e.value.status == mt.MT_ERR_INVALID
     srv.close()
+
+
+@pytest.mark.parametrize("precision", [mt.MT_FP64, mt.MT_MIXED])
+def test_species_in_a_batch(precision):
+    """A batch of realisations carrying four species runs the multi-kernel
+    pipeline; every realisation matches the oracle on its own, and species 2
+    and 3 of each realisation are read back in the caller's order."""
+    ns, Ls = [700, 1500, 400], [700.0, 1200.0, 500.0]
+    S = 4
+    k = 28  # cutoff 3 sqrt(4 D_mt dt) = 2.32: 2.32 2^k < 2^30
+    p = mt.mt_params_init(dim=1, L=(1.0,), D_mt=0.15, D_rw=0.2, precision=precision, species=S,
+                          frac_bits=k, observe_cap=4)
+    sim = mt.Simulation(p, batch=mt.make_batch(ns, Ls))
+    assert sim.params.seg_target == 0
+    xs = [synth.uniform_positions(n, L, seed=70 + i) for i, (n, L) in enumerate(zip(ns, Ls))]
+    Ms = [species_masses(n, S, seed=80 + i) for i, n in enumerate(ns)]
+    sim.upload(np.concatenate([x[0] for x in xs])[None, :], np.concatenate([m[0] for m in Ms]),
+               np.concatenate([m[1] for m in Ms]))
+    for s in range(2, S):
+        sim.set_species(s, np.concatenate([m[s] for m in Ms]))
+    offs = np.cumsum([0] + ns)
+    cur = []
+    for i, (n, L) in enumerate(zip(ns, Ls)):
+        po = O.params(frac_bits=k, L=(L,), D_mt=0.15, D_rw=0.2)
+        cur.append([O.quantize(xs[i], k), [m.copy() for m in Ms[i]], po])
+    xi = synth.normals(4, 1, sum(ns), seed=90)
+    for s in range(4):
+        sim.set_noise(xi[s])
+        sim.step()
+        for i, c in enumerate(cur):
+            c[0], c[1] = oracle_step_species(c[2], c[0], xi[s][:, offs[i]:offs[i + 1]], c[1])
+    T = sim.ticks()[0]
+    got = [sim.species(s) for s in range(S)]
+    for i, c in enumerate(cur):
+        sl = slice(offs[i], offs[i + 1])
+        assert np.array_equal(T[sl], c[0][0])
+        for s in range(S):
+            assert_masses(got[s][sl], c[1][s], TOL[precision], f"realisation {i} species {s}")
+    obs = sim.observables()
+    for i in range(len(ns)):  # each realisation's row sums its own A and B
+        sl = slice(offs[i], offs[i + 1])
+        np.testing.assert_allclose(obs[-1, i, :2], [got[0][sl].sum(), got[1][sl].sum()],
+                                   rtol=1e-12)
