@@ -786,7 +786,11 @@ __global__ void __launch_bounds__(kThreads) k_exchange_brute(Dev d, int sp) {
         if (CUT) {
           if (DIM == 1 ? !within1(dx, d.S) : !in_range2(dx, dy, d.S)) continue;
         }
-        const T P = normalised<T>(d.norm, W::eval(d, dx, dy), ip, s_ri[jj]);
+        const T w = W::eval(d, dx, dy);
+        // a weight that underflowed to zero adds exact zeros: skip the
+        // flux arithmetic (the full matrix still evaluates every weight)
+        if (w == T(0)) continue;
+        const T P = normalised<T>(d.norm, w, ip, s_ri[jj]);
         MS::acc(dA, P, MS::diff(s_a[jj], A));
         MS::acc(dB, P, MS::diff(s_b[jj], B));
       }
