@@ -105,7 +105,8 @@ typedef struct mt_params {
                            MT_WALLS_PERIODIC: the domain wraps, positions
                            live in [0, L) and pairs take the minimum-image
                            separation; needs s_max < L/2 per axis (any
-                           value with MT_SEARCH_FULL); single systems only */
+                           value with MT_SEARCH_FULL); in a batch, each
+                           realisation wraps on its own domain */
   int32_t species;      /* chemical species each particle carries: 0 or 2 =
                            A and B; 3 .. MT_MAX_SPECIES adds species 2, 3,
                            ... moved by the same transfer (Sec. 1.1: one

@@ -165,7 +165,6 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
   if (p.stored_p > 0 && (p.dim != 1 || p.search != MT_SEARCH_CELL || b))
     return fail(MT_ERR_INVALID, "stored_p needs a single 1-d system with MT_SEARCH_CELL");
   const bool periodic = p.walls == MT_WALLS_PERIODIC;
-  if (periodic && b) return fail(MT_ERR_INVALID, "batches use reflecting walls");
   if (p.frac_bits == 0) p.frac_bits = default_frac_bits(p);
   const int k = p.frac_bits;
   if (k < 1 || k > 62) return fail(MT_ERR_INVALID, "frac_bits must be in [1, 62] (got %d)", k);
@@ -185,10 +184,15 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
     return fail(MT_ERR_INVALID, "sqrt(2 D_rw dt) 2^frac_bits is too large for the grid");
   D.bq = (float)bw;
   D.S = (long long)std::floor(std::ldexp(p.cutoff, k));
-  if (periodic && p.search != MT_SEARCH_FULL)
+  if (periodic && p.search != MT_SEARCH_FULL) {
     for (int a = 0; a < p.dim; ++a)
-      if (2 * D.S >= D.Lq[a])
+      if (!b && 2 * D.S >= D.Lq[a])
         return fail(MT_ERR_INVALID, "periodic walls need the cutoff below L[%d]/2", a);
+    if (b)
+      for (int r = 0; r < b->count; ++r)
+        if (2 * D.S >= std::llrint(std::ldexp(b->L[r], k)))
+          return fail(MT_ERR_INVALID, "realisation %d: periodic walls need the cutoff below L/2", r);
+  }
   // cell grid
   std::vector<long long> lq;  // batch: each realisation's length in ticks
   double lq_sum = (double)D.Lq[0];

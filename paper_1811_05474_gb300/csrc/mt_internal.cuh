@@ -179,6 +179,24 @@ __device__ __forceinline__ long long wrap(long long y, long long Lq) {
   return m < 0 ? m + Lq : m;
 }
 
+// Periodic walls in 1-d: the ring of sorted slots a particle's walks go
+// around -- its realisation's slot range [off, off + n) -- and the domain
+// length the separations wrap at (a single system is realisation 0).
+struct Ring {
+  long long off, n, Lq;
+};
+__device__ __forceinline__ Ring ring_of(const Dev& d, int id) {
+  const Real& R = d.rt[id >> d.lbits];
+  return {R.off, R.n, R.Lq};
+}
+// Slot k steps to the right (left for k < 0, |k| < n) of slot p on ring g.
+__device__ __forceinline__ long long ring_step(const Ring& g, long long p, long long k) {
+  long long q = p + k;
+  if (q < g.off) q += g.n;
+  else if (q >= g.off + g.n) q -= g.n;
+  return q;
+}
+
 // Periodic walls: the minimum-image separation of two positions in [0, Lq),
 // in (-Lq/2, Lq/2].
 __device__ __forceinline__ long long min_image(long long s, long long Lq) {

@@ -178,13 +178,12 @@ __global__ void k_pairs_walk(Dev d, int* pi, int* pj, long long cap) {
     }
     return;
   }
-  // periodic: walk right around the ring (each pair is found from the
-  // particle that has the other on its right within Smax)
-  for (long long k = 1; k < d.n; ++k) {
-    long long q = p + k;
-    q = q >= d.n ? q - d.n : q;
-    long long D = X[q] - x;
-    D = D < 0 ? D + d.Lq[0] : D;
+  // periodic: walk right around the realisation's ring (each pair is found
+  // from the particle that has the other on its right within Smax)
+  const Ring g = ring_of(d, id[p]);
+  for (long long k = 1; k < g.n; ++k) {
+    const long long q = ring_step(g, p, k);
+    const long long D = wrap(X[q] - x, g.Lq);
     if (D > d.S) break;
     emit(d, id[p], id[q], pi, pj, cap);
   }

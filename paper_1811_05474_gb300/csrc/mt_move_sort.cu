@@ -47,8 +47,10 @@ __global__ void __launch_bounds__(kThreads) k_move(Dev d) {
     for (int a = 0; a < DIM; ++a) {
       // Eq. 2 on the grid: drift + rint(b * xi), then the wall mirror.
       const long long step = float_to_ll_rn(__fmul_rn(d.bq, z[a]));
-      if (d.periodic)  // single systems only: base = 0
-        pos[a] = wrap(pos[a] + d.drift[a] + step, a == 0 ? R->Lq : d.Lq[a]);
+      if (d.periodic && a == 0)
+        pos[0] = base + wrap(pos[0] - base + d.drift[0] + step, R->Lq);
+      else if (d.periodic)
+        pos[a] = wrap(pos[a] + d.drift[a] + step, d.Lq[a]);
       else if (a == 0)
         pos[0] = base + reflect(pos[0] - base + d.drift[0] + step, R->Lq);
       else

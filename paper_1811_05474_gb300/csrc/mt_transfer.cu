@@ -175,17 +175,16 @@ __global__ void __launch_bounds__(kThreads) k_rowsum_walk(Dev d) {
       r += W::eval(d, D, 0);
     }
   } else {
-    // periodic: the walks continue around the ring (2 Smax < L, so no slot
-    // is reached from both sides)
-    for (long long k = 1; k < d.n; ++k) {
-      const long long q = p - k < 0 ? p - k + d.n : p - k;
-      const long long D = wrap(x - Xs[q], d.Lq[0]);
+    // periodic: the walks continue around the realisation's ring (2 Smax <
+    // L, so no slot is reached from both sides)
+    const Ring g = ring_of(d, d.id[xc][d.src[p]]);
+    for (long long k = 1; k < g.n; ++k) {
+      const long long D = wrap(x - Xs[ring_step(g, p, -k)], g.Lq);
       if (D > d.S) break;
       r += W::eval(d, D, 0);
     }
-    for (long long k = 1; k < d.n; ++k) {
-      const long long q = p + k >= d.n ? p + k - d.n : p + k;
-      const long long D = wrap(Xs[q] - x, d.Lq[0]);
+    for (long long k = 1; k < g.n; ++k) {
+      const long long D = wrap(Xs[ring_step(g, p, k)] - x, g.Lq);
       if (D > d.S) break;
       r += W::eval(d, D, 0);
     }
@@ -238,15 +237,16 @@ __global__ void __launch_bounds__(kThreads) k_exchange_walk(Dev d, int sp) {
         pair(q, D);
       }
     } else {
-      for (long long k = 1; k < d.n; ++k) {
-        const long long q = p - k < 0 ? p - k + d.n : p - k;
-        const long long D = wrap(x - Xs[q], d.Lq[0]);
+      const Ring g = ring_of(d, d.id[xc ^ 1][p]);
+      for (long long k = 1; k < g.n; ++k) {
+        const long long q = ring_step(g, p, -k);
+        const long long D = wrap(x - Xs[q], g.Lq);
         if (D > d.S) break;
         pair(q, D);
       }
-      for (long long k = 1; k < d.n; ++k) {
-        const long long q = p + k >= d.n ? p + k - d.n : p + k;
-        const long long D = wrap(Xs[q] - x, d.Lq[0]);
+      for (long long k = 1; k < g.n; ++k) {
+        const long long q = ring_step(g, p, k);
+        const long long D = wrap(Xs[q] - x, g.Lq);
         if (D > d.S) break;
         pair(q, D);
       }

@@ -169,9 +169,13 @@ def test_periodic_walls_rules():
         assert e.value.status == mt.MT_ERR_INVALID
     mt.mt_resolve(mt.mt_params_init(dim=2, n=100, L=(10.0, 10.0), search=mt.MT_SEARCH_BRUTE,
                                     walls=mt.MT_WALLS_PERIODIC))
+    # batches: each realisation wraps on its own domain, which must exceed 2 s_max
+    rb = mt.mt_batch_resolve(mt.mt_params_init(dim=1, L=(1.0,), walls=mt.MT_WALLS_PERIODIC),
+                             mt.make_batch([10, 20], [10.0, 20.0]))
+    assert rb.walls == mt.MT_WALLS_PERIODIC and rb.seg_target == 0
     with pytest.raises(mt.MtError):
         mt.mt_batch_resolve(mt.mt_params_init(dim=1, L=(1.0,), walls=mt.MT_WALLS_PERIODIC),
-                            mt.make_batch([10], [10.0]))
+                            mt.make_batch([10, 20], [10.0, 3.0]))
 
 
 def test_species_rules():

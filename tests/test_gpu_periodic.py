@@ -88,3 +88,45 @@ def test_periodic_pair_across_the_wall():
         out.append(sim.masses()[0])
     assert 0.0 < out[0][1] < 0.5
     assert out[1][1] == 0.0
+
+
+@pytest.mark.parametrize("precision", [mt.MT_FP64, mt.MT_MIXED])
+def test_periodic_batch_each_realisation_wraps_on_its_own(precision):
+    """A batch with periodic walls: every realisation wraps on its own domain
+    (its walks go around its own slot range) and equals the oracle of that
+    realisation alone; the pair sets never join two realisations."""
+    ns, Ls = [800, 1500, 300], [600.0, 1500.0, 250.0]
+    k = 29
+    p = mt.mt_params_init(dim=1, L=(1.0,), v=(0.6,), D_rw=0.3, precision=precision, frac_bits=k,
+                          walls=mt.MT_WALLS_PERIODIC, observe_cap=4)
+    sim = mt.Simulation(p, batch=mt.make_batch(ns, Ls))
+    assert sim.params.seg_target == 0
+    xs = [synth.uniform_positions(n, L, seed=60 + i) for i, (n, L) in enumerate(zip(ns, Ls))]
+    AB = [synth.uniform_masses(n, seed=61 + i) for i, n in enumerate(ns)]
+    sim.upload(np.concatenate([x[0] for x in xs])[None, :], np.concatenate([a for a, _ in AB]),
+               np.concatenate([b for _, b in AB]))
+    offs = np.cumsum([0] + ns)
+    cur = []
+    for i, L in enumerate(Ls):
+        po = O.params(frac_bits=k, L=(L,), v=(0.6,), D_rw=0.3, walls=O.WALLS_PERIODIC)
+        cur.append([O.quantize(xs[i], k), AB[i][0].copy(), AB[i][1].copy(), po])
+    xi = synth.normals(6, 1, sum(ns), seed=62)
+    for s in range(6):
+        sim.set_noise(xi[s])
+        sim.step()
+        for i, c in enumerate(cur):
+            c[0], c[1], c[2] = O.step(c[3], c[0], xi[s][:, offs[i]:offs[i + 1]], c[1], c[2])
+    T = sim.ticks()[0]
+    ga, gb = sim.masses()
+    for i, c in enumerate(cur):
+        sl = slice(offs[i], offs[i + 1])
+        assert np.array_equal(T[sl], c[0][0]), f"realisation {i} positions"
+        assert_masses(ga[sl], c[1], TOL[precision], f"A of realisation {i}")
+        assert_masses(gb[sl], c[2], TOL[precision], f"B of realisation {i}")
+    gi, gj = sim.pairs()
+    got = set(zip(gi.tolist(), gj.tolist()))
+    want = set()
+    for i, c in enumerate(cur):
+        oi, oj = O.pairs_brute(c[3], c[0])
+        want |= set(zip((oi + offs[i]).tolist(), (oj + offs[i]).tolist()))
+    assert len(got) == len(gi) and got == want
