@@ -125,7 +125,7 @@ typedef struct mt_params {
                            order), and both passes read it; 1 chooses b from
                            the mean density with headroom, b >= 2 sets it.
                            Entries past the band are recomputed, so any b is
-                           correct.  1-d MT_SEARCH_CELL, single systems */
+                           correct.  1-d MT_SEARCH_CELL */
 } mt_params;
 
 #define MT_MAX_SPECIES 8

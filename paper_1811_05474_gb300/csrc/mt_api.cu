@@ -162,8 +162,8 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
     return fail(MT_ERR_INVALID, "species must be 0 or in [2, %d] (got %d)", MT_MAX_SPECIES,
                 p.species);
   if (p.stored_p < 0) return fail(MT_ERR_INVALID, "stored_p must be >= 0");
-  if (p.stored_p > 0 && (p.dim != 1 || p.search != MT_SEARCH_CELL || b))
-    return fail(MT_ERR_INVALID, "stored_p needs a single 1-d system with MT_SEARCH_CELL");
+  if (p.stored_p > 0 && (p.dim != 1 || p.search != MT_SEARCH_CELL))
+    return fail(MT_ERR_INVALID, "stored_p needs 1-d MT_SEARCH_CELL");
   const bool periodic = p.walls == MT_WALLS_PERIODIC;
   if (p.frac_bits == 0) p.frac_bits = default_frac_bits(p);
   const int k = p.frac_bits;

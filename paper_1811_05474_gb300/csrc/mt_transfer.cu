@@ -468,18 +468,30 @@ __device__ __forceinline__ long long band_at(const Dev& d, long long q, long lon
   return (((q >> 5) * d.band_cap) + (k - 1)) * 32 + (q & 31);
 }
 
-// Slot k steps to the right (left for k < 0) of p, around the ring when the
-// walls are periodic (a walk never takes more than n - 1 steps).
-__device__ __forceinline__ long long ring(const Dev& d, long long p, long long k) {
-  long long q = p + k;
-  if (d.periodic) q = q < 0 ? q + d.n : (q >= d.n ? q - d.n : q);
-  return q;
+// The slots a particle's walks cover: with periodic walls its realisation's
+// ring; else the whole sorted range (realisations are separated by more than
+// Smax, so the cutoff ends every walk inside its own realisation).
+__device__ __forceinline__ Ring walk_ring(const Dev& d, int id) {
+  return d.periodic ? ring_of(d, id) : Ring{0, d.n, 0};
+}
+
+// Slot k steps to the right (left for k < 0) of p.
+__device__ __forceinline__ long long ring(const Dev& d, const Ring& g, long long p, long long k) {
+  return d.periodic ? ring_step(g, p, k) : p + k;
+}
+
+// The longest right and left walks from slot p.
+__device__ __forceinline__ long long walk_right(const Dev& d, const Ring& g, long long p) {
+  return d.periodic ? g.n - 1 : d.n - 1 - p;
+}
+__device__ __forceinline__ long long walk_left(const Dev& d, const Ring& g, long long p) {
+  return d.periodic ? g.n - 1 : p;
 }
 
 // Tick distance from slot q up to slot p (p to the right of q).
-__device__ __forceinline__ long long gap(const Dev& d, const long long* Xs, long long q,
-                                         long long p) {
-  return d.periodic ? wrap(Xs[p] - Xs[q], d.Lq[0]) : Xs[p] - Xs[q];
+__device__ __forceinline__ long long gap(const Dev& d, const Ring& g, const long long* Xs,
+                                         long long q, long long p) {
+  return d.periodic ? wrap(Xs[p] - Xs[q], g.Lq) : Xs[p] - Xs[q];
 }
 
 template <bool MIX>
@@ -491,23 +503,24 @@ __global__ void __launch_bounds__(kThreads) k_band_build(Dev d) {
   const int xc = d.ctrl->xcur, mc = d.ctrl->mcur;
   const long long* Xs = d.X[xc ^ 1];
   T* band = static_cast<T*>(d.band);
+  const int s = d.src[p];
+  const Ring g = walk_ring(d, d.id[xc][s]);
   RowSum<MIX> r(T(0));
   long long k = 1;
-  const long long kr = d.periodic ? d.n - 1 : d.n - 1 - p;
+  const long long kr = walk_right(d, g, p);
   for (; k <= kr; ++k) {
-    const long long D = gap(d, Xs, p, ring(d, p, k));
+    const long long D = gap(d, g, Xs, p, ring(d, g, p, k));
     if (D > d.S) break;
     const T w = W::eval(d, D, 0);
     if (k <= d.band_cap) band[band_at(d, p, k)] = w;
     r.add(w);
   }
   d.cnt[p] = (int)(k - 1);
-  const long long kl = d.periodic ? d.n - 1 : p;
+  const long long kl = walk_left(d, g, p);
   for (k = 1; k <= kl; ++k)
-    if (gap(d, Xs, ring(d, p, -k), p) > d.S) break;
+    if (gap(d, g, Xs, ring(d, g, p, -k), p) > d.S) break;
   d.cnt[d.n + p] = (int)(k - 1);
   static_cast<T*>(d.rinv)[p] = r.value();  // right part of r_p, completed by band_rowsum
-  const int s = d.src[p];
   d.id[xc ^ 1][p] = d.id[xc][s];
   gather_masses(d, mc, p, s);
 }
@@ -519,15 +532,17 @@ __global__ void __launch_bounds__(kThreads) k_band_rowsum(Dev d) {
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (p >= d.n) return;
   const T* band = static_cast<const T*>(d.band);
+  const int xc = d.ctrl->xcur;
+  const Ring g = walk_ring(d, d.id[xc ^ 1][p]);
   RowSum<MIX> r(T(1));  // self
   r.add(static_cast<const T*>(d.rinv)[p]);  // right part
   const int kl = d.cnt[d.n + p];
   const int kb = kl < d.band_cap ? kl : d.band_cap;
 #pragma unroll 4
-  for (int k = 1; k <= kb; ++k) r.add(band[band_at(d, ring(d, p, -k), k)]);
+  for (int k = 1; k <= kb; ++k) r.add(band[band_at(d, ring(d, g, p, -k), k)]);
   if (kl > kb) {
-    const long long* Xs = d.X[d.ctrl->xcur ^ 1];
-    for (int k = kb + 1; k <= kl; ++k) r.add(W::eval(d, gap(d, Xs, ring(d, p, -k), p), 0));
+    const long long* Xs = d.X[xc ^ 1];
+    for (int k = kb + 1; k <= kl; ++k) r.add(W::eval(d, gap(d, g, Xs, ring(d, g, p, -k), p), 0));
   }
   store_rinv<MIX>(d, p, r.value());
 }
@@ -545,6 +560,7 @@ __global__ void __launch_bounds__(kThreads) k_band_exchange(Dev d, int sp) {
   MV A{}, B{};
   if (valid) {
     const long long* Xs = d.X[xc ^ 1];
+    const Ring g = walk_ring(d, d.id[xc ^ 1][p]);
     const unsigned long long* MA = d.M[mc ^ 1] + sq.oa;
     const unsigned long long* MB = d.M[mc ^ 1] + sq.ob;
     const T* band = static_cast<const T*>(d.band);
@@ -562,18 +578,18 @@ __global__ void __launch_bounds__(kThreads) k_band_exchange(Dev d, int sp) {
     const int br = kr < d.band_cap ? kr : d.band_cap;
 #pragma unroll 2
     for (int k = 1; k <= bl; ++k) {
-      const long long q = ring(d, p, -k);
+      const long long q = ring(d, g, p, -k);
       pair(q, band[band_at(d, q, k)]);
     }
     for (int k = bl + 1; k <= kl; ++k) {
-      const long long q = ring(d, p, -k);
-      pair(q, W::eval(d, gap(d, Xs, q, p), 0));
+      const long long q = ring(d, g, p, -k);
+      pair(q, W::eval(d, gap(d, g, Xs, q, p), 0));
     }
 #pragma unroll 2
-    for (int k = 1; k <= br; ++k) pair(ring(d, p, k), band[band_at(d, p, k)]);
+    for (int k = 1; k <= br; ++k) pair(ring(d, g, p, k), band[band_at(d, p, k)]);
     for (int k = br + 1; k <= kr; ++k) {
-      const long long q = ring(d, p, k);
-      pair(q, W::eval(d, gap(d, Xs, p, q), 0));
+      const long long q = ring(d, g, p, k);
+      pair(q, W::eval(d, gap(d, g, Xs, p, q), 0));
     }
     MS::update(A, B, dA, dB, TR ? 0 : d.react);
     MS::store(d.M[mc] + sq.oa, p, A);

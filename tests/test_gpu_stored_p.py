@@ -94,3 +94,41 @@ def test_stored_p_equals_on_the_fly(precision):
     tol = 1e-12 if precision == mt.MT_FP64 else 1e-6
     for a, b in zip(out[0], out[1]):
         assert_masses(b, a, tol, "stored vs on the fly")
+
+
+@pytest.mark.parametrize("walls", [mt.MT_WALLS_REFLECT, mt.MT_WALLS_PERIODIC])
+@pytest.mark.parametrize("precision", [mt.MT_FP64, mt.MT_MIXED])
+def test_stored_p_in_a_batch(walls, precision):
+    """The SPaM form for a batch: realisations at the paper's density side by
+    side (periodic: each wraps on its own ring), each equal to the oracle of
+    that realisation alone, with a band narrow enough that some weights are
+    recomputed past it."""
+    ns, Ls = [1500, 900, 2400], [7.5, 4.5, 12.0]
+    k = 29
+    p = mt.mt_params_init(dim=1, L=(1.0,), D_mt=0.5, D_rw=0.5, dt=0.1, precision=precision,
+                          frac_bits=k, walls=walls, stored_p=200, observe_cap=4)
+    sim = mt.Simulation(p, batch=mt.make_batch(ns, Ls))
+    assert sim.params.stored_p == 200 and sim.params.seg_target == 0
+    xs = [synth.uniform_positions(n, L, seed=40 + i) for i, (n, L) in enumerate(zip(ns, Ls))]
+    AB = [synth.uniform_masses(n, seed=50 + i) for i, n in enumerate(ns)]
+    sim.upload(np.concatenate([x[0] for x in xs])[None, :], np.concatenate([a for a, _ in AB]),
+               np.concatenate([b for _, b in AB]))
+    offs = np.cumsum([0] + ns)
+    cur = []
+    for i, L in enumerate(Ls):
+        po = O.params(frac_bits=k, L=(L,), D_mt=0.5, D_rw=0.5, dt=0.1, walls=walls)
+        cur.append([O.quantize(xs[i], k), AB[i][0].copy(), AB[i][1].copy(), po])
+    xi = synth.normals(3, 1, sum(ns), seed=55)
+    for s in range(3):
+        sim.set_noise(xi[s])
+        sim.step()
+        for i, c in enumerate(cur):
+            Xo, Ms = oracle_step_species(c[3], c[0], xi[s][:, offs[i]:offs[i + 1]], [c[1], c[2]])
+            c[0], c[1], c[2] = Xo, Ms[0], Ms[1]
+    T = sim.ticks()[0]
+    ga, gb = sim.masses()
+    for i, c in enumerate(cur):
+        sl = slice(offs[i], offs[i + 1])
+        assert np.array_equal(T[sl], c[0][0])
+        assert_masses(ga[sl], c[1], TOL[precision], f"A of realisation {i}")
+        assert_masses(gb[sl], c[2], TOL[precision], f"B of realisation {i}")
