@@ -40,7 +40,9 @@ __device__ void finish_step(const Dev& d, int flip_x, int flip_m) {
 
 // ------------------------------------------------------------ observables --
 // After every step (every path): sum A, sum B, sum (A - B) and mean A of each
-// realisation, one ring row per step.  Each realisation's slot range is cut
+// realisation, one ring row per step (sum A and sum B are conserved by the
+// symmetric transfer, sum (A - B) by the reaction too: the conservative
+// components of Sec. 3).  Each realisation's slot range is cut
 // into fixed chunks of kObsChunk slots (the state keeps a realisation's
 // particles in its own range); a CTA sums one chunk -- each thread its
 // strided slots in order, then fixed shuffle trees -- in the precision's
