@@ -250,10 +250,15 @@ mt_status mt_server_create(const mt_server_config* cfg, void* pool, size_t pool_
 
 /* Queue a request: params p, host arrays x (dim*n), A, B (n), steps to run.
  * *id receives its identifier.  A request whose footprint exceeds the whole
- * pool is refused (MT_ERR_WORKSPACE); one with more than two species is
- * refused (MT_ERR_INVALID). */
+ * pool is refused (MT_ERR_WORKSPACE); one with more than two species needs
+ * mt_server_submit_species (MT_ERR_INVALID here). */
 mt_status mt_server_submit(mt_server* s, const mt_params* p, const double* x, const double* A,
                            const double* B, int64_t steps, int64_t* id);
+
+/* The same for any species count: M holds species*n doubles (species 0 is
+ * A, 1 is B, then species 2, ...), each in the caller's particle order. */
+mt_status mt_server_submit_species(mt_server* s, const mt_params* p, const double* x,
+                                   const double* M, int64_t steps, int64_t* id);
 
 /* One scheduling round (retire finished chunks, enqueue next chunks, admit
  * queued requests); does not wait for running work.  *queued and *running
@@ -267,6 +272,10 @@ mt_status mt_server_info(const mt_server* s, int64_t id, mt_request_info* info);
  * when cap = 0); *rows (may be NULL) receives the rows written. */
 mt_status mt_server_result(const mt_server* s, int64_t id, double* A, double* B,
                            double* observables, int64_t cap, int64_t* rows);
+
+/* Species sp (0 = A, 1 = B, ...) of a finished request: n doubles in the
+ * caller's order into host memory out. */
+mt_status mt_server_result_species(const mt_server* s, int64_t id, int32_t sp, double* out);
 
 /* Forget a finished or failed request (frees its host copy). */
 mt_status mt_server_release(mt_server* s, int64_t id);

@@ -83,7 +83,8 @@ struct Request {
   int64_t id = 0;
   mt_params p{};
   int64_t steps = 0, done = 0;
-  std::vector<double> x, A, B;       // inputs until admitted, then results
+  std::vector<double> x;             // positions until admitted
+  std::vector<double> M;             // species masses [species][n]: inputs, then results
   std::vector<double> obs;           // observables rows after the last step
   int state = MT_REQ_QUEUED;
   mt_status status = MT_OK;
@@ -94,6 +95,9 @@ struct Request {
   int64_t chunk = 0;                 // steps of the chunk in flight
   double t_submit = 0, t_admit = 0, t_done = 0, gpu_ms = 0;
 };
+
+// Species a request carries (its parameters' 0 means 2).
+int species_of(const mt_params& p) { return p.species > 2 ? p.species : 2; }
 
 struct Slot {
   cudaStream_t stream = nullptr;
@@ -157,9 +161,11 @@ mt_status enqueue_chunk(mt_server* s, Request* r) {
 
 mt_status finish(mt_server* s, Request* r) {
   const size_t n = (size_t)r->p.n;
-  r->A.assign(n, 0.0);
-  r->B.assign(n, 0.0);
-  mt_status st = mt_read_masses(r->h, r->A.data(), r->B.data(), MT_MEM_HOST);
+  const int S = species_of(r->p);
+  r->M.assign((size_t)S * n, 0.0);
+  mt_status st = MT_OK;
+  for (int k = 0; k < S && st == MT_OK && n > 0; ++k)
+    st = mt_read_species(r->h, k, r->M.data() + (size_t)k * n, MT_MEM_HOST);
   if (st == MT_OK && r->p.observe_cap > 0) {
     const int64_t rows = std::min<int64_t>(r->p.observe_cap, r->steps);
     r->obs.assign((size_t)rows * 4, 0.0);
@@ -195,11 +201,13 @@ void admit(mt_server* s, Request* r, int k, size_t at) {
   r->state = MT_REQ_RUNNING;
   r->t_admit = s->now();
   mt_status st = mt_create(&r->p, s->pool_base + at, r->footprint, sl.stream, &r->h);
+  const size_t n = (size_t)r->p.n;
   if (st == MT_OK)
-    st = mt_upload(r->h, r->x.data(), r->A.data(), r->B.data(), MT_MEM_HOST);
+    st = mt_upload(r->h, r->x.data(), r->M.data(), r->M.data() + n, MT_MEM_HOST);
+  for (int k = 2; k < species_of(r->p) && st == MT_OK && n > 0; ++k)
+    st = mt_set_species(r->h, k, r->M.data() + (size_t)k * n, MT_MEM_HOST);
   if (st == MT_OK) {
-    r->A.clear();
-    r->B.clear();
+    r->M.clear();
     st = r->steps > 0 ? enqueue_chunk(s, r) : MT_OK;
   }
   if (st != MT_OK) fail_request(s, r, st);
@@ -252,15 +260,32 @@ mt_status mt_server_create(const mt_server_config* cfg, void* pool, size_t pool_
 
 mt_status mt_server_submit(mt_server* s, const mt_params* p, const double* x, const double* A,
                            const double* B, int64_t steps, int64_t* id) {
+  if (!p) return err(MT_ERR_INVALID, "mt_server_submit: NULL argument");
+  mt_params r;
+  mt_status st = mt_resolve(p, &r);
+  if (st != MT_OK) return st;
+  if (r.species != 2)
+    return err(MT_ERR_INVALID, "mt_server_submit: more than two species need mt_server_submit_species");
+  const size_t n = (size_t)r.n;
+  if (n > 0 && (!A || !B)) return err(MT_ERR_INVALID, "mt_server_submit: x, A, B required");
+  std::vector<double> M;
+  M.reserve(2 * n);
+  if (n > 0) {
+    M.assign(A, A + n);
+    M.insert(M.end(), B, B + n);
+  }
+  return mt_server_submit_species(s, p, x, M.data(), steps, id);
+}
+
+mt_status mt_server_submit_species(mt_server* s, const mt_params* p, const double* x,
+                                   const double* M, int64_t steps, int64_t* id) {
   if (!s || !p || !id) return err(MT_ERR_INVALID, "mt_server_submit: NULL argument");
   if (steps < 0) return err(MT_ERR_INVALID, "mt_server_submit: steps must be >= 0");
   mt_params r;
   mt_status st = mt_resolve(p, &r);
   if (st != MT_OK) return st;
-  if (r.species != 2)
-    return err(MT_ERR_INVALID, "mt_server_submit: requests carry two species (A and B)");
   const size_t n = (size_t)r.n, m = (size_t)r.dim * n;
-  if (n > 0 && (!x || !A || !B)) return err(MT_ERR_INVALID, "mt_server_submit: x, A, B required");
+  if (n > 0 && (!x || !M)) return err(MT_ERR_INVALID, "mt_server_submit: x and masses required");
   const size_t fp = footprint_of(*p);
   if (fp == 0) return err(MT_ERR_INVALID, "mt_server_submit: no workspace size for these params");
   if (fp > s->pool_bytes)
@@ -272,8 +297,7 @@ mt_status mt_server_submit(mt_server* s, const mt_params* p, const double* x, co
   q->steps = steps;
   q->footprint = fp;
   q->x.assign(x, x + m);
-  q->A.assign(A, A + n);
-  q->B.assign(B, B + n);
+  q->M.assign(M, M + (size_t)r.species * n);
   q->t_submit = s->now();
   *id = q->id;
   s->queue.push_back(q.get());
@@ -363,14 +387,30 @@ mt_status mt_server_result(const mt_server* s, int64_t id, double* A, double* B,
   const size_t n = (size_t)r.p.n;
   if (n > 0 && (!A || !B)) return err(MT_ERR_INVALID, "mt_server_result: A and B required");
   if (n > 0) {
-    std::memcpy(A, r.A.data(), n * 8);
-    std::memcpy(B, r.B.data(), n * 8);
+    std::memcpy(A, r.M.data(), n * 8);
+    std::memcpy(B, r.M.data() + n, n * 8);
   }
   const int64_t have = (int64_t)(r.obs.size() / 4);
   const int64_t give = std::min<int64_t>(have, cap > 0 ? cap : 0);
   if (give > 0 && !observables) return err(MT_ERR_INVALID, "mt_server_result: observables NULL");
   if (give > 0) std::memcpy(observables, r.obs.data() + (size_t)(have - give) * 4, (size_t)give * 32);
   if (rows) *rows = give;
+  return MT_OK;
+}
+
+mt_status mt_server_result_species(const mt_server* s, int64_t id, int32_t sp, double* out) {
+  if (!s) return err(MT_ERR_INVALID, "mt_server_result_species: server is NULL");
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return err(MT_ERR_INVALID, "mt_server_result_species: unknown request");
+  const Request& r = *it->second;
+  if (r.state == MT_REQ_FAILED) return err(r.status, "mt_server_result_species: the request failed");
+  if (r.state != MT_REQ_DONE)
+    return err(MT_ERR_STATE, "mt_server_result_species: request not finished");
+  const size_t n = (size_t)r.p.n;
+  if (sp < 0 || sp >= species_of(r.p))
+    return err(MT_ERR_INVALID, "mt_server_result_species: species out of range");
+  if (n > 0 && !out) return err(MT_ERR_INVALID, "mt_server_result_species: out is NULL");
+  if (n > 0) std::memcpy(out, r.M.data() + (size_t)sp * n, n * 8);
   return MT_OK;
 }
 

@@ -169,6 +169,8 @@ def lib(path: Path | None = None):
         "mt_server_poll": [H, ctypes.POINTER(i32), ctypes.POINTER(i32)],
         "mt_server_info": [H, i64, ctypes.POINTER(mt_request_info)],
         "mt_server_result": [H, i64, _vp, _vp, _vp, i64, ctypes.POINTER(i64)],
+        "mt_server_submit_species": [H, P, _vp, _vp, i64, ctypes.POINTER(i64)],
+        "mt_server_result_species": [H, i64, i32, _vp],
         "mt_server_release": [H, i64],
         "mt_server_stats": [H, ctypes.POINTER(mt_server_summary), _vp, i64],
     }
@@ -438,6 +440,16 @@ def mt_server_result(s, rid: int, A_ptr, B_ptr, obs_ptr, cap: int) -> int:
     return int(rows.value)
 
 
+def mt_server_submit_species(s, p, x_ptr, M_ptr, steps: int) -> int:
+    rid = ctypes.c_int64(0)
+    check(lib().mt_server_submit_species(s, ctypes.byref(p), x_ptr, M_ptr, steps, ctypes.byref(rid)))
+    return int(rid.value)
+
+
+def mt_server_result_species(s, rid: int, sp: int, out_ptr) -> None:
+    check(lib().mt_server_result_species(s, rid, sp, out_ptr))
+
+
 def mt_server_release(s, rid: int) -> None:
     check(lib().mt_server_release(s, rid))
 
@@ -607,6 +619,22 @@ class Server:
         rid = mt_server_submit(self.s, p, _ptr(x), _ptr(A), _ptr(B), steps)
         self.params[rid] = r
         return rid
+
+    def submit_species(self, p: mt_params, x, Ms, steps: int) -> int:
+        """A request carrying len(Ms) species (Ms[0] = A, Ms[1] = B, ...)."""
+        r = mt_resolve(p)
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+        M = np.ascontiguousarray(np.stack([np.asarray(m, dtype=np.float64) for m in Ms]))
+        assert x.size == r.dim * r.n and M.shape == (r.species, r.n)
+        rid = mt_server_submit_species(self.s, p, _ptr(x), _ptr(M), steps)
+        self.params[rid] = r
+        return rid
+
+    def result_species(self, rid: int, sp: int) -> np.ndarray:
+        r = self.params[rid]
+        out = np.empty(int(r.n))
+        mt_server_result_species(self.s, rid, sp, _ptr(out))
+        return out
 
     def poll(self):
         return mt_server_poll(self.s)

@@ -122,13 +122,35 @@ def test_two_species_path_unchanged_and_species_io():
     s3.close()
 
 
-def test_server_refuses_more_species():
-    p = mt.mt_params_init(n=100, L=(100.0,), species=3)
-    srv = mt.Server(pool_bytes=2 ** 24, max_active=1, chunk_steps=4)
+def test_server_requests_with_more_species():
+    """A request carrying three species, served beside a two-species one,
+    equals its run alone in every species; the two-species call refuses it."""
+    n, L, S = 3000, 3000.0, 3
+    p3 = mt.mt_params_init(n=n, L=(L,), species=S, precision=mt.MT_MIXED, seed=9, observe_cap=5)
+    x = synth.uniform_positions(n, L, seed=9)
+    Ms = species_masses(n, S, seed=9)
+    p2 = mt.mt_params_init(n=2000, L=(2000.0,), precision=mt.MT_MIXED, seed=10)
+    x2 = synth.uniform_positions(2000, 2000.0, seed=10)
+    A2, B2 = synth.uniform_masses(2000, seed=10)
+    srv = mt.Server(pool_bytes=2 ** 26, max_active=2, chunk_steps=4)
     with pytest.raises(mt.MtError) as e:
-        srv.submit(p, np.linspace(1, 99, 100), np.ones(100), np.zeros(100), 3)
+        srv.submit(p3, x, Ms[0], Ms[1], 10)
     assert e.value.status == mt.MT_ERR_INVALID
+    rid3 = srv.submit_species(p3, x, Ms, 10)
+    srv.submit(p2, x2, A2, B2, 10)
+    srv.drain()
+    alone = mt.Simulation(p3)
+    alone.upload(x, Ms[0], Ms[1])
+    alone.set_species(2, Ms[2])
+    alone.run(10)
+    for s in range(S):
+        assert np.array_equal(srv.result_species(rid3, s), alone.species(s)), f"species {s}"
+    gA, gB, gobs = srv.result(rid3)
+    assert np.array_equal(gA, alone.species(0)) and np.array_equal(gobs, alone.observables())
+    with pytest.raises(mt.MtError):
+        srv.result_species(rid3, S)
     srv.close()
+    alone.close()
 
 
 @pytest.mark.parametrize("precision", [mt.MT_FP64, mt.MT_MIXED])
