@@ -70,14 +70,16 @@ static int64_t wrap(int64_t y, int64_t Lq) {
 
 void mto_move(const mto_params* p, int64_t n, int64_t* X, const float* xi) {
   const int32_t k = p->frac_bits;
-  /* Eq. 2 with alpha_L = 0: the random walk carries D_rw (Sec. 3). */
-  const float b = (float)ldexp(sqrt(2.0 * p->D_rw * p->dt), k);
+  /* Eq. 2 with alpha_L = 0: the random walk carries D_rw (Sec. 3).  The
+   * displacement sqrt(2 D_rw dt) xi is a binary64 product (in grid units,
+   * b = sqrt(2 D_rw dt) 2^k), rounded once to the nearest tick. */
+  const double b = ldexp(sqrt(2.0 * p->D_rw * p->dt), k);
   for (int32_t d = 0; d < p->dim; ++d) {
     const int64_t drift = llrint(ldexp(p->v[d] * p->dt, k));
     const int64_t Lq = llrint(ldexp(p->L[d], k));
     for (int64_t i = 0; i < n; ++i) {
-      const float step = b * xi[(int64_t)d * n + i];
-      const int64_t y = X[(int64_t)d * n + i] + drift + (int64_t)llrintf(step);
+      const double step = b * (double)xi[(int64_t)d * n + i];
+      const int64_t y = X[(int64_t)d * n + i] + drift + (int64_t)llrint(step);
       X[(int64_t)d * n + i] = p->walls == MTO_WALLS_PERIODIC ? wrap(y, Lq) : reflect(y, Lq);
     }
   }

@@ -71,8 +71,8 @@ int64_t mto_cutoff_ticks(const mto_params* p);
 
 /* Move every particle once (Eq. 2; Sec. 3).  X holds dim*n ticks, axis-major
  * (all x, then all y).  xi holds dim*n standard normals (float, same layout).
- * The displacement in ticks is rint_f32(b_f32 * xi) with
- * b_f32 = (float)(sqrt(2 D_rw dt) * 2^k); the drift is rint(v dt 2^k).  A
+ * The displacement in ticks is rint(b * xi), b = sqrt(2 D_rw dt) * 2^k, the
+ * product formed in binary64 and rounded once; the drift is rint(v dt 2^k).  A
  * position outside [0, L] is mirrored at the wall it crossed, repeatedly,
  * until it lies inside (at most 64 mirrors, then clamped). */
 void mto_move(const mto_params* p, int64_t n, int64_t* X, const float* xi);

@@ -318,14 +318,14 @@ def test_sorted_pairs_equal_brute_pairs():
 # ---------------------------------------------------------------------- move
 
 def test_move_drift_rounding_and_reflection():
-    """Eq. 2 on the grid: drift rint(v dt 2^k), displacement rint_f32(b xi),
+    """Eq. 2 on the grid: drift rint(v dt 2^k), displacement rint(b xi),
     mirrored at 0 and at L (Sec. 3)."""
     p = O.params(L=(10.0,), v=(0.5,), D_rw=0.5, dt=1.0)  # b = sqrt(2*0.5*1) = 1
     X = q1([0.1, 5.0, 9.9])
     xi = np.array([[-0.7, 0.25, 0.3]], dtype=np.float32)
     X2 = O.move(p, X, xi)
-    b = np.float32(2.0 ** K)
-    disp = [int(np.rint(b * v)) for v in xi[0]]
+    # b = 1 unit = 2^K ticks, so b xi is exact: the nearest tick by hand
+    disp = [round(float(mp.mpf(float(v)) * 2 ** K)) for v in xi[0]]
     drift = int(0.5 * 2 ** K)
     Lq = 10 * 2 ** K
     raw = [int(X[0, i]) + drift + disp[i] for i in range(3)]
@@ -333,6 +333,31 @@ def test_move_drift_rounding_and_reflection():
            raw[2] if raw[2] <= Lq else 2 * Lq - raw[2]]
     assert X2[0].tolist() == exp
     assert raw[2] > Lq  # the last particle really crossed the wall
+
+
+@pytest.mark.parametrize("D_rw,dt,k", [(0.1, 1.0, 29), (0.5, 0.1, 33), (0.037, 0.25, 40)])
+def test_move_displacement_is_eq2_in_binary64(D_rw, dt, k):
+    """Eq. 2's random-walk displacement sqrt(2 D_rw dt) xi, evaluated in
+    40-digit arithmetic and rounded to the nearest tick, for 400 normals:
+    the oracle's displacement must equal it exactly.  A displacement formed
+    as a binary32 product (the square root or the product rounded to 24
+    bits, about 2^-24 relative, i.e. tens of ticks at k = 29) fails this pin,
+    which the second half checks on the same values."""
+    L = 2.0 ** 20
+    p = O.params(L=(L,), v=(0.0,), D_rw=D_rw, dt=dt, frac_bits=k)
+    n = 400
+    xi = synth.normals(1, 1, n, seed=77)[0]
+    xi[0, :4] = np.array([5.7, -5.7, 1e-3, 0.0], dtype=np.float32)
+    X = np.full((1, n), 2 ** (k + 19), dtype=np.int64)  # mid-domain, no wall
+    got = O.move(p, X, xi)[0] - X[0]
+    mp.mp.dps = 40
+    b = mp.sqrt(2 * mp.mpf(D_rw) * mp.mpf(dt)) * mp.mpf(2) ** k
+    want = [int(mp.nint(b * mp.mpf(float(v)))) for v in xi[0]]
+    assert got.tolist() == want
+    # the same pin rejects a binary32 displacement
+    b32 = np.float32(math.ldexp(math.sqrt(2.0 * D_rw * dt), k))
+    f32 = [int(np.rint(np.float32(b32 * v))) for v in xi[0]]
+    assert sum(a != w for a, w in zip(f32, want)) > n // 4
 
 
 def test_move_statistics():
