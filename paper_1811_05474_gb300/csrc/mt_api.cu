@@ -47,7 +47,7 @@ bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 struct Derived {
   mt_params p;  // resolved
   long long S = 0, Lq[2] = {0, 0}, drift[2] = {0, 0};
-  float bq = 0.f;
+  double bq = 0.0;
   int cshift = 0;
   long long ncx = 1, ncy = 1, ncell = 0;
   long long nbig_cap = 0, ntiles = 0;
@@ -182,7 +182,7 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
   const double bw = std::ldexp(std::sqrt(2.0 * p.D_rw * p.dt), k);
   if (bw * 64.0 >= kTwo61 / 4)
     return fail(MT_ERR_INVALID, "sqrt(2 D_rw dt) 2^frac_bits is too large for the grid");
-  D.bq = (float)bw;
+  D.bq = bw;
   D.S = (long long)std::floor(std::ldexp(p.cutoff, k));
   if (periodic && p.search != MT_SEARCH_FULL) {
     for (int a = 0; a < p.dim; ++a)
@@ -255,7 +255,7 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
     const long long w = 1LL << D.cshift;
     D.hc = (2 * D.S + w - 1) / w + 1;
     double dr = std::fabs((double)D.drift[0]);
-    const long long dc = (long long)((dr + std::ceil((double)D.bq * 5.78) + 2.0) / (double)w) + 2;
+    const long long dc = (long long)((dr + std::ceil(D.bq * 5.78) + 2.0) / (double)w) + 2;
     const double per_cell = (double)p.n / (double)D.ncell;
     long long T = 1024;
     while (T >= 64 && (double)T + 2.0 * (double)(D.hc + dc + 1) * per_cell * 1.5 + 64.0 >

@@ -218,7 +218,7 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
           z = box_muller(u.x, u.y).x;
         }
         const long long x =
-            base + reflect(Xs[e] - base + d.drift[0] + float_to_ll_rn(__fmul_rn(d.bq, z)), R->Lq);
+            base + reflect(Xs[e] - base + d.drift[0] + walk_ticks(d.bq, z), R->Lq);
         rx[k] = x;
         lt = slot >= o0 && slot < o1 && x < xlo;
         if (x >= wlo && x < whi) {
@@ -972,7 +972,7 @@ __global__ void k_noise_bound(Dev d, const float* xi, long long count) {
   unsigned long long mine = 0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long v = float_to_ll_rn(__fmul_rn(d.bq, xi[i]));
+    const long long v = walk_ticks(d.bq, xi[i]);
     const unsigned long long a = (unsigned long long)(v < 0 ? -v : v);
     mine = a > mine ? a : mine;
   }
@@ -1152,7 +1152,7 @@ cudaError_t launch_noise_bound(const Dev& d, const float* xi, cudaStream_t s) {
       const long long d2 = d.drift[1] < 0 ? -d.drift[1] : d.drift[1];
       dr = d2 > dr ? d2 : dr;
     }
-    k_set_dmax<<<1, 1, 0, s>>>(d, dr + (long long)ceil((double)d.bq * 5.78) + 2);
+    k_set_dmax<<<1, 1, 0, s>>>(d, dr + (long long)ceil(d.bq * 5.78) + 2);
     return cudaGetLastError();
   }
   k_set_dmax<<<1, 1, 0, s>>>(d, 0);

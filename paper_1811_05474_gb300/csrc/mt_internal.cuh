@@ -114,7 +114,7 @@ struct Dev {
   long long S;              // cutoff in ticks
   long long Lq[2];          // domain length in ticks
   long long drift[2];       // v dt in ticks
-  float bq;                 // sqrt(2 D_rw dt) 2^k as float
+  double bq;                // sqrt(2 D_rw dt) 2^k
   float inv8f;              // 1 / (8 D_mt dt) 2^-2k, float
   double inv8;              // 1 / (8 D_mt dt), double
   double scale;             // 2^-k
@@ -280,9 +280,9 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned int k0, unsigne
   return c;
 }
 
-// 64-bit integer <-> binary32 conversions through 32-bit instructions
+// 64-bit integer -> binary32 conversion through 32-bit instructions
 // (conversions with a 64-bit integer operand run on the binary64 pipe, which
-// is narrow on this GPU).  Both round to nearest even, like the 64-bit forms.
+// is narrow on this GPU).  Rounds to nearest even, like the 64-bit form.
 __device__ __forceinline__ float ll_to_float(long long v) {
   if (v >= -2147483647LL && v <= 2147483647LL) return __int2float_rn((int)v);
   // |v| >= 2^31: the high word carries every bit binary32 can keep except
@@ -292,15 +292,10 @@ __device__ __forceinline__ float ll_to_float(long long v) {
   return __fadd_rn(hi, lo);
 }
 
-__device__ __forceinline__ long long float_to_ll_rn(float f) {
-  if (fabsf(f) < 2147483520.0f) return (long long)__float2int_rn(f);
-  // |f| >= 2^31 - 128: f is an integer (at most 24 significant bits), so
-  // shift its significand into place exactly.
-  const unsigned int b = __float_as_uint(f);
-  const int e = (int)((b >> 23) & 0xff) - 127;  // >= 30
-  const long long m = (long long)((b & 0x7fffff) | 0x800000);
-  const long long mag = e >= 23 ? (e - 23 < 40 ? (m << (e - 23)) : 0x7fffffffffffffffLL) : m;
-  return (b >> 31) ? -mag : mag;
+// Eq. 2's random-walk displacement on the grid: the nearest tick to b xi,
+// b = sqrt(2 D_rw dt) 2^k, with the product formed in binary64.
+__device__ __forceinline__ long long walk_ticks(double b, float xi) {
+  return __double2ll_rn(__dmul_rn(b, (double)xi));
 }
 
 // Two standard normals from two 32-bit words (Box-Muller, binary32, with

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(kThreads) k_move(Dev d) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       // Eq. 2 on the grid: drift + rint(b * xi), then the wall mirror.
-      const long long step = float_to_ll_rn(__fmul_rn(d.bq, z[a]));
+      const long long step = walk_ticks(d.bq, z[a]);
       if (d.periodic && a == 0)
         pos[0] = base + wrap(pos[0] - base + d.drift[0] + step, R->Lq);
       else if (d.periodic)
