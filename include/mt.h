@@ -30,9 +30,14 @@
  * that grid; the cutoff is s_max rounded down to it (Smax = floor(s_max 2^k)
  * ticks) and the pair test is exact integer arithmetic.  MT_FP64 computes
  * weights, normalisation, exchange and reaction in IEEE binary64.  MT_MIXED
- * computes weights and normalised weights in binary32 and keeps the masses as
- * unevaluated sums of two binary32 numbers (about 48 significant bits), with
- * compensated additions for the update and the reaction.
+ * computes the weights (exponentials), their row sums and the normalised
+ * weights in binary32, and everything that touches a mass in binary64: the
+ * masses are stored as binary64, and each flux term P_ij (M_j - M_i), its sum
+ * over j, the update and the reaction are binary64 operations.
+ * MT_MIXED_DF32 (not part of the paper's arithmetic; a faster variant) keeps
+ * binary32 weights and stores each mass as an unevaluated sum of two binary32
+ * numbers (about 48 significant bits), with binary32 flux terms summed with
+ * compensation and compensated additions for the update and the reaction.
  *
  * Conventions.
  *   - Every function returns mt_status (0 = MT_OK, < 0 error) and never
@@ -72,7 +77,7 @@ typedef enum {
 } mt_status;
 
 enum { MT_SEARCH_CELL = 0, MT_SEARCH_BRUTE = 1, MT_SEARCH_FULL = 2 };
-enum { MT_FP64 = 0, MT_MIXED = 1 };
+enum { MT_FP64 = 0, MT_MIXED = 1, MT_MIXED_DF32 = 2 };
 enum { MT_NORM_SYM = 0, MT_NORM_ROW = 1 };
 enum { MT_MEM_HOST = 0, MT_MEM_DEVICE = 1 };
 enum { MT_WALLS_REFLECT = 0, MT_WALLS_PERIODIC = 1 };
@@ -89,7 +94,7 @@ typedef struct mt_params {
   double dt;            /* time step, > 0 */
   double cutoff;        /* s_max; <= 0 selects 3 sqrt(4 D_mt dt) */
   int32_t search;       /* MT_SEARCH_* */
-  int32_t precision;    /* MT_FP64 or MT_MIXED */
+  int32_t precision;    /* MT_FP64, MT_MIXED or MT_MIXED_DF32 */
   int32_t norm;         /* MT_NORM_* */
   int32_t react;        /* 1: apply A + B -> E after the transfer */
   uint64_t seed;        /* key of the Philox4x32-10 random-walk generator */
@@ -355,7 +360,7 @@ mt_status mt_read_ticks(mt_handle* h, int64_t* X, int32_t mem);
  * 4 doubles each: sum A, sum B, sum (A - B), mean A after the step (a batch
  * handle: 4 per realisation, realisation 0 first).  The sums are taken after
  * every step over fixed chunks of the state in a fixed order, in the
- * precision's arithmetic (binary64, or double-binary32 in MIXED), so they are
+ * precision's arithmetic (binary64, or double-binary32 in MT_MIXED_DF32), so they are
  * bitwise reproducible.  out: host memory for 4*cap doubles (4*count*cap for
  * a batch).  *count receives the rows written. */
 mt_status mt_read_observables(mt_handle* h, double* out, int64_t cap,

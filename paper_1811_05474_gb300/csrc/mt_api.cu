@@ -149,7 +149,7 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
   if (p.cutoff <= 0.0) p.cutoff = 3.0 * std::sqrt(4.0 * p.D_mt * p.dt);
   if (p.search < MT_SEARCH_CELL || p.search > MT_SEARCH_FULL)
     return fail(MT_ERR_INVALID, "unknown search %d", p.search);
-  if (p.precision != MT_FP64 && p.precision != MT_MIXED)
+  if (p.precision != MT_FP64 && p.precision != MT_MIXED && p.precision != MT_MIXED_DF32)
     return fail(MT_ERR_INVALID, "unknown precision %d", p.precision);
   if (p.norm != MT_NORM_SYM && p.norm != MT_NORM_ROW)
     return fail(MT_ERR_INVALID, "unknown norm %d", p.norm);
@@ -361,7 +361,7 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
   D.o_sreal = take(D.sreal.size() * 4);
   D.o_cnt = take(D.band > 0 ? 2 * n * 4 : 0);
   D.o_band = take(D.band > 0 ? (size_t)D.band * ((n + 31) / 32 * 32) *
-                                   (p.precision == MT_MIXED ? 4 : 8)
+                                   (p.precision == MT_FP64 ? 8 : 4)
                              : 0);
   D.o_ochunk = take(D.ochunk.size() * 4);
   D.o_opart = take((D.ochunk.size() - 1) * 4 * 8);

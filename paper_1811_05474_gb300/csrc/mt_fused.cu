@@ -66,7 +66,7 @@ static_assert(Fast::kCap == kFusedCap, "staging capacity");
 
 template <typename TR>
 size_t tier_smem(int precision) {
-  const size_t r = precision == MT_MIXED ? 4 : 8;
+  const size_t r = precision == MT_FP64 ? 8 : 4;  // 1 / r_i
   return (size_t)TR::kCap * (8 + 8 + 8 + 4 + r) + (size_t)(2 * TR::kBins + 1) * 4;
 }
 
@@ -131,13 +131,13 @@ __device__ __forceinline__ SegScalars load_seg(const Dev& d, int sc, long long D
 // 0; each thread adds the particles it updates to its observables
 // accumulators (obs_sum, in shared memory).  Returns kSegOk, or why the
 // segment does not fit this tier (then nothing of it has been written).
-template <bool MIX, typename TR, int CL>
+template <int PR, typename TR, int CL>
 __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const SegScalars& g,
                              int slice, int nslice, bool route_heavy,
                              bool* heavy_out = nullptr) {
-  using W = Weight<MIX, 1>;
+  using W = Weight<mixw(PR), 1>;
   using T = typename W::T;
-  using MS = Mass<MIX>;
+  using MS = Mass<PR>;
   using MV = typename MS::V;
   constexpr int NT = TR::kT, PER = TR::kPer, CAP = TR::kCap, NB = TR::kBins;
   long long* sx = reinterpret_cast<long long*>(smem);
@@ -514,7 +514,7 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
       T r = T(1);
       for (int q = j - 1; q >= 0 && x - sx[q] <= S; --q) r += W::near(d, x - sx[q]);
       for (int q = j + 1; q < m && sx[q] - x <= S; ++q) r += W::near(d, sx[q] - x);
-      sr[j] = MIX ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
+      sr[j] = mixw(PR) ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
     }
   }
   __syncthreads();
@@ -538,7 +538,7 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
       }
       for (; q < hi; q += 32) r0 += W::near(d, x > sx[q] ? x - sx[q] : sx[q] - x);
       const T r = warp_sum((r0 + r1) + (r2 + r3));
-      if (lane == 0) sr[j] = MIX ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
+      if (lane == 0) sr[j] = mixw(PR) ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
     }
   }
   if constexpr (CL > 1) {
@@ -745,7 +745,7 @@ __device__ __forceinline__ void end_of_tier(const Dev& d, cudaGraphConditionalHa
 // First tier: a persistent grid (a few CTAs per SM) looping over the
 // segments; each segment's boundary scalars are loaded while the previous
 // segment is processed.
-template <bool MIX>
+template <int PR>
 __global__ void __launch_bounds__(Fast::kT, kFusedCtasPerSm) k_step1d(Dev d, cudaGraphConditionalHandle cond,
                                                          int use_cond) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -773,7 +773,7 @@ __global__ void __launch_bounds__(Fast::kT, kFusedCtasPerSm) k_step1d(Dev d, cud
     SegScalars nxt = {};
     if (next < d.nseg) nxt = load_seg(d, sc, Dc, next);
     if (!d.use_pred || !pcur[seg]) {
-      const int st = fused_segment<MIX, Fast, 1>(d, seg, smem, cur, 0, 1, true);
+      const int st = fused_segment<PR, Fast, 1>(d, seg, smem, cur, 0, 1, true);
       if (st != kSegOk && threadIdx.x == 0) d.ovlist[atomicAdd(&c->nov, 1)] = seg;
       if (threadIdx.x == 0) {
         pnext[seg] = st == kSegOk ? 0 : 1;
@@ -802,7 +802,7 @@ __global__ void __launch_bounds__(Fast::kT, kFusedCtasPerSm) k_step1d(Dev d, cud
 // in index order (an ordered compaction per chunk of indices) and process
 // them one after another like the second tier; each records whether its
 // segment is still heavy for the next step's prediction.
-template <bool MIX, int CL>
+template <int PR, int CL>
 __global__ void __launch_bounds__(Big::kT, 1)
     k_step1d_pred(Dev d, cudaGraphConditionalHandle cond, int use_cond) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -840,7 +840,7 @@ __global__ void __launch_bounds__(Big::kT, 1)
       for (int k = 0; k < nl; ++k) {
         const int seg = s_list[k];
         bool heavy = true;
-        const int st = fused_segment<MIX, Big, CL>(d, seg, smem, load_seg(d, sc, Dc, seg), rank,
+        const int st = fused_segment<PR, Big, CL>(d, seg, smem, load_seg(d, sc, Dc, seg), rank,
                                                    CL, false, &heavy);
         if (st != kSegOk && tid == 0 && atomicExch(&c->overflow, 1) == 0) {
           c->ov_reason = st;
@@ -872,7 +872,7 @@ __global__ void __launch_bounds__(Big::kT, 1)
 // it, each forms the row sums of every CL-th particle (shared through
 // distributed shared memory) and the exchange of every CL-th own particle.
 // Clusters loop over the queue.
-template <bool MIX, int CL>
+template <int PR, int CL>
 __global__ void __launch_bounds__(Big::kT, 1)
     k_step1d_big(Dev d, cudaGraphConditionalHandle cond, int use_cond) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -886,7 +886,7 @@ __global__ void __launch_bounds__(Big::kT, 1)
   for (int q = cid; q < nov; q += ncl) {
     const int seg = d.ovlist[q];
     const int st =
-        fused_segment<MIX, Big, CL>(d, seg, smem, load_seg(d, sc, Dc, seg), rank, CL, false);
+        fused_segment<PR, Big, CL>(d, seg, smem, load_seg(d, sc, Dc, seg), rank, CL, false);
     if (st != kSegOk && threadIdx.x == 0 && atomicExch(&c->overflow, 1) == 0) {
       c->ov_reason = st;
       c->ov_seg = seg;
@@ -999,14 +999,14 @@ static int g_big_cluster = 8;
 // CTAs should take their SMs before the first tier fills them).
 static int g_top_priority = 0;
 
-template <bool MIX, int CL>
+template <int PR, int CL>
 static cudaError_t configure_big(int precision) {
-  auto k = k_step1d_big<MIX, CL>;
+  auto k = k_step1d_big<PR, CL>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)tier_smem<Big>(precision));
   if (e == cudaSuccess && CL > 8)
     e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  auto kp = k_step1d_pred<MIX, CL>;
+  auto kp = k_step1d_pred<PR, CL>;
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tier_smem<Big>(precision));
@@ -1015,7 +1015,7 @@ static cudaError_t configure_big(int precision) {
   return e;
 }
 
-template <bool MIX, int CL>
+template <int PR, int CL>
 static int max_active_clusters(int precision) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
@@ -1029,27 +1029,32 @@ static int max_active_clusters(int precision) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_step1d_big<MIX, CL>, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, k_step1d_big<PR, CL>, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   return n;
 }
 
+template <int PR>
+static cudaError_t configure_tiers(int cl) {
+  cudaError_t e = cudaFuncSetAttribute(k_step1d<PR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tier_smem<Fast>(PR));
+  if (e != cudaSuccess) return e;
+  return cl == 16 ? configure_big<PR, 16>(PR) : configure_big<PR, 8>(PR);
+}
+
 cudaError_t fused_configure() {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_step1d<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)tier_smem<Fast>(MT_MIXED))) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_step1d<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)tier_smem<Fast>(MT_FP64))) != cudaSuccess)
-    return e;
-  if ((e = configure_big<true, 8>(MT_MIXED)) != cudaSuccess) return e;
-  if ((e = configure_big<false, 8>(MT_FP64)) != cudaSuccess) return e;
+  if ((e = configure_tiers<MT_FP64>(8)) != cudaSuccess) return e;
+  if ((e = configure_tiers<MT_MIXED>(8)) != cudaSuccess) return e;
+  if ((e = configure_tiers<MT_MIXED_DF32>(8)) != cudaSuccess) return e;
   g_big_cluster = 8;
-  if (configure_big<true, 16>(MT_MIXED) == cudaSuccess &&
-      configure_big<false, 16>(MT_FP64) == cudaSuccess &&
-      max_active_clusters<true, 16>(MT_MIXED) >= 1 && max_active_clusters<false, 16>(MT_FP64) >= 1)
+  if (configure_tiers<MT_FP64>(16) == cudaSuccess && configure_tiers<MT_MIXED>(16) == cudaSuccess &&
+      configure_tiers<MT_MIXED_DF32>(16) == cudaSuccess &&
+      max_active_clusters<MT_FP64, 16>(MT_FP64) >= 1 &&
+      max_active_clusters<MT_MIXED, 16>(MT_MIXED) >= 1 &&
+      max_active_clusters<MT_MIXED_DF32, 16>(MT_MIXED_DF32) >= 1)
     g_big_cluster = 16;
   cudaGetLastError();  // a refused non-portable size leaves the 8-CTA choice
   int lo = 0, hi = 0;
@@ -1063,15 +1068,17 @@ cudaError_t launch_fused_step(const Dev& d, int precision, cudaGraphConditionalH
   const size_t sm = tier_smem<Fast>(precision);
   const int g = d.nseg < kFusedCtasPerSm * d.nsm ? d.nseg : kFusedCtasPerSm * d.nsm;
   if (precision == MT_MIXED)
-    k_step1d<true><<<g, Fast::kT, sm, s>>>(d, cond, use_cond);
+    k_step1d<MT_MIXED><<<g, Fast::kT, sm, s>>>(d, cond, use_cond);
+  else if (precision == MT_MIXED_DF32)
+    k_step1d<MT_MIXED_DF32><<<g, Fast::kT, sm, s>>>(d, cond, use_cond);
   else
-    k_step1d<false><<<g, Fast::kT, sm, s>>>(d, cond, use_cond);
+    k_step1d<MT_FP64><<<g, Fast::kT, sm, s>>>(d, cond, use_cond);
   return cudaGetLastError();
 }
 
-template <bool MIX, int CL>
-static cudaError_t launch_big(const Dev& d, int precision, cudaGraphConditionalHandle cond,
-                              int use_cond, cudaStream_t s) {
+template <int PR, int CL>
+static cudaError_t launch_big(const Dev& d, cudaGraphConditionalHandle cond, int use_cond,
+                              cudaStream_t s) {
   // up to 8 clusters, fewer if there are fewer segments
   const int clusters = d.nseg < 8 ? d.nseg : 8;
   cudaLaunchConfig_t cfg = {};
@@ -1082,25 +1089,16 @@ static cudaError_t launch_big(const Dev& d, int precision, cudaGraphConditionalH
   at[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3((unsigned int)(clusters * CL));
   cfg.blockDim = dim3(Big::kT);
-  cfg.dynamicSmemBytes = tier_smem<Big>(precision);
+  cfg.dynamicSmemBytes = tier_smem<Big>(PR);
   cfg.stream = s;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_step1d_big<MIX, CL>, d, cond, use_cond);
+  return cudaLaunchKernelEx(&cfg, k_step1d_big<PR, CL>, d, cond, use_cond);
 }
 
-cudaError_t launch_fused_big(const Dev& d, int precision, cudaGraphConditionalHandle cond,
-                             int use_cond, cudaStream_t s) {
-  if (g_big_cluster == 16)
-    return precision == MT_MIXED ? launch_big<true, 16>(d, precision, cond, use_cond, s)
-                                 : launch_big<false, 16>(d, precision, cond, use_cond, s);
-  return precision == MT_MIXED ? launch_big<true, 8>(d, precision, cond, use_cond, s)
-                               : launch_big<false, 8>(d, precision, cond, use_cond, s);
-}
-
-template <bool MIX, int CL>
-static cudaError_t launch_pred(const Dev& d, int precision, cudaGraphConditionalHandle cond,
-                               int use_cond, cudaStream_t s) {
+template <int PR, int CL>
+static cudaError_t launch_pred(const Dev& d, cudaGraphConditionalHandle cond, int use_cond,
+                               cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1111,20 +1109,37 @@ static cudaError_t launch_pred(const Dev& d, int precision, cudaGraphConditional
   at[1].val.priority = g_top_priority;
   cfg.gridDim = dim3((unsigned int)CL);  // one cluster
   cfg.blockDim = dim3(Big::kT);
-  cfg.dynamicSmemBytes = tier_smem<Big>(precision);
+  cfg.dynamicSmemBytes = tier_smem<Big>(PR);
   cfg.stream = s;
   cfg.attrs = at;
   cfg.numAttrs = 2;
-  return cudaLaunchKernelEx(&cfg, k_step1d_pred<MIX, CL>, d, cond, use_cond);
+  return cudaLaunchKernelEx(&cfg, k_step1d_pred<PR, CL>, d, cond, use_cond);
+}
+
+template <int PR>
+static cudaError_t launch_cluster_tier(const Dev& d, bool pred, cudaGraphConditionalHandle cond,
+                                       int use_cond, cudaStream_t s) {
+  if (g_big_cluster == 16)
+    return pred ? launch_pred<PR, 16>(d, cond, use_cond, s) : launch_big<PR, 16>(d, cond, use_cond, s);
+  return pred ? launch_pred<PR, 8>(d, cond, use_cond, s) : launch_big<PR, 8>(d, cond, use_cond, s);
+}
+
+static cudaError_t launch_cluster(const Dev& d, int precision, bool pred,
+                                  cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) {
+  if (precision == MT_MIXED) return launch_cluster_tier<MT_MIXED>(d, pred, cond, use_cond, s);
+  if (precision == MT_MIXED_DF32)
+    return launch_cluster_tier<MT_MIXED_DF32>(d, pred, cond, use_cond, s);
+  return launch_cluster_tier<MT_FP64>(d, pred, cond, use_cond, s);
+}
+
+cudaError_t launch_fused_big(const Dev& d, int precision, cudaGraphConditionalHandle cond,
+                             int use_cond, cudaStream_t s) {
+  return launch_cluster(d, precision, false, cond, use_cond, s);
 }
 
 cudaError_t launch_fused_pred(const Dev& d, int precision, cudaGraphConditionalHandle cond,
                               int use_cond, cudaStream_t s) {
-  if (g_big_cluster == 16)
-    return precision == MT_MIXED ? launch_pred<true, 16>(d, precision, cond, use_cond, s)
-                                 : launch_pred<false, 16>(d, precision, cond, use_cond, s);
-  return precision == MT_MIXED ? launch_pred<true, 8>(d, precision, cond, use_cond, s)
-                               : launch_pred<false, 8>(d, precision, cond, use_cond, s);
+  return launch_cluster(d, precision, true, cond, use_cond, s);
 }
 
 // Direct launches without a predicted segment: the first tier's partner in

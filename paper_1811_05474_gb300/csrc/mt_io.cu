@@ -60,7 +60,7 @@ cudaError_t launch_upload(const Dev& d, const double* x, const double* A, const 
                           int precision, cudaStream_t s) {
   const double pow2k = 1.0 / d.scale;
   k_upload<<<blocks_for(d.n, kThreads), kThreads, 0, s>>>(d, x, A, B, pow2k,
-                                                          precision == MT_MIXED);
+                                                          precision == MT_MIXED_DF32);
   return cudaGetLastError();
 }
 
@@ -88,7 +88,7 @@ __global__ void k_read_masses(Dev d, double* A, double* B, int mixed) {
 cudaError_t launch_read_masses(const Dev& d, double* A, double* B, int precision,
                                cudaStream_t s) {
   k_read_masses<<<blocks_for(d.n, kThreads), kThreads, 0, s>>>(d, A, B,
-                                                               precision == MT_MIXED);
+                                                               precision == MT_MIXED_DF32);
   return cudaGetLastError();
 }
 
@@ -124,7 +124,7 @@ __global__ void k_species_io(Dev d, int sp, double* out, const double* in, int m
 cudaError_t launch_species_io(const Dev& d, int sp, double* out, const double* in, int precision,
                               cudaStream_t s) {
   k_species_io<<<blocks_for(d.n, kThreads), kThreads, 0, s>>>(d, sp, out, in,
-                                                              precision == MT_MIXED);
+                                                              precision == MT_MIXED_DF32);
   return cudaGetLastError();
 }
 

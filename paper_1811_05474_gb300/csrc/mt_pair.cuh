@@ -60,14 +60,17 @@ struct Weight<true, DIM> {
   }
 };
 
+// Binary32 weights, normalised weights and 1 / r_i: both mixed precisions.
+constexpr bool mixw(int precision) { return precision != MT_FP64; }
+
 // ------------------------------------------------------------ mass access --
 
-template <bool MIX>
+template <int PR>
 struct Mass;
 
-// Per-particle accumulation of sum_j P_ij (M_j - M_i): binary64 in FP64;
-// in MIXED the binary32 terms are summed by cascaded compensated summation
-// (Ogita, Rump & Oishi's Sum2): each addition's exact rounding error, from
+// Per-particle accumulation of sum_j P_ij (M_j - M_i): binary64 in MT_FP64
+// and MT_MIXED; in MT_MIXED_DF32 the binary32 terms are summed by cascaded
+// compensated summation (Ogita, Rump & Oishi's Sum2): each addition's exact rounding error, from
 // Knuth's two-sum, is added into a second sum, and the pair (s, c) is used
 // unrounded.  The flux P_ij (M_j - M_i) is bitwise antisymmetric between i
 // and j, so the transfer conserves mass to the pair's precision.
@@ -75,7 +78,7 @@ struct kahan {
   float s, c;
 };
 template <>
-struct Mass<false> {
+struct Mass<MT_FP64> {
   using V = double;
   using Acc = double;
   static __device__ __forceinline__ void acc(double& a, double P, double d) { a += P * d; }
@@ -100,8 +103,35 @@ struct Mass<false> {
   static __device__ __forceinline__ double to_double(double v) { return v; }
 };
 
+// MT_MIXED: the normalised weight P is binary32; the masses, the
+// difference M_j - M_i, the flux term P (M_j - M_i) (P widened exactly), its
+// sum, the update and the reaction are binary64.
 template <>
-struct Mass<true> {
+struct Mass<MT_MIXED> {
+  using V = double;
+  using Acc = double;
+  static __device__ __forceinline__ void acc(double& a, float P, double d) {
+    a += (double)P * d;
+  }
+  static __device__ __forceinline__ double load(const unsigned long long* M, long long i) {
+    return f64_load(M, i);
+  }
+  static __device__ __forceinline__ void store(unsigned long long* M, long long i, double v) {
+    f64_store(M, i, v);
+  }
+  static __device__ __forceinline__ double diff(double a, double b) { return a - b; }
+  static __device__ __forceinline__ void update(double& A, double& B, double dA, double dB,
+                                                int react) {
+    Mass<MT_FP64>::update(A, B, dA, dB, react);
+  }
+  static __device__ __forceinline__ double to_double(double v) { return v; }
+};
+
+// MT_MIXED_DF32: masses as unevaluated sums of two binary32 numbers, flux
+// terms in binary32 summed with compensation, compensated update and
+// reaction (binary32 arithmetic only).
+template <>
+struct Mass<MT_MIXED_DF32> {
   using V = df;
   using Acc = kahan;
   static __device__ __forceinline__ void acc(kahan& a, float P, float d) {
@@ -150,7 +180,7 @@ __device__ __forceinline__ SpeciesPair species_pair(const Dev& d, int sp) {
 }
 
 // Row sum r_i over a dense neighbourhood (hundreds to thousands of terms):
-// binary64, or in MIXED a binary32 sum with each addition's rounding error
+// binary64, or with binary32 weights a binary32 sum with each addition's rounding error
 // (Knuth's two-sum) collected in a second term, so the sum keeps about twice
 // binary32's precision however many weights it adds.
 template <bool MIX>

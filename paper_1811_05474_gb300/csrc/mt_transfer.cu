@@ -12,7 +12,7 @@
 //         particle's cell (cell width > Smax), contiguous per row.
 //   brute all n particles in shared-memory tiles, with (BRUTE) or without
 //         (FULL, the paper's full-matrix reference) the cutoff test.
-// Precision: MIX = false is IEEE binary64 throughout; MIX = true forms
+// Precision: mixw(PR) = false is IEEE binary64 throughout; mixw(PR) = true forms
 // weights and normalised weights in binary32 and updates the double-binary32
 // masses with compensated additions.
 #include "mt_pair.cuh"
@@ -56,10 +56,10 @@ __device__ void finish_step(const Dev& d, int flip_x, int flip_m) {
 // added with Knuth's two-sum, the rounding errors and the low parts collected
 // in a second term; as accurate here as double-binary32 additions, at a third
 // of the operations).
-template <bool MIX>
+template <int PR>
 struct ThreadObs;
 template <>
-struct ThreadObs<false> {
+struct ThreadObs<false> {  // binary64 masses
   Obs3<double> v{};
   __device__ __forceinline__ void add(double a, double b) {
     v = obs3_add(v, Obs3<double>{a, b, a - b});
@@ -67,7 +67,7 @@ struct ThreadObs<false> {
   __device__ __forceinline__ Obs3<double> value() const { return v; }
 };
 template <>
-struct ThreadObs<true> {
+struct ThreadObs<true> {  // double-binary32 masses
   kahan a{0.f, 0.f}, b{0.f, 0.f}, d{0.f, 0.f};
   static __device__ __forceinline__ void put(kahan& k, float hi, float lo) {
     const df e = two_sum(k.s, hi);
@@ -85,9 +85,9 @@ struct ThreadObs<true> {
   }
 };
 
-template <bool MIX>
+template <int PR>
 __global__ void __launch_bounds__(kThreads) k_obs(Dev d) {
-  using MS = Mass<MIX>;
+  using MS = Mass<PR>;
   using MV = typename MS::V;
   constexpr int kPer = kObsChunk / kThreads;  // slots per thread
   __shared__ Obs3<MV> s_w[kThreads / 32];
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kThreads) k_obs(Dev d) {
     va[k] = p < a1 ? MS::load(M, p) : MV{};
     vb[k] = p < a1 ? MS::load(M, d.n + p) : MV{};
   }
-  ThreadObs<MIX> acc;
+  ThreadObs<PR == MT_MIXED_DF32> acc;
 #pragma unroll
   for (int k = 0; k < kPer; ++k) acc.add(va[k], vb[k]);
   const Obs3<MV> t = obs3_block<MV, kThreads>(acc.value(), s_w);
@@ -146,18 +146,18 @@ __global__ void __launch_bounds__(kThreads) k_obs(Dev d) {
 
 cudaError_t launch_obs(const Dev& d, int precision, cudaStream_t s) {
   if (d.observe_cap <= 0 || d.nochunk <= 0) return cudaSuccess;
-  if (precision == MT_MIXED)
-    k_obs<true><<<d.nochunk, kThreads, 0, s>>>(d);
+  if (precision == MT_MIXED_DF32)
+    k_obs<MT_MIXED_DF32><<<d.nochunk, kThreads, 0, s>>>(d);
   else
-    k_obs<false><<<d.nochunk, kThreads, 0, s>>>(d);
+    k_obs<MT_FP64><<<d.nochunk, kThreads, 0, s>>>(d);  // binary64 masses
   return cudaGetLastError();
 }
 
 // ================================================================ 1-d walk ==
 
-template <bool MIX>
+template <int PR>
 __global__ void __launch_bounds__(kThreads) k_rowsum_walk(Dev d) {
-  using W = Weight<MIX, 1>;
+  using W = Weight<mixw(PR), 1>;
   using T = typename W::T;
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (p >= d.n) return;
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kThreads) k_rowsum_walk(Dev d) {
       r += W::eval(d, D, 0);
     }
   }
-  store_rinv<MIX>(d, p, r);
+  store_rinv<mixw(PR)>(d, p, r);
   // gather id and masses into the sorted slots (stage buffer)
   const int s = d.src[p];
   d.id[xc ^ 1][p] = d.id[xc][s];
@@ -202,11 +202,11 @@ __global__ void __launch_bounds__(kThreads) k_rowsum_walk(Dev d) {
 // observables and the end of the step.  TR = true: the extra species sp and
 // sp + 1 (sp alone when it is the last), conservative, run before the A/B
 // pass of the same step.
-template <bool MIX, bool TR>
+template <int PR, bool TR>
 __global__ void __launch_bounds__(kThreads) k_exchange_walk(Dev d, int sp) {
-  using W = Weight<MIX, 1>;
+  using W = Weight<mixw(PR), 1>;
   using T = typename W::T;
-  using MS = Mass<MIX>;
+  using MS = Mass<PR>;
   using MV = typename MS::V;
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
   const bool valid = p < d.n;
@@ -218,12 +218,12 @@ __global__ void __launch_bounds__(kThreads) k_exchange_walk(Dev d, int sp) {
     const unsigned long long* MA = d.M[mc ^ 1] + sq.oa;
     const unsigned long long* MB = d.M[mc ^ 1] + sq.ob;
     const long long x = Xs[p];
-    const T ip = load_rinv<MIX>(d, p);
+    const T ip = load_rinv<mixw(PR)>(d, p);
     A = MS::load(MA, p);
     B = MS::load(MB, p);
     typename MS::Acc dA{}, dB{};
     auto pair = [&](long long q, long long D) {
-      const T P = normalised<T>(d.norm, W::eval(d, D, 0), ip, load_rinv<MIX>(d, q));
+      const T P = normalised<T>(d.norm, W::eval(d, D, 0), ip, load_rinv<mixw(PR)>(d, q));
       MS::acc(dA, P, MS::diff(MS::load(MA, q), A));
       MS::acc(dB, P, MS::diff(MS::load(MB, q), B));
     };
@@ -317,9 +317,9 @@ __device__ __forceinline__ TileRanges tile_ranges(long long jl, long long jr, lo
   return t;
 }
 
-template <bool MIX>
+template <int PR>
 __global__ void __launch_bounds__(kThreads) k_rowsum_tile(Dev d) {
-  using W = Weight<MIX, 1>;
+  using W = Weight<mixw(PR), 1>;
   using T = typename W::T;
   __shared__ unsigned int s_x[kTileChunk];
   __shared__ long long s_lohi[2];
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(kThreads) k_rowsum_tile(Dev d) {
   // chains) and each group's sum enters a compensated sum: the group sums'
   // rounding (at most kTileGroup terms of at most 1) stays near binary32's
   // precision relative to r_p, at a plain addition per weight.
-  RowSum<MIX> r(T(0));
+  RowSum<mixw(PR)> r(T(0));
   for (long long c0 = t.lo; c0 < t.hi; c0 += kTileChunk) {
     const int nc = (int)min((long long)kTileChunk, t.hi - c0);
     for (int i = threadIdx.x; i < nc; i += kThreads) s_x[i] = (unsigned int)Xs[c0 + i];
@@ -366,17 +366,17 @@ __global__ void __launch_bounds__(kThreads) k_rowsum_tile(Dev d) {
     __syncthreads();
   }
   if (!valid) return;
-  store_rinv<MIX>(d, p, r.value());
+  store_rinv<mixw(PR)>(d, p, r.value());
   const int s = d.src[p];
   d.id[xc ^ 1][p] = d.id[xc][s];
   gather_masses(d, mc, p, s);
 }
 
-template <bool MIX, bool TR>
+template <int PR, bool TR>
 __global__ void __launch_bounds__(kThreads) k_exchange_tile(Dev d, int sp) {
-  using W = Weight<MIX, 1>;
+  using W = Weight<mixw(PR), 1>;
   using T = typename W::T;
-  using MS = Mass<MIX>;
+  using MS = Mass<PR>;
   using MV = typename MS::V;
   __shared__ unsigned int s_x[kTileChunk];
   __shared__ T s_r[kTileChunk];
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(kThreads) k_exchange_tile(Dev d, int sp) {
   if (valid) {
     A = MS::load(MA, p);
     B = MS::load(MB, p);
-    ip = load_rinv<MIX>(d, p);
+    ip = load_rinv<mixw(PR)>(d, p);
   }
   // two accumulator sets (even and odd candidates) halve the dependent
   // chain of compensated additions
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(kThreads) k_exchange_tile(Dev d, int sp) {
     const int nc = (int)min((long long)kTileChunk, t.hi - c0);
     for (int i = threadIdx.x; i < nc; i += kThreads) {
       s_x[i] = (unsigned int)Xs[c0 + i];
-      s_r[i] = sym ? load_rinv<MIX>(d, c0 + i) : T(0);
+      s_r[i] = sym ? load_rinv<mixw(PR)>(d, c0 + i) : T(0);
       s_a[i] = MS::load(MA, c0 + i);
       s_b[i] = MS::load(MB, c0 + i);
     }
@@ -496,9 +496,9 @@ __device__ __forceinline__ long long gap(const Dev& d, const Ring& g, const long
   return d.periodic ? wrap(Xs[p] - Xs[q], g.Lq) : Xs[p] - Xs[q];
 }
 
-template <bool MIX>
+template <int PR>
 __global__ void __launch_bounds__(kThreads) k_band_build(Dev d) {
-  using W = Weight<MIX, 1>;
+  using W = Weight<mixw(PR), 1>;
   using T = typename W::T;
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (p >= d.n) return;
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(kThreads) k_band_build(Dev d) {
   T* band = static_cast<T*>(d.band);
   const int s = d.src[p];
   const Ring g = walk_ring(d, d.id[xc][s]);
-  RowSum<MIX> r(T(0));
+  RowSum<mixw(PR)> r(T(0));
   long long k = 1;
   const long long kr = walk_right(d, g, p);
   for (; k <= kr; ++k) {
@@ -527,16 +527,16 @@ __global__ void __launch_bounds__(kThreads) k_band_build(Dev d) {
   gather_masses(d, mc, p, s);
 }
 
-template <bool MIX>
+template <int PR>
 __global__ void __launch_bounds__(kThreads) k_band_rowsum(Dev d) {
-  using W = Weight<MIX, 1>;
+  using W = Weight<mixw(PR), 1>;
   using T = typename W::T;
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (p >= d.n) return;
   const T* band = static_cast<const T*>(d.band);
   const int xc = d.ctrl->xcur;
   const Ring g = walk_ring(d, d.id[xc ^ 1][p]);
-  RowSum<MIX> r(T(1));  // self
+  RowSum<mixw(PR)> r(T(1));  // self
   r.add(static_cast<const T*>(d.rinv)[p]);  // right part
   const int kl = d.cnt[d.n + p];
   const int kb = kl < d.band_cap ? kl : d.band_cap;
@@ -546,14 +546,14 @@ __global__ void __launch_bounds__(kThreads) k_band_rowsum(Dev d) {
     const long long* Xs = d.X[xc ^ 1];
     for (int k = kb + 1; k <= kl; ++k) r.add(W::eval(d, gap(d, g, Xs, ring(d, g, p, -k), p), 0));
   }
-  store_rinv<MIX>(d, p, r.value());
+  store_rinv<mixw(PR)>(d, p, r.value());
 }
 
-template <bool MIX, bool TR>
+template <int PR, bool TR>
 __global__ void __launch_bounds__(kThreads) k_band_exchange(Dev d, int sp) {
-  using W = Weight<MIX, 1>;
+  using W = Weight<mixw(PR), 1>;
   using T = typename W::T;
-  using MS = Mass<MIX>;
+  using MS = Mass<PR>;
   using MV = typename MS::V;
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
   const bool valid = p < d.n;
@@ -566,12 +566,12 @@ __global__ void __launch_bounds__(kThreads) k_band_exchange(Dev d, int sp) {
     const unsigned long long* MA = d.M[mc ^ 1] + sq.oa;
     const unsigned long long* MB = d.M[mc ^ 1] + sq.ob;
     const T* band = static_cast<const T*>(d.band);
-    const T ip = load_rinv<MIX>(d, p);
+    const T ip = load_rinv<mixw(PR)>(d, p);
     A = MS::load(MA, p);
     B = MS::load(MB, p);
     typename MS::Acc dA{}, dB{};
     auto pair = [&](long long q, T w) {
-      const T P = normalised<T>(d.norm, w, ip, load_rinv<MIX>(d, q));
+      const T P = normalised<T>(d.norm, w, ip, load_rinv<mixw(PR)>(d, q));
       MS::acc(dA, P, MS::diff(MS::load(MA, q), A));
       MS::acc(dB, P, MS::diff(MS::load(MB, q), B));
     };
@@ -603,18 +603,18 @@ __global__ void __launch_bounds__(kThreads) k_band_exchange(Dev d, int sp) {
 // =============================================================== 2-d cells ==
 
 // One run [q0, q1) of candidate slots for the particle in slot p at (x, y).
-template <bool MIX, bool EXCHANGE, bool PER>
+template <int PR, bool EXCHANGE, bool PER>
 __device__ __forceinline__ void cell2_run(const Dev& d, const long long* Xs, long long p,
                                           long long x, long long y, int q0, int q1,
-                                          typename Weight<MIX, 2>::T& r,
+                                          typename Weight<mixw(PR), 2>::T& r,
                                           const unsigned long long* M,
-                                          typename Weight<MIX, 2>::T ip,
-                                          typename Mass<MIX>::V A, typename Mass<MIX>::V B,
-                                          typename Mass<MIX>::Acc& dA,
-                                          typename Mass<MIX>::Acc& dB, long long ob) {
-  using W = Weight<MIX, 2>;
+                                          typename Weight<mixw(PR), 2>::T ip,
+                                          typename Mass<PR>::V A, typename Mass<PR>::V B,
+                                          typename Mass<PR>::Acc& dA,
+                                          typename Mass<PR>::Acc& dB, long long ob) {
+  using W = Weight<mixw(PR), 2>;
   using T = typename W::T;
-  using MS = Mass<MIX>;
+  using MS = Mass<PR>;
   for (int q = q0; q < q1; ++q) {
     long long dx = Xs[q] - x, dy = Xs[d.n + q] - y;
     if (PER) {
@@ -626,7 +626,7 @@ __device__ __forceinline__ void cell2_run(const Dev& d, const long long* Xs, lon
     if (!EXCHANGE) {
       r += w;
     } else if (q != p) {
-      const T P = normalised<T>(d.norm, w, ip, load_rinv<MIX>(d, q));
+      const T P = normalised<T>(d.norm, w, ip, load_rinv<mixw(PR)>(d, q));
       MS::acc(dA, P, MS::diff(MS::load(M, q), A));
       MS::acc(dB, P, MS::diff(MS::load(M, ob + q), B));
     }
@@ -636,18 +636,18 @@ __device__ __forceinline__ void cell2_run(const Dev& d, const long long* Xs, lon
 // All candidates of the particle in slot p: the 3 x 3 block of cells around
 // its cell (reflecting walls), or the wrapped cell spans (periodic).  M:
 // the first species' masses; the second's are ob words further.
-template <bool MIX, bool EXCHANGE, bool PER>
+template <int PR, bool EXCHANGE, bool PER>
 __device__ __forceinline__ void cell2_loop(const Dev& d, const long long* Xs, long long p,
                                            long long x, long long y,
-                                           typename Weight<MIX, 2>::T& r,
+                                           typename Weight<mixw(PR), 2>::T& r,
                                            const unsigned long long* M,
-                                           typename Weight<MIX, 2>::T ip,
-                                           typename Mass<MIX>::V A, typename Mass<MIX>::V B,
-                                           typename Mass<MIX>::Acc& dA,
-                                           typename Mass<MIX>::Acc& dB, long long ob) {
+                                           typename Weight<mixw(PR), 2>::T ip,
+                                           typename Mass<PR>::V A, typename Mass<PR>::V B,
+                                           typename Mass<PR>::Acc& dA,
+                                           typename Mass<PR>::Acc& dB, long long ob) {
   if (PER) {
     cells2_visit(d, x, y, [&](int q0, int q1) {
-      cell2_run<MIX, EXCHANGE, true>(d, Xs, p, x, y, q0, q1, r, M, ip, A, B, dA, dB, ob);
+      cell2_run<PR, EXCHANGE, true>(d, Xs, p, x, y, q0, q1, r, M, ip, A, B, dA, dB, ob);
     });
     return;
   }
@@ -658,35 +658,35 @@ __device__ __forceinline__ void cell2_loop(const Dev& d, const long long* Xs, lo
   const long long kx1 = kx + 1 < d.ncx ? kx + 1 : d.ncx - 1;
   for (long long row = ky - 1; row <= ky + 1; ++row) {
     if (row < 0 || row >= d.ncy) continue;
-    cell2_run<MIX, EXCHANGE, false>(d, Xs, p, x, y, d.start[row * d.ncx + kx0],
+    cell2_run<PR, EXCHANGE, false>(d, Xs, p, x, y, d.start[row * d.ncx + kx0],
                                     d.start[row * d.ncx + kx1 + 1], r, M, ip, A, B, dA, dB, ob);
   }
 }
 
 // PER: periodic walls (wrapped cell spans, minimum-image separations), a
 // separate instantiation so the reflecting kernels keep their registers.
-template <bool MIX, bool PER>
+template <int PR, bool PER>
 __global__ void __launch_bounds__(kThreads) k_rowsum_cell2(Dev d) {
-  using T = typename Weight<MIX, 2>::T;
+  using T = typename Weight<mixw(PR), 2>::T;
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (p >= d.n) return;
   const int xc = d.ctrl->xcur, mc = d.ctrl->mcur;
   const long long* Xs = d.X[xc ^ 1];
   T r = T(0);
-  typename Mass<MIX>::Acc dummy{};
-  typename Mass<MIX>::V z{};
-  cell2_loop<MIX, false, PER>(d, Xs, p, Xs[p], Xs[d.n + p], r, nullptr, T(0), z, z, dummy,
+  typename Mass<PR>::Acc dummy{};
+  typename Mass<PR>::V z{};
+  cell2_loop<PR, false, PER>(d, Xs, p, Xs[p], Xs[d.n + p], r, nullptr, T(0), z, z, dummy,
                               dummy, 0);
-  store_rinv<MIX>(d, p, r);
+  store_rinv<mixw(PR)>(d, p, r);
   const int s = d.src[p];
   d.id[xc ^ 1][p] = d.id[xc][s];
   gather_masses(d, mc, p, s);
 }
 
-template <bool MIX, bool TR, bool PER>
+template <int PR, bool TR, bool PER>
 __global__ void __launch_bounds__(kThreads) k_exchange_cell2(Dev d, int sp) {
-  using T = typename Weight<MIX, 2>::T;
-  using MS = Mass<MIX>;
+  using T = typename Weight<mixw(PR), 2>::T;
+  using MS = Mass<PR>;
   using MV = typename MS::V;
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
   const bool valid = p < d.n;
@@ -701,7 +701,7 @@ __global__ void __launch_bounds__(kThreads) k_exchange_cell2(Dev d, int sp) {
     B = MS::load(MB, p);
     T r = T(0);
     typename MS::Acc dA{}, dB{};
-    cell2_loop<MIX, true, PER>(d, Xs, p, Xs[p], Xs[d.n + p], r, MA, load_rinv<MIX>(d, p), A, B,
+    cell2_loop<PR, true, PER>(d, Xs, p, Xs[p], Xs[d.n + p], r, MA, load_rinv<mixw(PR)>(d, p), A, B,
                                dA, dB, sq.ob - sq.oa);
     MS::update(A, B, dA, dB, TR ? 0 : d.react);
     MS::store(d.M[mc] + sq.oa, p, A);
@@ -714,9 +714,9 @@ __global__ void __launch_bounds__(kThreads) k_exchange_cell2(Dev d, int sp) {
 // All pairs, j-particles staged through shared memory in tiles.  Particles
 // keep their caller order (no sort); masses ping-pong between buffers.
 
-template <bool MIX, bool CUT, int DIM>
+template <int PR, bool CUT, int DIM>
 __global__ void __launch_bounds__(kThreads) k_rowsum_brute(Dev d) {
-  using W = Weight<MIX, DIM>;
+  using W = Weight<mixw(PR), DIM>;
   using T = typename W::T;
   __shared__ long long s_x[kBruteTile];
   __shared__ long long s_y[DIM == 2 ? kBruteTile : 1];
@@ -750,14 +750,14 @@ __global__ void __launch_bounds__(kThreads) k_rowsum_brute(Dev d) {
     }
     __syncthreads();
   }
-  if (valid) store_rinv<MIX>(d, p, r);
+  if (valid) store_rinv<mixw(PR)>(d, p, r);
 }
 
-template <bool MIX, bool CUT, int DIM, bool TR>
+template <int PR, bool CUT, int DIM, bool TR>
 __global__ void __launch_bounds__(kThreads) k_exchange_brute(Dev d, int sp) {
-  using W = Weight<MIX, DIM>;
+  using W = Weight<mixw(PR), DIM>;
   using T = typename W::T;
-  using MS = Mass<MIX>;
+  using MS = Mass<PR>;
   using MV = typename MS::V;
   __shared__ long long s_x[kBruteTile];
   __shared__ long long s_y[DIM == 2 ? kBruteTile : 1];
@@ -778,7 +778,7 @@ __global__ void __launch_bounds__(kThreads) k_exchange_brute(Dev d, int sp) {
   if (valid) {
     A = MS::load(MA, p);
     B = MS::load(MB, p);
-    ip = load_rinv<MIX>(d, p);
+    ip = load_rinv<mixw(PR)>(d, p);
   }
   typename MS::Acc dA{}, dB{};
   for (long long j0 = 0; j0 < d.n; j0 += kBruteTile) {
@@ -786,7 +786,7 @@ __global__ void __launch_bounds__(kThreads) k_exchange_brute(Dev d, int sp) {
     if (j < d.n) {
       s_x[threadIdx.x] = X[j];
       if (DIM == 2) s_y[threadIdx.x] = X[d.n + j];
-      s_ri[threadIdx.x] = load_rinv<MIX>(d, j);
+      s_ri[threadIdx.x] = load_rinv<mixw(PR)>(d, j);
       s_a[threadIdx.x] = MS::load(MA, j);
       s_b[threadIdx.x] = MS::load(MB, j);
     }
@@ -832,119 +832,121 @@ __global__ void __launch_bounds__(kThreads) k_gather_species(Dev d) {
 
 // --------------------------------------------------------------- launch --
 
-template <bool MIX, bool PER>
+template <int PR, bool PER>
 static void cell2_passes(const Dev& d, unsigned int g, cudaStream_t s, Marker& mk) {
   mk("rowsum_cell2", s);
-  k_rowsum_cell2<MIX, PER><<<g, kThreads, 0, s>>>(d);
+  k_rowsum_cell2<PR, PER><<<g, kThreads, 0, s>>>(d);
   if (d.nspec > 2) {
     mk("gather_species", s);
     k_gather_species<<<g, kThreads, 0, s>>>(d);
   }
   for (int sp = 2; sp < d.nspec; sp += 2) {
     mk("exchange_cell2_species", s);
-    k_exchange_cell2<MIX, true, PER><<<g, kThreads, 0, s>>>(d, sp);
+    k_exchange_cell2<PR, true, PER><<<g, kThreads, 0, s>>>(d, sp);
   }
   mk("exchange_cell2", s);
-  k_exchange_cell2<MIX, false, PER><<<g, kThreads, 0, s>>>(d, 0);
+  k_exchange_cell2<PR, false, PER><<<g, kThreads, 0, s>>>(d, 0);
 }
 
-template <bool MIX, bool TR>
+template <int PR, bool TR>
 static void launch_exchange_brute(const Dev& d, bool cut, unsigned int g, cudaStream_t s,
                                   int sp) {
   if (cut) {
     if (d.dim == 1)
-      k_exchange_brute<MIX, true, 1, TR><<<g, kThreads, 0, s>>>(d, sp);
+      k_exchange_brute<PR, true, 1, TR><<<g, kThreads, 0, s>>>(d, sp);
     else
-      k_exchange_brute<MIX, true, 2, TR><<<g, kThreads, 0, s>>>(d, sp);
+      k_exchange_brute<PR, true, 2, TR><<<g, kThreads, 0, s>>>(d, sp);
   } else {
     if (d.dim == 1)
-      k_exchange_brute<MIX, false, 1, TR><<<g, kThreads, 0, s>>>(d, sp);
+      k_exchange_brute<PR, false, 1, TR><<<g, kThreads, 0, s>>>(d, sp);
     else
-      k_exchange_brute<MIX, false, 2, TR><<<g, kThreads, 0, s>>>(d, sp);
+      k_exchange_brute<PR, false, 2, TR><<<g, kThreads, 0, s>>>(d, sp);
   }
 }
 
 // The extra species' passes (pairs 2-3, 4-5, ...) run between the row sums
 // and the A/B pass, which ends the step.
-template <bool MIX>
+template <int PR>
 static void transfer_t(const Dev& d, int search, cudaStream_t s, Marker& mk) {
   const unsigned int g = (unsigned int)((d.n + kThreads - 1) / kThreads);
   if (search == MT_SEARCH_CELL) {
     if (d.dim == 1 && d.band_cap > 0) {
       mk("band_build", s);
-      k_band_build<MIX><<<g, kThreads, 0, s>>>(d);
+      k_band_build<PR><<<g, kThreads, 0, s>>>(d);
       mk("band_rowsum", s);
-      k_band_rowsum<MIX><<<g, kThreads, 0, s>>>(d);
+      k_band_rowsum<PR><<<g, kThreads, 0, s>>>(d);
       if (d.nspec > 2) {
         mk("gather_species", s);
         k_gather_species<<<g, kThreads, 0, s>>>(d);
       }
       for (int sp = 2; sp < d.nspec; sp += 2) {
         mk("band_exchange_species", s);
-        k_band_exchange<MIX, true><<<g, kThreads, 0, s>>>(d, sp);
+        k_band_exchange<PR, true><<<g, kThreads, 0, s>>>(d, sp);
       }
       mk("band_exchange", s);
-      k_band_exchange<MIX, false><<<g, kThreads, 0, s>>>(d, 0);
+      k_band_exchange<PR, false><<<g, kThreads, 0, s>>>(d, 0);
     } else if (d.dim == 1 && d.tile) {
       mk("rowsum_tile", s);
-      k_rowsum_tile<MIX><<<g, kThreads, 0, s>>>(d);
+      k_rowsum_tile<PR><<<g, kThreads, 0, s>>>(d);
       if (d.nspec > 2) {
         mk("gather_species", s);
         k_gather_species<<<g, kThreads, 0, s>>>(d);
       }
       for (int sp = 2; sp < d.nspec; sp += 2) {
         mk("exchange_tile_species", s);
-        k_exchange_tile<MIX, true><<<g, kThreads, 0, s>>>(d, sp);
+        k_exchange_tile<PR, true><<<g, kThreads, 0, s>>>(d, sp);
       }
       mk("exchange_tile", s);
-      k_exchange_tile<MIX, false><<<g, kThreads, 0, s>>>(d, 0);
+      k_exchange_tile<PR, false><<<g, kThreads, 0, s>>>(d, 0);
     } else if (d.dim == 1) {
       mk("rowsum_walk", s);
-      k_rowsum_walk<MIX><<<g, kThreads, 0, s>>>(d);
+      k_rowsum_walk<PR><<<g, kThreads, 0, s>>>(d);
       if (d.nspec > 2) {
         mk("gather_species", s);
         k_gather_species<<<g, kThreads, 0, s>>>(d);
       }
       for (int sp = 2; sp < d.nspec; sp += 2) {
         mk("exchange_walk_species", s);
-        k_exchange_walk<MIX, true><<<g, kThreads, 0, s>>>(d, sp);
+        k_exchange_walk<PR, true><<<g, kThreads, 0, s>>>(d, sp);
       }
       mk("exchange_walk", s);
-      k_exchange_walk<MIX, false><<<g, kThreads, 0, s>>>(d, 0);
+      k_exchange_walk<PR, false><<<g, kThreads, 0, s>>>(d, 0);
     } else if (d.periodic) {
-      cell2_passes<MIX, true>(d, g, s, mk);
+      cell2_passes<PR, true>(d, g, s, mk);
     } else {
-      cell2_passes<MIX, false>(d, g, s, mk);
+      cell2_passes<PR, false>(d, g, s, mk);
     }
   } else {
     const bool cut = search == MT_SEARCH_BRUTE;
     mk(cut ? "rowsum_brute" : "rowsum_full", s);
     if (cut) {
       if (d.dim == 1)
-        k_rowsum_brute<MIX, true, 1><<<g, kThreads, 0, s>>>(d);
+        k_rowsum_brute<PR, true, 1><<<g, kThreads, 0, s>>>(d);
       else
-        k_rowsum_brute<MIX, true, 2><<<g, kThreads, 0, s>>>(d);
+        k_rowsum_brute<PR, true, 2><<<g, kThreads, 0, s>>>(d);
     } else {
       if (d.dim == 1)
-        k_rowsum_brute<MIX, false, 1><<<g, kThreads, 0, s>>>(d);
+        k_rowsum_brute<PR, false, 1><<<g, kThreads, 0, s>>>(d);
       else
-        k_rowsum_brute<MIX, false, 2><<<g, kThreads, 0, s>>>(d);
+        k_rowsum_brute<PR, false, 2><<<g, kThreads, 0, s>>>(d);
     }
     for (int sp = 2; sp < d.nspec; sp += 2) {
       mk(cut ? "exchange_brute_species" : "exchange_full_species", s);
-      launch_exchange_brute<MIX, true>(d, cut, g, s, sp);
+      launch_exchange_brute<PR, true>(d, cut, g, s, sp);
     }
     mk(cut ? "exchange_brute" : "exchange_full", s);
-    launch_exchange_brute<MIX, false>(d, cut, g, s, 0);
+    launch_exchange_brute<PR, false>(d, cut, g, s, 0);
   }
 }
 
 cudaError_t launch_transfer(const Dev& d, int search, int precision, cudaStream_t s,
                             Marker& mk) {
   if (precision == MT_MIXED)
-    transfer_t<true>(d, search, s, mk);
+    transfer_t<MT_MIXED>(d, search, s, mk);
+  else if (precision == MT_MIXED_DF32)
+    transfer_t<MT_MIXED_DF32>(d, search, s, mk);
   else
-    transfer_t<false>(d, search, s, mk);
+    transfer_t<MT_FP64>(d, search, s, mk);
   return cudaGetLastError();
 }
 

@@ -24,7 +24,7 @@ MT_ERR_TIMEOUT = -5
 MT_ERR_STATE = -6
 
 MT_SEARCH_CELL, MT_SEARCH_BRUTE, MT_SEARCH_FULL = 0, 1, 2
-MT_FP64, MT_MIXED = 0, 1
+MT_FP64, MT_MIXED, MT_MIXED_DF32 = 0, 1, 2
 MT_NORM_SYM, MT_NORM_ROW = 0, 1
 MT_MEM_HOST, MT_MEM_DEVICE = 0, 1
 MT_WALLS_REFLECT, MT_WALLS_PERIODIC = 0, 1

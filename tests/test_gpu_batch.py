@@ -10,7 +10,7 @@ import pytest
 import oracle as O
 from paper_1811_05474_gb300 import mt, synth
 
-from .test_gpu_parity import TOL, assert_masses
+from .test_gpu_parity import PRECISIONS, TOL, assert_masses
 
 pytestmark = pytest.mark.gpu
 
@@ -69,7 +69,7 @@ def run_batch_vs_oracle(sim, ns, Ls, xs, As, Bs, steps, seed, check_every=1):
     return Xs, a, b, po
 
 
-@pytest.mark.parametrize("precision", [mt.MT_FP64, mt.MT_MIXED])
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_batch_matches_oracle_per_realisation(precision):
     """Uneven realisations (1 to 3000 particles, density 1 and denser ones)
     with observables and pair sets per realisation."""

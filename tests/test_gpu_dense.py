@@ -8,7 +8,7 @@ import pytest
 import oracle as O
 from paper_1811_05474_gb300 import mt, synth
 
-from .test_gpu_parity import TOL, assert_masses
+from .test_gpu_parity import PRECISIONS, TOL, assert_masses
 from .test_oracle_species import oracle_step_species, species_masses
 
 pytestmark = pytest.mark.gpu
@@ -34,7 +34,7 @@ def profile_names(sim):
     (77, 0.4, 2, 3),          # one partial CTA, every particle within reach of every other
     (1000, 3.3, 2, 3),        # four CTAs, a ragged last one
 ])
-@pytest.mark.parametrize("precision", [mt.MT_FP64, mt.MT_MIXED])
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_dense_tiles_match_oracle(n, L, S, steps, precision):
     p = mt.mt_params_init(n=n, L=(L,), v=(0.05,), D_mt=0.5, D_rw=0.5, dt=0.1,
                           precision=precision, species=S, observe_cap=4)

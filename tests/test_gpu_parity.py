@@ -17,7 +17,8 @@ from paper_1811_05474_gb300 import mt, synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = {mt.MT_FP64: 1e-12, mt.MT_MIXED: 1e-6}
+TOL = {mt.MT_FP64: 1e-12, mt.MT_MIXED: 1e-6, mt.MT_MIXED_DF32: 1e-6}
+PRECISIONS = [mt.MT_FP64, mt.MT_MIXED, mt.MT_MIXED_DF32]
 MREF = 0.5
 
 
@@ -89,18 +90,19 @@ def test_1d_n1000_100_steps_fp64(search):
 
 
 @pytest.mark.parametrize("search", [mt.MT_SEARCH_CELL, mt.MT_SEARCH_BRUTE, mt.MT_SEARCH_FULL])
-def test_1d_n1000_100_steps_mixed(search):
+@pytest.mark.parametrize("precision", [mt.MT_MIXED, mt.MT_MIXED_DF32])
+def test_1d_n1000_100_steps_mixed(search, precision):
     n, L, steps = 1000, 1000.0, 100
     x = synth.uniform_positions(n, L, seed=0)
     A, B = synth.uniform_masses(n, seed=0)
-    sim = make(n, L, search=search, precision=mt.MT_MIXED, observe_cap=steps)
+    sim = make(n, L, search=search, precision=precision, observe_cap=steps)
     run_both(sim, x, A, B, steps, check_every=False)
 
 
 # ------------------------------------------------------------ edge cases --
 
 @pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 255, 256, 257, 4099])
-@pytest.mark.parametrize("precision", [mt.MT_FP64, mt.MT_MIXED])
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_sizes_and_ragged_tails(n, precision):
     L = max(4.0, n * 0.8)
     x = synth.uniform_positions(n, L, seed=n)
@@ -153,7 +155,7 @@ def test_large_cells(cluster):
 # ------------------------------------------------------------------ 2-d --
 
 @pytest.mark.parametrize("search", [mt.MT_SEARCH_CELL, mt.MT_SEARCH_BRUTE, mt.MT_SEARCH_FULL])
-@pytest.mark.parametrize("precision", [mt.MT_FP64, mt.MT_MIXED])
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_2d(search, precision):
     n, L = 1500, (60.0, 40.0)
     x = synth.uniform_positions(n, L, dim=2, seed=3)
@@ -164,7 +166,7 @@ def test_2d(search, precision):
 
 # ---------------------------------------------------------- normalisation --
 
-@pytest.mark.parametrize("precision", [mt.MT_FP64, mt.MT_MIXED])
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_row_normalisation(precision):
     n, L = 2000, 1000.0
     x = synth.uniform_positions(n, L, seed=4)
@@ -183,7 +185,7 @@ def test_no_reaction_and_advection():
 
 # ---------------------------------------------------------- determinism --
 
-@pytest.mark.parametrize("precision", [mt.MT_FP64, mt.MT_MIXED])
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_bitwise_deterministic(precision):
     n, L = 20000, 20000.0
     x = synth.uniform_positions(n, L, seed=11)
@@ -474,7 +476,7 @@ def test_fused_dense_bins_sorted_in_place(cluster, tiers):
         assert "move" not in names
 
 
-@pytest.mark.parametrize("precision", [mt.MT_FP64, mt.MT_MIXED])
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_workload2_n1e5_1000_steps_oracle_on_strided_steps(precision):
     """N = 1e5 uniform on [0, 1e5], no advection, 1000 steps on the built-in
     generator; every 100th step is taken from the GPU's own state with
