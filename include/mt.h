@@ -426,7 +426,9 @@ const char* mt_profile_name(const mt_handle* h, int32_t idx);
  * array's address, so make it before any stream capture.  All calls share
  * the array: calls that overlap on the GPU race and give wrong results.
  * Runs on stream (NULL: the default stream) and waits for it before
- * returning; MT_ERR_INVALID if a position is outside [0, L] or unsorted. */
+ * returning; MT_ERR_INVALID if a position is outside [0, L], NaN or out of
+ * ascending order, and A_out and B_out are then undefined (they may have
+ * been written). */
 mt_status mt_transfer_1d_noalloc(const double* x, const double* A, const double* B,
                                  double* A_out, double* B_out, int64_t n, double L,
                                  double D_mt, double dt, double cutoff, int32_t norm,

@@ -5,10 +5,11 @@
 //
 // Some callers cannot call cudaMalloc: code running where the allocator is
 // owned by someone else (a host application that hands out only its own
-// buffers, a plug-in inside another runtime, a CUDA-graph-driven pipeline
-// that forbids allocation during its run).  They still pass their own input
-// and output arrays; the per-particle intermediates (positions on the tick
-// grid and 1 / r_i) live in the fixed array g_noalloc_scratch below.
+// buffers, a plug-in inside another runtime, a pipeline that forbids
+// allocation while it runs).  They still pass their own input and output
+// arrays; the per-particle intermediates (positions on the tick grid and
+// 1 / r_i) live in the fixed array g_noalloc_scratch below.  The call waits
+// for its stream before it returns (it reads back the input check).
 //
 // The scratch array is a file-scope __device__ variable: every GPU that loads
 // libmt holds its 16 MiB + 256 bytes until the process exits, whether or not
@@ -68,9 +69,19 @@ __global__ void k_na_rowsum(const long long* ticks, long long n, long long S, do
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const long long x = ticks[p];
+  // Each walk stops at the first neighbour out of range, or out of order: on
+  // unsorted input (rejected after the call) the work stays O(n k).
   double r = 1.0;
-  for (long long q = p - 1; q >= 0 && x - ticks[q] <= S; --q) r += na_weight(x - ticks[q], scale, inv8);
-  for (long long q = p + 1; q < n && ticks[q] - x <= S; ++q) r += na_weight(ticks[q] - x, scale, inv8);
+  for (long long q = p - 1; q >= 0; --q) {
+    const long long D = x - ticks[q];
+    if (D < 0 || D > S) break;
+    r += na_weight(D, scale, inv8);
+  }
+  for (long long q = p + 1; q < n; ++q) {
+    const long long D = ticks[q] - x;
+    if (D < 0 || D > S) break;
+    r += na_weight(D, scale, inv8);
+  }
   rinv[p] = 1.0 / r;
 }
 
@@ -85,7 +96,7 @@ __global__ void k_na_exchange(const long long* ticks, const double* rinv, const 
   for (int side = 0; side < 2; ++side) {
     for (long long q = side ? p + 1 : p - 1; q >= 0 && q < n; q += side ? 1 : -1) {
       const long long D = side ? ticks[q] - x : x - ticks[q];
-      if (D > S) break;
+      if (D < 0 || D > S) break;
       const double w = na_weight(D, scale, inv8);
       const double P = norm == MT_NORM_ROW ? w * ip : 0.5 * w * (ip + rinv[q]);
       dA += P * (A[q] - a);
