@@ -394,6 +394,17 @@ mt_status mt_philox(mt_handle* h, uint32_t c0, uint32_t c1, uint32_t c2,
                     uint32_t c3, uint32_t k0, uint32_t k1, int64_t n,
                     uint32_t* out);
 
+/* Test hook for failure detection (not part of the paper).  With hold = 1
+ * the first tile of the cell-list scan (the multi-kernel pipeline's
+ * decoupled look-back prefix sum) stops publishing its status word, so every
+ * later tile's wait for it runs out after spin_limit polls (0: the built-in
+ * bound) and the step reports MT_ERR_TIMEOUT at the next mt_sync or
+ * mt_read_* instead of hanging; the state of that step is then undefined.
+ * hold = 0 restores normal operation; mt_upload clears both settings.
+ * Errors: MT_ERR_STATE before mt_upload, MT_ERR_INVALID for hold not 0/1
+ * or spin_limit < 0.  Waits for the stream. */
+mt_status mt_test_hold_scan(mt_handle* h, int32_t hold, int64_t spin_limit);
+
 /* Per-kernel timing: with on = 1 every following step records a CUDA event
  * on the handle's stream before each of its kernels and one after the last
  * (graph replays included; turning it on or off drops a captured graph).

@@ -854,6 +854,20 @@ mt_status mt_set_noise(mt_handle* h, const float* xi) {
   return MT_OK;
 }
 
+mt_status mt_test_hold_scan(mt_handle* h, int32_t hold, int64_t spin_limit) {
+  if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
+  if (!h->uploaded) return fail(MT_ERR_STATE, "mt_test_hold_scan before mt_upload");
+  if ((hold != 0 && hold != 1) || spin_limit < 0)
+    return fail(MT_ERR_INVALID, "hold must be 0 or 1 and spin_limit >= 0");
+  const int hv = hold;
+  const long long lv = spin_limit;
+  CU(cudaMemcpyAsync(&h->dev.ctrl->scan_hold, &hv, sizeof(hv), cudaMemcpyHostToDevice, h->stream));
+  CU(cudaMemcpyAsync(&h->dev.ctrl->spin_limit, &lv, sizeof(lv), cudaMemcpyHostToDevice,
+                     h->stream));
+  CU(cudaStreamSynchronize(h->stream));  // the sources live on this stack frame
+  return MT_OK;
+}
+
 mt_status mt_run(mt_handle* h, int64_t nsteps) {
   if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
   if (!h->uploaded) return fail(MT_ERR_STATE, "mt_run before mt_upload");

@@ -54,6 +54,8 @@ struct Ctrl {
   unsigned int kjoin;           // of the two concurrent fused kernels, how many are done
   int npred;                    // segments predicted pair-heavy for this step
   int npred_next;               // ... counted during this step for the next
+  int scan_hold;                // test hook: the scan's first tile withholds its status
+  long long spin_limit;         // bound of each look-back wait (0: kSpinLimit)
 };
 
 // One realisation of a batch (a single system is a batch of one).  Batched

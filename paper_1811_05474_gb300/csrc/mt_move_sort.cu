@@ -117,15 +117,18 @@ __global__ void __launch_bounds__(kThreads) k_scan(Dev d) {
     volatile unsigned long long* st = d.scan_status;
     long long excl = 0;
     if (tile == 0) {
-      atomicExch(&d.scan_status[0], pack(tag, 2, block_total));
+      // (the test hook withholds this word: every later tile's wait then
+      // runs out and raises kErrTimeout)
+      if (!c->scan_hold) atomicExch(&d.scan_status[0], pack(tag, 2, block_total));
     } else {
       atomicExch(&d.scan_status[tile], pack(tag, 1, block_total));
+      const long long limit = c->spin_limit > 0 ? c->spin_limit : kSpinLimit;
       long long t = tile - 1, spins = 0;
       while (t >= 0) {
         const unsigned long long w = st[t];
         const unsigned long long flag = (w >> 46) & 3ULL;
         if ((w >> 48) != tag || flag == 0) {
-          if (++spins > kSpinLimit) {
+          if (++spins > limit) {
             raise_error(c, kErrTimeout, tile);
             break;
           }

@@ -158,6 +158,7 @@ def lib(path: Path | None = None):
         "mt_steps_done": [H, ctypes.POINTER(i64)],
         "mt_philox": [H, u32, u32, u32, u32, u32, u32, i64, _vp],
         "mt_set_profiling": [H, i32],
+        "mt_test_hold_scan": [H, i32, i64],
         "mt_transfer_1d_noalloc": [_vp, _vp, _vp, _vp, _vp, i64, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, i32, i32,
                                    _vp],
@@ -389,6 +390,11 @@ def mt_read_profile(h):
 
 def mt_profile_name(h, idx: int) -> str:
     return lib().mt_profile_name(h, idx).decode()
+
+
+def mt_test_hold_scan(h, hold: int, spin_limit: int = 0) -> None:
+    """Test hook: withhold the scan's first status word (see include/mt.h)."""
+    check(lib().mt_test_hold_scan(h, hold, spin_limit))
 
 
 def mt_transfer_1d_noalloc(x_ptr, A_ptr, B_ptr, Ao_ptr, Bo_ptr, n: int, L: float, D_mt: float,

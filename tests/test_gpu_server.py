@@ -127,3 +127,51 @@ def test_server_poisson_mix_matches_alone_on_sampled_requests():
         aA, aB, _ = alone(p, x, A, B, steps)
         assert np.array_equal(gA, aA) and np.array_equal(gB, aB)
     srv.close()
+
+
+def test_served_requests_equal_the_oracle():
+    """Served results against the CPU oracle, not only against the library
+    run alone.  The requests have no random walk (D_rw = 0) and a constant
+    drift, so every position is fixed by Eq. 2 and the walls alone and the
+    oracle reproduces each whole served run: 1-d and 2-d, two and three
+    species, all three precisions, served side by side with chunks that
+    interleave on the device.  Positions are compared through the masses
+    (a moved particle would change its neighbours), masses per particle to
+    1e-12 (FP64) or 1e-6 (mixed forms) relative to max(|m|, 0.5)."""
+    import oracle as O
+
+    from .test_gpu_parity import TOL, assert_masses
+    from .test_oracle_species import oracle_step_species, species_masses
+
+    specs = [  # (n, dim, species, steps, precision, v)
+        (3000, 1, 2, 25, mt.MT_FP64, (0.3, 0.0)),
+        (5000, 1, 3, 20, mt.MT_MIXED, (-0.4, 0.0)),
+        (1600, 2, 2, 12, mt.MT_MIXED, (0.25, -0.15)),
+        (2500, 1, 2, 30, mt.MT_MIXED_DF32, (0.5, 0.0)),
+        (900, 2, 3, 10, mt.MT_FP64, (0.0, 0.2)),
+    ]
+    srv = mt.Server(pool_bytes=2 ** 28, max_active=3, chunk_steps=4)
+    runs = []
+    for i, (n, dim, S, steps, prec, v) in enumerate(specs):
+        L = (float(np.sqrt(n) * 10.0),) * 2 if dim == 2 else (float(n),)
+        p = mt.mt_params_init(dim=dim, n=n, L=L, v=v, D_rw=0.0, precision=prec, species=S,
+                              seed=200 + i)
+        x = synth.uniform_positions(n, L if dim == 2 else L[0], dim=dim, seed=200 + i)
+        Ms = species_masses(n, S, seed=300 + i)
+        rid = srv.submit_species(p, x, Ms, steps) if S > 2 else srv.submit(p, x, *Ms, steps)
+        runs.append((rid, mt.mt_resolve(p), x, Ms, steps))
+        srv.poll()
+    srv.drain()
+    for rid, r, x, Ms, steps in runs:
+        po = O.params(dim=r.dim, frac_bits=r.frac_bits, L=tuple(r.L), v=tuple(r.v), D_mt=r.D_mt,
+                      D_rw=0.0, dt=r.dt, smax=r.cutoff, norm=r.norm, react=r.react)
+        X = O.quantize(np.asarray(x).reshape(r.dim, -1), int(r.frac_bits))
+        xi = np.zeros((r.dim, r.n), dtype=np.float32)
+        cur = [np.array(m, dtype=np.float64) for m in Ms]
+        for _ in range(steps):
+            X, cur = oracle_step_species(po, X, xi, cur)
+        tol = TOL[int(r.precision)]
+        for s in range(int(r.species)):
+            got = srv.result_species(rid, s) if r.species > 2 else srv.result(rid)[s]
+            assert_masses(got, cur[s], tol, f"request {rid} species {s}")
+    srv.close()
