@@ -7,16 +7,19 @@ observables) for every particle of the workload.  Workload: 1-d, N = 1e6
 particles uniform on [0, 1e6], A and B masses uniform on [0, 1), D = 0.1,
 dt = 1, advection v = 0.5, cutoff 3 sigma of the co-location kernel,
 synthetic and seeded.  The headline runs the MIXED precision path (binary32
-weights, double-binary32 mass accumulation); the FP64 path is reported in
-the "fp64" object.
+weights and exponentials; binary64 masses, flux terms, sums, update and
+reaction).  The same line carries the binary64 path ("fp64"), the
+double-binary32 variant ("mixed_df32"), the two smaller workloads
+("workloads": N = 1e3 with the cell list, the cutoff brute force and the
+full matrix; N = 1e5 in each precision), the batched, serving, accuracy
+and paper-density forms, and the CPU oracle on one core and on all cores.
 
 Timing: W warm-up steps, then K steps each replayed from a CUDA graph and
 bracketed by CUDA events on the simulation's stream, with a 512 MiB write
 (then read, so no dirty line is left) between steps to flush L2 (129 MB);
-value = particles * K / sum of step
-times, max over ranks.  Per-kernel durations come from a second pass of
-the same steps with events recorded between the step's kernels inside the
-graph.
+value = particles * K / sum of step times, max over ranks.  Per-kernel
+durations come from a second pass of the same steps with events recorded
+between the step's kernels inside the graph.
 
 ``--impl reference`` times the CPU oracle (single thread) on a bounded
 sample of the same workload instead.
@@ -60,6 +63,28 @@ ALGO_BYTES = {
 
 CSRC = os.path.join(ROOT, "paper_1811_05474_gb300", "csrc")
 
+DTYPES = {
+    "mixed": "mixed: f32 weights and exp, f64 masses, flux terms, sums, update and reaction; "
+             "i64 positions",
+    "fp64": "f64 weights, masses and arithmetic; i64 positions",
+    "df32": "mixed_df32: f32 weights, f32x2 (double-binary32) masses and compensated sums; "
+            "i64 positions",
+}
+
+
+def prec_code(name: str) -> int:
+    from paper_1811_05474_gb300 import mt
+
+    return {"mixed": mt.MT_MIXED, "fp64": mt.MT_FP64, "df32": mt.MT_MIXED_DF32}[name]
+
+
+def config_dict(precision: str) -> dict:
+    """The headline workload's description, identical in both arms."""
+    return {"workload": WORKLOAD, "n_particles": N, "L": L, "v": V, "D_mt": D, "D_rw": D,
+            "dt": DT, "steps_per_run": 1000, "cutoff": "3*sqrt(4*D_mt*dt)",
+            "normalisation": "symmetric", "precision": precision,
+            "l2": "flushed between timed steps (512 MiB write, then read)"}
+
 
 # The sources of the one-kernel step's device code: its translation unit and
 # the internal headers it includes (the public header adds only the MT_*
@@ -86,8 +111,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison line")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "df32"])
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the binary64 and double-binary32 objects")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the N = 1e3 and N = 1e5 workloads")
+    ap.add_argument("--detail", default=None,
+                    help="also write the full result (every per-kernel list) to this JSON file")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ncu", action="store_true",
                     help="profiling mode: upload, W graph steps, then K direct steps, nothing else")
@@ -176,7 +206,14 @@ class ClockSampler:
         if not mine and rows:
             idx0 = rows[0][1]
             mine = [r for r in rows if len(r) >= 11 and r[1] == idx0]
-        if self.t0 is not None and self.t1 is not None:
+        self.rows = mine
+        return self.summary(self.t0, self.t1)
+
+    def summary(self, t0, t1):
+        """Median SM clock, max clock and throttle reasons of the samples
+        taken between t0 and t1 (all samples if no window is given)."""
+        mine = getattr(self, "rows", [])
+        if t0 is not None and t1 is not None:
             from datetime import datetime
 
             def ts(r):
@@ -185,7 +222,7 @@ class ClockSampler:
                 except ValueError:
                     return None
 
-            inside = [r for r in mine if (ts(r) or 0) >= self.t0 - 0.05 and (ts(r) or 0) <= self.t1 + 0.05]
+            inside = [r for r in mine if (ts(r) or 0) >= t0 - 0.05 and (ts(r) or 0) <= t1 + 0.05]
             if inside:
                 mine = inside
         sm = [float(r[3]) for r in mine if r[3].replace(".", "").isdigit()]
@@ -218,23 +255,28 @@ def cpu_oracle_rate(n: int, steps: int, seed: int = 0):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands (sorted-window search,
+    one thread) on a bounded sample of the headline workload, each step of
+    the run timed on an n-particle density-1 piece of it, n chosen so the
+    whole run takes about two minutes."""
     ws, rank, _ = dist()
     if rank != 0:
         return 0
-    # size the per-step sample so that warm-up + timed steps take ~2 minutes
     per_particle = 0.7e-6
     budget = 120.0
     n = int(min(N, max(10 ** 4, budget / max(args.steps + args.warmup, 1) / per_particle)))
     cpu_oracle_rate(n, max(args.warmup, 0))
     rate, secs = cpu_oracle_rate(n, args.steps, seed=1)
+    info = cpu_info()
     line = {
         "impl": "reference", "metric": "particle-steps/s", "value": rate,
         "unit": "particle-steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * secs / max(args.steps, 1) * (N / n), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample_particles": n, "search": "sorted window (1-d)"},
+        "config": config_dict(args.precision),
         "cpu_baseline": {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} steps of a {n}-particle density-1 sample"},
+                         "sample": f"{args.steps} steps of a {n}-particle density-1 piece of the "
+                                   f"workload (sorted-window search, one thread)", **info},
         "e2e": {"value": rate, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -251,7 +293,7 @@ def gpu_run(args, precision: str, steps: int, warmup: int, local: int, realisati
     from paper_1811_05474_gb300 import mt, synth
 
     dev = torch.device("cuda", local)
-    prec = mt.MT_MIXED if precision == "mixed" else mt.MT_FP64
+    prec = prec_code(precision)
     p = mt.mt_params_init(n=N, L=(L,), v=(V, 0.0), D_mt=D, D_rw=D, dt=DT,
                           search=mt.MT_SEARCH_CELL, precision=prec, norm=mt.MT_NORM_SYM,
                           react=1, seed=2024, realisation=realisation,
@@ -278,6 +320,7 @@ def gpu_run(args, precision: str, steps: int, warmup: int, local: int, realisati
     sim.sync()
     # timed region: steps enqueued back to back (no host sync inside), each
     # bracketed by events after its L2 flush
+    t_start = time.time()
     if sampler:
         sampler.mark("t0")
     for i in range(steps):
@@ -286,6 +329,7 @@ def gpu_run(args, precision: str, steps: int, warmup: int, local: int, realisati
         sim.run(1)
         e1[i].record(s)
     torch.cuda.synchronize(dev)
+    t_end = time.time()
     if sampler:
         sampler.mark("t1")
     # kernel breakdown: a second timed pass with events between the step's
@@ -315,10 +359,11 @@ def gpu_run(args, precision: str, steps: int, warmup: int, local: int, realisati
     del flush
     return {"total_ms": sum(step_ms), "step_ms": step_ms, "kernels": kernels,
             "launches_per_step": launches_per_step, "npairs": npairs,
-            "mean_A_last": float(obs[-1, 3]) if len(obs) else None}
+            "mean_A_last": float(obs[-1, 3]) if len(obs) else None,
+            "t0": t_start, "t1": t_end}
 
 
-def e2e_run(steps: int, local: int, realisation: int):
+def e2e_run(steps: int, local: int, realisation: int, precision: str = "mixed"):
     """Through the public API with host buffers: upload from pinned host
     memory, then every step enqueue it and the copy of its observables row
     into pinned host memory (no wait between steps), then read the final
@@ -330,7 +375,7 @@ def e2e_run(steps: int, local: int, realisation: int):
 
     dev = torch.device("cuda", local)
     p = mt.mt_params_init(n=N, L=(L,), v=(V, 0.0), D_mt=D, D_rw=D, dt=DT,
-                          precision=mt.MT_MIXED, seed=7, realisation=realisation,
+                          precision=prec_code(precision), seed=7, realisation=realisation,
                           observe_cap=1)
     sim = mt.Simulation(p, device=dev)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
@@ -764,11 +809,11 @@ def accuracy_run(local: int):
 
 
 def precision_report(local: int, steps: int):
-    """MIXED against the FP64 GPU path on the headline workload: both run
-    `steps` steps from the same state with the same random walk (positions
-    are identical integers), then masses and the mean-A series are compared.
-    (Each path's error against the CPU oracle is asserted by the parity
-    tests: 1e-12 FP64, 1e-6 MIXED.)"""
+    """MIXED and double-binary32 against the binary64 GPU path on the
+    headline workload: all run `steps` steps from the same state with the
+    same random walk (positions are identical integers), then masses and the
+    mean-A series are compared.  (Each path's error against the CPU oracle
+    is asserted by the parity tests: 1e-12 binary64, 1e-6 the mixed forms.)"""
     import numpy as np
     import torch
 
@@ -779,26 +824,170 @@ def precision_report(local: int, steps: int):
     A0, B0 = synth.uniform_masses(N, seed=5)
     rel = lambda g, o: float(np.max(np.abs(g - o) / np.maximum(np.abs(o), 0.5)))
     res = {}
-    for prec, name in ((mt.MT_FP64, "fp64"), (mt.MT_MIXED, "mixed")):
-        p = mt.mt_params_init(n=N, L=(L,), v=(V, 0.0), D_mt=D, D_rw=D, dt=DT, precision=prec,
-                              seed=99, observe_cap=steps)
+    for name in ("fp64", "mixed", "df32"):
+        p = mt.mt_params_init(n=N, L=(L,), v=(V, 0.0), D_mt=D, D_rw=D, dt=DT,
+                              precision=prec_code(name), seed=99, observe_cap=steps)
         sim = mt.Simulation(p, device=dev)
         sim.upload(x, A0, B0)
         sim.run(steps)
         res[name] = (sim.ticks(), *sim.masses(), sim.observables())
         sim.close()
-    (X64, a64, b64, o64), (X32, a32, b32, o32) = res["fp64"], res["mixed"]
+    X64, a64, b64, o64 = res["fp64"]
     d0 = float(np.sum(A0 - B0))
-    return {"workload": WORKLOAD, "steps": steps,
-            "relative_to": "max(|m_fp64|, 0.5) per particle (0.5 = mean initial mass)",
-            "positions_identical": bool(np.array_equal(X64, X32)),
-            "mixed_vs_fp64_max_rel_err_A": rel(a32, a64),
-            "mixed_vs_fp64_max_rel_err_B": rel(b32, b64),
-            "mean_A_series_max_abs_diff": float(np.max(np.abs(o32[:, 3] - o64[:, 3]))),
-            "mean_A_last": {"mixed": float(o32[-1, 3]), "fp64": float(o64[-1, 3])},
-            "sum_A_minus_B_drift": {"mixed": float(abs(o32[-1, 2] - d0)),
-                                    "fp64": float(abs(o64[-1, 2] - d0)),
-                                    "sum_A_plus_B_initial": float(np.sum(A0 + B0))}}
+    out = {"workload": WORKLOAD, "steps": steps,
+           "relative_to": "max(|m_fp64|, 0.5) per particle (0.5 = mean initial mass)",
+           "sum_A_plus_B_initial": float(np.sum(A0 + B0)),
+           "fp64": {"mean_A_last": float(o64[-1, 3]),
+                    "sum_A_minus_B_drift": float(abs(o64[-1, 2] - d0))}}
+    for name in ("mixed", "df32"):
+        X, a, b, o = res[name]
+        out[name] = {"positions_identical": bool(np.array_equal(X64, X)),
+                     "vs_fp64_max_rel_err_A": rel(a, a64), "vs_fp64_max_rel_err_B": rel(b, b64),
+                     "mean_A_series_max_abs_diff": float(np.max(np.abs(o[:, 3] - o64[:, 3]))),
+                     "mean_A_last": float(o[-1, 3]),
+                     "sum_A_minus_B_drift": float(abs(o[-1, 2] - d0))}
+    return out
+
+
+def make_flush(dev):
+    """A function that flushes L2 on a stream: write 512 MiB, then read it
+    back so the lines left are clean."""
+    import torch
+
+    buf = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    acc = torch.empty((), dtype=torch.int64, device=dev)
+
+    def flush_l2(s):
+        with torch.cuda.stream(s):
+            buf.zero_()
+            torch.sum(buf.view(torch.int64), dim=0, out=acc)
+    return flush_l2
+
+
+def workloads_run(local: int, flush_l2):
+    """The two smaller workloads, timed like the headline (graph steps,
+    events on the simulation's stream, L2 flushed between steps).
+    N = 1e3 uniform on [0, 1e3], 100 steps, binary64: the cell list, the
+    cutoff brute force (every pair tested) and the full matrix (every
+    pair's weight, the paper's reference).  N = 1e5 uniform on [0, 1e5],
+    1000 steps, no advection: binary64, MIXED and double-binary32.
+    pair-interactions/s counts the unordered pairs within the cutoff (the
+    full matrix: every unordered pair it evaluates, labelled as such)."""
+    import torch
+
+    from paper_1811_05474_gb300 import mt, synth
+
+    dev = torch.device("cuda", local)
+    out = {}
+    n1, steps1 = 1000, 100
+    x1 = synth.uniform_positions(n1, 1000.0, seed=0)
+    A1, B1 = synth.uniform_masses(n1, seed=0)
+    w1 = {"workload": "1d_uniform_n1e3_L1e3_D0.1_dt1_cutoff3sigma_fp64", "steps": steps1}
+    for name, search in (("cell", mt.MT_SEARCH_CELL), ("brute", mt.MT_SEARCH_BRUTE),
+                         ("full", mt.MT_SEARCH_FULL)):
+        p = mt.mt_params_init(n=n1, L=(1000.0,), D_mt=D, D_rw=D, dt=DT, search=search,
+                              precision=mt.MT_FP64, seed=0)
+        sim = mt.Simulation(p, device=dev)
+        sim.upload(x1, A1, B1)
+        ms = timed_steps(sim, steps1, 3, flush_l2)
+        if search == mt.MT_SEARCH_FULL:
+            pairs, label = n1 * (n1 - 1) // 2, "all unordered pairs (evaluated)"
+        else:
+            pairs, label = mt.mt_read_pairs(sim.h, None, None, 0), "unordered pairs within the cutoff"
+        sim.close()
+        w1[name] = {"value": n1 * steps1 / (ms * 1e-3), "unit": "particle-steps/s",
+                    "ms_per_step": ms / steps1, "pairs_per_step": int(pairs), "pairs": label,
+                    "pair_interactions_per_s": pairs * steps1 / (ms * 1e-3)}
+    out["n1e3"] = w1
+    n2, steps2 = 10 ** 5, 1000
+    x2 = synth.uniform_positions(n2, 1e5, seed=0)
+    A2, B2 = synth.uniform_masses(n2, seed=0)
+    w2 = {"workload": "1d_uniform_n1e5_L1e5_D0.1_dt1_cutoff3sigma", "steps": steps2,
+          "search": "cell list (one-kernel step)"}
+    for name in ("fp64", "mixed", "df32"):
+        p = mt.mt_params_init(n=n2, L=(1e5,), D_mt=D, D_rw=D, dt=DT, precision=prec_code(name),
+                              seed=0)
+        sim = mt.Simulation(p, device=dev)
+        sim.upload(x2, A2, B2)
+        ms = timed_steps(sim, steps2, 3, flush_l2)
+        pairs = mt.mt_read_pairs(sim.h, None, None, 0)
+        sim.close()
+        w2[name] = {"value": n2 * steps2 / (ms * 1e-3), "unit": "particle-steps/s",
+                    "ms_per_step": ms / steps2, "dtype": DTYPES[name],
+                    "pair_interactions_per_s": pairs * steps2 / (ms * 1e-3)}
+    out["n1e5"] = w2
+    return out
+
+
+def cpu_info():
+    """Host core count and CPU model (for the CPU baseline's record)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or "unknown"}
+
+
+def cpu_baselines(n: int = N, steps: int = 10):
+    """The CPU oracle on the host: (i) the sorted-window step (Sec. 2.1's
+    fixed-radius search without a tree) on the headline workload, on one
+    core and on all cores (the oracle's per-particle loops on OpenMP
+    threads; its sort stays on one core), `steps` steps each, per-step time
+    extrapolated to the 1000-step run; (ii) the full-matrix transfer (every
+    pair, the paper's reference): N = 1e3 for 100 steps, and N = 1e4 for one
+    step, whose per-pair rate extrapolates one step at N = 1e5 (1e10
+    pairs), stated as extrapolated."""
+    import oracle as O
+    from paper_1811_05474_gb300 import synth
+
+    info = cpu_info()
+    cores = info["nproc"] or 1
+    single, secs1 = cpu_oracle_rate(n, steps, seed=0)
+    used = O.set_threads(cores)
+    try:
+        multi, secsm = cpu_oracle_rate(n, steps, seed=0)
+    finally:
+        O.set_threads(1)
+    full = {}
+    for nf, sf in ((1000, 100), (10000, 1)):
+        p = O.params(L=(float(nf),), D_mt=D, D_rw=D, dt=DT, frac_bits=29, search=O.SEARCH_FULL)
+        X = O.quantize(synth.uniform_positions(nf, float(nf), seed=0), 29)
+        A, B = synth.uniform_masses(nf, seed=0)
+        xi = synth.normals(sf, 1, nf, seed=1)
+        t0 = time.perf_counter()
+        for k in range(sf):
+            X, A, B = O.step(p, X, xi[k], A, B)
+        dt = time.perf_counter() - t0
+        full[f"n{nf}"] = {"steps": sf, "seconds": dt, "particle_steps_per_s": nf * sf / dt,
+                          "pair_evaluations_per_s": 2.0 * nf * nf * sf / dt}
+    per_pair = full["n10000"]["seconds"] / (2.0 * 10000 * 10000)
+    full["n1e5_one_step_seconds_extrapolated"] = per_pair * 2.0 * 1e5 * 1e5
+    return {"value": single, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} steps of the full {n}-particle workload, single thread, "
+                      f"sorted-window search ({secs1:.1f} s; 1000 steps extrapolate to "
+                      f"{secs1 * 1000 / steps:.0f} s)",
+            **info,
+            "all_cores": {"value": multi, "unit": "particle-steps/s", "cores": used,
+                          "kind": "oracle",
+                          "sample": f"{steps} steps, per-particle loops on {used} OpenMP threads "
+                                    f"({secsm:.1f} s; 1000 steps extrapolate to "
+                                    f"{secsm * 1000 / steps:.0f} s)"},
+            "full_matrix": full}
 
 
 def load_peaks():
@@ -860,7 +1049,7 @@ def run_ncu(args):
     from paper_1811_05474_gb300 import mt, synth
 
     n = args.n
-    prec = mt.MT_MIXED if args.precision == "mixed" else mt.MT_FP64
+    prec = prec_code(args.precision)
     if args.ncu_search.startswith("dense"):
         # the paper's density (200 per unit length, D = 1 split, dt = 0.1)
         Ln = float(n) * 5000.0 / 1e6
@@ -886,6 +1075,36 @@ def run_ncu(args):
     return 0
 
 
+def compact_kernels(kernels):
+    ksum = sum(k["ms_per_step"] for k in kernels)
+    return [{"name": k["name"], "ms": round(k["ms"], 5), "launches_per_step": k["launches_per_step"],
+             "share": round(k["ms_per_step"] / ksum, 4) if ksum else None} for k in kernels]
+
+
+def variant_object(r, steps: int, name: str, peak: float, peak_kind: str, clocks, exp_peak):
+    """A precision's own result on the headline workload: rate, its
+    dominant kernel against HBM (48 B per particle-step) and, with binary64
+    weights, against the measured binary64 exponential rate (one exponential
+    per unordered pair within the cutoff, the method's minimum)."""
+    dom = max(r["kernels"], key=lambda k: k["ms_per_step"])
+    achieved = ALGO_BYTES.get(dom["name"], 48) * N / (dom["ms"] * 1e-3) / 1e9
+    obj = {"value": N * steps / (r["total_ms"] * 1e-3), "unit": "particle-steps/s",
+           "ms_per_step": r["total_ms"] / steps, "steps": steps, "dtype": DTYPES[name],
+           "pair_interactions_per_s": r["npairs"] * steps / (r["total_ms"] * 1e-3),
+           "roofline": {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak,
+                        "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                        "algo_bytes_per_launch": ALGO_BYTES.get(dom["name"], 48) * N,
+                        "traffic": load_traffic(dom["name"] + ("" if name == "mixed" else "_" + name))},
+           "clocks": clocks, "kernels": compact_kernels(r["kernels"])}
+    if name == "fp64" and exp_peak:
+        rate = r["npairs"] / (dom["ms"] * 1e-3)
+        obj["exp_roofline"] = {"bound": "alu", "kernel": dom["name"], "achieved": rate,
+                               "peak": exp_peak, "unit": "binary64 exp/s", "frac": rate / exp_peak,
+                               "peak_kind": "measured (mt_probe_rate: binary64 exp)",
+                               "algo": "one exponential per unordered pair within the cutoff"}
+    return obj
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -906,6 +1125,9 @@ def main():
         _b.build()
     if ws > 1:
         torch.distributed.barrier()
+    from paper_1811_05474_gb300 import mt
+
+    dev = torch.device("cuda", local)
     uuid = None
     try:
         uuid = str(torch.cuda.get_device_properties(local).uuid)
@@ -922,18 +1144,26 @@ def main():
     if ws > 1:
         total_ms = rank_reduce([total_ms], "max", device="cuda")[0]
         torch.distributed.barrier()
-    clocks = sampler.stop()
-    fp64 = None
-    if not args.no_fp64 and args.precision == "mixed":
-        k64 = max(10, min(args.steps, 200))
-        r64 = gpu_run(args, "fp64", k64, 3, local, rank, None)
-        dom = max(r64["kernels"], key=lambda k: k["ms_per_step"])
-        fp64 = {"value": N * k64 / (r64["total_ms"] * 1e-3), "unit": "particle-steps/s",
-                "ms_per_step": r64["total_ms"] / k64, "steps": k64,
-                "dominant_kernel": dom["name"], "dominant_ms": dom["ms"],
-                "bound": "alu (binary64 pipe)"}
-    e2e = e2e_run(args.steps, local, rank)
     peak, peak_kind = load_peaks()
+    probes = None
+    if rank == 0:
+        probes = {"binary64_fma_per_s": mt.mt_probe_rate(mt.PROBE_DFMA, dev),
+                  "binary32_fma_per_s": mt.mt_probe_rate(mt.PROBE_FFMA, dev),
+                  "binary32_fast_exp_per_s": mt.mt_probe_rate(mt.PROBE_EXPF, dev),
+                  "binary64_exp_per_s": mt.mt_probe_rate(mt.PROBE_EXP, dev),
+                  "how": "mt_probe_rate: 8 independent chains per thread, 8 CTAs x 256 threads "
+                         "per SM, fastest of 3 event-timed launches"}
+    variants = {}
+    if not args.no_fp64 and rank == 0:
+        for name in ("fp64", "mixed", "df32"):
+            if name != args.precision:
+                k = max(10, min(args.steps, 200))
+                variants[name] = (gpu_run(args, name, k, 3, local, rank, None), k)
+    flush_l2 = make_flush(dev)
+    workloads = None
+    if not args.no_workloads and rank == 0:
+        workloads = workloads_run(local, flush_l2)
+    e2e = e2e_run(args.steps, local, rank, args.precision)
     batched = None
     if not args.no_batch and rank == 0:
         batched = batch_run(local, args.steps, peak)
@@ -946,15 +1176,18 @@ def main():
     accuracy = None
     if not args.no_accuracy and rank == 0:
         accuracy = accuracy_run(local)
+    sm_now = None
     brute = None
     if not args.no_brute and rank == 0:
-        brute = brute_run(local, sm_mhz=clocks.get("sm_mhz") if clocks else None)
+        brute = brute_run(local, sm_mhz=sm_now)
     dense = None
     if not args.no_dense and rank == 0:
-        dense = dense_run(local, sm_mhz=clocks.get("sm_mhz") if clocks else None, peak_gbs=peak)
+        dense = dense_run(local, sm_mhz=sm_now, peak_gbs=peak)
     species = None
     if not args.no_species and rank == 0:
         species = species_run(local)
+    sampler.stop()
+    clocks = sampler.summary(main_run["t0"], main_run["t1"])
     if ws > 1:
         # the slowest replica's rate times the replicas
         e2e["value"] = rank_reduce([e2e["value"]], "min", device="cuda")[0] * ws
@@ -968,57 +1201,56 @@ def main():
     value = replicas_value(N, K, total_ms, ws)
     ms_step = total_ms / K
     kernels = main_run["kernels"]
-    ksum = sum(k["ms_per_step"] for k in kernels)
-    for k in kernels:
-        k["share"] = k["ms_per_step"] / ksum if ksum else None
     dom = max(kernels, key=lambda k: k["ms_per_step"])
     dom_bytes = ALGO_BYTES.get(dom["name"], 0) * N
     achieved = dom_bytes / (dom["ms"] * 1e-3) / 1e9 if dom["ms"] > 0 else 0.0
     step_bytes = ALGO_BYTES["step"] * N
     path_achieved = step_bytes / (ms_step * 1e-3) / 1e9
+    exp_peak = probes["binary64_exp_per_s"] if probes else None
+    objs = {name: variant_object(r, k, name, peak, peak_kind,
+                                 sampler.summary(r["t0"], r["t1"]), exp_peak)
+            for name, (r, k) in variants.items()}
     cpu = None
     if ws == 1 and not args.no_cpu:
-        n_cpu, steps_cpu = N, 20
-        rate, secs = cpu_oracle_rate(n_cpu, steps_cpu, seed=0)
-        cpu = {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-               "sample": f"{steps_cpu} steps of the full {n_cpu}-particle workload "
-                         f"({secs:.1f} s, single thread, sorted-window search)"}
+        cpu = cpu_baselines()
+    traffic_key = dom["name"] + ("" if args.precision == "mixed" else "_" + args.precision)
     line = {
         "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
         "n_gpus": ws, "steps": K, "warmup": max(args.warmup, 3), "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": ("mixed: f32 weights, f32x2 mass accumulation, i64 positions"
-                  if args.precision == "mixed" else "f64 weights and masses, i64 positions"),
+        "dtype": DTYPES[args.precision],
         "data": "synthetic: seeded uniform positions and U[0,1) masses",
-        "config": {"workload": WORKLOAD, "n_particles": N, "L": L, "v": V, "D_mt": D, "D_rw": D,
-                   "dt": DT, "cutoff": "3*sqrt(4*D_mt*dt)", "search": "cell list (fused 1-d step)",
-                   "precision": args.precision, "normalisation": "symmetric",
-                   "l2": "flushed between timed steps (512 MiB write, then read)",
-                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "config": config_dict(args.precision),
         "pair_interactions_per_s": ws * main_run["npairs"] * K / (total_ms * 1e-3),
         "pairs_per_step": main_run["npairs"],
         "roofline": {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
-                     "algo_bytes_per_launch": dom_bytes,
-                     "traffic": load_traffic(dom["name"])},
-        "path_roofline": {"bound": "hbm", "achieved": path_achieved, "peak": peak, "unit": "GB/s",
-                          "frac": path_achieved / peak, "algo_bytes_per_step": step_bytes},
-        "issue_roofline": load_issue(dom["name"], dom["ms"], clocks.get("sm_mhz") if clocks else None),
-        "kernels": kernels,
+                     "algo_bytes_per_launch": dom_bytes, "traffic": load_traffic(traffic_key)},
         "gpu_launches": int(round(K * main_run["launches_per_step"])),
         "clocks": clocks,
         "e2e": e2e,
         "cpu_baseline": cpu,
-        "fp64": fp64,
+        "fp64": objs.get("fp64"),
+        "mixed": objs.get("mixed"),
+        "mixed_df32": objs.get("df32"),
+        "workloads": workloads,
+        "path_roofline": {"bound": "hbm", "achieved": path_achieved, "peak": peak, "unit": "GB/s",
+                          "frac": path_achieved / peak, "algo_bytes_per_step": step_bytes},
+        "issue_roofline": load_issue(traffic_key, dom["ms"], clocks.get("sm_mhz") if clocks else None),
+        "kernels": compact_kernels(kernels),
+        "probes": probes,
+        "precision": precision,
         "batched": batched,
         "serving": serving,
-        "accuracy": accuracy,
         "paper_density": dense,
         "brute_force": brute,
+        "accuracy": accuracy,
         "species": species,
-        "precision": precision,
         "mean_A_last_step": main_run["mean_A_last"],
     }
+    if args.detail:
+        with open(args.detail, "w") as f:
+            json.dump(line, f, indent=1)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.barrier()

@@ -445,6 +445,19 @@ mt_status mt_transfer_1d_noalloc(const double* x, const double* A, const double*
                                  double D_mt, double dt, double cutoff, int32_t norm,
                                  int32_t react, void* stream);
 
+/* Device throughput probe (not part of the paper; it measures the peaks
+ * that the binary64 and all-pairs passes are compared against).  which:
+ * 0 binary64 fused multiply-adds, 1 binary32 fused multiply-adds, 2 binary32
+ * fast exponentials (__expf), 3 binary64 exponentials (exp).  Runs
+ * independent chains of that operation on 8 CTAs of 256 threads per
+ * multiprocessor of the current device (about 10 ms per launch), times the
+ * fastest of three launches with CUDA events on stream (NULL: the default
+ * stream) and stores operations per second in *ops_per_s.  scratch: device
+ * memory of at least 8 bytes per CTA (64 KiB covers 1024 SMs), overwritten.
+ * Errors: MT_ERR_INVALID (which), MT_ERR_WORKSPACE (scratch), MT_ERR_CUDA. */
+mt_status mt_probe_rate(int32_t which, void* scratch, size_t scratch_bytes, void* stream,
+                        double* ops_per_s);
+
 /* Description of the last error on this thread (static storage). */
 const char* mt_last_error(void);
 

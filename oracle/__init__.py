@@ -75,9 +75,11 @@ def build(force: bool = False) -> Path:
     if newer and not force:
         return LIB
     tmp = BUILD_DIR / f"libmt_oracle.{os.getpid()}.so"
-    subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off",
-                    "-fno-fast-math", "-fPIC", "-shared", "-o", str(tmp),
-                    str(SRC), "-lm"], check=True)
+    base = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+            "-shared", "-o", str(tmp), str(SRC), "-lm"]
+    # OpenMP (for the all-cores baseline) where the compiler has it
+    if subprocess.run(base + ["-fopenmp"], capture_output=True).returncode != 0:
+        subprocess.run(base, check=True)
     os.replace(tmp, LIB)
     return LIB
 
@@ -114,6 +116,8 @@ def lib():
             f.restype = i64
         L.mto_step.argtypes = [pp, i64, vp, vp, vp, vp]; L.mto_step.restype = ctypes.c_int
         L.mto_observables.argtypes = [i64, vp, vp, vp]; L.mto_observables.restype = None
+        L.mto_set_threads.argtypes = [i32]; L.mto_set_threads.restype = ctypes.c_int
+        L.mto_set_threads(1)
         _lib = L
     return _lib
 
@@ -252,3 +256,10 @@ def observables(A, B):
     out = np.empty(4, dtype=np.float64)
     lib().mto_observables(len(A), _ptr(A), _ptr(B), _ptr(out))
     return out
+
+
+def set_threads(threads: int) -> int:
+    """Threads of the sorted-window transfer's per-particle loops (OpenMP
+    builds; the results do not depend on the count).  Returns the count in
+    effect: 1 when the oracle was built without OpenMP."""
+    return int(lib().mto_set_threads(int(threads)))

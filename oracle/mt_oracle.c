@@ -10,6 +10,25 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the per-particle loops of the sorted-window transfer (1 unless
+ * set; each particle's sums are computed alone, in the same order, whatever
+ * the thread count, so results do not depend on it). */
+static int g_threads = 1;
+
+int mto_set_threads(int32_t threads) {
+#ifdef _OPENMP
+  g_threads = threads >= 1 ? threads : 1;
+  return g_threads;
+#else
+  (void)threads;
+  g_threads = 1;
+  return 1;
+#endif
+}
 
 int64_t mto_quantize(double x, int32_t k) { return llrint(ldexp(x, k)); }
 
@@ -315,6 +334,9 @@ int mto_mass_transfer_sorted_1d(const mto_params* p, int64_t n,
     lo[a] = b;
     hi[a] = e;
   }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+#endif
   for (int64_t a = 0; a < n; ++a) {
     const int64_t i = ord[a];
     double s = 0.0;
@@ -322,6 +344,9 @@ int mto_mass_transfer_sorted_1d(const mto_params* p, int64_t n,
     r[a] = s;
   }
   for (int32_t s = 0; s < nspec; ++s)
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+#endif
     for (int64_t a = 0; a < n; ++a) {
       const int64_t i = ord[a];
       double acc = 0.0;

@@ -28,7 +28,8 @@
  * the number of fractional bits.  The cutoff is s_max rounded down to that
  * grid, Smax = floor(s_max * 2^k) ticks; a pair is in range iff
  * |dX| <= Smax (1-d) or dX^2 + dY^2 <= Smax^2 (2-d), evaluated exactly in
- * integers.  Every function is single-threaded, plain loops, FP64.
+ * integers.  Every function is plain loops in FP64, single-threaded except
+ * the sorted-window transfer's per-particle loops (see mto_set_threads).
  */
 #ifndef MT_ORACLE_H
 #define MT_ORACLE_H
@@ -105,10 +106,17 @@ int mto_mass_transfer_sample(const mto_params* p, int64_t n, const int64_t* X,
 
 /* 1-d only: the same step with the fixed-radius search done by sorting the
  * particles by position and scanning windows (Sec. 2.1's sparse search, no
- * tree).  Visits exactly the pairs the cutoff admits. */
+ * tree).  Visits exactly the pairs the cutoff admits.  Its per-particle
+ * loops run on mto_set_threads() threads (1 by default); each particle's
+ * sums are the same whatever the thread count. */
 int mto_mass_transfer_sorted_1d(const mto_params* p, int64_t n,
                                 const int64_t* X, int32_t nspec,
                                 const double* const* M, double* const* Mout);
+
+/* Threads for the sorted-window transfer's per-particle loops when the
+ * oracle is built with OpenMP (for the all-cores CPU baseline); returns the
+ * count in effect (1 without OpenMP). */
+int mto_set_threads(int32_t threads);
 
 /* Irreversible equilibrium reaction per particle (Sec. 3, Sec. 7). */
 void mto_react(int64_t n, double* A, double* B);

@@ -18,7 +18,7 @@ CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "libmt.so"
 SOURCES = ["mt_api.cu", "mt_move_sort.cu", "mt_transfer.cu", "mt_io.cu", "mt_noalloc.cu", "mt_fused.cu",
-           "mt_tune.cu", "mt_server.cu"]
+           "mt_tune.cu", "mt_server.cu", "mt_probe.cu"]
 HEADERS = [CSRC / "mt_internal.cuh", CSRC / "mt_pair.cuh", ROOT / "include" / "mt.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

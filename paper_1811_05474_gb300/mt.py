@@ -159,6 +159,7 @@ def lib(path: Path | None = None):
         "mt_philox": [H, u32, u32, u32, u32, u32, u32, i64, _vp],
         "mt_set_profiling": [H, i32],
         "mt_test_hold_scan": [H, i32, i64],
+        "mt_probe_rate": [i32, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(ctypes.c_double)],
         "mt_transfer_1d_noalloc": [_vp, _vp, _vp, _vp, _vp, i64, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, i32, i32,
                                    _vp],
@@ -390,6 +391,20 @@ def mt_read_profile(h):
 
 def mt_profile_name(h, idx: int) -> str:
     return lib().mt_profile_name(h, idx).decode()
+
+
+PROBE_DFMA, PROBE_FFMA, PROBE_EXPF, PROBE_EXP = 0, 1, 2, 3
+
+
+def mt_probe_rate(which: int, device="cuda") -> float:
+    """Operations per second of one device pipe (see include/mt.h)."""
+    import torch
+
+    scratch = torch.empty(64 * 1024, dtype=torch.uint8, device=device)
+    out = ctypes.c_double(0.0)
+    check(lib().mt_probe_rate(which, scratch.data_ptr(), scratch.numel(), None,
+                              ctypes.byref(out)))
+    return float(out.value)
 
 
 def mt_test_hold_scan(h, hold: int, spin_limit: int = 0) -> None:

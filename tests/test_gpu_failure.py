@@ -75,7 +75,8 @@ def test_bad_index_reports_device_error():
     ids = np.arange(n, dtype=np.int32)
     hits = [o for o in np.flatnonzero(w[:w.size - n + 1] == 0) if np.array_equal(w[o:o + n], ids)]
     assert hits, "the id array was not found in the workspace"
-    w[hits[0] + 500] = n + 7
+    for o in hits:  # both ping-pong id buffers hold the identity after the upload's sort
+        w[o + 500] = n + 7
     bad = ws.copy()
     bad[:w.size * 4] = w.view(np.uint8)
     sim.workspace.copy_(torch.from_numpy(bad).to(sim.workspace.device))

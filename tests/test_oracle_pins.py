@@ -456,3 +456,20 @@ def test_observables_closed_form():
     B = A[::-1].copy()
     o = O.observables(A, B)
     assert o.tolist() == [n * (n + 1) / 2, n * (n + 1) / 2, 0.0, (n + 1) / 2]
+
+
+def test_sorted_window_threads_do_not_change_results():
+    """The all-cores CPU baseline runs the sorted-window transfer's
+    per-particle loops on several threads: bit-identical to one thread."""
+    n = 20000
+    p = O.params(L=(20000.0,), v=(0.5,))
+    X = O.quantize(synth.uniform_positions(n, 20000.0, seed=41), K)
+    A, B = synth.uniform_masses(n, seed=41)
+    one = O.mass_transfer_sorted_1d(p, X, [A, B])
+    try:
+        O.set_threads(4)
+        four = O.mass_transfer_sorted_1d(p, X, [A, B])
+    finally:
+        O.set_threads(1)
+    for u, w in zip(one, four):
+        assert np.array_equal(u, w)
