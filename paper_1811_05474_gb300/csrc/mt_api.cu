@@ -257,18 +257,23 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
     double dr = std::fabs((double)D.drift[0]);
     const long long dc = (long long)((dr + std::ceil(D.bq * 5.78) + 2.0) / (double)w) + 2;
     const double per_cell = (double)p.n / (double)D.ncell;
+    // right neighbours per particle (mean density x Smax): the first tier
+    // lists the pairs of owners within about T + 3 Smax of density
+    const double rn = (double)D.S * (double)p.n / lq_sum;
     long long T = 1024;
-    while (T >= 64 && (double)T + 2.0 * (double)(D.hc + dc + 1) * per_cell * 1.5 + 64.0 >
-                          (double)kFusedCap)
+    while (T >= 64 && ((double)T + 2.0 * (double)(D.hc + dc + 1) * per_cell * 1.5 + 64.0 >
+                           (double)kFusedCap ||
+                       ((double)T + 3.0 * rn) * rn * 1.5 + 64.0 > (double)kFusedPairCap))
       T /= 2;
     if (p.seg_target != 0) {
       if (p.seg_target < 16 || p.seg_target > kFusedCap)
         return fail(MT_ERR_INVALID, "seg_target must be 0 or in [16, %d]", kFusedCap);
       T = p.seg_target;
     } else if (T >= 64) {
-      // whole waves: the step's persistent CTAs (kFusedCtasPerSm per SM of
-      // the current device) each take the same number of segments
-      const long long slots = (long long)kFusedCtasPerSm * device_sms();
+      // whole waves: the step's persistent CTAs (the resident first-tier
+      // CTAs per SM of the current device) each take the same number of
+      // segments
+      const long long slots = (long long)fused_ctas_per_sm(p.precision) * device_sms();
       if (slots > 0) {
         const long long waves = (p.n + T * slots - 1) / (T * slots);
         T = (p.n + waves * slots - 1) / (waves * slots);
@@ -728,7 +733,8 @@ mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace
   }
   // the predicted-segment kernel pays off when the first tier has more than
   // one wave of segments (large systems); small ones keep the plain chain
-  d.use_pred = D.fused && D.nseg > (long long)kFusedCtasPerSm * d.nsm ? 1 : 0;
+  d.use_pred =
+      D.fused && D.nseg > (long long)fused_ctas_per_sm(D.p.precision) * d.nsm ? 1 : 0;
   d.periodic = D.p.walls == MT_WALLS_PERIODIC ? 1 : 0;
   d.nspec = D.p.species;
   d.band_cap = (int)D.band;

@@ -70,7 +70,6 @@ size_t tier_smem(int precision) {
   return (size_t)TR::kCap * (8 + 8 + 8 + 4 + r) + (size_t)(2 * TR::kBins + 1) * 4;
 }
 
-size_t fused_smem_bytes(int precision) { return tier_smem<Fast>(precision); }
 
 __device__ __forceinline__ long long lmin(long long a, long long b) { return a < b ? a : b; }
 __device__ __forceinline__ long long lmax(long long a, long long b) { return a > b ? a : b; }
@@ -123,6 +122,237 @@ __device__ __forceinline__ SegScalars load_seg(const Dev& d, int sc, long long D
   s.o0 = So[lmax(s.c0 - Dc, 0)];
   s.o1 = So[lmin(s.c0 + Dc, ncell)];
   return s;
+}
+
+// ------------------------------------------------ first tier: pair list --
+// The first tier's transfer (row sums, exchange, reaction) over a list of
+// the unordered pairs of its staged, sorted particles.  Owners are the
+// staged slots j with x_j in [xlo - 2 Smax, xhi + Smax); each owns its pairs
+// (j, k), k > j, x_k - x_j <= Smax -- R_j consecutive slots, since the slots
+// are sorted -- and pair q of owner j sits at pfx[j] + (k - j - 1) in the
+// list.  The weight nu (Eq. 3) of every listed pair is evaluated once, by
+// one thread per pair (no divergent walks), and stored; the row sums
+// r_j = 1 + sum of its left pairs' weights + sum of its right pairs' (in
+// that order, the order of the cluster tiers' walks) and the exchange of
+// own particles then read the stored weights.  A slot's left pairs are
+// (j - t, j) for t = 1, 2, ... while R_{j-t} >= t.
+constexpr int kPairCap = kFusedPairCap;
+
+template <typename TR, typename T>
+__host__ __device__ constexpr size_t pair_region_offset() {
+  return ((size_t)TR::kCap * (8 + 8 + 8 + 4 + sizeof(T)) + (size_t)(2 * TR::kBins + 1) * 4 + 7) &
+         ~(size_t)7;
+}
+template <typename TR, typename T>
+__host__ __device__ constexpr size_t pair_region_bytes() {
+  return (size_t)kPairCap * sizeof(T) + (size_t)(TR::kCap + 1) * 2 + (size_t)kPairCap * 2;
+}
+
+// Dynamic shared memory of the first tier: staging, bins and the pair list.
+size_t fused_smem_bytes(int precision) {
+  return precision == MT_FP64 ? pair_region_offset<Fast, double>() + pair_region_bytes<Fast, double>()
+                              : pair_region_offset<Fast, float>() + pair_region_bytes<Fast, float>();
+}
+
+// In-place exclusive prefix sum of v[0 .. cnt) (cnt <= NT * 4) into
+// v[0 .. cnt]; all NT threads call it.  Returns the total.
+template <int NT>
+__device__ __forceinline__ int block_scan_u16(unsigned short* v, int cnt, int* s_part) {
+  constexpr int E = 4;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int loc[E];
+  int sum = 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = tid * E + e;
+    loc[e] = i < cnt ? v[i] : 0;
+    sum += loc[e];
+  }
+  int inc = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) s_part[warp] = inc;
+  __syncthreads();
+  int run = inc - sum;
+  int total = 0;
+  for (int w = 0; w < NT / 32; ++w) {
+    const int t = s_part[w];
+    if (w < warp) run += t;
+    total += t;
+  }
+  __syncthreads();  // every thread has read its inputs and s_part
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = tid * E + e;
+    if (i < cnt) v[i] = (unsigned short)run;
+    run += loc[e];
+  }
+  if (tid == 0) v[cnt] = (unsigned short)total;
+  __syncthreads();
+  return total;
+}
+
+template <int PR, typename TR>
+__device__ bool pair_transfer(const Dev& d, unsigned char* smem, bool active, int m, int w0,
+                              int w1, long long out0, long long xlo, long long xhi) {
+  using W = Weight<mixw(PR), 1>;
+  using T = typename W::T;
+  using MS = Mass<PR>;
+  using MV = typename MS::V;
+  constexpr int NT = TR::kT, CAP = TR::kCap;
+  long long* sx = reinterpret_cast<long long*>(smem);
+  unsigned long long* sA = reinterpret_cast<unsigned long long*>(sx + CAP);
+  unsigned long long* sB = sA + CAP;
+  int* sid = reinterpret_cast<int*>(sB + CAP);
+  T* sr = reinterpret_cast<T*>(sid + CAP);
+  T* sw = reinterpret_cast<T*>(smem + pair_region_offset<TR, T>());  // [kPairCap]
+  unsigned short* pfx = reinterpret_cast<unsigned short*>(sw + kPairCap);  // [CAP + 1]
+  unsigned short* own = pfx + CAP + 1;                                    // [kPairCap]
+  __shared__ int s_olo, s_rlo, s_rhi;
+  __shared__ int s_part[NT / 32];
+  const int tid = threadIdx.x;
+  const long long S = d.S;
+  if (active && tid == 0) {
+    s_olo = lower_at_least(sx, m, xlo - 2 * S);
+    s_rlo = lower_at_least(sx, m, xlo - S);
+    s_rhi = lower_at_least(sx, m, xhi + S);
+  }
+  __syncthreads();
+  const int olo = active ? s_olo : 0, rlo = active ? s_rlo : 0, rhi = active ? s_rhi : 0;
+  const int no = rhi - olo;  // owners
+  // right-neighbour counts R_j
+  for (int jj = tid; jj < no; jj += NT) {
+    const int j = olo + jj;
+    const long long x = sx[j];
+    int c = 0;
+    for (int k = j + 1; k < m && sx[k] - x <= S; ++k) ++c;
+    pfx[jj] = (unsigned short)c;
+  }
+  __syncthreads();
+  const int np = block_scan_u16<NT>(pfx, no, s_part);
+  if (np > kPairCap) return false;  // uniform across the CTA
+  for (int jj = tid; jj < no; jj += NT)
+    for (int q = pfx[jj]; q < pfx[jj + 1]; ++q) own[q] = (unsigned short)jj;
+  __syncthreads();
+  // one weight per unordered pair
+  for (int q = tid; q < np; q += NT) {
+    const int jj = own[q];
+    const int j = olo + jj, k = j + 1 + (q - pfx[jj]);
+    sw[q] = W::near(d, sx[k] - sx[j]);
+  }
+  __syncthreads();
+  // row sums of the slots within Smax of an own particle
+  for (int j = rlo + tid; j < rhi; j += NT) {
+    const int jj = j - olo;
+    T r = T(1);
+    for (int t = 1; jj - t >= 0; ++t) {
+      const int ii = jj - t;
+      if (pfx[ii + 1] - pfx[ii] < t) break;
+      r += sw[pfx[ii] + t - 1];
+    }
+    for (int q = pfx[jj]; q < pfx[jj + 1]; ++q) r += sw[q];
+    sr[j] = mixw(PR) ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
+  }
+  __syncthreads();
+  // symmetric normalisation: each listed pair's P = nu (1/r_j + 1/r_k) / 2
+  // once, in place of nu (pairs with an end outside the row-sum range are
+  // never read)
+  const bool sym = d.norm != MT_NORM_ROW;
+  if (sym) {
+    for (int q = tid; q < np; q += NT) {
+      const int jj = own[q];
+      const int j = olo + jj, k = j + 1 + (q - pfx[jj]);
+      if (j >= rlo && k < rhi) sw[q] = normalised<T>(MT_NORM_SYM, sw[q], sr[j], sr[k]);
+    }
+  }
+  // Own particles ordered by neighbour count (counting sort; the order
+  // within a count does not matter): a warp's lanes then take particles with
+  // equal counts and the exchange loops below do not diverge.  Each
+  // particle's sums are the same whatever lane computes them.
+  constexpr int kCnt = 64;
+  constexpr int PERT = CAP / NT;
+  __shared__ int s_hist[kCnt];
+  int* perm = reinterpret_cast<int*>(sr + CAP) + TR::kBins + 1;  // the bins' scatter cursors
+  const int nown = active ? w1 - w0 : 0;
+  for (int b = tid; b < kCnt; b += NT) s_hist[b] = 0;
+  __syncthreads();
+  int cj[PERT];
+#pragma unroll
+  for (int e = 0; e < PERT; ++e) {
+    const int j = w0 + tid + e * NT;
+    cj[e] = -1;
+    if (tid + e * NT < nown) {
+      const int jj = j - olo;
+      int c = pfx[jj + 1] - pfx[jj];
+      for (int t = 1; jj - t >= 0 && pfx[jj - t + 1] - pfx[jj - t] >= t; ++t) ++c;
+      cj[e] = c < kCnt ? c : kCnt - 1;
+      atomicAdd(&s_hist[cj[e]], 1);
+    }
+  }
+  __syncthreads();
+  if (tid < 32) {  // exclusive scan of the 64 counts by one warp
+    const int h0 = s_hist[2 * tid], h1 = s_hist[2 * tid + 1];
+    int inc = h0 + h1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (tid >= o) inc += t;
+    }
+    s_hist[2 * tid] = inc - h0 - h1;
+    s_hist[2 * tid + 1] = inc - h1;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < PERT; ++e)
+    if (cj[e] >= 0) perm[atomicAdd(&s_hist[cj[e]], 1)] = w0 + tid + e * NT;
+  __syncthreads();
+  if (active) {
+    Ctrl* c = d.ctrl;
+    const int xc = c->xcur, mc = c->mcur;
+    long long* Xn = d.X[xc ^ 1];
+    int* In = d.id[xc ^ 1];
+    unsigned long long* Mn = d.M[mc ^ 1];
+    if (out0 + (w1 - w0) > d.n) raise_error(c, kErrIndex, out0);
+    for (int p = tid; p < nown; p += NT) {
+      const int j = perm[p];
+      const int jj = j - olo;
+      const T ip = sr[j];
+      MV A = MS::load(sA, j), B = MS::load(sB, j);
+      typename MS::Acc dA{}, dB{};
+      for (int t = 1; jj - t >= 0; ++t) {  // left pairs (j - t, j)
+        const int ii = jj - t;
+        if (pfx[ii + 1] - pfx[ii] < t) break;
+        const int i = j - t;
+        const T w = sw[pfx[ii] + t - 1];
+        const T P = sym ? w : normalised<T>(MT_NORM_ROW, w, ip, sr[i]);
+        MS::acc(dA, P, MS::diff(MS::load(sA, i), A));
+        MS::acc(dB, P, MS::diff(MS::load(sB, i), B));
+      }
+      for (int q = pfx[jj], k = j + 1; q < pfx[jj + 1]; ++q, ++k) {  // right pairs (j, k)
+        const T P = sym ? sw[q] : normalised<T>(MT_NORM_ROW, sw[q], ip, sr[k]);
+        MS::acc(dA, P, MS::diff(MS::load(sA, k), A));
+        MS::acc(dB, P, MS::diff(MS::load(sB, k), B));
+      }
+      MS::update(A, B, dA, dB, d.react);
+      const long long o = out0 + (j - w0);
+      if (o < d.n) {
+        MS::store(Mn, o, A);
+        MS::store(Mn, d.n + o, B);
+      }
+    }
+    for (int j = w0 + tid; j < w1; j += NT) {  // positions and ids, coalesced
+      const long long o = out0 + (j - w0);
+      if (o < d.n) {
+        Xn[o] = sx[j];
+        In[o] = sid[j];
+      }
+    }
+  }
+  __syncthreads();
+  return true;
 }
 
 // Process one segment with the CTA (all NT threads call it).  The CTA
@@ -491,154 +721,109 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
   const int w0 = s_w0, w1 = s_w1;
   const long long out0 = o0 + s_lt;
   const long long S = d.S;
-  // Row sums.  A particle with more than kWalk neighbours on a side is
-  // dense: it is queued (in bcur, free by now) and summed by a whole warp,
-  // lanes striding over its neighbour range, combined in a fixed tree.  The
-  // choice and the order depend only on the neighbourhood, so every CTA that
-  // forms r_j forms the same value.
-  int* dlist = bcur;
-  if (active) {
-    for (int t = tid;; t += NT) {
-      const int j = CL > 1 ? t * CL + slice : t;  // with a cluster: every CL-th
-      if (j >= m) break;
-      const long long x = sx[j];
-      if (x < xlo - S || x >= xhi + S) continue;  // not a neighbour of an own particle
-      if (dense_at(sx, m, j, x, S)) {
-        const int at = atomicAdd(&s_nd, 1);
-        if (at < NB) {
-          dlist[at] = j;
-          continue;
-        }
-      }
-      // at most kWalk neighbours a side (or the dense list is full)
-      T r = T(1);
-      for (int q = j - 1; q >= 0 && x - sx[q] <= S; --q) r += W::near(d, x - sx[q]);
-      for (int q = j + 1; q < m && sx[q] - x <= S; ++q) r += W::near(d, sx[q] - x);
-      sr[j] = mixw(PR) ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
+  if constexpr (CL == 1) {
+    if (!pair_transfer<PR, TR>(d, smem, active, m, w0, w1, out0, xlo, xhi)) {
+      status = kSegHeavy;  // more pairs than the list holds: the second tier takes it
+      active = false;
     }
-  }
-  __syncthreads();
-  if (active) {
-    const int nd = s_nd < NB ? s_nd : NB;
-    for (int k = warp; k < nd; k += NT / 32) {
-      const int j = dlist[k];
-      const long long x = sx[j];
-      const int lo = lower_at_least(sx, m, x - S), hi = lower_at_least(sx, m, x + S + 1);
-      // second tier: four chains per lane (dense particles are its work);
-      // first tier: one (registers are scarce there)
-      T r0 = T(0), r1 = T(0), r2 = T(0), r3 = T(0);
-      int q = lo + lane;
-      if constexpr (CL > 1) {
-        for (; q + 96 < hi; q += 128) {
-          r0 += W::near(d, x > sx[q] ? x - sx[q] : sx[q] - x);
-          r1 += W::near(d, x > sx[q + 32] ? x - sx[q + 32] : sx[q + 32] - x);
-          r2 += W::near(d, x > sx[q + 64] ? x - sx[q + 64] : sx[q + 64] - x);
-          r3 += W::near(d, x > sx[q + 96] ? x - sx[q + 96] : sx[q + 96] - x);
-        }
-      }
-      for (; q < hi; q += 32) r0 += W::near(d, x > sx[q] ? x - sx[q] : sx[q] - x);
-      const T r = warp_sum((r0 + r1) + (r2 + r3));
-      if (lane == 0) sr[j] = mixw(PR) ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
-    }
-  }
-  if constexpr (CL > 1) {
-    // Every CTA of the cluster staged and sorted the same particles; each
-    // formed the row sums of every CL-th one.  Gather the rest from the
-    // peers' shared memory (distributed shared memory), between two cluster
-    // barriers so no CTA reads a peer that has moved on.
-    cg::cluster_group cl = cg::this_cluster();
-    cl.sync();
-    if (active) {
-      for (int j = tid; j < m; j += NT) {
-        const int owner = j % CL;
-        if (owner == slice) continue;
-        const long long x = sx[j];
-        if (x < xlo - S || x >= xhi + S) continue;
-        sr[j] = *cl.map_shared_rank(&sr[j], owner);
-      }
-    }
-    cl.sync();
   } else {
-    __syncthreads();
-  }
-  if (active) {
-    long long* Xn = d.X[xc ^ 1];
-    int* In = d.id[xc ^ 1];
-    unsigned long long* Mn = d.M[mc ^ 1];
-    if (out0 + (w1 - w0) > d.n) raise_error(c, kErrIndex, out0);
-    for (int j = w0 + slice + tid * nslice; j < w1; j += NT * nslice) {
-      const long long x = sx[j];
-      const T ip = sr[j];
-      if (dense_at(sx, m, j, x, S)) {
-        const int at = atomicAdd(&s_nd2, 1);
-        if (at < NB) {
-          dlist[at] = j;  // a warp does it below
-          continue;
+    // Row sums.  A particle with more than kWalk neighbours on a side is
+    // dense: it is queued (in bcur, free by now) and summed by a whole warp,
+    // lanes striding over its neighbour range, combined in a fixed tree.  The
+    // choice and the order depend only on the neighbourhood, so every CTA that
+    // forms r_j forms the same value.
+    int* dlist = bcur;
+    if (active) {
+      for (int t = tid;; t += NT) {
+        const int j = CL > 1 ? t * CL + slice : t;  // with a cluster: every CL-th
+        if (j >= m) break;
+        const long long x = sx[j];
+        if (x < xlo - S || x >= xhi + S) continue;  // not a neighbour of an own particle
+        if (dense_at(sx, m, j, x, S)) {
+          const int at = atomicAdd(&s_nd, 1);
+          if (at < NB) {
+            dlist[at] = j;
+            continue;
+          }
         }
-      }
-      MV A = MS::load(sA, j), B = MS::load(sB, j);
-      typename MS::Acc dA{}, dB{};
-      for (int q = j - 1; q >= 0 && x - sx[q] <= S; --q) {
-        const T P = normalised<T>(d.norm, W::near(d, x - sx[q]), ip, sr[q]);
-        MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
-        MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
-      }
-      for (int q = j + 1; q < m && sx[q] - x <= S; ++q) {
-        const T P = normalised<T>(d.norm, W::near(d, sx[q] - x), ip, sr[q]);
-        MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
-        MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
-      }
-      MS::update(A, B, dA, dB, d.react);
-      const long long o = out0 + (j - w0);
-      if (o < d.n) {
-        Xn[o] = x;
-        In[o] = sid[j];
-        MS::store(Mn, o, A);
-        MS::store(Mn, d.n + o, B);
+        // at most kWalk neighbours a side (or the dense list is full)
+        T r = T(1);
+        for (int q = j - 1; q >= 0 && x - sx[q] <= S; --q) r += W::near(d, x - sx[q]);
+        for (int q = j + 1; q < m && sx[q] - x <= S; ++q) r += W::near(d, sx[q] - x);
+        sr[j] = mixw(PR) ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
       }
     }
-  }
-  __syncthreads();
-  if (active) {
-    // dense own particles: one warp each, lanes striding the neighbourhood
-    long long* Xn = d.X[xc ^ 1];
-    int* In = d.id[xc ^ 1];
-    unsigned long long* Mn = d.M[mc ^ 1];
-    const int nd = s_nd2 < NB ? s_nd2 : NB;
-    for (int k = warp; k < nd; k += NT / 32) {
-      const int j = dlist[k];
-      const long long x = sx[j];
-      const T ip = sr[j];
-      MV A = MS::load(sA, j), B = MS::load(sB, j);
-      typename MS::Acc dA{}, dB{};
-      const int lo = lower_at_least(sx, m, x - S), hi = lower_at_least(sx, m, x + S + 1);
-      // second tier: four chains per lane (q, q + 32, q + 64, q + 96),
-      // merged at the end; first tier: one
-      typename MS::Acc cA[4] = {}, cB[4] = {};
-      auto pair = [&](int qq, int ch) {
-        if (qq == j) return;
-        const T P =
-            normalised<T>(d.norm, W::near(d, x > sx[qq] ? x - sx[qq] : sx[qq] - x), ip, sr[qq]);
-        MS::acc(cA[ch], P, MS::diff(MS::load(sA, qq), A));
-        MS::acc(cB[ch], P, MS::diff(MS::load(sB, qq), B));
-      };
-      int q = lo + lane;
-      if constexpr (CL > 1) {
-        for (; q + 96 < hi; q += 128) {
-          pair(q, 0);
-          pair(q + 32, 1);
-          pair(q + 64, 2);
-          pair(q + 96, 3);
+    __syncthreads();
+    if (active) {
+      const int nd = s_nd < NB ? s_nd : NB;
+      for (int k = warp; k < nd; k += NT / 32) {
+        const int j = dlist[k];
+        const long long x = sx[j];
+        const int lo = lower_at_least(sx, m, x - S), hi = lower_at_least(sx, m, x + S + 1);
+        // second tier: four chains per lane (dense particles are its work);
+        // first tier: one (registers are scarce there)
+        T r0 = T(0), r1 = T(0), r2 = T(0), r3 = T(0);
+        int q = lo + lane;
+        if constexpr (CL > 1) {
+          for (; q + 96 < hi; q += 128) {
+            r0 += W::near(d, x > sx[q] ? x - sx[q] : sx[q] - x);
+            r1 += W::near(d, x > sx[q + 32] ? x - sx[q + 32] : sx[q + 32] - x);
+            r2 += W::near(d, x > sx[q + 64] ? x - sx[q + 64] : sx[q + 64] - x);
+            r3 += W::near(d, x > sx[q + 96] ? x - sx[q + 96] : sx[q + 96] - x);
+          }
         }
-        for (; q < hi; q += 32) pair(q, 0);
-        dA = acc_warp_sum(acc_merge(acc_merge(cA[0], cA[1]), acc_merge(cA[2], cA[3])));
-        dB = acc_warp_sum(acc_merge(acc_merge(cB[0], cB[1]), acc_merge(cB[2], cB[3])));
-      } else {
-        for (; q < hi; q += 32) pair(q, 0);
-        dA = acc_warp_sum(cA[0]);
-        dB = acc_warp_sum(cB[0]);
+        for (; q < hi; q += 32) r0 += W::near(d, x > sx[q] ? x - sx[q] : sx[q] - x);
+        const T r = warp_sum((r0 + r1) + (r2 + r3));
+        if (lane == 0) sr[j] = mixw(PR) ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
       }
-      if (lane == 0) {
+    }
+    if constexpr (CL > 1) {
+      // Every CTA of the cluster staged and sorted the same particles; each
+      // formed the row sums of every CL-th one.  Gather the rest from the
+      // peers' shared memory (distributed shared memory), between two cluster
+      // barriers so no CTA reads a peer that has moved on.
+      cg::cluster_group cl = cg::this_cluster();
+      cl.sync();
+      if (active) {
+        for (int j = tid; j < m; j += NT) {
+          const int owner = j % CL;
+          if (owner == slice) continue;
+          const long long x = sx[j];
+          if (x < xlo - S || x >= xhi + S) continue;
+          sr[j] = *cl.map_shared_rank(&sr[j], owner);
+        }
+      }
+      cl.sync();
+    } else {
+      __syncthreads();
+    }
+    if (active) {
+      long long* Xn = d.X[xc ^ 1];
+      int* In = d.id[xc ^ 1];
+      unsigned long long* Mn = d.M[mc ^ 1];
+      if (out0 + (w1 - w0) > d.n) raise_error(c, kErrIndex, out0);
+      for (int j = w0 + slice + tid * nslice; j < w1; j += NT * nslice) {
+        const long long x = sx[j];
+        const T ip = sr[j];
+        if (dense_at(sx, m, j, x, S)) {
+          const int at = atomicAdd(&s_nd2, 1);
+          if (at < NB) {
+            dlist[at] = j;  // a warp does it below
+            continue;
+          }
+        }
+        MV A = MS::load(sA, j), B = MS::load(sB, j);
+        typename MS::Acc dA{}, dB{};
+        for (int q = j - 1; q >= 0 && x - sx[q] <= S; --q) {
+          const T P = normalised<T>(d.norm, W::near(d, x - sx[q]), ip, sr[q]);
+          MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
+          MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
+        }
+        for (int q = j + 1; q < m && sx[q] - x <= S; ++q) {
+          const T P = normalised<T>(d.norm, W::near(d, sx[q] - x), ip, sr[q]);
+          MS::acc(dA, P, MS::diff(MS::load(sA, q), A));
+          MS::acc(dB, P, MS::diff(MS::load(sB, q), B));
+        }
         MS::update(A, B, dA, dB, d.react);
         const long long o = out0 + (j - w0);
         if (o < d.n) {
@@ -646,6 +831,58 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
           In[o] = sid[j];
           MS::store(Mn, o, A);
           MS::store(Mn, d.n + o, B);
+        }
+      }
+    }
+    __syncthreads();
+    if (active) {
+      // dense own particles: one warp each, lanes striding the neighbourhood
+      long long* Xn = d.X[xc ^ 1];
+      int* In = d.id[xc ^ 1];
+      unsigned long long* Mn = d.M[mc ^ 1];
+      const int nd = s_nd2 < NB ? s_nd2 : NB;
+      for (int k = warp; k < nd; k += NT / 32) {
+        const int j = dlist[k];
+        const long long x = sx[j];
+        const T ip = sr[j];
+        MV A = MS::load(sA, j), B = MS::load(sB, j);
+        typename MS::Acc dA{}, dB{};
+        const int lo = lower_at_least(sx, m, x - S), hi = lower_at_least(sx, m, x + S + 1);
+        // second tier: four chains per lane (q, q + 32, q + 64, q + 96),
+        // merged at the end; first tier: one
+        typename MS::Acc cA[4] = {}, cB[4] = {};
+        auto pair = [&](int qq, int ch) {
+          if (qq == j) return;
+          const T P =
+              normalised<T>(d.norm, W::near(d, x > sx[qq] ? x - sx[qq] : sx[qq] - x), ip, sr[qq]);
+          MS::acc(cA[ch], P, MS::diff(MS::load(sA, qq), A));
+          MS::acc(cB[ch], P, MS::diff(MS::load(sB, qq), B));
+        };
+        int q = lo + lane;
+        if constexpr (CL > 1) {
+          for (; q + 96 < hi; q += 128) {
+            pair(q, 0);
+            pair(q + 32, 1);
+            pair(q + 64, 2);
+            pair(q + 96, 3);
+          }
+          for (; q < hi; q += 32) pair(q, 0);
+          dA = acc_warp_sum(acc_merge(acc_merge(cA[0], cA[1]), acc_merge(cA[2], cA[3])));
+          dB = acc_warp_sum(acc_merge(acc_merge(cB[0], cB[1]), acc_merge(cB[2], cB[3])));
+        } else {
+          for (; q < hi; q += 32) pair(q, 0);
+          dA = acc_warp_sum(cA[0]);
+          dB = acc_warp_sum(cB[0]);
+        }
+        if (lane == 0) {
+          MS::update(A, B, dA, dB, d.react);
+          const long long o = out0 + (j - w0);
+          if (o < d.n) {
+            Xn[o] = x;
+            In[o] = sid[j];
+            MS::store(Mn, o, A);
+            MS::store(Mn, d.n + o, B);
+          }
         }
       }
     }
@@ -1036,12 +1273,38 @@ static int max_active_clusters(int precision) {
   return n;
 }
 
+// Resident first-tier CTAs per SM for each precision (the persistent grid
+// is that many per SM), from the occupancy calculator at configuration.
+static int g_fast_ctas_per_sm[3] = {kFusedCtasPerSm, kFusedCtasPerSm, kFusedCtasPerSm};
+
 template <int PR>
 static cudaError_t configure_tiers(int cl) {
   cudaError_t e = cudaFuncSetAttribute(k_step1d<PR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)tier_smem<Fast>(PR));
+                                       (int)fused_smem_bytes(PR));
   if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step1d<PR>, Fast::kT,
+                                                    fused_smem_bytes(PR));
+  if (e != cudaSuccess) return e;
+  const int slot = PR == MT_FP64 ? 0 : PR == MT_MIXED ? 1 : 2;
+  g_fast_ctas_per_sm[slot] = per_sm < 1 ? 1 : (per_sm > kFusedCtasPerSm ? kFusedCtasPerSm : per_sm);
   return cl == 16 ? configure_big<PR, 16>(PR) : configure_big<PR, 8>(PR);
+}
+
+int fused_ctas_per_sm(int precision) {
+  const int slot = precision == MT_FP64 ? 0 : precision == MT_MIXED ? 1 : 2;
+  static bool known[3] = {false, false, false};
+  if (!known[slot]) {
+    const cudaError_t e = precision == MT_FP64   ? configure_tiers<MT_FP64>(8)
+                          : precision == MT_MIXED ? configure_tiers<MT_MIXED>(8)
+                                                  : configure_tiers<MT_MIXED_DF32>(8);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return kFusedCtasPerSm;
+    }
+    known[slot] = true;
+  }
+  return g_fast_ctas_per_sm[slot];
 }
 
 cudaError_t fused_configure() {
@@ -1065,8 +1328,9 @@ cudaError_t fused_configure() {
 
 cudaError_t launch_fused_step(const Dev& d, int precision, cudaGraphConditionalHandle cond,
                               int use_cond, cudaStream_t s) {
-  const size_t sm = tier_smem<Fast>(precision);
-  const int g = d.nseg < kFusedCtasPerSm * d.nsm ? d.nseg : kFusedCtasPerSm * d.nsm;
+  const size_t sm = fused_smem_bytes(precision);
+  const int per_sm = g_fast_ctas_per_sm[precision == MT_FP64 ? 0 : precision == MT_MIXED ? 1 : 2];
+  const int g = d.nseg < per_sm * d.nsm ? d.nseg : per_sm * d.nsm;
   if (precision == MT_MIXED)
     k_step1d<MT_MIXED><<<g, Fast::kT, sm, s>>>(d, cond, use_cond);
   else if (precision == MT_MIXED_DF32)

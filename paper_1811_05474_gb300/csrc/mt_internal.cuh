@@ -19,7 +19,8 @@ constexpr long long kSpinLimit = 1LL << 22;  // bounded waits (scan look-back)
 constexpr int kObsChunk = 2048;  // slots per observables chunk (8 per thread)
 constexpr double kTileMinNeighbours = 32.0;  // mean neighbours a side for tiled passes
 constexpr int kFusedCap = 1024;        // particles one fused-step CTA stages
-constexpr int kFusedCtasPerSm = 4;     // resident CTAs per SM of the fused step
+constexpr int kFusedCtasPerSm = 4;     // resident CTAs per SM of the fused step (at most)
+constexpr int kFusedPairCap = 2048;    // unordered pairs one fused-step CTA lists
 
 // Device error codes (Ctrl::err); the first one raised is kept.
 enum : int { kErrNone = 0, kErrIndex = 1, kErrTimeout = 2, kErrInput = 3 };
@@ -416,6 +417,7 @@ cudaError_t launch_pairs(const Dev& d, int search, int* pi, int* pj, long long c
 // Fused 1-d step (mt_fused.cu).
 size_t fused_smem_bytes(int precision);
 cudaError_t fused_configure();  // opt in to the large dynamic shared memory
+int fused_ctas_per_sm(int precision);  // resident first-tier CTAs per SM
 cudaError_t launch_fused_step(const Dev& d, int precision, cudaGraphConditionalHandle cond,
                               int use_cond, cudaStream_t s);
 cudaError_t launch_fused_pred(const Dev& d, int precision, cudaGraphConditionalHandle cond,

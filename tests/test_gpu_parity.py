@@ -454,12 +454,13 @@ def test_fused_segments_many_steps_with_drift_and_walls():
             assert_masses(gb, b, TOL[mt.MT_MIXED], f"B step {s}")
 
 
-@pytest.mark.parametrize("cluster,tiers", [(60, ["fused_step"]), (300, ["fused_step", "fused_big"])])
+@pytest.mark.parametrize("cluster,tiers", [(40, ["fused_step"]), (300, ["fused_step", "fused_big"])])
 def test_fused_dense_bins_sorted_in_place(cluster, tiers):
     """A cluster denser than a cell (particles piled up like at a wall) is
-    sorted in place by the whole CTA; a small one stays in the first tier, a
-    pair-heavy one (O(n^2) work) goes to the second tier, whose exchange is
-    split across several CTAs.  Results match the oracle."""
+    sorted in place by the whole CTA; a small one (40 particles, 780 pairs:
+    within the first tier's pair list) stays in the first tier, a pair-heavy
+    one (O(n^2) work) goes to the second tier, whose exchange is split
+    across several CTAs.  Results match the oracle."""
     n = 5000
     x = synth.uniform_positions(n, 5000.0, seed=23)
     x[0, :cluster] = 2500.0 + synth.uniform_positions(cluster, 1.0, seed=24)[0]
