@@ -244,53 +244,31 @@ __device__ bool pair_transfer(const Dev& d, unsigned char* smem, bool active, in
     sw[q] = W::near(d, sx[k] - sx[j]);
   }
   __syncthreads();
-  // row sums of the slots within Smax of an own particle
-  for (int j = rlo + tid; j < rhi; j += NT) {
-    const int jj = j - olo;
-    T r = T(1);
-    for (int t = 1; jj - t >= 0; ++t) {
-      const int ii = jj - t;
-      if (pfx[ii + 1] - pfx[ii] < t) break;
-      r += sw[pfx[ii] + t - 1];
-    }
-    for (int q = pfx[jj]; q < pfx[jj + 1]; ++q) r += sw[q];
-    sr[j] = mixw(PR) ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
-  }
-  __syncthreads();
-  // symmetric normalisation: each listed pair's P = nu (1/r_j + 1/r_k) / 2
-  // once, in place of nu (pairs with an end outside the row-sum range are
-  // never read)
-  const bool sym = d.norm != MT_NORM_ROW;
-  if (sym) {
-    for (int q = tid; q < np; q += NT) {
-      const int jj = own[q];
-      const int j = olo + jj, k = j + 1 + (q - pfx[jj]);
-      if (j >= rlo && k < rhi) sw[q] = normalised<T>(MT_NORM_SYM, sw[q], sr[j], sr[k]);
-    }
-  }
-  // Own particles ordered by neighbour count (counting sort; the order
-  // within a count does not matter): a warp's lanes then take particles with
-  // equal counts and the exchange loops below do not diverge.  Each
-  // particle's sums are the same whatever lane computes them.
+  // The slots within Smax of an own particle, [rlo, rhi), ordered by their
+  // pair count c = L + R (left and right pairs; counting sort, the order
+  // within a count does not matter): a warp's lanes then take slots with
+  // equal counts and run the same number of iterations of the loops below,
+  // each over the slot's left pairs then its right pairs in one sequence.
+  // Each slot's sums are the same whatever lane forms them.
   constexpr int kCnt = 64;
-  constexpr int PERT = CAP / NT;
   __shared__ int s_hist[kCnt];
   int* perm = reinterpret_cast<int*>(sr + CAP) + TR::kBins + 1;  // the bins' scatter cursors
-  const int nown = active ? w1 - w0 : 0;
+  const int nrs = rhi - rlo;
   for (int b = tid; b < kCnt; b += NT) s_hist[b] = 0;
   __syncthreads();
-  int cj[PERT];
-#pragma unroll
-  for (int e = 0; e < PERT; ++e) {
-    const int j = w0 + tid + e * NT;
-    cj[e] = -1;
-    if (tid + e * NT < nown) {
-      const int jj = j - olo;
-      int c = pfx[jj + 1] - pfx[jj];
-      for (int t = 1; jj - t >= 0 && pfx[jj - t + 1] - pfx[jj - t] >= t; ++t) ++c;
-      cj[e] = c < kCnt ? c : kCnt - 1;
-      atomicAdd(&s_hist[cj[e]], 1);
-    }
+  // (count bin, perm entry) of slot rlo + e: left count in the entry's high bits
+  auto slot_key = [&](int e, int& bin) {
+    const int j = rlo + e, jj = j - olo;
+    int left = 0;
+    while (jj - left - 1 >= 0 && pfx[jj - left] - pfx[jj - left - 1] >= left + 1) ++left;
+    const int c = left + (pfx[jj + 1] - pfx[jj]);
+    bin = c < kCnt ? c : kCnt - 1;
+    return j | (left << 16);
+  };
+  for (int e = tid; e < nrs; e += NT) {
+    int bin;
+    slot_key(e, bin);
+    atomicAdd(&s_hist[bin], 1);
   }
   __syncthreads();
   if (tid < 32) {  // exclusive scan of the 64 counts by one warp
@@ -305,9 +283,48 @@ __device__ bool pair_transfer(const Dev& d, unsigned char* smem, bool active, in
     s_hist[2 * tid + 1] = inc - h1;
   }
   __syncthreads();
-#pragma unroll
-  for (int e = 0; e < PERT; ++e)
-    if (cj[e] >= 0) perm[atomicAdd(&s_hist[cj[e]], 1)] = w0 + tid + e * NT;
+  for (int e = tid; e < nrs; e += NT) {
+    int bin;
+    const int key = slot_key(e, bin);
+    perm[atomicAdd(&s_hist[bin], 1)] = key;
+  }
+  __syncthreads();
+  // Pair u of slot j (u < c): u < L is the left pair (j - u - 1, j), else
+  // the right pair (j, j + 1 + u - L); its list index and its partner slot.
+  auto pair_of = [&](int j, int jj, int left, int u, int& q, int& partner) {
+    if (u < left) {
+      const int t = u + 1;
+      q = pfx[jj - t] + t - 1;
+      partner = j - t;
+    } else {
+      q = pfx[jj] + (u - left);
+      partner = j + 1 + (u - left);
+    }
+  };
+  // row sums: 1 + left pairs' weights + right pairs' weights, in that order
+  for (int p = tid; p < nrs; p += NT) {
+    const int v = perm[p], j = v & 0xffff, left = v >> 16, jj = j - olo;
+    const int c = left + (pfx[jj + 1] - pfx[jj]);
+    T r = T(1);
+    for (int u = 0; u < c; ++u) {
+      int q, partner;
+      pair_of(j, jj, left, u, q, partner);
+      r += sw[q];
+    }
+    sr[j] = mixw(PR) ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
+  }
+  __syncthreads();
+  // symmetric normalisation: each listed pair's P = nu (1/r_j + 1/r_k) / 2
+  // once, in place of nu (pairs with an end outside the row-sum range are
+  // never read)
+  const bool sym = d.norm != MT_NORM_ROW;
+  if (sym) {
+    for (int q = tid; q < np; q += NT) {
+      const int jj = own[q];
+      const int j = olo + jj, k = j + 1 + (q - pfx[jj]);
+      if (j >= rlo && k < rhi) sw[q] = normalised<T>(MT_NORM_SYM, sw[q], sr[j], sr[k]);
+    }
+  }
   __syncthreads();
   if (active) {
     Ctrl* c = d.ctrl;
@@ -316,25 +333,19 @@ __device__ bool pair_transfer(const Dev& d, unsigned char* smem, bool active, in
     int* In = d.id[xc ^ 1];
     unsigned long long* Mn = d.M[mc ^ 1];
     if (out0 + (w1 - w0) > d.n) raise_error(c, kErrIndex, out0);
-    for (int p = tid; p < nown; p += NT) {
-      const int j = perm[p];
-      const int jj = j - olo;
+    for (int p = tid; p < nrs; p += NT) {
+      const int v = perm[p], j = v & 0xffff, left = v >> 16, jj = j - olo;
+      if (j < w0 || j >= w1) continue;  // a neighbour of own particles only
+      const int cnt = left + (pfx[jj + 1] - pfx[jj]);
       const T ip = sr[j];
       MV A = MS::load(sA, j), B = MS::load(sB, j);
       typename MS::Acc dA{}, dB{};
-      for (int t = 1; jj - t >= 0; ++t) {  // left pairs (j - t, j)
-        const int ii = jj - t;
-        if (pfx[ii + 1] - pfx[ii] < t) break;
-        const int i = j - t;
-        const T w = sw[pfx[ii] + t - 1];
-        const T P = sym ? w : normalised<T>(MT_NORM_ROW, w, ip, sr[i]);
+      for (int u = 0; u < cnt; ++u) {
+        int q, i;
+        pair_of(j, jj, left, u, q, i);
+        const T P = sym ? sw[q] : normalised<T>(MT_NORM_ROW, sw[q], ip, sr[i]);
         MS::acc(dA, P, MS::diff(MS::load(sA, i), A));
         MS::acc(dB, P, MS::diff(MS::load(sB, i), B));
-      }
-      for (int q = pfx[jj], k = j + 1; q < pfx[jj + 1]; ++q, ++k) {  // right pairs (j, k)
-        const T P = sym ? sw[q] : normalised<T>(MT_NORM_ROW, sw[q], ip, sr[k]);
-        MS::acc(dA, P, MS::diff(MS::load(sA, k), A));
-        MS::acc(dB, P, MS::diff(MS::load(sB, k), B));
       }
       MS::update(A, B, dA, dB, d.react);
       const long long o = out0 + (j - w0);
