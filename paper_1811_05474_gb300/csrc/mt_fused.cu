@@ -42,6 +42,7 @@
 // realisation's particle can reach).  The CTA that finishes the last segment
 // of a realisation reduces that realisation's observables.
 #include <cooperative_groups.h>
+#include <cuda_pipeline.h>
 
 #include "mt_pair.cuh"
 
@@ -124,6 +125,54 @@ __device__ __forceinline__ SegScalars load_seg(const Dev& d, int sc, long long D
   return s;
 }
 
+// Asynchronous load of the next segment's scalars into shared memory while
+// the current segment is processed (the first tier), so that no global
+// round trip sits between two segments: stage 1 (thread 0, at the segment
+// start) copies c0, c1 and the aligned word holding its prediction flag;
+// stage 2 (thread 0, part-way through the segment) copies the four cell
+// starts that c0 and c1 select.  The words land in w[0 .. 6]: c0, c1, a0,
+// start of cell c1 + Hc + Dc, o0, o1, prediction word.
+struct SegPrefetch {
+  int* w;     // shared words
+  int seg;    // the segment (>= nseg: none)
+  int sc;
+  long long Dc;
+};
+
+__device__ __forceinline__ void prefetch_stage1(const Dev& d, const SegPrefetch& pf) {
+  if (pf.seg >= d.nseg) return;
+  __pipeline_memcpy_async(&pf.w[0], &d.cb[pf.sc][pf.seg], 4);
+  __pipeline_memcpy_async(&pf.w[1], &d.cb[pf.sc][pf.seg + 1], 4);
+  if (d.use_pred)
+    __pipeline_memcpy_async(&pf.w[6], d.pred[pf.sc] + (pf.seg & ~3), 4);  // 4-aligned in the buffer
+  __pipeline_commit();
+}
+
+__device__ __forceinline__ void prefetch_stage2(const Dev& d, const SegPrefetch& pf) {
+  if (pf.seg >= d.nseg) return;
+  __pipeline_wait_prior(0);
+  const int* So = d.fstart[pf.sc];
+  const long long c0 = pf.w[0], c1 = pf.w[1], Hc = d.hc, ncell = d.ncell, Dc = pf.Dc;
+  __pipeline_memcpy_async(&pf.w[2], &So[lmax(c0 - Hc - Dc, 0)], 4);
+  __pipeline_memcpy_async(&pf.w[3], &So[lmin(c1 + Hc + Dc, ncell)], 4);
+  __pipeline_memcpy_async(&pf.w[4], &So[lmax(c0 - Dc, 0)], 4);
+  __pipeline_memcpy_async(&pf.w[5], &So[lmin(c0 + Dc, ncell)], 4);
+  __pipeline_commit();
+}
+
+// The step's control words, read once per kernel launch (they change only
+// when the step ends).
+struct StepState {
+  int xc, mc, sc;             // current X / id, mass and segment buffers
+  unsigned long long step;    // steps completed
+  const float* noise;         // injected normals or null
+};
+
+__device__ __forceinline__ StepState step_state(const Dev& d) {
+  const Ctrl* c = d.ctrl;
+  return {c->xcur, c->mcur, c->scur, c->step, c->noise};
+}
+
 // ------------------------------------------------ first tier: pair list --
 // The first tier's transfer (row sums, exchange, reaction) over a list of
 // the unordered pairs of its staged, sorted particles.  Owners are the
@@ -154,139 +203,156 @@ size_t fused_smem_bytes(int precision) {
                               : pair_region_offset<Fast, float>() + pair_region_bytes<Fast, float>();
 }
 
-// In-place exclusive prefix sum of v[0 .. cnt) (cnt <= NT * 4) into
-// v[0 .. cnt]; all NT threads call it.  Returns the total.
-template <int NT>
-__device__ __forceinline__ int block_scan_u16(unsigned short* v, int cnt, int* s_part) {
-  constexpr int E = 4;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int loc[E];
-  int sum = 0;
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int i = tid * E + e;
-    loc[e] = i < cnt ? v[i] : 0;
-    sum += loc[e];
+// First index q in [0, m) with a[q] >= key (a sorted ascending), by one
+// warp: each round the 32 lanes probe evenly spaced slots and the ballot
+// narrows the range 32-fold (two rounds for m <= 1024).  Called by all 32
+// lanes; every lane gets the result.
+__device__ __forceinline__ int warp_lower_at_least(const long long* a, int m, long long key) {
+  const int lane = threadIdx.x & 31;
+  int lo = 0, hi = m;  // the answer lies in [lo, hi]
+  while (hi - lo > 32) {
+    const int step = (hi - lo + 31) >> 5;
+    const int p = lo + lane * step;
+    const unsigned int below = __ballot_sync(0xffffffffu, p < hi && a[p] < key);
+    const int cnt = __popc(below);  // probes below key form a prefix
+    if (cnt == 0) return lo;
+    const int last = lo + (cnt - 1) * step;
+    hi = min(hi, last + step);
+    lo = last + 1;
   }
-  int inc = sum;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += t;
-  }
-  if (lane == 31) s_part[warp] = inc;
-  __syncthreads();
-  int run = inc - sum;
-  int total = 0;
-  for (int w = 0; w < NT / 32; ++w) {
-    const int t = s_part[w];
-    if (w < warp) run += t;
-    total += t;
-  }
-  __syncthreads();  // every thread has read its inputs and s_part
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int i = tid * E + e;
-    if (i < cnt) v[i] = (unsigned short)run;
-    run += loc[e];
-  }
-  if (tid == 0) v[cnt] = (unsigned short)total;
-  __syncthreads();
-  return total;
+  const int p = lo + lane;
+  return lo + __popc(__ballot_sync(0xffffffffu, p < hi && a[p] < key));
 }
 
 template <int PR, typename TR>
-__device__ bool pair_transfer(const Dev& d, unsigned char* smem, bool active, int m, int w0,
-                              int w1, long long out0, long long xlo, long long xhi) {
+__device__ bool pair_transfer(const Dev& d, const StepState& st, unsigned char* smem, bool active,
+                              int m, int w0, int w1, long long out0, long long xlo, long long xhi) {
   using W = Weight<mixw(PR), 1>;
   using T = typename W::T;
   using MS = Mass<PR>;
   using MV = typename MS::V;
   constexpr int NT = TR::kT, CAP = TR::kCap;
+  constexpr int kCnt = 64;  // pair-count bins of the lane assignment
   long long* sx = reinterpret_cast<long long*>(smem);
   unsigned long long* sA = reinterpret_cast<unsigned long long*>(sx + CAP);
   unsigned long long* sB = sA + CAP;
   int* sid = reinterpret_cast<int*>(sB + CAP);
   T* sr = reinterpret_cast<T*>(sid + CAP);
+  int* perm = reinterpret_cast<int*>(sr + CAP) + TR::kBins + 1;  // the bins' scatter cursors
   T* sw = reinterpret_cast<T*>(smem + pair_region_offset<TR, T>());  // [kPairCap]
   unsigned short* pfx = reinterpret_cast<unsigned short*>(sw + kPairCap);  // [CAP + 1]
   unsigned short* own = pfx + CAP + 1;                                    // [kPairCap]
-  __shared__ int s_olo, s_rlo, s_rhi;
+  __shared__ int s_idx[3];
   __shared__ int s_part[NT / 32];
-  const int tid = threadIdx.x;
+  __shared__ int s_hist[kCnt];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const long long S = d.S;
-  if (active && tid == 0) {
-    s_olo = lower_at_least(sx, m, xlo - 2 * S);
-    s_rlo = lower_at_least(sx, m, xlo - S);
-    s_rhi = lower_at_least(sx, m, xhi + S);
+  // (A) owners [olo, rhi) and row-sum slots [rlo, rhi), one search per warp
+  if (warp < 3) {
+    const long long key = warp == 0 ? xlo - 2 * S : warp == 1 ? xlo - S : xhi + S;
+    const int v = active ? warp_lower_at_least(sx, m, key) : 0;
+    if (lane == 0) s_idx[warp] = v;
+  } else if (warp == 3) {
+    for (int b = lane; b < kCnt; b += 32) s_hist[b] = 0;
   }
   __syncthreads();
-  const int olo = active ? s_olo : 0, rlo = active ? s_rlo : 0, rhi = active ? s_rhi : 0;
-  const int no = rhi - olo;  // owners
-  // right-neighbour counts R_j
-  for (int jj = tid; jj < no; jj += NT) {
-    const int j = olo + jj;
+  const int olo = s_idx[0], rlo = s_idx[1], rhi = s_idx[2];
+  const int no = rhi - olo, nrs = rhi - rlo;
+  // Left and right pair counts of slot j: R_j = slots k > j with
+  // x_k - x_j <= Smax, L_j = slots i < j with x_j - x_i <= Smax.
+  auto right_count = [&](int j) {
     const long long x = sx[j];
     int c = 0;
     for (int k = j + 1; k < m && sx[k] - x <= S; ++k) ++c;
-    pfx[jj] = (unsigned short)c;
+    return c;
+  };
+  auto left_count = [&](int j) {
+    const long long x = sx[j];
+    int c = 0;
+    for (int i = j - 1; i >= 0 && x - sx[i] <= S; --i) ++c;
+    return c;
+  };
+  // (B) R_j of every owner; the count c = L + R of every row-sum slot
+  for (int jj = tid; jj < no; jj += NT) {
+    const int j = olo + jj;
+    const int R = right_count(j);
+    pfx[jj] = (unsigned short)R;
+    if (j >= rlo) {
+      const int c = R + left_count(j);
+      atomicAdd(&s_hist[c < kCnt ? c : kCnt - 1], 1);
+    }
   }
   __syncthreads();
-  const int np = block_scan_u16<NT>(pfx, no, s_part);
+  // (C) exclusive prefix sums: pair offsets pfx[0 .. no] (each thread its
+  // four consecutive owners) and, by warp 0, the count bins
+  int np;
+  {
+    constexpr int E = CAP / NT;
+    int loc[E];
+    int sum = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int i = tid * E + e;
+      loc[e] = i < no ? pfx[i] : 0;
+      sum += loc[e];
+    }
+    int inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) s_part[warp] = inc;
+    __syncthreads();
+    int run = inc - sum;
+    np = 0;
+    for (int w = 0; w < NT / 32; ++w) {
+      const int t = s_part[w];
+      if (w < warp) run += t;
+      np += t;
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int i = tid * E + e;
+      if (i < no) pfx[i] = (unsigned short)run;
+      run += loc[e];
+    }
+    if (tid == 0) pfx[no] = (unsigned short)np;
+    if (warp == 0) {
+      const int h0 = s_hist[2 * lane], h1 = s_hist[2 * lane + 1];
+      int hin = h0 + h1;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, hin, o);
+        if (lane >= o) hin += t;
+      }
+      s_hist[2 * lane] = hin - h0 - h1;
+      s_hist[2 * lane + 1] = hin - h1;
+    }
+    __syncthreads();
+  }
   if (np > kPairCap) return false;  // uniform across the CTA
-  for (int jj = tid; jj < no; jj += NT)
-    for (int q = pfx[jj]; q < pfx[jj + 1]; ++q) own[q] = (unsigned short)jj;
+  // (D) the pair list's owners, and the row-sum slots in order of their
+  // pair count (counting sort; the order within a count does not matter):
+  // a warp's lanes then take slots with equal counts and run the same
+  // number of iterations of the loops below, each over the slot's left
+  // pairs then its right pairs in one sequence.  Each slot's sums are the
+  // same whatever lane forms them.
+  for (int jj = tid; jj < no; jj += NT) {
+    const int q1 = pfx[jj + 1];
+    for (int q = pfx[jj]; q < q1; ++q) own[q] = (unsigned short)jj;
+    const int j = olo + jj;
+    if (j >= rlo) {
+      const int L = left_count(j), c = L + (q1 - pfx[jj]);
+      perm[atomicAdd(&s_hist[c < kCnt ? c : kCnt - 1], 1)] = j | (L << 16);
+    }
+  }
   __syncthreads();
-  // one weight per unordered pair
+  // (E) one weight per unordered pair
   for (int q = tid; q < np; q += NT) {
     const int jj = own[q];
     const int j = olo + jj, k = j + 1 + (q - pfx[jj]);
     sw[q] = W::near(d, sx[k] - sx[j]);
-  }
-  __syncthreads();
-  // The slots within Smax of an own particle, [rlo, rhi), ordered by their
-  // pair count c = L + R (left and right pairs; counting sort, the order
-  // within a count does not matter): a warp's lanes then take slots with
-  // equal counts and run the same number of iterations of the loops below,
-  // each over the slot's left pairs then its right pairs in one sequence.
-  // Each slot's sums are the same whatever lane forms them.
-  constexpr int kCnt = 64;
-  __shared__ int s_hist[kCnt];
-  int* perm = reinterpret_cast<int*>(sr + CAP) + TR::kBins + 1;  // the bins' scatter cursors
-  const int nrs = rhi - rlo;
-  for (int b = tid; b < kCnt; b += NT) s_hist[b] = 0;
-  __syncthreads();
-  // (count bin, perm entry) of slot rlo + e: left count in the entry's high bits
-  auto slot_key = [&](int e, int& bin) {
-    const int j = rlo + e, jj = j - olo;
-    int left = 0;
-    while (jj - left - 1 >= 0 && pfx[jj - left] - pfx[jj - left - 1] >= left + 1) ++left;
-    const int c = left + (pfx[jj + 1] - pfx[jj]);
-    bin = c < kCnt ? c : kCnt - 1;
-    return j | (left << 16);
-  };
-  for (int e = tid; e < nrs; e += NT) {
-    int bin;
-    slot_key(e, bin);
-    atomicAdd(&s_hist[bin], 1);
-  }
-  __syncthreads();
-  if (tid < 32) {  // exclusive scan of the 64 counts by one warp
-    const int h0 = s_hist[2 * tid], h1 = s_hist[2 * tid + 1];
-    int inc = h0 + h1;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, inc, o);
-      if (tid >= o) inc += t;
-    }
-    s_hist[2 * tid] = inc - h0 - h1;
-    s_hist[2 * tid + 1] = inc - h1;
-  }
-  __syncthreads();
-  for (int e = tid; e < nrs; e += NT) {
-    int bin;
-    const int key = slot_key(e, bin);
-    perm[atomicAdd(&s_hist[bin], 1)] = key;
   }
   __syncthreads();
   // Pair u of slot j (u < c): u < L is the left pair (j - u - 1, j), else
@@ -301,7 +367,7 @@ __device__ bool pair_transfer(const Dev& d, unsigned char* smem, bool active, in
       partner = j + 1 + (u - left);
     }
   };
-  // row sums: 1 + left pairs' weights + right pairs' weights, in that order
+  // (F) row sums: 1 + left pairs' weights + right pairs' weights, in that order
   for (int p = tid; p < nrs; p += NT) {
     const int v = perm[p], j = v & 0xffff, left = v >> 16, jj = j - olo;
     const int c = left + (pfx[jj + 1] - pfx[jj]);
@@ -314,25 +380,26 @@ __device__ bool pair_transfer(const Dev& d, unsigned char* smem, bool active, in
     sr[j] = mixw(PR) ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
   }
   __syncthreads();
-  // symmetric normalisation: each listed pair's P = nu (1/r_j + 1/r_k) / 2
-  // once, in place of nu (pairs with an end outside the row-sum range are
-  // never read)
+  // (G) binary64 weights under the symmetric normalisation: each listed
+  // pair's P = nu (1/r_j + 1/r_k) / 2 once, in place of nu (pairs with an
+  // end outside the row-sum range are never read); binary32 weights form P
+  // where they are used (three binary32 operations)
   const bool sym = d.norm != MT_NORM_ROW;
-  if (sym) {
+  constexpr bool kPairP = !mixw(PR);
+  if (kPairP && sym) {
     for (int q = tid; q < np; q += NT) {
       const int jj = own[q];
       const int j = olo + jj, k = j + 1 + (q - pfx[jj]);
       if (j >= rlo && k < rhi) sw[q] = normalised<T>(MT_NORM_SYM, sw[q], sr[j], sr[k]);
     }
+    __syncthreads();
   }
-  __syncthreads();
+  // (H) exchange and reaction of own particles
   if (active) {
-    Ctrl* c = d.ctrl;
-    const int xc = c->xcur, mc = c->mcur;
-    long long* Xn = d.X[xc ^ 1];
-    int* In = d.id[xc ^ 1];
-    unsigned long long* Mn = d.M[mc ^ 1];
-    if (out0 + (w1 - w0) > d.n) raise_error(c, kErrIndex, out0);
+    long long* Xn = d.X[st.xc ^ 1];
+    int* In = d.id[st.xc ^ 1];
+    unsigned long long* Mn = d.M[st.mc ^ 1];
+    if (out0 + (w1 - w0) > d.n) raise_error(d.ctrl, kErrIndex, out0);
     for (int p = tid; p < nrs; p += NT) {
       const int v = perm[p], j = v & 0xffff, left = v >> 16, jj = j - olo;
       if (j < w0 || j >= w1) continue;  // a neighbour of own particles only
@@ -343,7 +410,7 @@ __device__ bool pair_transfer(const Dev& d, unsigned char* smem, bool active, in
       for (int u = 0; u < cnt; ++u) {
         int q, i;
         pair_of(j, jj, left, u, q, i);
-        const T P = sym ? sw[q] : normalised<T>(MT_NORM_ROW, sw[q], ip, sr[i]);
+        const T P = kPairP && sym ? sw[q] : normalised<T>(d.norm, sw[q], ip, sr[i]);
         MS::acc(dA, P, MS::diff(MS::load(sA, i), A));
         MS::acc(dB, P, MS::diff(MS::load(sB, i), B));
       }
@@ -373,9 +440,9 @@ __device__ bool pair_transfer(const Dev& d, unsigned char* smem, bool active, in
 // accumulators (obs_sum, in shared memory).  Returns kSegOk, or why the
 // segment does not fit this tier (then nothing of it has been written).
 template <int PR, typename TR, int CL>
-__device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const SegScalars& g,
-                             int slice, int nslice, bool route_heavy,
-                             bool* heavy_out = nullptr) {
+__device__ int fused_segment(const Dev& d, const StepState& st, int seg, unsigned char* smem,
+                             const SegScalars& g, int slice, int nslice, bool route_heavy,
+                             bool* heavy_out = nullptr, const SegPrefetch* pf = nullptr) {
   using W = Weight<mixw(PR), 1>;
   using T = typename W::T;
   using MS = Mass<PR>;
@@ -394,7 +461,7 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
 
   Ctrl* c = d.ctrl;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int xc = c->xcur, mc = c->mcur, sc = c->scur;
+  const int xc = st.xc, mc = st.mc, sc = st.sc;
   const long long* Xo = d.X[xc];
   const int* Io = d.id[xc];
   const unsigned long long* Mo = d.M[mc];
@@ -436,8 +503,8 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
   long long rx[PER];
   int rbin[PER];
   if (active) {
-    const unsigned long long step = c->step;
-    const float* noise = c->noise;
+    const unsigned long long step = st.step;
+    const float* noise = st.noise;
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const long long e = tid + (long long)k * NT;
@@ -481,6 +548,7 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
       }
     }
   }
+  if (pf && tid == 0) prefetch_stage2(d, *pf);  // the next segment's cell starts
   __syncthreads();
 
   // ---- 3: counting sort into bins, then (x, id) order inside each bin -----
@@ -733,7 +801,7 @@ __device__ int fused_segment(const Dev& d, int seg, unsigned char* smem, const S
   const long long out0 = o0 + s_lt;
   const long long S = d.S;
   if constexpr (CL == 1) {
-    if (!pair_transfer<PR, TR>(d, smem, active, m, w0, w1, out0, xlo, xhi)) {
+    if (!pair_transfer<PR, TR>(d, st, smem, active, m, w0, w1, out0, xlo, xhi)) {
       status = kSegHeavy;  // more pairs than the list holds: the second tier takes it
       active = false;
     }
@@ -999,37 +1067,60 @@ __global__ void __launch_bounds__(Fast::kT, kFusedCtasPerSm) k_step1d(Dev d, cud
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ bool s_last;
   Ctrl* c = d.ctrl;
-  const int sc = c->scur;
+  const StepState st = step_state(d);
+  const int sc = st.sc;
   const long long Dc = (c->dmax >> d.cshift) + 2;
   const unsigned char* pcur = d.pred[sc];
   unsigned char* pnext = d.pred[sc ^ 1];
-  // Segments: the first wave by CTA index, then one ticket at a time (drawn
-  // while the current one is processed, so its scalars load meanwhile).
-  // Segments predicted pair-heavy belong to the predicted-segment kernel.
-  // (two ticket words: a skipped segment has no barrier of its own before
-  // the next ticket is written)
+  // Segments: the first wave by CTA index, then tickets.  Two segments
+  // ahead: while segment `seg` is processed, the next one's scalars and
+  // prediction flag load and the ticket after it is drawn, so no global
+  // round trip sits between two segments.  Segments predicted pair-heavy
+  // belong to the predicted-segment kernel.  (two ticket words: a skipped
+  // segment has no barrier of its own before the next ticket is written)
   __shared__ int s_ticket[2];
+  __shared__ int s_pre[2][8];
+  if (threadIdx.x == 0) s_ticket[1] = (int)gridDim.x + atomicAdd(&c->seg_ctr, 1);
+  __syncthreads();
   int par = 0;
-  int seg = blockIdx.x;
+  int seg = blockIdx.x, s1 = s_ticket[1];
   SegScalars cur = {};
-  if (seg < d.nseg) cur = load_seg(d, sc, Dc, seg);
+  unsigned char pc = 0;
+  if (seg < d.nseg) {
+    cur = load_seg(d, sc, Dc, seg);
+    pc = d.use_pred ? pcur[seg] : 0;
+  }
   while (seg < d.nseg) {
-    if (threadIdx.x == 0) s_ticket[par] = (int)gridDim.x + atomicAdd(&c->seg_ctr, 1);
-    __syncthreads();
-    const int next = s_ticket[par];
-    par ^= 1;
-    SegScalars nxt = {};
-    if (next < d.nseg) nxt = load_seg(d, sc, Dc, next);
-    if (!d.use_pred || !pcur[seg]) {
-      const int st = fused_segment<PR, Fast, 1>(d, seg, smem, cur, 0, 1, true);
-      if (st != kSegOk && threadIdx.x == 0) d.ovlist[atomicAdd(&c->nov, 1)] = seg;
-      if (threadIdx.x == 0) {
-        pnext[seg] = st == kSegOk ? 0 : 1;
-        if (st != kSegOk) atomicAdd(&c->npred_next, 1);
-      }
+    const SegPrefetch pf{s_pre[par], s1, sc, Dc};
+    int tk = d.nseg;
+    if (threadIdx.x == 0) {
+      if (s1 < d.nseg) tk = (int)gridDim.x + atomicAdd(&c->seg_ctr, 1);
+      prefetch_stage1(d, pf);
     }
-    cur = nxt;
-    seg = next;
+    if (!pc) {
+      const int rc = fused_segment<PR, Fast, 1>(d, st, seg, smem, cur, 0, 1, true, nullptr, &pf);
+      if (rc != kSegOk && threadIdx.x == 0) d.ovlist[atomicAdd(&c->nov, 1)] = seg;
+      if (threadIdx.x == 0) {
+        pnext[seg] = rc == kSegOk ? 0 : 1;
+        if (rc != kSegOk) atomicAdd(&c->npred_next, 1);
+      }
+    } else if (threadIdx.x == 0) {
+      prefetch_stage2(d, pf);
+    }
+    if (threadIdx.x == 0) {
+      __pipeline_wait_prior(0);
+      s_ticket[par] = tk;
+    }
+    __syncthreads();
+    const int s2 = s_ticket[par];
+    if (s1 < d.nseg) {
+      const int* w = s_pre[par];
+      cur = {w[0], w[1], w[2], w[3] - w[2], w[4], w[5]};
+      pc = d.use_pred ? (unsigned char)((unsigned int)w[6] >> (8 * (s1 & 3))) : 0;
+    }
+    par ^= 1;
+    seg = s1;
+    s1 = s2;
   }
   if (threadIdx.x == 0) {
     __threadfence();
@@ -1059,7 +1150,8 @@ __global__ void __launch_bounds__(Big::kT, 1)
   __shared__ int s_list[Big::kT];
   __shared__ int s_nlist;
   Ctrl* c = d.ctrl;
-  const int sc = c->scur;
+  const StepState st = step_state(d);
+  const int sc = st.sc;
   const long long Dc = (c->dmax >> d.cshift) + 2;
   const int rank = blockIdx.x % CL;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1088,10 +1180,10 @@ __global__ void __launch_bounds__(Big::kT, 1)
       for (int k = 0; k < nl; ++k) {
         const int seg = s_list[k];
         bool heavy = true;
-        const int st = fused_segment<PR, Big, CL>(d, seg, smem, load_seg(d, sc, Dc, seg), rank,
-                                                   CL, false, &heavy);
-        if (st != kSegOk && tid == 0 && atomicExch(&c->overflow, 1) == 0) {
-          c->ov_reason = st;
+        const int rc = fused_segment<PR, Big, CL>(d, st, seg, smem, load_seg(d, sc, Dc, seg),
+                                                   rank, CL, false, &heavy);
+        if (rc != kSegOk && tid == 0 && atomicExch(&c->overflow, 1) == 0) {
+          c->ov_reason = rc;
           c->ov_seg = seg;
         }
         if (tid == 0 && rank == 0) {
@@ -1127,16 +1219,17 @@ __global__ void __launch_bounds__(Big::kT, 1)
   __shared__ bool s_last;
   Ctrl* c = d.ctrl;
   const int nov = c->nov;
-  const int sc = c->scur;
+  const StepState st = step_state(d);
+  const int sc = st.sc;
   const long long Dc = (c->dmax >> d.cshift) + 2;
   const int rank = blockIdx.x % CL, cid = blockIdx.x / CL;
   const int ncl = gridDim.x / CL;
   for (int q = cid; q < nov; q += ncl) {
     const int seg = d.ovlist[q];
-    const int st =
-        fused_segment<PR, Big, CL>(d, seg, smem, load_seg(d, sc, Dc, seg), rank, CL, false);
-    if (st != kSegOk && threadIdx.x == 0 && atomicExch(&c->overflow, 1) == 0) {
-      c->ov_reason = st;
+    const int rc =
+        fused_segment<PR, Big, CL>(d, st, seg, smem, load_seg(d, sc, Dc, seg), rank, CL, false);
+    if (rc != kSegOk && threadIdx.x == 0 && atomicExch(&c->overflow, 1) == 0) {
+      c->ov_reason = rc;
       c->ov_seg = seg;
     }
   }
