@@ -405,6 +405,19 @@ mt_status mt_philox(mt_handle* h, uint32_t c0, uint32_t c1, uint32_t c2,
  * or spin_limit < 0.  Waits for the stream. */
 mt_status mt_test_hold_scan(mt_handle* h, int32_t hold, int64_t spin_limit);
 
+/* The built-in random walk's standard normals (Eq. 2's xi) for particles
+ * given by their index gid in a system (its caller order), at step `step`:
+ * the values a single handle with p's seed and realisation draws for those
+ * particles at that step (Philox4x32-10 keyed by the seed, counter (gid,
+ * step, realisation); Box-Muller).  gid: device array of n indices (< 2^32);
+ * out: device array of dim*n floats, axis-major, in the order of gid.  For
+ * the domain decomposition (Sec. 2.2, Sec. 6): a slab's particles take the
+ * same walk as in the undivided system (pass them to mt_set_noise).
+ * Enqueued on stream (NULL: the default stream).  Errors: MT_ERR_INVALID
+ * (dim, n < 0, NULL arrays). */
+mt_status mt_walk_normals(const mt_params* p, const int64_t* gid, int64_t n, uint64_t step,
+                          float* out, void* stream);
+
 /* Per-kernel timing: with on = 1 every following step records a CUDA event
  * on the handle's stream before each of its kernels and one after the last
  * (graph replays included; turning it on or off drops a captured graph).

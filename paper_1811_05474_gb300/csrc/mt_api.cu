@@ -1065,6 +1065,18 @@ mt_status mt_philox(mt_handle* h, uint32_t c0, uint32_t c1, uint32_t c2, uint32_
   return MT_OK;
 }
 
+mt_status mt_walk_normals(const mt_params* p, const int64_t* gid, int64_t n, uint64_t step,
+                          float* out, void* stream) {
+  if (!p) return fail(MT_ERR_INVALID, "params is NULL");
+  if (p->dim != 1 && p->dim != 2) return fail(MT_ERR_INVALID, "dim must be 1 or 2");
+  if (n < 0 || (n > 0 && (!gid || !out))) return fail(MT_ERR_INVALID, "bad arrays");
+  CU(launch_walk_normals(reinterpret_cast<const long long*>(gid), n, step,
+                         (unsigned int)p->realisation, (unsigned int)(p->seed & 0xffffffffu),
+                         (unsigned int)(p->seed >> 32), p->dim, out,
+                         static_cast<cudaStream_t>(stream)));
+  return MT_OK;
+}
+
 mt_status mt_set_profiling(mt_handle* h, int32_t on) {
   if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
   const bool want = on != 0;

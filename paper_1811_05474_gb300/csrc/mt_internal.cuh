@@ -430,5 +430,8 @@ cudaError_t launch_noise_bound(const Dev& d, const float* xi, cudaStream_t s);
 
 cudaError_t launch_philox(uint4 c, unsigned int k0, unsigned int k1, long long n,
                           unsigned int* out, cudaStream_t s);
+cudaError_t launch_walk_normals(const long long* gid, long long n, unsigned long long step,
+                                unsigned int real, unsigned int k0, unsigned int k1, int dim,
+                                float* out, cudaStream_t s);
 
 }  // namespace mt

@@ -385,6 +385,30 @@ cudaError_t launch_permute(const Dev& d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The built-in random walk's normals of particles given by their indices in
+// a system (the counter a single handle uses for caller index gid): one per
+// axis, axis-major.
+__global__ void k_walk_normals(const long long* gid, long long n, unsigned long long step,
+                               unsigned int real, unsigned int k0, unsigned int k1, int dim,
+                               float* out) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const long long id = gid[p];
+  const uint4 u = philox4x32_10(
+      make_uint4((unsigned int)id, (unsigned int)step, (unsigned int)(step >> 32), real), k0, k1);
+  const float2 g = box_muller(u.x, u.y);
+  out[p] = g.x;
+  if (dim == 2) out[n + p] = g.y;
+}
+
+cudaError_t launch_walk_normals(const long long* gid, long long n, unsigned long long step,
+                                unsigned int real, unsigned int k0, unsigned int k1, int dim,
+                                float* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_walk_normals<<<blocks_for(n, 256), 256, 0, s>>>(gid, n, step, real, k0, k1, dim, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_philox(uint4 c, unsigned int k0, unsigned int k1, long long n,
                           unsigned int* out, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;

@@ -159,6 +159,7 @@ def lib(path: Path | None = None):
         "mt_philox": [H, u32, u32, u32, u32, u32, u32, i64, _vp],
         "mt_set_profiling": [H, i32],
         "mt_test_hold_scan": [H, i32, i64],
+        "mt_walk_normals": [P, _vp, i64, ctypes.c_uint64, _vp, _vp],
         "mt_probe_rate": [i32, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(ctypes.c_double)],
         "mt_transfer_1d_noalloc": [_vp, _vp, _vp, _vp, _vp, i64, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, i32, i32,
@@ -391,6 +392,11 @@ def mt_read_profile(h):
 
 def mt_profile_name(h, idx: int) -> str:
     return lib().mt_profile_name(h, idx).decode()
+
+
+def mt_walk_normals(p: mt_params, gid_ptr, n: int, step: int, out_ptr, stream_ptr=None) -> None:
+    """Built-in walk normals of particles gid at a step (see include/mt.h)."""
+    check(lib().mt_walk_normals(ctypes.byref(p), gid_ptr, n, step, out_ptr, stream_ptr))
 
 
 PROBE_DFMA, PROBE_FFMA, PROBE_EXPF, PROBE_EXP = 0, 1, 2, 3
