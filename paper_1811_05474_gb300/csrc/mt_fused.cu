@@ -64,6 +64,7 @@ struct Tier {
 using Fast = Tier<256, 4>;
 using Big = Tier<512, 8>;
 static_assert(Fast::kCap == kFusedCap, "staging capacity");
+static_assert(Fast::kCap <= kFusedPairCap, "left counts share the pair list's weights");
 
 template <typename TR>
 size_t tier_smem(int precision) {
@@ -272,13 +273,16 @@ __device__ bool pair_transfer(const Dev& d, const StepState& st, unsigned char* 
     for (int i = j - 1; i >= 0 && x - sx[i] <= S; --i) ++c;
     return c;
   };
-  // (B) R_j of every owner; the count c = L + R of every row-sum slot
+  // (B) R_j of every owner; L_j and the count c = L + R of every row-sum
+  // slot (L_j kept in the weights' array, free until (E))
+  int* lcount = reinterpret_cast<int*>(sw);  // [no] (no <= CAP <= kPairCap words)
   for (int jj = tid; jj < no; jj += NT) {
     const int j = olo + jj;
     const int R = right_count(j);
     pfx[jj] = (unsigned short)R;
     if (j >= rlo) {
-      const int c = R + left_count(j);
+      const int Lc = left_count(j), c = R + Lc;
+      lcount[jj] = Lc;
       atomicAdd(&s_hist[c < kCnt ? c : kCnt - 1], 1);
     }
   }
@@ -343,7 +347,7 @@ __device__ bool pair_transfer(const Dev& d, const StepState& st, unsigned char* 
     for (int q = pfx[jj]; q < q1; ++q) own[q] = (unsigned short)jj;
     const int j = olo + jj;
     if (j >= rlo) {
-      const int L = left_count(j), c = L + (q1 - pfx[jj]);
+      const int L = lcount[jj], c = L + (q1 - pfx[jj]);
       perm[atomicAdd(&s_hist[c < kCnt ? c : kCnt - 1], 1)] = j | (L << 16);
     }
   }
