@@ -260,23 +260,25 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
     // right neighbours per particle (mean density x Smax): the first tier
     // lists the pairs of owners within about T + 3 Smax of density
     const double rn = (double)D.S * (double)p.n / lq_sum;
-    long long T = 1024;
-    while (T >= 64 && ((double)T + 2.0 * (double)(D.hc + dc + 1) * per_cell * 1.5 + 64.0 >
-                           (double)kFusedCap ||
-                       ((double)T + 3.0 * rn) * rn * 1.5 + 64.0 > (double)kFusedPairCap))
-      T /= 2;
+    // As many particles per segment as the staging and the pair list hold
+    // with 50 % headroom, at most kSegMax: larger segments spread the
+    // segment's fixed cost (barriers, bins, halo) over more particles, and
+    // the tickets balance the CTAs (measured at N = 10^6: 412 particles per
+    // segment 184 us per step, 600-700 about 167 us, MIXED).
+    constexpr double kSegMax = 640.0;
+    const double t_stage = (double)kFusedCap - 64.0 - 2.0 * (double)(D.hc + dc + 1) * per_cell * 1.5;
+    const double t_pairs = rn > 0.0 ? ((double)kFusedPairCap - 64.0) / (1.5 * rn) - 3.0 * rn : 1e9;
+    long long T = (long long)std::floor(std::min(std::min(t_stage, t_pairs), kSegMax));
     if (p.seg_target != 0) {
       if (p.seg_target < 16 || p.seg_target > kFusedCap)
         return fail(MT_ERR_INVALID, "seg_target must be 0 or in [16, %d]", kFusedCap);
       T = p.seg_target;
     } else if (T >= 64) {
-      // whole waves: the step's persistent CTAs (the resident first-tier
-      // CTAs per SM of the current device) each take the same number of
-      // segments
+      // a system smaller than one wave of such segments: one segment per
+      // resident first-tier CTA of the current device, so all SMs work
       const long long slots = (long long)fused_ctas_per_sm(p.precision) * device_sms();
-      if (slots > 0) {
-        const long long waves = (p.n + T * slots - 1) / (T * slots);
-        T = (p.n + waves * slots - 1) / (waves * slots);
+      if (slots > 0 && p.n < T * slots) {
+        T = (p.n + slots - 1) / slots;
         if (T < 64) T = 64;
       }
     }
