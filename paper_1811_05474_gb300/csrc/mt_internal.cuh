@@ -16,7 +16,7 @@ constexpr int kSmallCell = 32;         // cells up to this size sort in one thre
 constexpr int kBigSortCap = 2048;      // cells up to this size sort in shared memory
 constexpr int kBruteTile = 256;        // j-particles staged per tile, brute force
 constexpr long long kSpinLimit = 1LL << 22;  // bounded waits (scan look-back)
-constexpr int kObsChunk = 2048;  // slots per observables chunk (8 per thread)
+constexpr int kObsChunk = 4096;  // slots per observables chunk (16 per thread)
 constexpr double kTileMinNeighbours = 32.0;  // mean neighbours a side for tiled passes
 constexpr int kFusedCap = 1024;        // particles one fused-step CTA stages
 constexpr int kFusedCtasPerSm = 4;     // resident CTAs per SM of the fused step (at most)
