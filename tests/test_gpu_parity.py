@@ -152,6 +152,24 @@ def test_large_cells(cluster):
     run_both(sim, x, A, B, 2, pairs=(cluster < 1000))
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_segments_beyond_the_pair_list(precision):
+    """Segments of 900 particles at density 1.25 stage about 920 particles
+    (within the staging) but list about 2150 pairs, beyond the first tier's
+    pair list (2048): they go to the cluster tier; every step still equals
+    the oracle, and the pair set is exact."""
+    n, L = 75000, 60000.0
+    x = synth.uniform_positions(n, L, seed=13)
+    A, B = synth.uniform_masses(n, seed=13)
+    p = mt.mt_params_init(n=n, L=(L,), v=(0.3,), precision=precision, seg_target=900, seed=1)
+    sim = mt.Simulation(p)
+    run_both(sim, x, A, B, 3, seed=13)
+    mt.mt_set_profiling(sim.h, True)
+    sim.step()
+    names = [k for k, _ in mt.mt_read_profile(sim.h)]
+    assert "fused_step" in names and "move" not in names
+
+
 # ------------------------------------------------------------------ 2-d --
 
 @pytest.mark.parametrize("search", [mt.MT_SEARCH_CELL, mt.MT_SEARCH_BRUTE, mt.MT_SEARCH_FULL])
@@ -286,9 +304,12 @@ def test_builtin_noise_statistics(dim):
 # ------------------------------------------------------- full-size checks --
 
 @pytest.mark.parametrize("precision", [mt.MT_MIXED, mt.MT_FP64])
-def test_full_size_step_after_graph_run(precision):
+@pytest.mark.parametrize("before", [20, 1000])
+def test_full_size_step_after_graph_run(precision, before):
     """N = 1e6 on [0, 1e6], v = 0.5, in the benchmark's launch configuration
-    (CUDA graph, built-in generator) for 20 steps; then one injected-noise
+    (CUDA graph, built-in generator) for 20 or 1000 steps (by then the drift
+    has piled ~500 particles against the wall at x = L, a pair-heavy layer
+    the cluster kernel takes beside the first tier); then one injected-noise
     step from the read-back state, compared with the oracle element by
     element (sorted-window search)."""
     n, L = 10 ** 6, 1e6
@@ -296,7 +317,7 @@ def test_full_size_step_after_graph_run(precision):
     x = synth.uniform_positions(n, L, seed=2)
     A, B = synth.uniform_masses(n, seed=2)
     sim.upload(x, A, B)
-    sim.run(20)
+    sim.run(before)
     X0 = sim.ticks()
     a0, b0 = sim.masses()
     assert X0.min() >= 0 and X0.max() <= int(L * 2 ** int(sim.params.frac_bits))
