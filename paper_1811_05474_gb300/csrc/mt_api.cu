@@ -400,6 +400,14 @@ struct mt_handle {
   // the first tier (fork / join events around it in the captured graph)
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
+  // fused path with observables, first tier bound by the binary64 pipe
+  // (MT_FP64, MT_MIXED): the previous step's observables run on a third
+  // stream beside the step in the graph, in the pipe's idle issue slots;
+  // the last step's are pending until a call that reads them (flush_obs).
+  // With MT_MIXED_DF32 they follow the step in its graph.
+  cudaStream_t side2 = nullptr;
+  cudaEvent_t join2 = nullptr;
+  bool obs_pending = false;
   bool uploaded = false;
   long long steps = 0;     // host mirror of the step counter
   const float* noise = nullptr;
@@ -435,6 +443,16 @@ mt_status check_device(mt_handle* h) {
   return MT_OK;
 }
 
+// The observables of the last graph step on the fused path, which the next
+// step's graph would have computed beside itself: enqueue them now (a call
+// is about to read the ring, the state, or to leave the graph).
+mt_status flush_obs(mt_handle* h) {
+  if (!h->obs_pending) return MT_OK;
+  h->obs_pending = false;
+  CU(launch_obs(h->dev, h->D.p.precision, h->stream));
+  return MT_OK;
+}
+
 // The general pipeline: move + histogram, scan, scatter, cell sort, two
 // transfer passes; on the 1-d cell path it also refreshes the fused path's
 // cell starts and segment boundaries.
@@ -462,6 +480,10 @@ mt_status enqueue_general(mt_handle* h, const Dev& d, Marker& mk) {
 mt_status enqueue_step(mt_handle* h, const Dev& d) {
   const mt_params& p = h->D.p;
   if (p.n == 0) return MT_OK;
+  {
+    const mt_status s = flush_obs(h);
+    if (s != MT_OK) return s;
+  }
   Marker mk;
   if (h->profile) {
     mk.ev = h->ev;
@@ -526,44 +548,64 @@ mt_status build_graph(mt_handle* h) {
   mt_status s = MT_OK;
   Marker none;
   if (h->D.fused) {
-    // g: [fast tier] -> IF(queued) { [second tier] -> IF(overflow) { general } }
+    // g: [snapshot] -> { [previous step's observables] | [predicted segments]
+    //   | [fast tier] } -> IF(queued) { [second tier] -> IF(overflow) { general } }
     cudaGraphConditionalHandle cond1, cond2;
     CU(cudaGraphConditionalHandleCreate(&cond1, g, 0, 0));
     // large systems fork: the predicted-segment kernel on the side stream,
-    // the first tier on the handle's stream; join before the conditional
+    // the first tier on the handle's stream; with observables, the previous
+    // step's on a third stream (they read the mass buffer the step only
+    // reads); all join before the conditional
     const bool fork = d.use_pred != 0;
+    const bool obs = h->side2 != nullptr;
     CU(cudaStreamBeginCaptureToGraph(h->stream, g, nullptr, nullptr, 0, mode));
     cudaError_t e1 = cudaSuccess;
+    if (obs) e1 = launch_obs_snapshot(d, h->stream);
+    if ((fork || obs) && e1 == cudaSuccess) e1 = cudaEventRecord(h->fork, h->stream);
     if (fork) {
-      e1 = cudaEventRecord(h->fork, h->stream);
       if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(h->side, h->fork, 0);
       if (e1 == cudaSuccess) e1 = launch_fused_pred(d, h->D.p.precision, cond1, 1, h->side);
+    }
+    if (obs) {
+      if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(h->side2, h->fork, 0);
+      if (e1 == cudaSuccess) e1 = launch_obs_prev(d, h->D.p.precision, h->side2);
     }
     if (e1 == cudaSuccess) e1 = launch_fused_step(d, h->D.p.precision, cond1, 1, h->stream);
     if (fork && e1 == cudaSuccess) e1 = cudaEventRecord(h->join, h->side);
     if (fork && e1 == cudaSuccess) e1 = cudaStreamWaitEvent(h->stream, h->join, 0);
+    if (obs && e1 == cudaSuccess) e1 = cudaEventRecord(h->join2, h->side2);
+    if (obs && e1 == cudaSuccess) e1 = cudaStreamWaitEvent(h->stream, h->join2, 0);
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
       cudaGraphDestroy(g);
       return fail(MT_ERR_CUDA, "graph capture of the fused step failed");
     }
     cudaGraph_t body1 = nullptr;
-    cudaGraphNode_t cnode = nullptr;  // the IF node; the observables follow it
+    cudaGraphNode_t cnode = nullptr;  // the IF node
     {
-      const size_t want = fork ? 2 : 1;
-      cudaGraphNode_t knodes[2] = {nullptr, nullptr};
-      size_t nn = 2;
+      // the IF node follows every kernel node without a dependent (the
+      // snapshot precedes the others)
+      const size_t want = 1 + (fork ? 1 : 0) + (obs ? 2 : 0);
+      cudaGraphNode_t knodes[4] = {nullptr, nullptr, nullptr, nullptr};
+      size_t nn = 4;
       CU(cudaGraphGetNodes(g, knodes, &nn));
       if (nn != want) {
         cudaGraphDestroy(g);
         return fail(MT_ERR_CUDA, "fused step graph: expected %zu kernel nodes, got %zu", want, nn);
+      }
+      cudaGraphNode_t leaves[4];
+      size_t nleaf = 0;
+      for (size_t i = 0; i < nn; ++i) {
+        size_t ndep = 0;
+        CU(cudaGraphNodeGetDependentNodes(knodes[i], nullptr, nullptr, &ndep));
+        if (ndep == 0) leaves[nleaf++] = knodes[i];
       }
       cudaGraphNodeParams cp = {};
       cp.type = cudaGraphNodeTypeConditional;
       cp.conditional.handle = cond1;
       cp.conditional.type = cudaGraphCondTypeIf;
       cp.conditional.size = 1;
-      CU(cudaGraphAddNode(&cnode, g, knodes, nullptr, want, &cp));
+      CU(cudaGraphAddNode(&cnode, g, leaves, nullptr, nleaf, &cp));
       body1 = cp.conditional.phGraph_out[0];
     }
     CU(cudaGraphConditionalHandleCreate(&cond2, body1, 0, 0));
@@ -592,7 +634,9 @@ mt_status build_graph(mt_handle* h) {
     s = enqueue_general(h, d, none);
     const cudaError_t e3 = cudaStreamEndCapture(h->stream, &body2);
     if (s == MT_OK && e3 != cudaSuccess) s = fail(MT_ERR_CUDA, "graph capture of the fallback failed");
-    if (s == MT_OK && h->D.p.observe_cap > 0) {
+    // the step's own observables: the next step's graph (or flush_obs)
+    // where they are deferred, else after the IF node
+    if (s == MT_OK && !obs && h->D.p.observe_cap > 0) {
       CU(cudaStreamBeginCaptureToGraph(h->stream, g, &cnode, nullptr, 1, mode));
       const cudaError_t e4 = launch_obs(d, h->D.p.precision, h->stream);
       const cudaError_t e5 = cudaStreamEndCapture(h->stream, &g);
@@ -780,9 +824,15 @@ mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace
   cudaError_t e = D.fused ? fused_configure() : cudaSuccess;
   if (e == cudaSuccess && d.use_pred) {
     e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming);
   }
+  if (e == cudaSuccess && D.fused && D.p.observe_cap > 0 && d.nochunk > 0 &&
+      D.p.precision != MT_MIXED_DF32) {
+    e = cudaStreamCreateWithFlags(&h->side2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join2, cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess && (h->side || h->side2))
+    e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->ws, 0, D.total, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(w + D.o_rt, hd.rt.data(), hd.rt.size() * sizeof(Real),
@@ -802,8 +852,10 @@ mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     if (h->side) cudaStreamDestroy(h->side);
+    if (h->side2) cudaStreamDestroy(h->side2);
     if (h->fork) cudaEventDestroy(h->fork);
     if (h->join) cudaEventDestroy(h->join);
+    if (h->join2) cudaEventDestroy(h->join2);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
     return fail(MT_ERR_CUDA, "handle setup: %s", cudaGetErrorString(e));
@@ -827,6 +879,7 @@ mt_status mt_upload(mt_handle* h, const double* x, const double* A, const double
   if (h->D.ntiles > 0) CU(cudaMemsetAsync(h->ws + h->D.o_status, 0, h->D.ntiles * 8, h->stream));
   h->steps = 0;
   h->uploaded = true;
+  h->obs_pending = false;
   if (n == 0) return MT_OK;
   const Dev& d = h->dev;
   // the control block was cleared: restore the noise source and its bound
@@ -896,6 +949,7 @@ mt_status mt_run(mt_handle* h, int64_t nsteps) {
     CU(cudaGraphLaunch(h->graph, h->stream));
     ++h->steps;
   }
+  if (nsteps > 0 && h->side2) h->obs_pending = true;
   return MT_OK;
 }
 
@@ -907,6 +961,8 @@ mt_status mt_step(mt_handle* h) {
 
 mt_status mt_sync(mt_handle* h) {
   if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
+  const mt_status s = flush_obs(h);
+  if (s != MT_OK) return s;
   return check_device(h);
 }
 
@@ -999,6 +1055,10 @@ mt_status mt_read_ticks(mt_handle* h, int64_t* X, int32_t mem) {
 
 mt_status mt_read_observables(mt_handle* h, double* out, int64_t cap, int64_t* count) {
   if (!h || !count) return fail(MT_ERR_INVALID, "handle or count is NULL");
+  {
+    const mt_status fs = flush_obs(h);
+    if (fs != MT_OK) return fs;
+  }
   const long long ocap = h->D.p.observe_cap;
   long long have = h->steps < ocap ? h->steps : ocap;
   if (cap < have) have = cap < 0 ? 0 : cap;
@@ -1023,6 +1083,10 @@ mt_status mt_read_observables(mt_handle* h, double* out, int64_t cap, int64_t* c
 
 mt_status mt_copy_observables_async(mt_handle* h, double* out, int64_t rows) {
   if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
+  {
+    const mt_status fs = flush_obs(h);
+    if (fs != MT_OK) return fs;
+  }
   const long long ocap = h->D.p.observe_cap;
   const long long have = h->steps < ocap ? h->steps : ocap;
   if (rows < 1 || rows > have)
@@ -1165,10 +1229,15 @@ mt_status read_header(FILE* f, CkptHeader* hd) {
 
 mt_status mt_save(mt_handle* h, const char* path) {
   if (!h || !path) return fail(MT_ERR_INVALID, "mt_save: NULL argument");
+  {
+    const mt_status fs = flush_obs(h);
+    if (fs != MT_OK) return fs;
+  }
   if (!h->uploaded) return fail(MT_ERR_STATE, "mt_save before mt_upload");
   mt_status s = check_device(h);  // waits for the stream
   if (s != MT_OK) return s;
   if (h->side) CU(cudaStreamSynchronize(h->side));
+  if (h->side2) CU(cudaStreamSynchronize(h->side2));
   std::vector<char> ws(h->D.total);
   if (!ws.empty()) CU(cudaMemcpy(ws.data(), h->ws, ws.size(), cudaMemcpyDeviceToHost));
   CkptHeader hd;
@@ -1227,8 +1296,10 @@ mt_status mt_load(mt_handle* h, const char* path) {
   if (s != MT_OK) return s;
   CU(cudaStreamSynchronize(h->stream));
   if (h->side) CU(cudaStreamSynchronize(h->side));
+  if (h->side2) CU(cudaStreamSynchronize(h->side2));
   if (!ws.empty()) CU(cudaMemcpy(h->ws, ws.data(), ws.size(), cudaMemcpyHostToDevice));
   h->steps = hd.steps;
+  h->obs_pending = false;  // the saved state's rows were written before it was saved
   h->uploaded = true;
   // the saved noise pointer belongs to the saving process: use this handle's
   CU(cudaMemcpyAsync(&h->dev.ctrl->noise, &h->noise, sizeof(h->noise), cudaMemcpyHostToDevice,
@@ -1249,8 +1320,13 @@ void mt_destroy(mt_handle* h) {
     cudaStreamSynchronize(h->side);
     cudaStreamDestroy(h->side);
   }
+  if (h->side2) {
+    cudaStreamSynchronize(h->side2);
+    cudaStreamDestroy(h->side2);
+  }
   if (h->fork) cudaEventDestroy(h->fork);
   if (h->join) cudaEventDestroy(h->join);
+  if (h->join2) cudaEventDestroy(h->join2);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
 }

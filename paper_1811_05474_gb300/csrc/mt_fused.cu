@@ -1343,6 +1343,11 @@ static int g_big_cluster = 8;
 // Highest launch priority of the device (the predicted-segment kernel's
 // CTAs should take their SMs before the first tier fills them).
 static int g_top_priority = 0;
+// The first tier's launch priority: just below the predicted-segment kernel,
+// above the default (lowest) priority of the work that runs beside the step
+// (the previous step's observables), whose CTAs then fill the SMs the first
+// tier leaves at its tail instead of taking them at its start.
+static int g_fast_priority = 0;
 
 template <int PR, int CL>
 static cudaError_t configure_big(int precision) {
@@ -1429,7 +1434,10 @@ cudaError_t fused_configure() {
     g_big_cluster = 16;
   cudaGetLastError();  // a refused non-portable size leaves the 8-CTA choice
   int lo = 0, hi = 0;
-  if (cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess) g_top_priority = hi;
+  if (cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess) {
+    g_top_priority = hi;
+    g_fast_priority = hi < lo ? hi + 1 : hi;  // numerically smaller is higher
+  }
   cudaGetLastError();
   return cudaSuccess;
 }
@@ -1439,13 +1447,20 @@ cudaError_t launch_fused_step(const Dev& d, int precision, cudaGraphConditionalH
   const size_t sm = fused_smem_bytes(precision);
   const int per_sm = g_fast_ctas_per_sm[precision == MT_FP64 ? 0 : precision == MT_MIXED ? 1 : 2];
   const int g = d.nseg < per_sm * d.nsm ? d.nseg : per_sm * d.nsm;
-  if (precision == MT_MIXED)
-    k_step1d<MT_MIXED><<<g, Fast::kT, sm, s>>>(d, cond, use_cond);
-  else if (precision == MT_MIXED_DF32)
-    k_step1d<MT_MIXED_DF32><<<g, Fast::kT, sm, s>>>(d, cond, use_cond);
-  else
-    k_step1d<MT_FP64><<<g, Fast::kT, sm, s>>>(d, cond, use_cond);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributePriority;
+  at[0].val.priority = g_fast_priority;
+  cfg.gridDim = dim3((unsigned int)g);
+  cfg.blockDim = dim3(Fast::kT);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (precision == MT_MIXED) return cudaLaunchKernelEx(&cfg, k_step1d<MT_MIXED>, d, cond, use_cond);
+  if (precision == MT_MIXED_DF32)
+    return cudaLaunchKernelEx(&cfg, k_step1d<MT_MIXED_DF32>, d, cond, use_cond);
+  return cudaLaunchKernelEx(&cfg, k_step1d<MT_FP64>, d, cond, use_cond);
 }
 
 template <int PR, int CL>

@@ -57,6 +57,14 @@ struct Ctrl {
   int npred_next;               // ... counted during this step for the next
   int scan_hold;                // test hook: the scan's first tile withholds its status
   long long spin_limit;         // bound of each look-back wait (0: kSpinLimit)
+  // Observables of the previous step, computed beside a step (the fused
+  // path's graph): the state's mass buffer and step at the step's start,
+  // whether that step's rows are still to be written, and the last step
+  // whose rows were written.
+  int obs_mc;
+  int obs_prev_todo;
+  unsigned long long obs_step;
+  unsigned long long obs_done_step;
 };
 
 // One realisation of a batch (a single system is a batch of one).  Batched
@@ -404,6 +412,10 @@ cudaError_t launch_permute(const Dev& d, cudaStream_t s);  // gather id/masses a
 cudaError_t launch_transfer(const Dev& d, int search, int precision, cudaStream_t s, Marker& mk);
 // after a step: the observables row of every realisation
 cudaError_t launch_obs(const Dev& d, int precision, cudaStream_t s);
+// the fused path's graph: snapshot the state's buffer and step, then (beside
+// the step's kernels) the observables of the state at the snapshot
+cudaError_t launch_obs_snapshot(const Dev& d, cudaStream_t s);
+cudaError_t launch_obs_prev(const Dev& d, int precision, cudaStream_t s);
 cudaError_t launch_upload(const Dev& d, const double* x, const double* A,
                           const double* B, int precision, cudaStream_t s);
 cudaError_t launch_read_masses(const Dev& d, double* A, double* B, int precision,

@@ -85,7 +85,10 @@ struct ThreadObs<true> {  // double-binary32 masses
   }
 };
 
-template <int PR>
+// PREV: the state at the step's start (snapshot by k_obs_snapshot), while
+// the step runs beside it (it writes the other mass buffer); otherwise the
+// current state.  Either writes the row of the step the state follows.
+template <int PR, bool PREV>
 __global__ void __launch_bounds__(kThreads) k_obs(Dev d) {
   using MS = Mass<PR>;
   using MV = typename MS::V;
@@ -93,8 +96,10 @@ __global__ void __launch_bounds__(kThreads) k_obs(Dev d) {
   __shared__ Obs3<MV> s_w[kThreads / 32];
   __shared__ bool s_last;
   Ctrl* c = d.ctrl;
+  if (PREV && !c->obs_prev_todo) return;  // fixed before the launch: every CTA agrees
+  const unsigned long long step = PREV ? c->obs_step : c->step;
   const int ch = blockIdx.x;
-  const unsigned long long* M = d.M[c->mcur];
+  const unsigned long long* M = d.M[PREV ? c->obs_mc : c->mcur];
   // this thread's slots: loaded together, then added in slot order
   const long long a0 = d.ochunk[ch], a1 = d.ochunk[ch + 1];
   MV va[kPer], vb[kPer];
@@ -138,18 +143,41 @@ __global__ void __launch_bounds__(kThreads) k_obs(Dev d) {
   for (; k < k1; k += kThreads) u = obs3_add(u, get(k));
   u = obs3_block<MV, kThreads>(u, s_w);
   if (threadIdx.x == 0) {
-    const long long row = (long long)((c->step - 1) % (unsigned long long)d.observe_cap);
+    const long long row = (long long)((step - 1) % (unsigned long long)d.observe_cap);
     obs_row(d, row, r, R.n, u);
     d.ocnt[r] = 0;
+    c->obs_done_step = step;
   }
+}
+
+__global__ void k_obs_snapshot(Dev d) {
+  Ctrl* c = d.ctrl;
+  c->obs_mc = c->mcur;
+  c->obs_step = c->step;
+  c->obs_prev_todo = c->step > 0 && c->obs_done_step != c->step ? 1 : 0;
+}
+
+cudaError_t launch_obs_snapshot(const Dev& d, cudaStream_t s) {
+  if (d.observe_cap <= 0 || d.nochunk <= 0) return cudaSuccess;
+  k_obs_snapshot<<<1, 1, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_obs_prev(const Dev& d, int precision, cudaStream_t s) {
+  if (d.observe_cap <= 0 || d.nochunk <= 0) return cudaSuccess;
+  if (precision == MT_MIXED_DF32)
+    k_obs<MT_MIXED_DF32, true><<<d.nochunk, kThreads, 0, s>>>(d);
+  else
+    k_obs<MT_FP64, true><<<d.nochunk, kThreads, 0, s>>>(d);  // binary64 masses
+  return cudaGetLastError();
 }
 
 cudaError_t launch_obs(const Dev& d, int precision, cudaStream_t s) {
   if (d.observe_cap <= 0 || d.nochunk <= 0) return cudaSuccess;
   if (precision == MT_MIXED_DF32)
-    k_obs<MT_MIXED_DF32><<<d.nochunk, kThreads, 0, s>>>(d);
+    k_obs<MT_MIXED_DF32, false><<<d.nochunk, kThreads, 0, s>>>(d);
   else
-    k_obs<MT_FP64><<<d.nochunk, kThreads, 0, s>>>(d);  // binary64 masses
+    k_obs<MT_FP64, false><<<d.nochunk, kThreads, 0, s>>>(d);  // binary64 masses
   return cudaGetLastError();
 }
 
