@@ -1082,13 +1082,14 @@ def compact_kernels(kernels):
 
 
 def fp64_ops_per_step(npairs: int, n: int) -> float:
-    """Binary64 operations the step needs with binary64 masses (MIXED and
-    FP64): per ordered pair within the cutoff and species, the difference
-    M_j - M_i, its product with P and the accumulation (3 x 2 species x 2
-    orders per unordered pair); per particle and species the update (1),
-    per particle the reaction (a comparison and two subtractions) and the
-    walk's product (1)."""
-    return 12.0 * npairs + 6.0 * n
+    """Binary64 pipe instructions (per lane) the step needs with binary64
+    masses (MIXED and FP64), the unit of the measured FMA rate: per ordered
+    pair within the cutoff and species, the difference M_j - M_i and one
+    fused multiply-add of it with P into the accumulator (2 x 2 species x 2
+    orders per unordered pair); per particle and species the update (one
+    fused multiply-add), per particle the reaction (a minimum and two
+    subtractions) and the walk's product (1)."""
+    return 8.0 * npairs + 6.0 * n
 
 
 def alu_roofline(r, n: int, dfma_peak: float):
@@ -1105,10 +1106,11 @@ def alu_roofline(r, n: int, dfma_peak: float):
     ops = fp64_ops_per_step(r["npairs"], n)
     achieved = ops / (t * 1e-3)
     return {"bound": "alu", "kernel": "fused_step || fused_pred (concurrent)", "achieved": achieved,
-            "peak": dfma_peak, "unit": "binary64 op/s", "frac": achieved / dfma_peak,
+            "peak": dfma_peak, "unit": "binary64 instr/s", "frac": achieved / dfma_peak,
             "peak_kind": "measured (mt_probe_rate: binary64 FMA, lane operations per second)",
             "algo_ops_per_launch": ops, "launch_ms": t,
-            "algo": "12 per unordered pair within the cutoff + 6 per particle"}
+            "algo": "8 per unordered pair within the cutoff + 6 per particle "
+                    "(an FMA counts once, as in the peak)"}
 
 
 def variant_object(r, steps: int, name: str, peak: float, peak_kind: str, clocks, exp_peak,

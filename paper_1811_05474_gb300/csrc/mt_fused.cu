@@ -161,6 +161,19 @@ __device__ __forceinline__ void prefetch_stage2(const Dev& d, const SegPrefetch&
   __pipeline_commit();
 }
 
+// A bulk prefetch into L2 of bytes [lo, hi) of a workspace array (arrays
+// start on 256-byte boundaries and their regions are multiples of 256
+// bytes, so rounding the range out to 16 bytes stays inside the region).
+// Nothing waits for it: it only turns later loads into L2 hits.
+__device__ __forceinline__ void l2_prefetch(const void* base, long long lo, long long hi) {
+  const long long b0 = lo & ~15LL, b1 = (hi + 15) & ~15LL;
+  if (b1 > b0)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
+                     static_cast<const char*>(base) + b0),
+                 "r"((unsigned int)(b1 - b0))
+                 : "memory");
+}
+
 // The step's control words, read once per kernel launch (they change only
 // when the step ends).
 struct StepState {
@@ -172,6 +185,22 @@ struct StepState {
 __device__ __forceinline__ StepState step_state(const Dev& d) {
   const Ctrl* c = d.ctrl;
   return {c->xcur, c->mcur, c->scur, c->step, c->noise};
+}
+
+// The next segment's staged slots [a0, a0 + L) (positions, ids, both mass
+// arrays) asked into L2 while the current segment runs its transfer, once
+// its cell starts have arrived (thread 0, after prefetch_stage2), so that
+// its staging loads do not wait on HBM.
+__device__ __forceinline__ void prefetch_next_l2(const Dev& d, const SegPrefetch& pf,
+                                                 const StepState& st) {
+  if (pf.seg >= d.nseg) return;
+  __pipeline_wait_prior(0);
+  const long long a0 = pf.w[2], e = pf.w[3];
+  if (e <= a0 || e - a0 > 2 * (long long)kFusedCap) return;  // nothing, or not staged
+  l2_prefetch(d.X[st.xc], a0 * 8, e * 8);
+  l2_prefetch(d.id[st.xc], a0 * 4, e * 4);
+  l2_prefetch(d.M[st.mc], a0 * 8, e * 8);
+  l2_prefetch(d.M[st.mc], (d.n + a0) * 8, (d.n + e) * 8);
 }
 
 // ------------------------------------------------ first tier: pair list --
@@ -805,6 +834,7 @@ __device__ int fused_segment(const Dev& d, const StepState& st, int seg, unsigne
   const long long out0 = o0 + s_lt;
   const long long S = d.S;
   if constexpr (CL == 1) {
+    if (pf && tid == 0) prefetch_next_l2(d, *pf, st);
     if (!pair_transfer<PR, TR>(d, st, smem, active, m, w0, w1, out0, xlo, xhi)) {
       status = kSegHeavy;  // more pairs than the list holds: the second tier takes it
       active = false;

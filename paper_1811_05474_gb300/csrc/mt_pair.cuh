@@ -81,7 +81,10 @@ template <>
 struct Mass<MT_FP64> {
   using V = double;
   using Acc = double;
-  static __device__ __forceinline__ void acc(double& a, double P, double d) { a += P * d; }
+  // the product and the accumulation as one fused multiply-add
+  static __device__ __forceinline__ void acc(double& a, double P, double d) {
+    a = __fma_rn(P, d, a);
+  }
   static __device__ __forceinline__ double load(const unsigned long long* M, long long i) {
     return f64_load(M, i);
   }
@@ -92,8 +95,8 @@ struct Mass<MT_FP64> {
   // M + dM/2 (Eq. 7 with the 1/2 of Eq. 4), then the reaction.
   static __device__ __forceinline__ void update(double& A, double& B, double dA, double dB,
                                                 int react) {
-    A = A + 0.5 * dA;
-    B = B + 0.5 * dB;
+    A = __fma_rn(0.5, dA, A);  // 0.5 dA is exact: the same as A + 0.5 dA
+    B = __fma_rn(0.5, dB, B);
     if (react) {
       const double m = A < B ? A : B;
       A = A - m;
@@ -111,7 +114,7 @@ struct Mass<MT_MIXED> {
   using V = double;
   using Acc = double;
   static __device__ __forceinline__ void acc(double& a, float P, double d) {
-    a += (double)P * d;
+    a = __fma_rn((double)P, d, a);
   }
   static __device__ __forceinline__ double load(const unsigned long long* M, long long i) {
     return f64_load(M, i);
