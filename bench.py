@@ -1087,9 +1087,10 @@ def fp64_ops_per_step(npairs: int, n: int) -> float:
     pair within the cutoff and species, the difference M_j - M_i and one
     fused multiply-add of it with P into the accumulator (2 x 2 species x 2
     orders per unordered pair); per particle and species the update (one
-    fused multiply-add), per particle the reaction (a minimum and two
-    subtractions) and the walk's product (1)."""
-    return 8.0 * npairs + 6.0 * n
+    fused multiply-add), per particle the reaction (a comparison and one
+    subtraction: the smaller mass becomes exactly 0) and the walk's product
+    (1)."""
+    return 8.0 * npairs + 5.0 * n
 
 
 def alu_roofline(r, n: int, dfma_peak: float):
@@ -1109,7 +1110,7 @@ def alu_roofline(r, n: int, dfma_peak: float):
             "peak": dfma_peak, "unit": "binary64 instr/s", "frac": achieved / dfma_peak,
             "peak_kind": "measured (mt_probe_rate: binary64 FMA, lane operations per second)",
             "algo_ops_per_launch": ops, "launch_ms": t,
-            "algo": "8 per unordered pair within the cutoff + 6 per particle "
+            "algo": "8 per unordered pair within the cutoff + 5 per particle "
                     "(an FMA counts once, as in the peak)"}
 
 

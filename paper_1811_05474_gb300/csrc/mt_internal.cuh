@@ -303,6 +303,31 @@ __device__ __forceinline__ float ll_to_float(long long v) {
   return __fadd_rn(hi, lo);
 }
 
+// Exact binary32 -> binary64 widening from the bits, with integer
+// operations only (the binary64 pipe is kept for arithmetic): the sign,
+// the exponent re-biased (subnormals normalised), the fraction moved to the
+// top of 52 bits; infinities and NaNs keep their class and payload.
+__device__ __forceinline__ double widen_exact(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  unsigned long long E, F;
+  if (e == 0xffu) {
+    E = 0x7ff;
+    F = (unsigned long long)m << 29;
+  } else if (e != 0u) {
+    E = e + 896u;
+    F = (unsigned long long)m << 29;
+  } else if (m != 0u) {  // m * 2^-149 with its leading bit at p
+    const int p = 31 - __clz(m);
+    E = (unsigned long long)(p + 874);
+    F = ((unsigned long long)m << (52 - p)) & ((1ULL << 52) - 1);
+  } else {
+    E = 0;
+    F = 0;
+  }
+  return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) | (E << 52) | F));
+}
+
 // Eq. 2's random-walk displacement on the grid: the nearest tick to b xi,
 // b = sqrt(2 D_rw dt) 2^k, with the product formed in binary64.
 __device__ __forceinline__ long long walk_ticks(double b, float xi) {

@@ -97,10 +97,14 @@ struct Mass<MT_FP64> {
                                                 int react) {
     A = __fma_rn(0.5, dA, A);  // 0.5 dA is exact: the same as A + 0.5 dA
     B = __fma_rn(0.5, dB, B);
-    if (react) {
-      const double m = A < B ? A : B;
-      A = A - m;
-      B = B - m;
+    if (react) {  // min(A, B) off both: the smaller becomes exactly 0
+      if (A < B) {
+        B = B - A;
+        A = 0.0;
+      } else {
+        A = A - B;
+        B = 0.0;
+      }
     }
   }
   static __device__ __forceinline__ double to_double(double v) { return v; }
@@ -114,7 +118,7 @@ struct Mass<MT_MIXED> {
   using V = double;
   using Acc = double;
   static __device__ __forceinline__ void acc(double& a, float P, double d) {
-    a = __fma_rn((double)P, d, a);
+    a = __fma_rn(widen_exact(P), d, a);
   }
   static __device__ __forceinline__ double load(const unsigned long long* M, long long i) {
     return f64_load(M, i);
