@@ -401,10 +401,10 @@ struct mt_handle {
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
   // fused path with observables, first tier bound by the binary64 pipe
-  // (MT_FP64, MT_MIXED): the previous step's observables run on a third
-  // stream beside the step in the graph, in the pipe's idle issue slots;
-  // the last step's are pending until a call that reads them (flush_obs).
-  // With MT_MIXED_DF32 they follow the step in its graph.
+  // (MT_FP64, MT_MIXED): the previous step's observables run beside the
+  // step in the graph (behind the predicted segments, or on this third
+  // stream); the last step's are pending until a call that reads them
+  // (flush_obs).  With MT_MIXED_DF32 they follow the step in its graph.
   cudaStream_t side2 = nullptr;
   cudaEvent_t join2 = nullptr;
   bool obs_pending = false;
@@ -548,14 +548,17 @@ mt_status build_graph(mt_handle* h) {
   mt_status s = MT_OK;
   Marker none;
   if (h->D.fused) {
-    // g: [snapshot] -> { [previous step's observables] | [predicted segments]
-    //   | [fast tier] } -> IF(queued) { [second tier] -> IF(overflow) { general } }
+    // g: [snapshot] -> { [predicted segments] -> [previous step's
+    //   observables] | [fast tier] } -> IF(queued) { [second tier] ->
+    //   IF(overflow) { general } }
     cudaGraphConditionalHandle cond1, cond2;
     CU(cudaGraphConditionalHandleCreate(&cond1, g, 0, 0));
     // large systems fork: the predicted-segment kernel on the side stream,
     // the first tier on the handle's stream; with observables, the previous
-    // step's on a third stream (they read the mass buffer the step only
-    // reads); all join before the conditional
+    // step's follow the predicted segments on the side stream (on the SMs
+    // those leave while the first tier still runs), or, without the fork,
+    // run on a third stream beside the first tier (they read the mass
+    // buffer the step only reads); all join before the conditional
     const bool fork = d.use_pred != 0;
     const bool obs = h->side2 != nullptr;
     CU(cudaStreamBeginCaptureToGraph(h->stream, g, nullptr, nullptr, 0, mode));
@@ -566,15 +569,17 @@ mt_status build_graph(mt_handle* h) {
       if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(h->side, h->fork, 0);
       if (e1 == cudaSuccess) e1 = launch_fused_pred(d, h->D.p.precision, cond1, 1, h->side);
     }
-    if (obs) {
+    if (obs && fork) {  // behind the predicted segments, on their SMs
+      if (e1 == cudaSuccess) e1 = launch_obs_prev(d, h->D.p.precision, h->side);
+    } else if (obs) {
       if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(h->side2, h->fork, 0);
       if (e1 == cudaSuccess) e1 = launch_obs_prev(d, h->D.p.precision, h->side2);
     }
     if (e1 == cudaSuccess) e1 = launch_fused_step(d, h->D.p.precision, cond1, 1, h->stream);
     if (fork && e1 == cudaSuccess) e1 = cudaEventRecord(h->join, h->side);
     if (fork && e1 == cudaSuccess) e1 = cudaStreamWaitEvent(h->stream, h->join, 0);
-    if (obs && e1 == cudaSuccess) e1 = cudaEventRecord(h->join2, h->side2);
-    if (obs && e1 == cudaSuccess) e1 = cudaStreamWaitEvent(h->stream, h->join2, 0);
+    if (obs && !fork && e1 == cudaSuccess) e1 = cudaEventRecord(h->join2, h->side2);
+    if (obs && !fork && e1 == cudaSuccess) e1 = cudaStreamWaitEvent(h->stream, h->join2, 0);
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
       cudaGraphDestroy(g);
