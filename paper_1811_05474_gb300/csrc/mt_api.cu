@@ -548,9 +548,9 @@ mt_status build_graph(mt_handle* h) {
   mt_status s = MT_OK;
   Marker none;
   if (h->D.fused) {
-    // g: [snapshot] -> { [predicted segments] -> [previous step's
-    //   observables] | [fast tier] } -> IF(queued) { [second tier] ->
-    //   IF(overflow) { general } }
+    // g: { [predicted segments, taking the observables' snapshot] ->
+    //   [previous step's observables] | [fast tier] } -> IF(queued)
+    //   { [second tier] -> IF(overflow) { general } }
     cudaGraphConditionalHandle cond1, cond2;
     CU(cudaGraphConditionalHandleCreate(&cond1, g, 0, 0));
     // large systems fork: the predicted-segment kernel on the side stream,
@@ -563,11 +563,15 @@ mt_status build_graph(mt_handle* h) {
     const bool obs = h->side2 != nullptr;
     CU(cudaStreamBeginCaptureToGraph(h->stream, g, nullptr, nullptr, 0, mode));
     cudaError_t e1 = cudaSuccess;
-    if (obs) e1 = launch_obs_snapshot(d, h->stream);
+    // the observables' snapshot: by the predicted-segment kernel where it
+    // runs (the observables follow it), else a kernel of its own
+    if (obs && !fork) e1 = launch_obs_snapshot(d, h->stream);
     if ((fork || obs) && e1 == cudaSuccess) e1 = cudaEventRecord(h->fork, h->stream);
     if (fork) {
       if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(h->side, h->fork, 0);
-      if (e1 == cudaSuccess) e1 = launch_fused_pred(d, h->D.p.precision, cond1, 1, h->side);
+      Dev dp = d;
+      dp.obs_snap = obs ? 1 : 0;
+      if (e1 == cudaSuccess) e1 = launch_fused_pred(dp, h->D.p.precision, cond1, 1, h->side);
     }
     if (obs && fork) {  // behind the predicted segments, on their SMs
       if (e1 == cudaSuccess) e1 = launch_obs_prev(d, h->D.p.precision, h->side);
@@ -588,9 +592,8 @@ mt_status build_graph(mt_handle* h) {
     cudaGraph_t body1 = nullptr;
     cudaGraphNode_t cnode = nullptr;  // the IF node
     {
-      // the IF node follows every kernel node without a dependent (the
-      // snapshot precedes the others)
-      const size_t want = 1 + (fork ? 1 : 0) + (obs ? 2 : 0);
+      // the IF node follows every kernel node without a dependent
+      const size_t want = 1 + (fork ? 1 : 0) + (obs ? (fork ? 1 : 2) : 0);
       cudaGraphNode_t knodes[4] = {nullptr, nullptr, nullptr, nullptr};
       size_t nn = 4;
       CU(cudaGraphGetNodes(g, knodes, &nn));

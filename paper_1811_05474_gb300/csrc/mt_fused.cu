@@ -1191,6 +1191,7 @@ __global__ void __launch_bounds__(Big::kT, 1)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned char* pcur = d.pred[sc];
   unsigned char* pnext = d.pred[sc ^ 1];
+  if (d.obs_snap && blockIdx.x == 0 && tid == 0) obs_snapshot(c);  // read behind this kernel
   if (blockIdx.x < CL && c->npred > 0) {  // the first cluster does the work
     for (int base = 0; base < d.nseg; base += Big::kT) {
       const int sidx = base + tid;

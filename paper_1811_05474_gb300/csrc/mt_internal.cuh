@@ -67,6 +67,14 @@ struct Ctrl {
   unsigned long long obs_done_step;
 };
 
+// The snapshot the previous step's observables read (one thread, at the
+// start of a step, before the step advances the control block).
+__device__ __forceinline__ void obs_snapshot(Ctrl* c) {
+  c->obs_mc = c->mcur;
+  c->obs_step = c->step;
+  c->obs_prev_todo = c->step > 0 && c->obs_done_step != c->step ? 1 : 0;
+}
+
 // One realisation of a batch (a single system is a batch of one).  Batched
 // realisations are 1-d and sit side by side on one tick axis: realisation r
 // owns [base, base + Lq], and consecutive domains are more than Smax apart,
@@ -109,6 +117,7 @@ struct Dev {
   int* ovlist;              // [nseg] segments queued for the second fused tier
   unsigned char* pred[2];   // [nseg] segments predicted pair-heavy (by scur parity)
   int use_pred;             // 1: the predicted-segment kernel runs beside the first tier
+  int obs_snap;             // 1: the predicted-segment kernel takes the observables' snapshot
   int periodic;             // 1: periodic walls (wrap, minimum-image separations)
   int nspec;                // species per particle (masses hold nspec * n words)
   int band_cap;             // SPaM form: stored weights per particle (0: off)

@@ -85,7 +85,8 @@ struct ThreadObs<true> {  // double-binary32 masses
   }
 };
 
-// PREV: the state at the step's start (snapshot by k_obs_snapshot), while
+// PREV: the state at the step's start (obs_snapshot, by k_obs_snapshot or
+// the predicted-segment kernel), while
 // the step runs beside it (it writes the other mass buffer); otherwise the
 // current state.  Either writes the row of the step the state follows.
 template <int PR, bool PREV>
@@ -150,12 +151,7 @@ __global__ void __launch_bounds__(kThreads) k_obs(Dev d) {
   }
 }
 
-__global__ void k_obs_snapshot(Dev d) {
-  Ctrl* c = d.ctrl;
-  c->obs_mc = c->mcur;
-  c->obs_step = c->step;
-  c->obs_prev_todo = c->step > 0 && c->obs_done_step != c->step ? 1 : 0;
-}
+__global__ void k_obs_snapshot(Dev d) { obs_snapshot(d.ctrl); }
 
 cudaError_t launch_obs_snapshot(const Dev& d, cudaStream_t s) {
   if (d.observe_cap <= 0 || d.nochunk <= 0) return cudaSuccess;
