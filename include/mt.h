@@ -461,7 +461,8 @@ mt_status mt_transfer_1d_noalloc(const double* x, const double* A, const double*
 /* Device throughput probe (not part of the paper; it measures the peaks
  * that the binary64 and all-pairs passes are compared against).  which:
  * 0 binary64 fused multiply-adds, 1 binary32 fused multiply-adds, 2 binary32
- * fast exponentials (__expf), 3 binary64 exponentials (exp).  Runs
+ * fast exponentials (__expf), 3 binary64 exponentials (the library's exp),
+ * 4 the binary64 exp(-t) the MT_FP64 weights (Eq. 3) use.  Runs
  * independent chains of that operation on 8 CTAs of 256 threads per
  * multiprocessor of the current device (about 10 ms per launch), times the
  * fastest of three launches with CUDA events on stream (NULL: the default
@@ -470,6 +471,14 @@ mt_status mt_transfer_1d_noalloc(const double* x, const double* A, const double*
  * Errors: MT_ERR_INVALID (which), MT_ERR_WORKSPACE (scratch), MT_ERR_CUDA. */
 mt_status mt_probe_rate(int32_t which, void* scratch, size_t scratch_bytes, void* stream,
                         double* ops_per_s);
+
+/* Test hook: the binary64 exp(-t) that the MT_FP64 weights (Eq. 3) use,
+ * out[i] = exp(-t[i]) for t[i] >= 0 (Tang's table-driven method; about one
+ * unit in the last place), so that tests can check it against the exact
+ * exponential.  t, out: device arrays of n doubles.  Enqueued on stream
+ * (NULL: the default stream).  Errors: MT_ERR_INVALID (n < 0, NULL arrays),
+ * MT_ERR_CUDA. */
+mt_status mt_test_exp_neg(const double* t, double* out, int64_t n, void* stream);
 
 /* Description of the last error on this thread (static storage). */
 const char* mt_last_error(void);

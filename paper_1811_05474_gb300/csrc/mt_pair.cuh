@@ -22,6 +22,49 @@ __device__ __forceinline__ bool in_range2(long long dx, long long dy, long long 
 template <bool MIX, int DIM>
 struct Weight;
 
+// ------------------------------------------------- binary64 exponential --
+// exp(-t) for t >= 0 in binary64 (the weights of Eq. 3 in MT_FP64), by
+// Tang's table-driven method (P. T. P. Tang, ACM TOMS 15(2), 1989): with
+// k = rint(-t 32/ln2) = 32 m + j (0 <= j < 32) and r = -t - k ln2/32
+// (|r| <= ln2/64; ln2/32 split into a 37-bit head, so that k times it is
+// exact for |k| < 2^16, and a tail), exp(-t) = 2^m 2^(j/32) e^r, where
+// 2^(j/32) comes from a table of its correctly rounded values and e^r - 1
+// = r + r^2 q(r) from the Taylor polynomial of degree 6 (truncation below
+// 2^-57 relative for |r| <= ln2/64).  The result is 2^(j/32) + 2^(j/32)
+// (e^r - 1) with one rounding, then scaled by 2^m in its exponent field.
+// Error about 1 ulp; 11 binary64 operations.
+__constant__ double kExp2j32[32] = {
+    0x1.0000000000000p+0, 0x1.059b0d3158574p+0, 0x1.0b5586cf9890fp+0, 0x1.11301d0125b51p+0,
+    0x1.172b83c7d517bp+0, 0x1.1d4873168b9aap+0, 0x1.2387a6e756238p+0, 0x1.29e9df51fdee1p+0,
+    0x1.306fe0a31b715p+0, 0x1.371a7373aa9cbp+0, 0x1.3dea64c123422p+0, 0x1.44e086061892dp+0,
+    0x1.4bfdad5362a27p+0, 0x1.5342b569d4f82p+0, 0x1.5ab07dd485429p+0, 0x1.6247eb03a5585p+0,
+    0x1.6a09e667f3bcdp+0, 0x1.71f75e8ec5f74p+0, 0x1.7a11473eb0187p+0, 0x1.82589994cce13p+0,
+    0x1.8ace5422aa0dbp+0, 0x1.93737b0cdc5e5p+0, 0x1.9c49182a3f090p+0, 0x1.a5503b23e255dp+0,
+    0x1.ae89f995ad3adp+0, 0x1.b7f76f2fb5e47p+0, 0x1.c199bdd85529cp+0, 0x1.cb720dcef9069p+0,
+    0x1.d5818dcfba487p+0, 0x1.dfc97337b9b5fp+0, 0x1.ea4afa2a490dap+0, 0x1.f50765b6e4540p+0,
+};
+__device__ __forceinline__ double exp_neg(double t) {
+  if (!(t <= 745.5)) return t > 745.5 ? 0.0 : t + t;  // underflow; a NaN stays one
+  const double x = -t;
+  const double kMagic = 0x1.8p52;  // rint by addition: ulp 1 at 1.5 * 2^52
+  const double kd = __fma_rn(x, 0x1.71547652b82fep+5, kMagic);  // x 32 / ln2
+  const int k = (int)(unsigned int)(unsigned long long)__double_as_longlong(kd);
+  const double kf = kd - kMagic;
+  double r = __fma_rn(-kf, 0x1.62e42fefa0000p-6, x);  // head of ln2 / 32
+  r = __fma_rn(-kf, 0x1.cf79abc9e3b3ap-45, r);        // tail
+  double q = __fma_rn(r, 0x1.6c16c16c16c17p-10, 0x1.1111111111111p-7);  // 1/720, 1/120
+  q = __fma_rn(r, q, 0x1.5555555555555p-5);                               // 1/24
+  q = __fma_rn(r, q, 0x1.5555555555555p-3);                               // 1/6
+  q = __fma_rn(r, q, 0.5);
+  const double em1 = __fma_rn(__dmul_rn(r, r), q, r);
+  const double T = kExp2j32[k & 31];
+  const double res = __fma_rn(T, em1, T);
+  const int m = k >> 5;
+  if (m >= -1021)
+    return __longlong_as_double(__double_as_longlong(res) + ((long long)m << 52));
+  return scalbn(res, m);  // a subnormal result
+}
+
 template <int DIM>
 struct Weight<false, DIM> {
   using T = double;
@@ -32,12 +75,12 @@ struct Weight<false, DIM> {
       const double sy = __dmul_rn((double)dy, d.scale);
       s2 = __dadd_rn(s2, __dmul_rn(sy, sy));
     }
-    return exp(-__dmul_rn(s2, d.inv8));
+    return exp_neg(__dmul_rn(s2, d.inv8));
   }
   // 1-d, |D| <= Smax < 2^30 (the same value as eval(d, D, 0))
   static __device__ __forceinline__ double near(const Dev& d, long long D) {
     const double sx = __dmul_rn((double)(int)D, d.scale);
-    return exp(-__dmul_rn(__dmul_rn(sx, sx), d.inv8));
+    return exp_neg(__dmul_rn(__dmul_rn(sx, sx), d.inv8));
   }
 };
 

@@ -1,8 +1,10 @@
 // mt_probe.cu -- throughput probes for the non-HBM rooflines of the
 // transfer kernels: binary64 fused multiply-add, binary32 fused
-// multiply-add, the binary32 fast exponential (__expf) and the binary64
-// exponential (exp).  Not part of the paper: they measure the device peaks
-// the FP64 and brute-force passes are compared against.
+// multiply-add, the binary32 fast exponential (__expf), the library's
+// binary64 exponential (exp) and the weights' own binary64 exponential
+// (exp_neg).  Not part of the paper: they measure the device peaks the FP64
+// and brute-force passes are compared against.  Also the test hook that
+// evaluates exp_neg on a device array.
 //
 // Each thread runs kChains independent dependency chains for `iters`
 // rounds (enough independent work per warp to keep the pipe busy), on a
@@ -11,7 +13,7 @@
 // operations / event-timed kernel duration (one warm-up launch first).
 #include <cmath>
 
-#include "mt_internal.cuh"
+#include "mt_pair.cuh"
 
 namespace mt {
 mt_status set_last_error(mt_status s, const char* msg);
@@ -42,11 +44,12 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(double* out, int iters,
       if (WHICH == 1) f[k] = __fmaf_rn(f[k], mf, cf);           // binary32 FMA
       if (WHICH == 2) f[k] = __expf(-f[k]);                     // binary32 fast exp
       if (WHICH == 3) a[k] = exp(-a[k]);                        // binary64 exp
+      if (WHICH == 4) a[k] = mt::exp_neg(a[k]);                 // the weights' exp(-t)
     }
   }
   double s = 0.0;
 #pragma unroll
-  for (int k = 0; k < kChains; ++k) s += (WHICH == 0 || WHICH == 3) ? a[k] : (double)f[k];
+  for (int k = 0; k < kChains; ++k) s += (WHICH == 0 || WHICH >= 3) ? a[k] : (double)f[k];
   __shared__ double red[kProbeThreads / 32];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -69,16 +72,33 @@ cudaError_t launch_which(int which, double* out, int blocks, int iters, cudaStre
     case 0: return launch_probe<0>(out, blocks, iters, s);
     case 1: return launch_probe<1>(out, blocks, iters, s);
     case 2: return launch_probe<2>(out, blocks, iters, s);
-    default: return launch_probe<3>(out, blocks, iters, s);
+    case 3: return launch_probe<3>(out, blocks, iters, s);
+    default: return launch_probe<4>(out, blocks, iters, s);
   }
+}
+
+__global__ void k_exp_neg(const double* t, double* out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = mt::exp_neg(t[i]);
 }
 
 }  // namespace
 
+extern "C" mt_status mt_test_exp_neg(const double* t, double* out, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!t || !out)))
+    return mt::set_last_error(MT_ERR_INVALID, "mt_test_exp_neg: n < 0 or NULL array");
+  if (n == 0) return MT_OK;
+  const long long blocks = (n + 255) / 256;
+  k_exp_neg<<<(unsigned int)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(t, out, n);
+  if (cudaGetLastError() != cudaSuccess)
+    return mt::set_last_error(MT_ERR_CUDA, "mt_test_exp_neg: launch failed");
+  return MT_OK;
+}
+
 extern "C" mt_status mt_probe_rate(int32_t which, void* scratch, size_t scratch_bytes,
                                    void* stream, double* ops_per_s) {
-  if (which < 0 || which > 3 || !ops_per_s)
-    return mt::set_last_error(MT_ERR_INVALID, "mt_probe_rate: which must be 0..3");
+  if (which < 0 || which > 4 || !ops_per_s)
+    return mt::set_last_error(MT_ERR_INVALID, "mt_probe_rate: which must be 0..4");
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -88,7 +108,7 @@ extern "C" mt_status mt_probe_rate(int32_t which, void* scratch, size_t scratch_
     return mt::set_last_error(MT_ERR_WORKSPACE, "mt_probe_rate: scratch too small");
   // rounds per thread: about 2^31 operations per launch for the fast pipes,
   // 2^28 for the binary64 ones
-  const int iters = which == 0 ? 2048 : which == 3 ? 256 : 16384;
+  const int iters = which == 0 ? 2048 : which >= 3 ? 256 : 16384;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* out = static_cast<double*>(scratch);
   cudaEvent_t e0, e1;

@@ -161,6 +161,7 @@ def lib(path: Path | None = None):
         "mt_test_hold_scan": [H, i32, i64],
         "mt_walk_normals": [P, _vp, i64, ctypes.c_uint64, _vp, _vp],
         "mt_probe_rate": [i32, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(ctypes.c_double)],
+        "mt_test_exp_neg": [_vp, _vp, i64, _vp],
         "mt_transfer_1d_noalloc": [_vp, _vp, _vp, _vp, _vp, i64, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, i32, i32,
                                    _vp],
@@ -399,7 +400,7 @@ def mt_walk_normals(p: mt_params, gid_ptr, n: int, step: int, out_ptr, stream_pt
     check(lib().mt_walk_normals(ctypes.byref(p), gid_ptr, n, step, out_ptr, stream_ptr))
 
 
-PROBE_DFMA, PROBE_FFMA, PROBE_EXPF, PROBE_EXP = 0, 1, 2, 3
+PROBE_DFMA, PROBE_FFMA, PROBE_EXPF, PROBE_EXP, PROBE_EXP_NEG = 0, 1, 2, 3, 4
 
 
 def mt_probe_rate(which: int, device="cuda") -> float:
@@ -411,6 +412,11 @@ def mt_probe_rate(which: int, device="cuda") -> float:
     check(lib().mt_probe_rate(which, scratch.data_ptr(), scratch.numel(), None,
                               ctypes.byref(out)))
     return float(out.value)
+
+
+def mt_test_exp_neg(t_ptr, out_ptr, n: int, stream_ptr=None) -> None:
+    """Test hook: the weights' binary64 exp(-t) on device arrays (see include/mt.h)."""
+    check(lib().mt_test_exp_neg(t_ptr, out_ptr, n, stream_ptr))
 
 
 def mt_test_hold_scan(h, hold: int, spin_limit: int = 0) -> None:
