@@ -502,6 +502,7 @@ mt_status enqueue_step(mt_handle* h, const Dev& d) {
         mk("fused_pred", h->stream);
         CU(launch_fused_pred(d, p.precision, 0, 0, h->stream));
       } else {
+        mk("join_stub", h->stream);  // (the graph launches the predicted-segment kernel here)
         CU(launch_join_stub(d, h->stream));  // the first tier's partner in the join
       }
     }
