@@ -38,6 +38,8 @@ mt_status fail(mt_status s, const char* fmt, ...) {
 constexpr double kTwo30 = 1073741824.0;            // 2^30
 constexpr double kTwo61 = 2305843009213693952.0;   // 2^61
 constexpr size_t kAlign = 256;
+constexpr long long kWcCap = 1LL << 22;  // 32 MiB of cached weights (rows of up to 2048 slots)
+constexpr long long kWcMinN = 1LL << 17;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
@@ -51,6 +53,7 @@ struct Derived {
   int cshift = 0;
   long long ncx = 1, ncy = 1, ncell = 0;
   long long nbig_cap = 0, ntiles = 0;
+  long long wc_cap = 0;  // doubles of the dense-row weight cache
   // fused 1-d step (one kernel per step) and its tiling
   bool fused = false;
   long long seg_target = 0, nseg = 0, hc = 0;
@@ -63,7 +66,7 @@ struct Derived {
   // workspace offsets
   size_t o_ctrl, o_X[2], o_id[2], o_M[2], o_src, o_rinv, o_count, o_start, o_cursor,
       o_status, o_big, o_obs, o_fstart[2], o_cb[2], o_ovlist, o_pred[2], o_rt, o_sslot,
-      o_sreal, o_ochunk, o_opart, o_ochr, o_ocnt, o_cnt, o_band, total;
+      o_sreal, o_ochunk, o_opart, o_ochr, o_ocnt, o_cnt, o_band, o_wc, total;
   long long band = 0;  // SPaM band entries per particle (0: off)
   bool tile = false;   // dense 1-d: tiled transfer passes
 };
@@ -362,6 +365,10 @@ mt_status resolve(const mt_params* in, const mt_batch* b, Derived* out) {
   for (int b2 = 0; b2 < 2; ++b2) D.o_fstart[b2] = take(D.fused ? (size_t)(D.ncell + 1) * 4 : 0);
   for (int b2 = 0; b2 < 2; ++b2) D.o_cb[b2] = take(D.fused ? (size_t)(D.nseg + 1) * 4 : 0);
   D.o_ovlist = take(D.fused ? (size_t)D.nseg * 4 : 0);
+  // binary64 weights of the wall layer's dense rows, kept between the
+  // predicted-segment kernel's row sums and its exchange (large systems)
+  D.wc_cap = D.fused && p.precision == MT_FP64 && p.n >= kWcMinN ? kWcCap : 0;
+  D.o_wc = take((size_t)D.wc_cap * 8);
   for (int b2 = 0; b2 < 2; ++b2) D.o_pred[b2] = take(D.fused ? (size_t)D.nseg : 0);
   D.o_rt = take(D.rt.size() * sizeof(Real));
   D.o_sslot = take(D.sslot.size() * 4);
@@ -818,6 +825,8 @@ mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace
   d.key1 = (unsigned int)(D.p.seed >> 32);
   d.real = (unsigned int)D.p.realisation;
   d.nbig_cap = (int)D.nbig_cap;
+  d.wc = reinterpret_cast<double*>(w + D.o_wc);
+  d.wc_cap = D.wc_cap;
   d.rt = reinterpret_cast<const Real*>(w + D.o_rt);
   d.nreal = D.nreal;
   d.lbits = D.lbits;

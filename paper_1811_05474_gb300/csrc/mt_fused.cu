@@ -475,7 +475,8 @@ __device__ bool pair_transfer(const Dev& d, const StepState& st, unsigned char* 
 template <int PR, typename TR, int CL>
 __device__ int fused_segment(const Dev& d, const StepState& st, int seg, unsigned char* smem,
                              const SegScalars& g, int slice, int nslice, bool route_heavy,
-                             bool* heavy_out = nullptr, const SegPrefetch* pf = nullptr) {
+                             bool* heavy_out = nullptr, const SegPrefetch* pf = nullptr,
+                             bool cache_w = false) {
   using W = Weight<mixw(PR), 1>;
   using T = typename W::T;
   using MS = Mass<PR>;
@@ -488,7 +489,7 @@ __device__ int fused_segment(const Dev& d, const StepState& st, int seg, unsigne
   T* sr = reinterpret_cast<T*>(sid + CAP);
   int* bstart = reinterpret_cast<int*>(sr + CAP);  // [NB + 1]
   int* bcur = bstart + NB + 1;                     // [NB]
-  __shared__ int s_lt, s_w0, s_w1, s_bad, s_nbig, s_work, s_nd, s_nd2;
+  __shared__ int s_lt, s_w0, s_w1, s_bad, s_nbig, s_work, s_nd, s_nd2, s_wcbad, s_wcok;
   __shared__ int s_big[kBigMax];
   __shared__ int s_scan[NT / 32];
 
@@ -867,25 +868,37 @@ __device__ int fused_segment(const Dev& d, const StepState& st, int seg, unsigne
       }
     }
     __syncthreads();
+    // Binary64 weights of dense rows are dear (an exponential each): the
+    // predicted-segment kernel keeps them, row j of the staged slots at
+    // wc[j m + q], between the row sums and the exchange (read through L2:
+    // the rows are written by other CTAs of the cluster)
+    constexpr bool kCache = PR == MT_FP64 && CL > 1;
+    const bool cw = kCache && cache_w && (long long)m * m <= d.wc_cap;
     if (active) {
       const int nd = s_nd < NB ? s_nd : NB;
       for (int k = warp; k < nd; k += NT / 32) {
         const int j = dlist[k];
         const long long x = sx[j];
         const int lo = lower_at_least(sx, m, x - S), hi = lower_at_least(sx, m, x + S + 1);
+        T* wrow = kCache ? reinterpret_cast<T*>(d.wc) + (size_t)j * m : nullptr;
+        auto nu = [&](int qq) {
+          const T w = W::near(d, x > sx[qq] ? x - sx[qq] : sx[qq] - x);
+          if (kCache && cw) wrow[qq] = w;
+          return w;
+        };
         // second tier: four chains per lane (dense particles are its work);
         // first tier: one (registers are scarce there)
         T r0 = T(0), r1 = T(0), r2 = T(0), r3 = T(0);
         int q = lo + lane;
         if constexpr (CL > 1) {
           for (; q + 96 < hi; q += 128) {
-            r0 += W::near(d, x > sx[q] ? x - sx[q] : sx[q] - x);
-            r1 += W::near(d, x > sx[q + 32] ? x - sx[q + 32] : sx[q + 32] - x);
-            r2 += W::near(d, x > sx[q + 64] ? x - sx[q + 64] : sx[q + 64] - x);
-            r3 += W::near(d, x > sx[q + 96] ? x - sx[q + 96] : sx[q + 96] - x);
+            r0 += nu(q);
+            r1 += nu(q + 32);
+            r2 += nu(q + 64);
+            r3 += nu(q + 96);
           }
         }
-        for (; q < hi; q += 32) r0 += W::near(d, x > sx[q] ? x - sx[q] : sx[q] - x);
+        for (; q < hi; q += 32) r0 += nu(q);
         const T r = warp_sum((r0 + r1) + (r2 + r3));
         if (lane == 0) sr[j] = mixw(PR) ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
       }
@@ -896,7 +909,13 @@ __device__ int fused_segment(const Dev& d, const StepState& st, int seg, unsigne
       // peers' shared memory (distributed shared memory), between two cluster
       // barriers so no CTA reads a peer that has moved on.
       cg::cluster_group cl = cg::this_cluster();
+      if (tid == 0) s_wcbad = s_nd > NB ? 1 : 0;  // a dense row summed without the cache
       cl.sync();
+      if (tid == 0) {
+        int bad = 0;
+        for (int r = 0; r < CL; ++r) bad |= *cl.map_shared_rank(&s_wcbad, r);
+        s_wcok = bad ? 0 : 1;
+      }
       if (active) {
         for (int j = tid; j < m; j += NT) {
           const int owner = j % CL;
@@ -964,10 +983,14 @@ __device__ int fused_segment(const Dev& d, const StepState& st, int seg, unsigne
         // second tier: four chains per lane (q, q + 32, q + 64, q + 96),
         // merged at the end; first tier: one
         typename MS::Acc cA[4] = {}, cB[4] = {};
+        // the row's weights from the cache where every dense row went in
+        const bool from_c = kCache && cw && s_wcok;
+        const T* wrow = reinterpret_cast<const T*>(d.wc) + (size_t)j * m;
         auto pair = [&](int qq, int ch) {
           if (qq == j) return;
-          const T P =
-              normalised<T>(d.norm, W::near(d, x > sx[qq] ? x - sx[qq] : sx[qq] - x), ip, sr[qq]);
+          const T w =
+              from_c ? __ldcg(&wrow[qq]) : W::near(d, x > sx[qq] ? x - sx[qq] : sx[qq] - x);
+          const T P = normalised<T>(d.norm, w, ip, sr[qq]);
           MS::acc(cA[ch], P, MS::diff(MS::load(sA, qq), A));
           MS::acc(cB[ch], P, MS::diff(MS::load(sB, qq), B));
         };
@@ -999,6 +1022,9 @@ __device__ int fused_segment(const Dev& d, const StepState& st, int seg, unsigne
         }
       }
     }
+    // no CTA of the cluster writes the next segment's cached rows before
+    // every CTA has read this segment's (cw is the same in all of them)
+    if (kCache && cw) cg::this_cluster().sync();
   }
   if (active && slice == 0) {
     // ---- 6: next step's cell starts and segment boundaries ----------------
@@ -1216,7 +1242,7 @@ __global__ void __launch_bounds__(Big::kT, 1)
         const int seg = s_list[k];
         bool heavy = true;
         const int rc = fused_segment<PR, Big, CL>(d, st, seg, smem, load_seg(d, sc, Dc, seg),
-                                                   rank, CL, false, &heavy);
+                                                   rank, CL, false, &heavy, nullptr, true);
         if (rc != kSegOk && tid == 0 && atomicExch(&c->overflow, 1) == 0) {
           c->ov_reason = rc;
           c->ov_seg = seg;

@@ -118,6 +118,8 @@ struct Dev {
   unsigned char* pred[2];   // [nseg] segments predicted pair-heavy (by scur parity)
   int use_pred;             // 1: the predicted-segment kernel runs beside the first tier
   int obs_snap;             // 1: the predicted-segment kernel takes the observables' snapshot
+  double* wc;               // [wc_cap] the cluster kernel's cache of dense rows' binary64 weights
+  long long wc_cap;         // doubles (0: none)
   int periodic;             // 1: periodic walls (wrap, minimum-image separations)
   int nspec;                // species per particle (masses hold nspec * n words)
   int band_cap;             // SPaM form: stored weights per particle (0: off)
