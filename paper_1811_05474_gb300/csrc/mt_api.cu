@@ -407,11 +407,13 @@ struct mt_handle {
   // the first tier (fork / join events around it in the captured graph)
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
-  // fused path with observables, first tier bound by the binary64 pipe
-  // (MT_FP64, MT_MIXED): the previous step's observables run beside the
-  // step in the graph (behind the predicted segments, or on this third
-  // stream); the last step's are pending until a call that reads them
-  // (flush_obs).  With MT_MIXED_DF32 they follow the step in its graph.
+  // fused path with observables: the previous step's observables run
+  // beside the step in the graph (obs_defer), behind the predicted segments
+  // where those run, else on this third stream when the first tier is
+  // bound by the binary64 pipe (MT_FP64, MT_MIXED; with MT_MIXED_DF32 and
+  // no predicted segments they follow the step in its graph); the last
+  // step's are pending until a call that reads them (flush_obs).
+  bool obs_defer = false;
   cudaStream_t side2 = nullptr;
   cudaEvent_t join2 = nullptr;
   bool obs_pending = false;
@@ -568,7 +570,7 @@ mt_status build_graph(mt_handle* h) {
     // run on a third stream beside the first tier (they read the mass
     // buffer the step only reads); all join before the conditional
     const bool fork = d.use_pred != 0;
-    const bool obs = h->side2 != nullptr;
+    const bool obs = h->obs_defer;
     CU(cudaStreamBeginCaptureToGraph(h->stream, g, nullptr, nullptr, 0, mode));
     cudaError_t e1 = cudaSuccess;
     // the observables' snapshot: by the predicted-segment kernel where it
@@ -844,8 +846,9 @@ mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace
     e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming);
   }
-  if (e == cudaSuccess && D.fused && D.p.observe_cap > 0 && d.nochunk > 0 &&
-      D.p.precision != MT_MIXED_DF32) {
+  h->obs_defer = D.fused && D.p.observe_cap > 0 && d.nochunk > 0 &&
+                 (d.use_pred || D.p.precision != MT_MIXED_DF32);
+  if (e == cudaSuccess && h->obs_defer && !d.use_pred) {
     e = cudaStreamCreateWithFlags(&h->side2, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join2, cudaEventDisableTiming);
   }
@@ -967,7 +970,7 @@ mt_status mt_run(mt_handle* h, int64_t nsteps) {
     CU(cudaGraphLaunch(h->graph, h->stream));
     ++h->steps;
   }
-  if (nsteps > 0 && h->side2) h->obs_pending = true;
+  if (nsteps > 0 && h->obs_defer) h->obs_pending = true;
   return MT_OK;
 }
 
