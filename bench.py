@@ -382,9 +382,11 @@ def gpu_run(args, precision: str, steps: int, warmup: int, local: int, realisati
 
 def e2e_run(steps: int, local: int, realisation: int, precision: str = "mixed"):
     """Through the public API with host buffers: upload from pinned host
-    memory, then every step enqueue it and the copy of its observables row
-    into pinned host memory (no wait between steps), then read the final
-    masses (which waits for all of it).  Wall-clock."""
+    memory, then every step enqueue it and the copy of an observables row
+    into pinned host memory -- the previous step's, which the step just
+    enqueued computes beside itself (mt_copy_observables_row_async), and
+    the last step's after the loop -- with no wait between steps, then read
+    the final masses (which waits for all of it).  Wall-clock."""
     import numpy as np
     import torch
 
@@ -393,7 +395,7 @@ def e2e_run(steps: int, local: int, realisation: int, precision: str = "mixed"):
     dev = torch.device("cuda", local)
     p = mt.mt_params_init(n=N, L=(L,), v=(V, 0.0), D_mt=D, D_rw=D, dt=DT,
                           precision=prec_code(precision), seed=7, realisation=realisation,
-                          observe_cap=1)
+                          observe_cap=2)
     sim = mt.Simulation(p, device=dev)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     x = pin(synth.uniform_positions(N, L, seed=realisation))
@@ -410,11 +412,14 @@ def e2e_run(steps: int, local: int, realisation: int, precision: str = "mixed"):
     mt.mt_upload(sim.h, ptr(x), ptr(A), ptr(B), mt.MT_MEM_HOST)
     for s in range(steps):
         mt.mt_run(sim.h, 1)
-        mt.mt_copy_observables_async(sim.h, ptr(rows[s]), 1)
+        if s >= 1:
+            mt.mt_copy_observables_row_async(sim.h, ptr(rows[s - 1]), s)
+    mt.mt_copy_observables_row_async(sim.h, ptr(rows[steps - 1]), steps)
     mt.mt_read_masses(sim.h, ptr(oa), ptr(ob), mt.MT_MEM_HOST)
     secs = time.perf_counter() - t0
-    mt.mt_read_observables(sim.h, ptr(last), 1)
-    assert np.array_equal(rows[-1], last[0]) and np.all(rows[:, 0] > 0), "observables rows"
+    last = np.empty((2, 4))
+    mt.mt_read_observables(sim.h, ptr(last), 2)
+    assert np.array_equal(rows[-2:], last) and np.all(rows[:, 0] > 0), "observables rows"
     sim.close()
     return {"value": N * steps / secs, "unit": "particle-steps/s",
             "h2d_bytes_per_step": (24 * N) / steps, "d2h_bytes_per_step": 32 + (16 * N) / steps}

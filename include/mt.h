@@ -376,6 +376,16 @@ mt_status mt_read_observables(mt_handle* h, double* out, int64_t cap,
  * row before it is copied. */
 mt_status mt_copy_observables_async(mt_handle* h, double* out, int64_t rows);
 
+/* The observables row of step number `step` (1 <= step <= steps enqueued,
+ * and one of the last observe_cap), copied to out (host or device memory,
+ * 4 doubles per realisation) by a copy enqueued on the handle's stream; the
+ * call does not wait.  On the one-kernel path a step's observables are
+ * computed beside the next step, so a pipelined reader asks for the row of
+ * the step before the one it just enqueued (no extra work is enqueued); the
+ * row of the last step enqueued is computed by this call first.  Errors:
+ * MT_ERR_INVALID (step out of range, out NULL). */
+mt_status mt_copy_observables_row_async(mt_handle* h, double* out, int64_t step);
+
 /* Pairs {i, j} (caller's particle indices, i < j) within the cutoff at the
  * current positions, as the handle's search finds them.  pi, pj: device
  * pointers with room for cap entries (may be NULL when cap = 0); *count

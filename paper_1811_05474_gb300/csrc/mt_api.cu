@@ -1123,6 +1123,26 @@ mt_status mt_copy_observables_async(mt_handle* h, double* out, int64_t rows) {
   return MT_OK;
 }
 
+mt_status mt_copy_observables_row_async(mt_handle* h, double* out, int64_t step) {
+  if (!h) return fail(MT_ERR_INVALID, "handle is NULL");
+  const long long ocap = h->D.p.observe_cap;
+  if (ocap <= 0 || step < 1 || step > h->steps || step <= h->steps - ocap)
+    return fail(MT_ERR_INVALID, "step must be in [max(1, %lld), %lld] (steps enqueued, observe_cap)",
+                h->steps - ocap + 1, h->steps);
+  if (!out) return fail(MT_ERR_INVALID, "out is NULL");
+  // the last step's row is still to be computed where the observables run
+  // beside the next step: enqueue it now; earlier rows are already behind
+  // the steps enqueued
+  if (step == h->steps) {
+    const mt_status fs = flush_obs(h);
+    if (fs != MT_OK) return fs;
+  }
+  const size_t width = (size_t)h->D.nreal * 4;
+  const long long r = (step - 1) % ocap;
+  CU(cudaMemcpyAsync(out, h->dev.obs + width * r, width * 8, cudaMemcpyDefault, h->stream));
+  return MT_OK;
+}
+
 mt_status mt_read_pairs(mt_handle* h, int32_t* pi, int32_t* pj, int64_t cap, int64_t* count) {
   if (!h || !count) return fail(MT_ERR_INVALID, "handle or count is NULL");
   if (!h->uploaded) return fail(MT_ERR_STATE, "no state uploaded");

@@ -155,6 +155,7 @@ def lib(path: Path | None = None):
         "mt_read_observables": [H, _vp, i64, ctypes.POINTER(i64)],
         "mt_read_pairs": [H, _vp, _vp, i64, ctypes.POINTER(i64)],
         "mt_copy_observables_async": [H, _vp, i64],
+        "mt_copy_observables_row_async": [H, _vp, i64],
         "mt_steps_done": [H, ctypes.POINTER(i64)],
         "mt_philox": [H, u32, u32, u32, u32, u32, u32, i64, _vp],
         "mt_set_profiling": [H, i32],
@@ -353,6 +354,11 @@ def mt_read_ticks(h, X_ptr, mem: int) -> None:
 
 def mt_copy_observables_async(h, out_ptr, rows: int) -> None:
     check(lib().mt_copy_observables_async(h, out_ptr, rows))
+
+
+def mt_copy_observables_row_async(h, out_ptr, step: int) -> None:
+    """Enqueue the copy of step `step`'s observables row (see include/mt.h)."""
+    check(lib().mt_copy_observables_row_async(h, out_ptr, step))
 
 
 def mt_read_observables(h, out_ptr, cap: int) -> int:

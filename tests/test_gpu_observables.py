@@ -72,3 +72,40 @@ def test_non_finite_mass_gives_non_finite_sums(precision):
     sim.close()
     assert not np.isfinite(row[0]) and not np.isfinite(row[2])
     assert np.isfinite(row[1])  # B holds no infinity after one step
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_pipelined_row_copies_equal_the_ring(precision):
+    """Each step's row copied one step late (the step that computes it
+    beside itself was just enqueued), the last one after the loop: the rows
+    equal those read from the ring, on a system large enough for the
+    predicted-segment kernel (where the observables run beside the next
+    step) and on a small one."""
+    import torch
+
+    for n in (300000, 20000):
+        L = float(n)
+        x = synth.uniform_positions(n, L, seed=41)
+        A, B = synth.uniform_masses(n, seed=41)
+        steps = 12
+        sim = make(n, L, precision=precision, observe_cap=steps, seed=6, v=(0.5, 0.0))
+        sim.upload(x, A, B)
+        rows = torch.zeros((steps, 4), dtype=torch.float64).pin_memory()
+        for s in range(steps):
+            mt.mt_run(sim.h, 1)
+            if s >= 1:
+                mt.mt_copy_observables_row_async(sim.h, rows[s - 1].data_ptr(), s)
+        mt.mt_copy_observables_row_async(sim.h, rows[steps - 1].data_ptr(), steps)
+        sim.sync()
+        ring = sim.observables()
+        sim.close()
+        assert np.array_equal(rows.numpy(), ring)
+    # a step that was not enqueued has no row
+    sim = make(1000, 1000.0, precision=precision, observe_cap=2)
+    sim.upload(synth.uniform_positions(1000, 1000.0, seed=1), *synth.uniform_masses(1000, seed=1))
+    sim.run(3)
+    buf = torch.zeros(4, dtype=torch.float64).pin_memory()
+    for bad in (0, 1, 4):  # 1 left the ring of two rows
+        with pytest.raises(mt.MtError):
+            mt.mt_copy_observables_row_async(sim.h, buf.data_ptr(), bad)
+    sim.close()
