@@ -407,6 +407,11 @@ struct mt_handle {
   // the first tier (fork / join events around it in the captured graph)
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
+  // fires once the predicted-segment kernel's CTAs have all begun: the first
+  // tier waits for it in the graph, so that its persistent CTAs, which fill
+  // every SM, never take the SMs the cluster needs before the cluster is
+  // placed (otherwise the cluster waits for the first tier to drain)
+  cudaEvent_t pstart = nullptr;
   // fused path with observables: the previous step's observables run
   // beside the step in the graph (obs_defer), behind the predicted segments
   // where those run, else on this third stream when the first tier is
@@ -581,7 +586,9 @@ mt_status build_graph(mt_handle* h) {
       if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(h->side, h->fork, 0);
       Dev dp = d;
       dp.obs_snap = obs ? 1 : 0;
-      if (e1 == cudaSuccess) e1 = launch_fused_pred(dp, h->D.p.precision, cond1, 1, h->side);
+      if (e1 == cudaSuccess)
+        e1 = launch_fused_pred(dp, h->D.p.precision, cond1, 1, h->side, h->pstart);
+      if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(h->stream, h->pstart, 0);
     }
     if (obs && fork) {  // behind the predicted segments, on their SMs
       if (e1 == cudaSuccess) e1 = launch_obs_prev(d, h->D.p.precision, h->side);
@@ -845,6 +852,7 @@ mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace
   if (e == cudaSuccess && d.use_pred) {
     e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->pstart, cudaEventDisableTiming);
   }
   h->obs_defer = D.fused && D.p.observe_cap > 0 && d.nochunk > 0 &&
                  (d.use_pred || D.p.precision != MT_MIXED_DF32);
@@ -877,6 +885,7 @@ mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace
     if (h->fork) cudaEventDestroy(h->fork);
     if (h->join) cudaEventDestroy(h->join);
     if (h->join2) cudaEventDestroy(h->join2);
+    if (h->pstart) cudaEventDestroy(h->pstart);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
     return fail(MT_ERR_CUDA, "handle setup: %s", cudaGetErrorString(e));
@@ -1368,6 +1377,7 @@ void mt_destroy(mt_handle* h) {
   if (h->fork) cudaEventDestroy(h->fork);
   if (h->join) cudaEventDestroy(h->join);
   if (h->join2) cudaEventDestroy(h->join2);
+  if (h->pstart) cudaEventDestroy(h->pstart);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
 }

@@ -1542,9 +1542,9 @@ static cudaError_t launch_big(const Dev& d, cudaGraphConditionalHandle cond, int
 
 template <int PR, int CL>
 static cudaError_t launch_pred(const Dev& d, cudaGraphConditionalHandle cond, int use_cond,
-                               cudaStream_t s) {
+                               cudaStream_t s, cudaEvent_t started) {
   cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute at[2];
+  cudaLaunchAttribute at[3];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = CL;
   at[0].val.clusterDim.y = 1;
@@ -1557,23 +1557,33 @@ static cudaError_t launch_pred(const Dev& d, cudaGraphConditionalHandle cond, in
   cfg.stream = s;
   cfg.attrs = at;
   cfg.numAttrs = 2;
+  if (started) {  // fires once every CTA of the cluster has begun
+    at[2].id = cudaLaunchAttributeLaunchCompletionEvent;
+    at[2].val.launchCompletionEvent.event = started;
+    at[2].val.launchCompletionEvent.flags = 0;
+    cfg.numAttrs = 3;
+  }
   return cudaLaunchKernelEx(&cfg, k_step1d_pred<PR, CL>, d, cond, use_cond);
 }
 
 template <int PR>
 static cudaError_t launch_cluster_tier(const Dev& d, bool pred, cudaGraphConditionalHandle cond,
-                                       int use_cond, cudaStream_t s) {
+                                       int use_cond, cudaStream_t s, cudaEvent_t started) {
   if (g_big_cluster == 16)
-    return pred ? launch_pred<PR, 16>(d, cond, use_cond, s) : launch_big<PR, 16>(d, cond, use_cond, s);
-  return pred ? launch_pred<PR, 8>(d, cond, use_cond, s) : launch_big<PR, 8>(d, cond, use_cond, s);
+    return pred ? launch_pred<PR, 16>(d, cond, use_cond, s, started)
+                : launch_big<PR, 16>(d, cond, use_cond, s);
+  return pred ? launch_pred<PR, 8>(d, cond, use_cond, s, started)
+              : launch_big<PR, 8>(d, cond, use_cond, s);
 }
 
 static cudaError_t launch_cluster(const Dev& d, int precision, bool pred,
-                                  cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) {
-  if (precision == MT_MIXED) return launch_cluster_tier<MT_MIXED>(d, pred, cond, use_cond, s);
+                                  cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s,
+                                  cudaEvent_t started = nullptr) {
+  if (precision == MT_MIXED)
+    return launch_cluster_tier<MT_MIXED>(d, pred, cond, use_cond, s, started);
   if (precision == MT_MIXED_DF32)
-    return launch_cluster_tier<MT_MIXED_DF32>(d, pred, cond, use_cond, s);
-  return launch_cluster_tier<MT_FP64>(d, pred, cond, use_cond, s);
+    return launch_cluster_tier<MT_MIXED_DF32>(d, pred, cond, use_cond, s, started);
+  return launch_cluster_tier<MT_FP64>(d, pred, cond, use_cond, s, started);
 }
 
 cudaError_t launch_fused_big(const Dev& d, int precision, cudaGraphConditionalHandle cond,
@@ -1582,8 +1592,8 @@ cudaError_t launch_fused_big(const Dev& d, int precision, cudaGraphConditionalHa
 }
 
 cudaError_t launch_fused_pred(const Dev& d, int precision, cudaGraphConditionalHandle cond,
-                              int use_cond, cudaStream_t s) {
-  return launch_cluster(d, precision, true, cond, use_cond, s);
+                              int use_cond, cudaStream_t s, cudaEvent_t started) {
+  return launch_cluster(d, precision, true, cond, use_cond, s, started);
 }
 
 // Direct launches without a predicted segment: the first tier's partner in

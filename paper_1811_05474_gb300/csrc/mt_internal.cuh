@@ -468,8 +468,10 @@ cudaError_t fused_configure();  // opt in to the large dynamic shared memory
 int fused_ctas_per_sm(int precision);  // resident first-tier CTAs per SM
 cudaError_t launch_fused_step(const Dev& d, int precision, cudaGraphConditionalHandle cond,
                               int use_cond, cudaStream_t s);
+// started (optional): an event that fires once every CTA of the kernel has
+// begun (a launch-completion event)
 cudaError_t launch_fused_pred(const Dev& d, int precision, cudaGraphConditionalHandle cond,
-                              int use_cond, cudaStream_t s);  // predicted heavy segments
+                              int use_cond, cudaStream_t s, cudaEvent_t started = nullptr);  // predicted heavy segments
 cudaError_t launch_join_stub(const Dev& d, cudaStream_t s);
 cudaError_t launch_fused_big(const Dev& d, int precision, cudaGraphConditionalHandle cond,
                              int use_cond, cudaStream_t s);
