@@ -457,8 +457,8 @@ const char* mt_profile_name(const mt_handle* h, int32_t idx);
  * Intermediates live in a fixed device array inside libmt, held by every GPU
  * that loads the library until exit: n may not exceed 1048576 (larger n is
  * rejected with MT_ERR_INVALID).  The first call on a device looks up that
- * array's address, so make it before any stream capture.  All calls share
- * the array: calls that overlap on the GPU race and give wrong results.
+ * array's address (cudaGetSymbolAddress).  All calls share the array:
+ * calls that overlap on the GPU race and give wrong results.
  * Runs on stream (NULL: the default stream) and waits for it before
  * returning; MT_ERR_INVALID if a position is outside [0, L], NaN or out of
  * ascending order, and A_out and B_out are then undefined (they may have
