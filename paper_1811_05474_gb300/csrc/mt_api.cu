@@ -830,6 +830,7 @@ mt_status mt_batch_create(const mt_params* p, const mt_batch* b, void* workspace
   d.inv8 = 1.0 / (8.0 * D.p.D_mt * D.p.dt);
   d.scale = std::ldexp(1.0, -D.p.frac_bits);
   d.inv8f = (float)(d.inv8 * d.scale * d.scale);
+  d.inv8s = std::ldexp(d.inv8, -2 * D.p.frac_bits);
   d.key0 = (unsigned int)(D.p.seed & 0xffffffffu);
   d.key1 = (unsigned int)(D.p.seed >> 32);
   d.real = (unsigned int)D.p.realisation;

@@ -410,7 +410,7 @@ __device__ bool pair_transfer(const Dev& d, const StepState& st, unsigned char* 
       pair_of(j, jj, left, u, q, partner);
       r += sw[q];
     }
-    sr[j] = mixw(PR) ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
+    sr[j] = mixw(PR) ? T(__frcp_rn((float)r)) : T(rcp_ge1((double)r));
   }
   __syncthreads();
   // (G) binary64 weights under the symmetric normalisation: each listed
@@ -864,7 +864,7 @@ __device__ int fused_segment(const Dev& d, const StepState& st, int seg, unsigne
         T r = T(1);
         for (int q = j - 1; q >= 0 && x - sx[q] <= S; --q) r += W::near(d, x - sx[q]);
         for (int q = j + 1; q < m && sx[q] - x <= S; ++q) r += W::near(d, sx[q] - x);
-        sr[j] = mixw(PR) ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
+        sr[j] = mixw(PR) ? T(__frcp_rn((float)r)) : T(rcp_ge1((double)r));
       }
     }
     __syncthreads();
@@ -900,7 +900,7 @@ __device__ int fused_segment(const Dev& d, const StepState& st, int seg, unsigne
         }
         for (; q < hi; q += 32) r0 += nu(q);
         const T r = warp_sum((r0 + r1) + (r2 + r3));
-        if (lane == 0) sr[j] = mixw(PR) ? T(__frcp_rn((float)r)) : T(1.0 / (double)r);
+        if (lane == 0) sr[j] = mixw(PR) ? T(__frcp_rn((float)r)) : T(rcp_ge1((double)r));
       }
     }
     if constexpr (CL > 1) {

@@ -140,6 +140,7 @@ struct Dev {
   float inv8f;              // 1 / (8 D_mt dt) 2^-2k, float
   double inv8;              // 1 / (8 D_mt dt), double
   double scale;             // 2^-k
+  double inv8s;             // inv8 scale^2 (exact): the weights' exponent from D^2 in ticks
   unsigned int key0, key1;  // Philox key (seed)
   unsigned int real;        // realisation counter word
   int nbig_cap;
@@ -337,6 +338,20 @@ __device__ __forceinline__ double widen_exact(float f) {
     F = 0;
   }
   return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) | (E << 52) | F));
+}
+
+// 1 / r for a row sum r >= 1 (finite) in binary64 without a division: a
+// binary32 reciprocal of r's leading 24 bits (read from its bits), widened,
+// then two Newton steps y <- y + y (1 - r y) with fused multiply-adds
+// (relative error 2^-22 -> 2^-44 -> below 2^-88 before the last rounding):
+// within one unit in the last place of 1 / r.
+__device__ __forceinline__ double rcp_ge1(double r) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(r);
+  const unsigned int e = (unsigned int)((u >> 52) & 0x7ff);
+  const float rf = __uint_as_float(((e - 1023u + 127u) << 23) | (unsigned int)((u >> 29) & 0x7fffffu));
+  double y = widen_exact(__frcp_rn(rf));
+  y = __fma_rn(y, __fma_rn(-r, y, 1.0), y);
+  return __fma_rn(y, __fma_rn(-r, y, 1.0), y);
 }
 
 // Eq. 2's random-walk displacement on the grid: the nearest tick to b xi,

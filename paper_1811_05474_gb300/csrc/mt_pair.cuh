@@ -77,10 +77,11 @@ struct Weight<false, DIM> {
     }
     return exp_neg(__dmul_rn(s2, d.inv8));
   }
-  // 1-d, |D| <= Smax < 2^30 (the same value as eval(d, D, 0))
+  // 1-d, |D| <= Smax < 2^30: the same value as eval(d, D, 0), since
+  // (D 2^-k)^2 rounds to fl(D^2) 2^-2k and inv8 2^-2k is exact
   static __device__ __forceinline__ double near(const Dev& d, long long D) {
-    const double sx = __dmul_rn((double)(int)D, d.scale);
-    return exp_neg(__dmul_rn(__dmul_rn(sx, sx), d.inv8));
+    const double dd = (double)(int)D;
+    return exp_neg(__dmul_rn(__dmul_rn(dd, dd), d.inv8s));
   }
 };
 
@@ -259,7 +260,7 @@ __device__ __forceinline__ void store_rinv(const Dev& d, long long p, typename W
   if (MIX)
     static_cast<float*>(d.rinv)[p] = __frcp_rn((float)r);
   else
-    static_cast<double*>(d.rinv)[p] = 1.0 / (double)r;
+    static_cast<double*>(d.rinv)[p] = rcp_ge1((double)r);
 }
 
 template <bool MIX>
