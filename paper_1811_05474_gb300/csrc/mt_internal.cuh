@@ -340,6 +340,17 @@ __device__ __forceinline__ double widen_exact(float f) {
   return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) | (E << 52) | F));
 }
 
+// An int as binary64 from its bits with integer operations only (exact:
+// every int is a binary64 number).
+__device__ __forceinline__ double i2d_exact(int v) {
+  if (v == 0) return 0.0;
+  const unsigned int a = v < 0 ? 0u - (unsigned int)v : (unsigned int)v;
+  const int p = 31 - __clz(a);  // leading bit
+  const unsigned long long m = ((unsigned long long)a << (52 - p)) & ((1ULL << 52) - 1);
+  return __longlong_as_double((long long)(((unsigned long long)(v < 0) << 63) |
+                                          ((unsigned long long)(p + 1023) << 52) | m));
+}
+
 // 1 / r for a row sum r >= 1 (finite) in binary64 without a division: a
 // binary32 reciprocal of r's leading 24 bits (read from its bits), widened,
 // then two Newton steps y <- y + y (1 - r y) with fused multiply-adds

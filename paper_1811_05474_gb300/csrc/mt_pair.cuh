@@ -80,7 +80,7 @@ struct Weight<false, DIM> {
   // 1-d, |D| <= Smax < 2^30: the same value as eval(d, D, 0), since
   // (D 2^-k)^2 rounds to fl(D^2) 2^-2k and inv8 2^-2k is exact
   static __device__ __forceinline__ double near(const Dev& d, long long D) {
-    const double dd = (double)(int)D;
+    const double dd = i2d_exact((int)D);  // (the binary64 pipe is kept for arithmetic)
     return exp_neg(__dmul_rn(__dmul_rn(dd, dd), d.inv8s));
   }
 };
