@@ -1120,10 +1120,11 @@ __device__ __forceinline__ void end_of_tier(const Dev& d, cudaGraphConditionalHa
 
 // First tier: a persistent grid (a few CTAs per SM) looping over the
 // segments; each segment's boundary scalars are loaded while the previous
-// segment is processed.
+// segment is processed.  MT_FP64's shared memory admits three CTAs per SM,
+// so it is compiled for three (more registers, none spilled).
 template <int PR>
-__global__ void __launch_bounds__(Fast::kT, kFusedCtasPerSm) k_step1d(Dev d, cudaGraphConditionalHandle cond,
-                                                         int use_cond) {
+__global__ void __launch_bounds__(Fast::kT, PR == MT_FP64 ? 3 : kFusedCtasPerSm)
+    k_step1d(Dev d, cudaGraphConditionalHandle cond, int use_cond) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ bool s_last;
   Ctrl* c = d.ctrl;
