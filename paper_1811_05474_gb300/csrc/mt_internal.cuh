@@ -321,6 +321,12 @@ __device__ __forceinline__ float ll_to_float(long long v) {
 // top of 52 bits; infinities and NaNs keep their class and payload.
 __device__ __forceinline__ double widen_exact(float f) {
   const unsigned int u = __float_as_uint(f);
+  const unsigned int ex = u & 0x7f800000u;
+  if (ex != 0u && ex != 0x7f800000u) {  // a normal number: the high word is the sign, the
+    // exponent + 896 and the fraction's top 20 bits; the low word its last 3 bits
+    const unsigned int hi = (u & 0x80000000u) | (((u & 0x7fffffffu) >> 3) + (896u << 20));
+    return __hiloint2double((int)hi, (int)(u << 29));
+  }
   const unsigned int e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
   unsigned long long E, F;
   if (e == 0xffu) {

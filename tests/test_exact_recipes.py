@@ -14,6 +14,11 @@ import numpy as np
 
 def widen_exact(f32_bits: int) -> float:
     u = f32_bits
+    ex = u & 0x7F800000
+    if ex not in (0, 0x7F800000):  # normal: the high and low words directly
+        hi = (u & 0x80000000) | (((u & 0x7FFFFFFF) >> 3) + (896 << 20))
+        lo = (u << 29) & 0xFFFFFFFF
+        return struct.unpack("<d", struct.pack("<Q", (hi << 32) | lo))[0]
     e, m = (u >> 23) & 0xFF, u & 0x7FFFFF
     if e == 0xFF:
         E, F = 0x7FF, m << 29
